@@ -1,0 +1,251 @@
+/*
+ * hyperim.h -- C ABI of the GB300 (sm_103a) HyperIM library.
+ *
+ * HyperIM ("Influence Maximization in Hypergraphs by Stratified Sampling for Efficient Generation
+ * of Reverse Reachable Sets", arXiv 2406.01911) picks k seed vertices of a hypergraph G = (V, HE)
+ * with the largest expected influence (Def. 1). Its hot path, implemented here in CUDA kernels:
+ *
+ *   load      -- incidence store (he -> members, v -> he; never the clique expansion G_w of
+ *                Sec. 2.1) and the per-vertex layer profile of A(mu) (Sec. 3.1.1);
+ *   plan      -- the RR-set budget theta_max, theta_0 and the doubling count (Eq. equation-max,
+ *                Sec. 4.3);
+ *   sample    -- stratified random RR sets (Algorithm 3 with the Binomial/Poisson strategies of
+ *                Sec. 3.1.3), roots drawn per stratum, output compacted to CSR;
+ *   select    -- greedy max coverage (Algorithm 1) over a pool, fixed theta or the adaptive
+ *                HyperIM_BRR schedule (Algorithm 4) with the bounds of Sec. 4.2;
+ *   spread    -- the RR estimate of a seed set's influence (Eq. 1).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a hyperim_status; no C++ exception crosses this boundary. On a non-OK
+ *     status hyperim_last_error() returns a thread-local message.
+ *   - Input pointers are borrowed for the duration of the call only. Handles own all device
+ *     memory they allocate (stream-ordered cudaMallocAsync on the graph's stream).
+ *   - All device work is ordered on the graph's CUDA stream (hyperim_load_args.cuda_stream, or
+ *     the legacy default stream when NULL). Calls that return host results synchronise it.
+ *   - Randomness: every draw is a word of Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     graph's 64-bit seed and a counter built from (pool tag, stratum, RR index, popped vertex,
+ *     layer, block). Results therefore do not depend on launch configuration or scheduling.
+ *   - Vertex ids are int32 in [0, n); n < 2^31 - 1. Hyperedges are vertex sets: repeated ids in
+ *     one hyperedge are collapsed on load; a hyperedge with fewer than two members links nobody.
+ */
+#ifndef HYPERIM_H
+#define HYPERIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYPERIM_OK = 0,
+    HYPERIM_EINVAL = -1,     /* bad argument: id out of range, k > n, eps not in (0,1), ... */
+    HYPERIM_ENOMEM = -2,     /* device allocation failed or the HBM budget would be exceeded */
+    HYPERIM_EOVERFLOW = -3,  /* theta cap or a fixed-size arena exceeded; results discarded */
+    HYPERIM_ETIMEDOUT = -4,  /* a bounded device-side wait gave up */
+    HYPERIM_ECUDA = -5,      /* a CUDA runtime call failed */
+    HYPERIM_ESTATE = -6      /* handle used in the wrong state (e.g. pool of another graph) */
+} hyperim_status;
+
+/* Activation probability of nu -> mu for nu in layer L_i of A(mu). */
+typedef enum {
+    HYPERIM_P_UNIFORM_PAIR = 0, /* one p for every co-member pair: p = uniform_threshold / 2^32 */
+    HYPERIM_P_WC = 1,           /* weighted cascade: p = floor(2^32 / deg(mu)) / 2^32, 1 if deg=1 */
+    HYPERIM_P_PAPER_LAYER = 2   /* Sec. 3.1.1: p = P(L_i)/n(L_i), P(L_i) = 1/(i ln(l_mu + 1)),
+                                   clamped to 1 */
+} hyperim_prob_model;
+
+typedef enum {
+    HYPERIM_ROOTS_PLAIN = 0,      /* roots uniform over V (Alg. 3, first step) */
+    HYPERIM_ROOTS_STRATIFIED = 1  /* roots uniform within strata s(mu) = min(l_mu, 15), with
+                                     n_s = ceil(theta |V_s| / n) sets per nonempty stratum */
+} hyperim_root_mode;
+
+typedef enum {
+    HYPERIM_STRAT_PAPER = 0,        /* Binomial if n(L_i) <= 20, else Poisson (Sec. 3.1.3) */
+    HYPERIM_STRAT_BINOMIAL_ONLY = 1 /* Binomial for every layer (exact IC semantics, Lemma 3) */
+} hyperim_strategy;
+
+typedef struct hyperim_graph* hyperim_graph_t;
+typedef struct hyperim_pool* hyperim_pool_t;
+
+#define HYPERIM_NSTRATA 16
+#define HYPERIM_P_ONE 4294967296ull /* uniform_threshold value meaning p = 1 */
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_load -- build the incidence store and layer profile of G on the device.
+ *   Sec. 2.1 (G, V(he), w(mu,nu), deg(mu)); Sec. 3.1.1 (layers of A(mu), l_mu, n(L_i), P(L_i)).
+ *   he_off[m+1], he_mem[he_off[m]]: hyperedge -> member CSR, int32; host pointers, or device
+ *   pointers when ptrs_on_device != 0 (read during the call only). Members of a hyperedge may
+ *   come in any order and may repeat.
+ *   EINVAL: n < 1, n >= 2^31 - 1, m < 0, he_off not monotone from 0, a member outside [0, n),
+ *   model out of range, uniform_threshold > 2^32. ENOMEM: allocation failed or the device
+ *   footprint would exceed hbm_budget_bytes (0 = no budget). On success *out owns the graph.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n;                   /* |V| */
+    int32_t m;                   /* |HE| */
+    const int32_t* he_off;       /* m + 1 offsets */
+    const int32_t* he_mem;       /* he_off[m] members */
+    int32_t ptrs_on_device;      /* 0: host pointers; 1: device pointers */
+    int32_t model;               /* hyperim_prob_model */
+    uint64_t uniform_threshold;  /* floor(p 2^32) for HYPERIM_P_UNIFORM_PAIR, <= 2^32 */
+    uint64_t seed;               /* Philox key (seed_lo, seed_hi) */
+    void* cuda_stream;           /* cudaStream_t, may be NULL */
+    size_t hbm_budget_bytes;     /* 0 = unlimited */
+} hyperim_load_args;
+
+hyperim_status hyperim_load(const hyperim_load_args* args, hyperim_graph_t* out);
+void hyperim_graph_free(hyperim_graph_t g);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_graph_stats -- scalar statistics of a loaded graph (host struct, filled on return).
+ *   theta_lstar is Thm 2's theta(l*) = (1/|V|) sum_v l_v / ln(l_v + 1).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n, m;
+    int64_t nnz;                           /* members after normalisation */
+    int64_t profile_entries;               /* sum_v l_v */
+    int32_t max_layers, max_dh;
+    int64_t max_deg;
+    int64_t stratum_size[HYPERIM_NSTRATA]; /* |V_s| */
+    double theta_lstar;
+    size_t device_bytes;                   /* device memory held by the graph */
+} hyperim_graph_stats_t;
+
+hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_graph_profile -- copy the layer profile to host buffers (Sec. 3.1.1).
+ *   Any pointer may be NULL to skip it. deg[n] = |A(v)|, nlayers[n] = l_v, stratum[n],
+ *   prof_off[n+1] (int64), and for each profile entry x in [prof_off[v], prof_off[v+1]) the
+ *   layer i = x - prof_off[v] + 1 of A(v): layer_w[x] = w_i (descending in i), layer_n[x] = n_i,
+ *   layer_thr[x] = floor(p_i 2^32) with 2^32 meaning p = 1. Buffers are caller-owned and sized
+ *   from hyperim_graph_stats. Synchronises the stream.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* nlayers,
+                                     int32_t* stratum, int64_t* prof_off, uint32_t* layer_w,
+                                     uint32_t* layer_n, uint64_t* layer_thr);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_plan_theta -- RR budget of Sec. 4.3 (host arithmetic, IEEE double).
+ *   delta = n^-ell (Sec. 6: delta = 1/|V| for ell = 1); ln C(n,k) = sum_{i<=k'} ln((n-k'+i)/i)
+ *   with k' = min(k, n-k);
+ *   theta_max = 2n (sqrt(ln(2/delta)) + sqrt(ln C(n,k) + ln(6/delta))) / (eps^2 k)
+ *   (Eq. equation-max, delta inside both logarithms); theta0 = ceil(theta_max eps^2 k / n);
+ *   i_max = ceil(log2(theta_max / theta0)).  EINVAL: k < 1, k > n, eps not in (0,1), ell <= 0.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    double delta;
+    double ln_binom;
+    double theta_max;         /* real value */
+    uint64_t theta_max_ceil;
+    uint64_t theta0;
+    int32_t i_max;
+} hyperim_theta_plan;
+
+hyperim_status hyperim_plan_theta(hyperim_graph_t g, int32_t k, double eps, double ell,
+                                  hyperim_theta_plan* out);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_sample_rr -- grow an RR pool to the allocation of theta (Algorithm 3).
+ *   If *inout is NULL a pool is created with (pool_tag, root_mode, strategy); otherwise those
+ *   arguments must match the pool's (ESTATE if not). Stratum s holds n_s(theta) sets, n_s as in
+ *   hyperim_root_mode; RR set (s, j) is a pure function of (seed, tag, s, j), so sets already in
+ *   the pool are kept and only j in [old n_s, new n_s) are generated. pool_tag < 256. Device
+ *   CSR output; the call synchronises the stream once to size the CSR.
+ *   EOVERFLOW: some n_s >= 2^32, or one layer draw needs more than 2^18 Philox words.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta,
+                                 int32_t root_mode, int32_t strategy, hyperim_pool_t* inout);
+void hyperim_pool_free(hyperim_pool_t p);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_pool_view -- read-only device view of a pool (valid until the pool grows or is freed).
+ *   RR set r has members rr_mem[rr_off[r] .. rr_off[r+1]) (ascending ids), stratum rr_stratum[r]
+ *   and index rr_j[r] within its stratum. Sets are stored in generation order: one stratum-major
+ *   block per growth step.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int64_t count;                         /* RR sets */
+    int64_t total;                         /* sum of sizes */
+    const int64_t* rr_off;                 /* device, count + 1 */
+    const int32_t* rr_mem;                 /* device, total */
+    const uint8_t* rr_stratum;             /* device, count */
+    const uint32_t* rr_j;                  /* device, count */
+    uint64_t n_s[HYPERIM_NSTRATA];         /* sets per stratum */
+    uint32_t pool_tag;
+    int32_t root_mode, strategy;
+    /* work counters of all generation launches so far (see hyperim_rr_stats) */
+    uint64_t pops, layers_seen, draws, mats, mat_he, mat_members, selected;
+} hyperim_pool_view_t;
+
+hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_pool_copy -- copy a pool's CSR to caller-owned HOST buffers (any may be NULL):
+ *   rr_off[count + 1], rr_mem[total], rr_stratum[count], rr_j[count], in the layout of
+ *   hyperim_pool_view. Synchronises the stream.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_mem,
+                                 uint8_t* rr_stratum, uint32_t* rr_j);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_select_seeds -- greedy max coverage (Algorithm 1) and, in BRR mode, HyperIM_BRR.
+ *   FIXED: greedy on r1 as it is (r2 may be NULL; if given, S_k's coverage of r2 is reported).
+ *   BRR:   r1 and r2 (distinct pools of this graph, pool tags 0 and 1 by convention, possibly
+ *          empty) are grown round by round to theta_i = theta0 2^i (Algorithm 4); greedy on r1
+ *          gives S_k; upper bound Lambda_R1(S_k)/(1 - (1 - 1/k)^k) n/|R1| (Eq. upper_6,
+ *          p_max = 1); lower bound ((sqrt(Lambda_R2 + 2 ln(1/delta)/9) - sqrt(ln(1/delta)/2))^2 -
+ *          ln(1/delta)/18) n/|R2| (Sec. 4.2); stop once lower/upper >= 1 - 1/e - eps or after
+ *          i_max doublings. theta_cap > 0 bounds theta_i (EOVERFLOW beyond it).
+ *          seconds_sample / seconds_select split the call's host wall time between growing
+ *          the pools and running greedy + coverage.
+ *   Greedy: marginal coverage (Eq. 2) weighted per stratum by floor(|V_s| 2^32 / n_s) (1 with
+ *   plain roots), ties to the lowest vertex id, never a vertex twice; when every marginal is 0
+ *   the lowest unpicked id is taken. seeds_host[k] receives S_k in pick order.
+ *   Estimate: sigma = sum_s |V_s|/n_s Lambda_s (Eq. 1 per stratum).
+ *   EINVAL: k < 1, k > n, bad mode; ESTATE: pools of another graph or r1 == r2.
+ * ------------------------------------------------------------------------------------------ */
+typedef enum { HYPERIM_SELECT_FIXED = 0, HYPERIM_SELECT_BRR = 1 } hyperim_select_mode;
+
+typedef struct {
+    int32_t mode;        /* hyperim_select_mode */
+    double eps, ell;     /* BRR only */
+    uint64_t theta_cap;  /* BRR only; 0 = no cap (the i_max doublings bound theta) */
+    int32_t root_mode;   /* BRR only: used when the pools are created empty */
+    int32_t strategy;    /* BRR only */
+} hyperim_select_opts;
+
+typedef struct {
+    int32_t rounds;                          /* BRR rounds run (1 in FIXED mode) */
+    uint64_t theta;                          /* target theta of the last round */
+    uint64_t pool_r1, pool_r2;               /* RR sets in r1 / r2 when the selection ended */
+    uint64_t lambda_r1[HYPERIM_NSTRATA];     /* coverage of S_k in r1 per stratum */
+    uint64_t lambda_r2[HYPERIM_NSTRATA];     /* coverage of S_k in r2 per stratum */
+    double sigma_r1, sigma_r2;               /* Eq. 1 estimates on r1 and r2 */
+    double upper, lower, alpha;              /* last round's bounds (BRR) */
+    double alpha_round[64];
+    double seconds_sample, seconds_select;   /* host wall time inside the call */
+} hyperim_select_result;
+
+hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperim_pool_t r2,
+                                    int32_t k, const hyperim_select_opts* opts,
+                                    int32_t* seeds_host, hyperim_select_result* out);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_spread -- Eq. 1 estimate of the influence of seeds_host[k] from a pool:
+ *   sigma = sum_s |V_s|/n_s Lambda_s, std_err^2 = sum_s (|V_s|/n_s)^2 n_s f_s (1 - f_s),
+ *   f_s = Lambda_s / n_s. Seeds may repeat. EINVAL: a seed outside [0, n).
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k,
+                              hyperim_pool_t pool, double* sigma_hat, double* std_err);
+
+/* Thread-local message describing the last non-OK status returned on this thread. */
+const char* hyperim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYPERIM_H */

@@ -1,0 +1,31 @@
+"""Compile the CPU oracle (test infrastructure) into oracle/_build/libhyperim_oracle.so.
+
+Plain C11, -O2, no FMA contraction (-ffp-contract=off) so that its double arithmetic is the
+literal sequence of IEEE operations written in the source.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "hyperim_oracle.c")
+HDR = os.path.join(HERE, "hyperim_oracle.h")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libhyperim_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(LIB):
+        t = os.path.getmtime(LIB)
+        if t >= os.path.getmtime(SRC) and t >= os.path.getmtime(HDR):
+            return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter", SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))
