@@ -1,0 +1,323 @@
+"""HyperIM on GB300: Python binding of the C ABI in include/hyperim.h.
+
+Argument marshalling only: every step of the hot path (incidence store, layer profile, RR-set
+generation, compaction, greedy max coverage, coverage of a seed set) runs in the CUDA kernels of
+``libhyperim.so``. Module-level functions carry the C names (``hyperim_load``,
+``hyperim_plan_theta``, ``hyperim_sample_rr``, ``hyperim_select_seeds``, ``hyperim_spread``,
+...); ``Graph`` and ``Pool`` wrap the handles. PyTorch only supplies the CUDA stream (and, when
+the caller passes CUDA tensors, the device pointers of the input CSR).
+
+There is no CPU fallback: importing works anywhere, but the first call raises if the compiled
+library is missing or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhyperim.so")
+
+NSTRATA = 16
+P_ONE = 1 << 32
+MODELS = {"uniform_pair": 0, "wc": 1, "paper_layer": 2}
+ROOTS = {"plain": 0, "stratified": 1}
+STRATEGIES = {"paper": 0, "binomial_only": 1}
+SELECT_MODES = {"fixed": 0, "brr": 1}
+STATUS = {0: "HYPERIM_OK", -1: "HYPERIM_EINVAL", -2: "HYPERIM_ENOMEM", -3: "HYPERIM_EOVERFLOW",
+          -4: "HYPERIM_ETIMEDOUT", -5: "HYPERIM_ECUDA", -6: "HYPERIM_ESTATE"}
+
+
+class HyperIMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class LoadArgs(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("he_off", C.c_void_p), ("he_mem", C.c_void_p),
+                ("ptrs_on_device", C.c_int32), ("model", C.c_int32),
+                ("uniform_threshold", C.c_uint64), ("seed", C.c_uint64),
+                ("cuda_stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t)]
+
+
+class GraphStats(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64),
+                ("profile_entries", C.c_int64), ("max_layers", C.c_int32), ("max_dh", C.c_int32),
+                ("max_deg", C.c_int64), ("stratum_size", C.c_int64 * NSTRATA),
+                ("theta_lstar", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+class ThetaPlan(C.Structure):
+    _fields_ = [("delta", C.c_double), ("ln_binom", C.c_double), ("theta_max", C.c_double),
+                ("theta_max_ceil", C.c_uint64), ("theta0", C.c_uint64), ("i_max", C.c_int32)]
+
+
+class PoolView(C.Structure):
+    _fields_ = [("count", C.c_int64), ("total", C.c_int64), ("rr_off", C.c_void_p),
+                ("rr_mem", C.c_void_p), ("rr_stratum", C.c_void_p), ("rr_j", C.c_void_p),
+                ("n_s", C.c_uint64 * NSTRATA), ("pool_tag", C.c_uint32), ("root_mode", C.c_int32),
+                ("strategy", C.c_int32), ("pops", C.c_uint64), ("layers_seen", C.c_uint64),
+                ("draws", C.c_uint64), ("mats", C.c_uint64), ("mat_he", C.c_uint64),
+                ("mat_members", C.c_uint64), ("selected", C.c_uint64)]
+
+
+class SelectOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("eps", C.c_double), ("ell", C.c_double),
+                ("theta_cap", C.c_uint64), ("root_mode", C.c_int32), ("strategy", C.c_int32)]
+
+
+class SelectResult(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("theta", C.c_uint64), ("pool_r1", C.c_uint64),
+                ("pool_r2", C.c_uint64), ("lambda_r1", C.c_uint64 * NSTRATA),
+                ("lambda_r2", C.c_uint64 * NSTRATA), ("sigma_r1", C.c_double),
+                ("sigma_r2", C.c_double), ("upper", C.c_double), ("lower", C.c_double),
+                ("alpha", C.c_double), ("alpha_round", C.c_double * 64),
+                ("seconds_sample", C.c_double), ("seconds_select", C.c_double)]
+
+
+_lib = None
+_vp = C.c_void_p
+_SIGNATURES = {
+    "hyperim_load": (C.c_int, [C.POINTER(LoadArgs), C.POINTER(_vp)]),
+    "hyperim_graph_free": (None, [_vp]),
+    "hyperim_graph_stats": (C.c_int, [_vp, C.POINTER(GraphStats)]),
+    "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hyperim_plan_theta": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.POINTER(ThetaPlan)]),
+    "hyperim_sample_rr": (C.c_int, [_vp, C.c_uint32, C.c_uint64, C.c_int32, C.c_int32,
+                                    C.POINTER(_vp)]),
+    "hyperim_pool_free": (None, [_vp]),
+    "hyperim_pool_view": (C.c_int, [_vp, C.POINTER(PoolView)]),
+    "hyperim_pool_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "hyperim_select_seeds": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(SelectOpts), _vp,
+                                       C.POINTER(SelectResult)]),
+    "hyperim_spread": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
+    "hyperim_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libhyperim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_2406_01911_gb300.build.build() "
+                "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def _check(status: int):
+    if status != 0:
+        raise HyperIMError(status, lib().hyperim_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def current_stream():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("HyperIM needs a CUDA device (no CPU fallback)")
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------------------------------------------
+# C-named entry points (thin wrappers)
+# ------------------------------------------------------------------------------------------------
+def hyperim_load(n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, seed=1,
+                 stream=None, hbm_budget_bytes=0):
+    """Returns a graph handle. he_off/he_mem: int32 numpy arrays (host) or CUDA tensors."""
+    keep = []
+    on_dev = 0
+    if hasattr(he_off, "is_cuda") and he_off.is_cuda:
+        import torch
+        he_off = he_off.to(torch.int32).contiguous()
+        he_mem = he_mem.to(torch.int32).contiguous()
+        keep += [he_off, he_mem]
+        p_off, p_mem, on_dev = he_off.data_ptr(), he_mem.data_ptr() if he_mem.numel() else None, 1
+    else:
+        he_off = np.ascontiguousarray(he_off, dtype=np.int32)
+        he_mem = np.ascontiguousarray(he_mem, dtype=np.int32)
+        keep += [he_off, he_mem]
+        p_off, p_mem = he_off.ctypes.data, (he_mem.ctypes.data if he_mem.size else None)
+    args = LoadArgs(int(n), len(he_off) - 1, p_off, p_mem, on_dev, MODELS[model],
+                    int(uniform_threshold), int(seed),
+                    stream if stream is not None else current_stream(), int(hbm_budget_bytes))
+    h = C.c_void_p()
+    _check(lib().hyperim_load(C.byref(args), C.byref(h)))
+    return h
+
+
+def hyperim_graph_free(h):
+    lib().hyperim_graph_free(h)
+
+
+def hyperim_plan_theta(h, k, eps, ell=1.0):
+    p = ThetaPlan()
+    _check(lib().hyperim_plan_theta(h, int(k), float(eps), float(ell), C.byref(p)))
+    return {f: getattr(p, f) for f, _ in ThetaPlan._fields_}
+
+
+def hyperim_sample_rr(h, pool_tag, theta, root_mode="plain", strategy="paper", pool=None):
+    ph = pool if pool is not None else C.c_void_p()
+    _check(lib().hyperim_sample_rr(h, int(pool_tag), int(theta), ROOTS[root_mode],
+                                   STRATEGIES[strategy], C.byref(ph)))
+    return ph
+
+
+def hyperim_select_seeds(h, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap=0,
+                         root_mode="stratified", strategy="paper"):
+    opts = SelectOpts(SELECT_MODES[mode], float(eps), float(ell), int(theta_cap), ROOTS[root_mode],
+                      STRATEGIES[strategy])
+    seeds = np.zeros(int(k), dtype=np.int32)
+    res = SelectResult()
+    _check(lib().hyperim_select_seeds(h, r1, r2, int(k), C.byref(opts), _ptr(seeds), C.byref(res)))
+    out = {f: getattr(res, f) for f, _ in SelectResult._fields_
+           if f not in ("lambda_r1", "lambda_r2", "alpha_round")}
+    out["lambda_r1"] = np.array(res.lambda_r1, dtype=np.uint64)
+    out["lambda_r2"] = np.array(res.lambda_r2, dtype=np.uint64)
+    out["alpha_round"] = list(res.alpha_round)[: res.rounds]
+    return seeds, out
+
+
+def hyperim_spread(h, seeds, pool):
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    sig, err = C.c_double(), C.c_double()
+    _check(lib().hyperim_spread(h, _ptr(s) if s.size else None, len(s), pool, C.byref(sig),
+                                C.byref(err)))
+    return sig.value, err.value
+
+
+# ------------------------------------------------------------------------------------------------
+# handle classes
+# ------------------------------------------------------------------------------------------------
+class Graph:
+    """A hypergraph loaded on the device (incidence store + layer profile)."""
+
+    def __init__(self, n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, seed=1,
+                 stream=None, hbm_budget_bytes=0):
+        self.n = int(n)
+        self.model = model
+        self._h = hyperim_load(n, he_off, he_mem, model, uniform_threshold, seed, stream,
+                               hbm_budget_bytes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hyperim_graph_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        s = GraphStats()
+        _check(lib().hyperim_graph_stats(self._h, C.byref(s)))
+        out = {f: getattr(s, f) for f, _ in GraphStats._fields_ if f != "stratum_size"}
+        out["stratum_size"] = list(s.stratum_size)
+        return out
+
+    def profile(self):
+        st = self.stats()
+        n, L = self.n, st["profile_entries"]
+        deg = np.zeros(n, np.int32)
+        nl = np.zeros(n, np.int32)
+        strat = np.zeros(n, np.int32)
+        poff = np.zeros(n + 1, np.int64)
+        lw = np.zeros(max(L, 1), np.uint32)
+        ln = np.zeros(max(L, 1), np.uint32)
+        lt = np.zeros(max(L, 1), np.uint64)
+        _check(lib().hyperim_graph_profile(self._h, _ptr(deg), _ptr(nl), _ptr(strat), _ptr(poff),
+                                           _ptr(lw), _ptr(ln), _ptr(lt)))
+        return {"deg": deg, "nlayers": nl, "stratum": strat, "prof_off": poff,
+                "layer_w": lw[:L], "layer_n": ln[:L], "layer_thr": lt[:L]}
+
+    def plan_theta(self, k, eps, ell=1.0):
+        return hyperim_plan_theta(self._h, k, eps, ell)
+
+    def pool(self, tag=0, roots="plain", strategy="paper"):
+        return Pool(self, tag, roots, strategy)
+
+    def select_seeds(self, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap=0):
+        return hyperim_select_seeds(self._h, r1.handle, r2.handle if r2 is not None else None, k,
+                                    mode, eps, ell, theta_cap, r1.roots, r1.strategy)
+
+    def spread(self, seeds, pool):
+        return hyperim_spread(self._h, seeds, pool.handle)
+
+
+class Pool:
+    """An RR-set pool of a graph (grown with sample())."""
+
+    def __init__(self, graph: Graph, tag=0, roots="plain", strategy="paper"):
+        self.graph = graph
+        self.tag = int(tag)
+        self.roots = roots
+        self.strategy = strategy
+        self._h = C.c_void_p()
+        # an empty pool: theta = 0 creates the handle without sampling
+        self._h = hyperim_sample_rr(graph.handle, self.tag, 0, roots, strategy, self._h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sample(self, theta):
+        self._h = hyperim_sample_rr(self.graph.handle, self.tag, theta, self.roots, self.strategy,
+                                    self._h)
+        return self
+
+    def view(self):
+        v = PoolView()
+        _check(lib().hyperim_pool_view(self._h, C.byref(v)))
+        out = {f: getattr(v, f) for f, _ in PoolView._fields_ if f != "n_s"}
+        out["n_s"] = np.array(v.n_s, dtype=np.uint64)
+        return out
+
+    def counters(self):
+        v = self.view()
+        return {k: v[k] for k in ("pops", "layers_seen", "draws", "mats", "mat_he", "mat_members",
+                                  "selected")}
+
+    def to_host(self):
+        v = self.view()
+        N, T = v["count"], v["total"]
+        off = np.zeros(N + 1, np.int64)
+        mem = np.zeros(max(T, 1), np.int32)
+        st = np.zeros(max(N, 1), np.uint8)
+        j = np.zeros(max(N, 1), np.uint32)
+        _check(lib().hyperim_pool_copy(self._h, _ptr(off), _ptr(mem), _ptr(st), _ptr(j)))
+        return off, mem[:T], st[:N], j[:N]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hyperim_pool_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

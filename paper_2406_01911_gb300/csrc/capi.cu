@@ -1,0 +1,479 @@
+// C ABI of the HyperIM library (declared in include/hyperim.h) and its host-side arithmetic:
+// the RR budget of Sec. 4.3, root allocation per stratum, the Eq. 1 estimate, and the
+// HyperIM_BRR doubling driver (Algorithm 4). Device work lives in load.cu, rr.cu, greedy.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace hyperim {
+
+static thread_local std::string g_last_error;
+
+hyperim_status set_error(hyperim_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+hyperim_status cuda_fail(cudaError_t e, const char* what) {
+    return set_error(e == cudaErrorMemoryAllocation ? HYPERIM_ENOMEM : HYPERIM_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (g->budget && g->device_bytes + bytes > g->budget)
+        return set_error(HYPERIM_ENOMEM, "device memory budget exceeded (" +
+                                             std::to_string(g->device_bytes + bytes) + " > " +
+                                             std::to_string(g->budget) + " bytes)");
+    cudaError_t e = cudaMallocAsync(p, bytes, g->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(HYPERIM_ENOMEM, std::string("cudaMallocAsync(") + std::to_string(bytes) +
+                                             "): " + cudaGetErrorString(e));
+    }
+    g->device_bytes += bytes;
+    return HYPERIM_OK;
+}
+
+void dev_free(hyperim_graph* g, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    cudaFreeAsync(p, g->stream);
+    g->device_bytes -= std::min(bytes, g->device_bytes);
+}
+
+hyperim_status check_device_status(hyperim_graph* g, const char* where) {
+    DevStatus h;
+    HYP_CUDA(cudaMemcpyAsync(&h, g->d_status, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    HYP_CUDA(cudaStreamSynchronize(g->stream));
+    if (h.code == kErrNone) return HYPERIM_OK;
+    HYP_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(DevStatus), g->stream));
+    HYP_CUDA(cudaStreamSynchronize(g->stream));
+    std::string msg = std::string(where) + ": ";
+    switch (h.code) {
+    case kErrBadMember:
+        return set_error(HYPERIM_EINVAL, msg + "member id outside [0, n) in hyperedge " +
+                                             std::to_string(h.detail));
+    case kErrBadOffsets:
+        return set_error(HYPERIM_EINVAL, msg + "hyperedge offsets not monotone from 0 at " +
+                                             std::to_string(h.detail));
+    case kErrWords:
+        return set_error(HYPERIM_EOVERFLOW, msg + "a layer draw at vertex " +
+                                                std::to_string(h.detail) +
+                                                " needs more than 2^18 Philox words");
+    case kErrCapacity:
+    case kErrBucket:
+        return set_error(HYPERIM_EOVERFLOW, msg + "scratch capacity exceeded at vertex " +
+                                                std::to_string(h.detail));
+    default:
+        return set_error(HYPERIM_ECUDA, msg + "device error " + std::to_string(h.code));
+    }
+}
+
+// ---- host arithmetic -----------------------------------------------------------------------
+// n_s = ceil(theta |V_s| / n) for every nonempty stratum (stratified roots); theta (plain).
+void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,
+                     uint64_t n_s[HYPERIM_NSTRATA]) {
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) n_s[s] = 0;
+    if (root_mode == HYPERIM_ROOTS_PLAIN) {
+        n_s[0] = theta;
+        return;
+    }
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+        if (g->stratum_size[s] == 0 || theta == 0) continue;
+        const unsigned __int128 num = (unsigned __int128)theta * (uint64_t)g->stratum_size[s];
+        n_s[s] = (uint64_t)((num + (uint64_t)g->n - 1) / (uint64_t)g->n);
+    }
+}
+
+// Eq. 1 per stratum: sigma = sum_s (|V_s| / n_s) Lambda_s, strata in ascending order.
+double estimate(const hyperim_graph* g, int32_t root_mode, const uint64_t n_s[HYPERIM_NSTRATA],
+                const uint64_t lambda_s[HYPERIM_NSTRATA]) {
+    double sigma = 0.0;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+        if (n_s[s] == 0) continue;
+        const double vs = root_mode == HYPERIM_ROOTS_PLAIN ? (double)g->n : (double)g->stratum_size[s];
+        sigma = sigma + (vs / (double)n_s[s]) * (double)lambda_s[s];
+    }
+    return sigma;
+}
+
+uint64_t stratum_weight(const hyperim_graph* g, int32_t root_mode, uint64_t n_s, int s) {
+    if (root_mode == HYPERIM_ROOTS_PLAIN) return 1;
+    if (n_s == 0) return 0;
+    return ((uint64_t)g->stratum_size[s] << 32) / n_s;
+}
+
+static hyperim_status plan_theta(int64_t n, int32_t k, double eps, double ell, hyperim_theta_plan* out) {
+    if (n < 2 || k < 1 || k > n) return set_error(HYPERIM_EINVAL, "need 1 <= k <= n and n >= 2");
+    if (!(eps > 0.0 && eps < 1.0)) return set_error(HYPERIM_EINVAL, "eps must lie in (0, 1)");
+    if (!(ell > 0.0)) return set_error(HYPERIM_EINVAL, "ell must be positive");
+    const double dn = (double)n, dk = (double)k;
+    const double delta = std::pow(dn, -ell);
+    // ln C(n, k) = sum_{i=1..k'} ln((n - k' + i) / i) with k' = min(k, n - k)
+    const int64_t kk = std::min<int64_t>(k, n - k);
+    double lnc = 0.0;
+    for (int64_t i = 1; i <= kk; ++i) lnc = lnc + std::log((double)(n - kk + i) / (double)i);
+    const double tmax = 2.0 * dn * (std::sqrt(std::log(2.0 / delta)) + std::sqrt(lnc + std::log(6.0 / delta))) /
+                        (eps * eps * dk);
+    const double t0 = tmax * eps * eps * dk / dn;
+    uint64_t t0c = (uint64_t)std::ceil(t0);
+    if (t0c < 1) t0c = 1;
+    int32_t imax = 0;
+    while ((double)t0c * std::ldexp(1.0, imax) < tmax) ++imax;
+    out->delta = delta;
+    out->ln_binom = lnc;
+    out->theta_max = tmax;
+    out->theta_max_ceil = (uint64_t)std::ceil(tmax);
+    out->theta0 = t0c;
+    out->i_max = imax;
+    return HYPERIM_OK;
+}
+
+// Eq. upper_6 with p_max = 1, scaled to spread units: Lambda1 / (1 - (1 - 1/k)^k) * n / |R1|.
+static double upper_bound(double lam1, int32_t k, int64_t n, uint64_t theta) {
+    const double base = 1.0 - 1.0 / (double)k;
+    double pw = 1.0;
+    for (int32_t i = 0; i < k; ++i) pw = pw * base;
+    return lam1 / (1.0 - pw) * (double)n / (double)theta;
+}
+
+// Sec. 4.2: ((sqrt(Lambda2 + 2 ln(1/delta)/9) - sqrt(ln(1/delta)/2))^2 - ln(1/delta)/18) n/|R2|.
+static double lower_bound(double lam2, double delta, int64_t n, uint64_t theta) {
+    const double L = std::log(1.0 / delta);
+    const double a = std::sqrt(lam2 + 2.0 * L / 9.0) - std::sqrt(L / 2.0);
+    return (a * a - L / 18.0) * (double)n / (double)theta;
+}
+
+}  // namespace hyperim
+
+using namespace hyperim;
+
+extern "C" {
+
+const char* hyperim_last_error(void) { return g_last_error.c_str(); }
+
+hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
+    if (!a || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    *out = nullptr;
+    if (a->n < 1 || a->n >= 0x7FFFFFFF) return set_error(HYPERIM_EINVAL, "n must lie in [1, 2^31 - 1)");
+    if (a->m < 0) return set_error(HYPERIM_EINVAL, "m must be >= 0");
+    if (!a->he_off) return set_error(HYPERIM_EINVAL, "he_off is null");
+    if (a->model < 0 || a->model > 2) return set_error(HYPERIM_EINVAL, "unknown probability model");
+    if (a->uniform_threshold > HYPERIM_P_ONE) return set_error(HYPERIM_EINVAL, "uniform_threshold > 2^32");
+    hyperim_graph* g = new (std::nothrow) hyperim_graph();
+    if (!g) return set_error(HYPERIM_ENOMEM, "host allocation failed");
+    g->n = a->n;
+    g->m = a->m;
+    g->model = a->model;
+    g->uniform_thr = a->uniform_threshold;
+    g->seed = a->seed;
+    g->stream = (cudaStream_t)a->cuda_stream;
+    g->budget = a->hbm_budget_bytes;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "device query");
+    }
+    g->id_bits = 1;
+    while (g->id_bits < 31 && (1ll << g->id_bits) < (int64_t)g->n) ++g->id_bits;
+    int32_t nnz_in = 0;
+    if (a->ptrs_on_device) {
+        e = cudaMemcpyAsync(&nnz_in, a->he_off + a->m, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            delete g;
+            return cuda_fail(e, "reading he_off[m]");
+        }
+    } else {
+        if (a->he_off[0] != 0) {
+            delete g;
+            return set_error(HYPERIM_EINVAL, "he_off[0] must be 0");
+        }
+        nnz_in = a->he_off[a->m];
+    }
+    if (nnz_in < 0 || (nnz_in > 0 && !a->he_mem)) {
+        delete g;
+        return set_error(HYPERIM_EINVAL, "bad member array");
+    }
+    hyperim_status st = dev_alloc(g, (void**)&g->d_status, sizeof(DevStatus));
+    if (st == HYPERIM_OK) st = dev_alloc(g, (void**)&g->d_counters, sizeof(RRCounters));
+    if (st == HYPERIM_OK) {
+        cudaMemsetAsync(g->d_status, 0, sizeof(DevStatus), g->stream);
+        st = build_graph(g, a->he_off, a->he_mem, nnz_in, a->ptrs_on_device != 0);
+    }
+    if (st != HYPERIM_OK) {
+        std::string keep = g_last_error;
+        hyperim_graph_free(g);
+        g_last_error = keep;
+        return st;
+    }
+    *out = g;
+    return HYPERIM_OK;
+}
+
+void hyperim_graph_free(hyperim_graph_t g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->prof_off, g->prof, g->deg,
+                    g->stratum, g->vs_off, g->vs_list, g->d_status, g->d_counters, g->scratch.list,
+                    g->scratch.bitmap, g->scratch.big, g->scratch.picks, g->scratch.arena};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, g->stream);
+    cudaStreamSynchronize(g->stream);
+    delete g;
+}
+
+hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out) {
+    if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    out->n = g->n;
+    out->m = g->m;
+    out->nnz = g->nnz;
+    out->profile_entries = g->profile_entries;
+    out->max_layers = g->max_layers;
+    out->max_dh = g->max_dh;
+    out->max_deg = g->max_deg;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) out->stratum_size[s] = g->stratum_size[s];
+    out->theta_lstar = g->theta_lstar;
+    out->device_bytes = g->device_bytes;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* nlayers, int32_t* stratum,
+                                     int64_t* prof_off, uint32_t* layer_w, uint32_t* layer_n,
+                                     uint64_t* layer_thr) {
+    if (!g) return set_error(HYPERIM_EINVAL, "null graph");
+    const size_t n = (size_t)g->n, L = (size_t)g->profile_entries;
+    std::vector<int32_t> off(n + 1);
+    std::vector<uint8_t> strat(n);
+    std::vector<uint4> prof(L);
+    HYP_CUDA(cudaMemcpyAsync(off.data(), g->prof_off, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, g->stream));
+    HYP_CUDA(cudaMemcpyAsync(strat.data(), g->stratum, n, cudaMemcpyDeviceToHost, g->stream));
+    if (L) HYP_CUDA(cudaMemcpyAsync(prof.data(), g->prof, sizeof(uint4) * L, cudaMemcpyDeviceToHost, g->stream));
+    if (deg) HYP_CUDA(cudaMemcpyAsync(deg, g->deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, g->stream));
+    HYP_CUDA(cudaStreamSynchronize(g->stream));
+    for (size_t v = 0; v < n; ++v) {
+        if (nlayers) nlayers[v] = off[v + 1] - off[v];
+        if (stratum) stratum[v] = strat[v];
+    }
+    if (prof_off)
+        for (size_t v = 0; v <= n; ++v) prof_off[v] = off[v];
+    for (size_t x = 0; x < L; ++x) {
+        if (layer_w) layer_w[x] = prof[x].x & ~kPOneFlag;
+        if (layer_n) layer_n[x] = prof[x].y;
+        if (layer_thr) layer_thr[x] = (prof[x].x & kPOneFlag) ? HYPERIM_P_ONE : (uint64_t)prof[x].z;
+    }
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_plan_theta(hyperim_graph_t g, int32_t k, double eps, double ell,
+                                  hyperim_theta_plan* out) {
+    if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    return plan_theta(g->n, k, eps, ell, out);
+}
+
+static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_mode, int32_t strategy,
+                                  hyperim_pool** out) {
+    if (tag > 0xFF) return set_error(HYPERIM_EINVAL, "pool_tag must be < 256");
+    if (root_mode != HYPERIM_ROOTS_PLAIN && root_mode != HYPERIM_ROOTS_STRATIFIED)
+        return set_error(HYPERIM_EINVAL, "unknown root mode");
+    if (strategy != HYPERIM_STRAT_PAPER && strategy != HYPERIM_STRAT_BINOMIAL_ONLY)
+        return set_error(HYPERIM_EINVAL, "unknown strategy");
+    hyperim_pool* p = new (std::nothrow) hyperim_pool();
+    if (!p) return set_error(HYPERIM_ENOMEM, "host allocation failed");
+    p->g = g;
+    p->tag = tag;
+    p->root_mode = root_mode;
+    p->strategy = strategy;
+    *out = p;
+    return HYPERIM_OK;
+}
+
+static hyperim_status pool_grow(hyperim_graph* g, hyperim_pool* p, uint64_t theta) {
+    uint64_t ns[HYPERIM_NSTRATA];
+    allocate_strata(g, p->root_mode, theta, ns);
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) ns[s] = std::max(ns[s], p->n_s[s]);
+    return sample_rr(g, p, ns);
+}
+
+hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
+                                 int32_t strategy, hyperim_pool_t* inout) {
+    if (!g || !inout) return set_error(HYPERIM_EINVAL, "null argument");
+    hyperim_status st;
+    bool created = false;
+    if (!*inout) {
+        if ((st = pool_create(g, pool_tag, root_mode, strategy, inout))) return st;
+        created = true;
+    } else {
+        hyperim_pool* p = *inout;
+        if (p->g != g) return set_error(HYPERIM_ESTATE, "pool belongs to another graph");
+        if (p->tag != pool_tag || p->root_mode != root_mode || p->strategy != strategy)
+            return set_error(HYPERIM_ESTATE, "pool was created with other tag/root mode/strategy");
+    }
+    st = pool_grow(g, *inout, theta);
+    if (st != HYPERIM_OK && created) {
+        std::string keep = g_last_error;
+        hyperim_pool_free(*inout);
+        *inout = nullptr;
+        g_last_error = keep;
+    }
+    return st;
+}
+
+void hyperim_pool_free(hyperim_pool_t p) {
+    if (!p) return;
+    hyperim_graph* g = p->g;
+    dev_free(g, p->rr_off, sizeof(int64_t) * p->cap_off);
+    dev_free(g, p->rr_mem, sizeof(int32_t) * p->cap_total);
+    dev_free(g, p->rr_stratum, p->cap_stratum);
+    dev_free(g, p->rr_j, sizeof(uint32_t) * p->cap_j);
+    cudaStreamSynchronize(g->stream);
+    delete p;
+}
+
+hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
+    if (!p || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    out->count = p->count;
+    out->total = p->total;
+    out->rr_off = p->rr_off;
+    out->rr_mem = p->rr_mem;
+    out->rr_stratum = p->rr_stratum;
+    out->rr_j = p->rr_j;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) out->n_s[s] = p->n_s[s];
+    out->pool_tag = p->tag;
+    out->root_mode = p->root_mode;
+    out->strategy = p->strategy;
+    out->pops = p->counters.pops;
+    out->layers_seen = p->counters.layers_seen;
+    out->draws = p->counters.draws;
+    out->mats = p->counters.mats;
+    out->mat_he = p->counters.mat_he;
+    out->mat_members = p->counters.mat_members;
+    out->selected = p->counters.selected;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_mem, uint8_t* rr_stratum,
+                                 uint32_t* rr_j) {
+    if (!p) return set_error(HYPERIM_EINVAL, "null pool");
+    cudaStream_t s = p->g->stream;
+    const size_t N = (size_t)p->count, T = (size_t)p->total;
+    if (rr_off) {
+        if (N) HYP_CUDA(cudaMemcpyAsync(rr_off, p->rr_off, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
+        else rr_off[0] = 0;
+    }
+    if (rr_mem && T) HYP_CUDA(cudaMemcpyAsync(rr_mem, p->rr_mem, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s));
+    if (rr_stratum && N) HYP_CUDA(cudaMemcpyAsync(rr_stratum, p->rr_stratum, N, cudaMemcpyDeviceToHost, s));
+    if (rr_j && N) HYP_CUDA(cudaMemcpyAsync(rr_j, p->rr_j, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperim_pool_t r2, int32_t k,
+                                    const hyperim_select_opts* opts, int32_t* seeds_host,
+                                    hyperim_select_result* out) {
+    if (!g || !r1 || !opts || !seeds_host || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    if (k < 1 || k > g->n) return set_error(HYPERIM_EINVAL, "need 1 <= k <= n");
+    if (r1->g != g || (r2 && r2->g != g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    if (r1 == r2) return set_error(HYPERIM_ESTATE, "r1 and r2 must be distinct pools");
+    std::memset(out, 0, sizeof(*out));
+    hyperim_status st;
+    using clk = std::chrono::steady_clock;
+    double t_sample = 0.0, t_select = 0.0;
+    if (opts->mode == HYPERIM_SELECT_FIXED) {
+        auto t0 = clk::now();
+        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1))) return st;
+        out->sigma_r1 = estimate(g, r1->root_mode, r1->n_s, out->lambda_r1);
+        if (r2) {
+            if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
+            out->sigma_r2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
+        }
+        t_select = std::chrono::duration<double>(clk::now() - t0).count();
+        out->rounds = 1;
+        out->pool_r1 = (uint64_t)r1->count;
+        out->pool_r2 = r2 ? (uint64_t)r2->count : 0;
+        out->seconds_select = t_select;
+        return HYPERIM_OK;
+    }
+    if (opts->mode != HYPERIM_SELECT_BRR) return set_error(HYPERIM_EINVAL, "unknown select mode");
+    if (!r2) return set_error(HYPERIM_EINVAL, "BRR needs two pools");
+    if (r1->root_mode != r2->root_mode || r1->strategy != r2->strategy)
+        return set_error(HYPERIM_ESTATE, "r1 and r2 differ in root mode or strategy");
+    hyperim_theta_plan plan;
+    if ((st = plan_theta(g->n, k, opts->eps, opts->ell, &plan))) return st;
+    const double target = 1.0 - std::exp(-1.0) - opts->eps;
+    for (int32_t i = 0;; ++i) {
+        if (i > 62) return set_error(HYPERIM_EOVERFLOW, "theta doubling overflow");
+        const uint64_t theta = plan.theta0 << i;
+        if (opts->theta_cap && theta > opts->theta_cap)
+            return set_error(HYPERIM_EOVERFLOW, "theta_i = " + std::to_string(theta) + " exceeds theta_cap");
+        auto t0 = clk::now();
+        if ((st = pool_grow(g, r1, theta))) return st;
+        if ((st = pool_grow(g, r2, theta))) return st;
+        auto t1 = clk::now();
+        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1))) return st;
+        if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
+        auto t2 = clk::now();
+        t_sample += std::chrono::duration<double>(t1 - t0).count();
+        t_select += std::chrono::duration<double>(t2 - t1).count();
+        const uint64_t N1 = (uint64_t)r1->count, N2 = (uint64_t)r2->count;
+        const double s1 = estimate(g, r1->root_mode, r1->n_s, out->lambda_r1);
+        const double s2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
+        const double lam1 = s1 * (double)N1 / (double)g->n;
+        const double lam2 = s2 * (double)N2 / (double)g->n;
+        const double up = upper_bound(lam1, k, g->n, N1);
+        const double lo = lower_bound(lam2, plan.delta, g->n, N2);
+        const double alpha = lo / up;
+        out->rounds = i + 1;
+        out->theta = theta;
+        out->pool_r1 = N1;
+        out->pool_r2 = N2;
+        out->sigma_r1 = s1;
+        out->sigma_r2 = s2;
+        out->upper = up;
+        out->lower = lo;
+        out->alpha = alpha;
+        if (i < 64) out->alpha_round[i] = alpha;
+        if (alpha >= target || i >= plan.i_max) break;
+    }
+    out->seconds_sample = t_sample;
+    out->seconds_select = t_select;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k, hyperim_pool_t pool,
+                              double* sigma_hat, double* std_err) {
+    if (!g || !pool || (k > 0 && !seeds_host)) return set_error(HYPERIM_EINVAL, "null argument");
+    if (pool->g != g) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    if (k < 0) return set_error(HYPERIM_EINVAL, "k must be >= 0");
+    for (int32_t i = 0; i < k; ++i)
+        if (seeds_host[i] < 0 || seeds_host[i] >= g->n) return set_error(HYPERIM_EINVAL, "seed outside [0, n)");
+    uint64_t lam[HYPERIM_NSTRATA];
+    hyperim_status st = coverage(g, pool, seeds_host, k, lam);
+    if (st) return st;
+    const double sigma = estimate(g, pool->root_mode, pool->n_s, lam);
+    double var = 0.0;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+        if (pool->n_s[s] == 0) continue;
+        const double vs = pool->root_mode == HYPERIM_ROOTS_PLAIN ? (double)g->n : (double)g->stratum_size[s];
+        const double ns = (double)pool->n_s[s];
+        const double f = (double)lam[s] / ns;
+        const double wgt = vs / ns;
+        var += wgt * wgt * ns * f * (1.0 - f);
+    }
+    if (sigma_hat) *sigma_hat = sigma;
+    if (std_err) *std_err = std::sqrt(var);
+    return HYPERIM_OK;
+}
+
+}  // extern "C"

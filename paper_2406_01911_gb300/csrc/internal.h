@@ -1,0 +1,153 @@
+// Internal structures of the HyperIM CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hyperim.h"
+
+namespace hyperim {
+
+// Device-side error word: the first kernel to fail stores its code (and a detail value).
+enum DevErr : int32_t {
+    kErrNone = 0,
+    kErrBadMember = 1,     // member id outside [0, n)
+    kErrBadOffsets = 2,    // he_off not monotone
+    kErrProfile = 3,       // layer sizes inconsistent with the profile
+    kErrWords = 4,         // a layer draw needed more than 2^18 Philox words
+    kErrCapacity = 5,      // a scratch capacity was exceeded
+    kErrBucket = 6,        // id bucket larger than the on-chip buffer
+};
+
+struct DevStatus {
+    int32_t code;
+    int32_t detail;
+    uint64_t arena_need;   // bytes of RR output requested by the last generation launch
+};
+
+// Work counters of RR generation (same definitions as the pool view's counters).
+struct RRCounters {
+    unsigned long long pops, layers_seen, draws, mats, mat_he, mat_members, selected;
+};
+
+// Profile entry of layer i of A(mu): 16 bytes.
+//   x: w_i | (p == 1 ? 1u << 31 : 0)
+//   y: n_i
+//   z: floor(p 2^32) for 0 <= p < 1
+//   w: T0 -- the draw is h = 0 whenever word 0 < T0 (0 disables this shortcut); it equals the
+//      first CDF threshold of the Binomial or single-part Poisson inversion, capped at 2^32 - 1.
+constexpr uint32_t kPOneFlag = 0x80000000u;
+
+struct Scratch {
+    // per resident block of the RR kernel
+    int blocks = 0;
+    size_t list_cap = 0;         // entries per block (>= n)
+    size_t bitmap_words = 0;     // words per block of the global visited bitmap (0 if on-chip)
+    size_t big_cap = 0;          // entries per block for bucketed neighbourhoods
+    size_t pick_cap = 0;         // entries per block for picks
+    int32_t* list = nullptr;
+    uint32_t* bitmap = nullptr;
+    uint32_t* big = nullptr;
+    uint32_t* picks = nullptr;
+    // output arena
+    int32_t* arena = nullptr;
+    size_t arena_cap = 0;        // entries
+};
+
+}  // namespace hyperim
+
+struct hyperim_graph {
+    int32_t n = 0, m = 0;
+    int64_t nnz = 0;
+    int32_t model = 0;
+    uint64_t uniform_thr = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t device_bytes = 0;
+    int id_bits = 1;             // ceil(log2 n)
+    // incidence store
+    int32_t* he_off = nullptr;   // m + 1
+    int32_t* he_mem = nullptr;   // nnz, sorted within each hyperedge
+    int32_t* v_off = nullptr;    // n + 1
+    int32_t* v_he = nullptr;     // nnz, ascending hyperedge ids per vertex
+    int32_t* tsum = nullptr;     // n: sum of |he| over he containing v
+    // layer profile
+    int32_t* prof_off = nullptr; // n + 1
+    uint4* prof = nullptr;       // profile entries
+    int32_t* deg = nullptr;      // n
+    uint8_t* stratum = nullptr;  // n
+    int32_t* vs_off = nullptr;   // 17
+    int32_t* vs_list = nullptr;  // n (vertices grouped by stratum, ascending id)
+    // host copies of scalars
+    int64_t profile_entries = 0;
+    int32_t max_layers = 0, max_dh = 0;
+    int64_t max_deg = 0, max_tsum = 0, max_layer_n = 0;
+    int64_t stratum_size[HYPERIM_NSTRATA] = {};
+    double theta_lstar = 0.0;
+    // device status + scratch
+    hyperim::DevStatus* d_status = nullptr;
+    hyperim::RRCounters* d_counters = nullptr;
+    hyperim::Scratch scratch;
+    int sm_count = 0;
+};
+
+struct hyperim_pool {
+    hyperim_graph* g = nullptr;
+    uint32_t tag = 0;
+    int32_t root_mode = 0, strategy = 0;
+    uint64_t n_s[HYPERIM_NSTRATA] = {};
+    int64_t count = 0, total = 0;
+    size_t cap_off = 0, cap_stratum = 0, cap_j = 0, cap_total = 0;  // allocated entries
+    int64_t* rr_off = nullptr;      // count + 1
+    int32_t* rr_mem = nullptr;      // total
+    uint8_t* rr_stratum = nullptr;  // count
+    uint32_t* rr_j = nullptr;       // count
+    hyperim::RRCounters counters = {};
+    double mean_size_hint = 0.0;
+};
+
+namespace hyperim {
+
+// error handling (capi.cu)
+hyperim_status set_error(hyperim_status st, const std::string& msg);
+hyperim_status cuda_fail(cudaError_t e, const char* what);
+#define HYP_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::hyperim::cuda_fail(e_, #call);  \
+    } while (0)
+
+// device memory (capi.cu): stream-ordered allocation accounted against the graph's budget
+hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes);
+void dev_free(hyperim_graph* g, void* p, size_t bytes);
+hyperim_status check_device_status(hyperim_graph* g, const char* where);
+
+// load.cu
+hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off, const int32_t* he_mem,
+                           int32_t nnz_in, bool on_device);
+
+// scan.cu: exclusive scan of n uint32/int32 counts into int64 (out has n + 1 entries)
+hyperim_status exclusive_scan_u32_to_i64(hyperim_graph* g, const uint32_t* in, int64_t* out,
+                                         int64_t n);
+hyperim_status exclusive_scan_i64(hyperim_graph* g, const int64_t* in, int64_t* out, int64_t n);
+
+// rr.cu
+hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]);
+
+// greedy.cu
+hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
+                      uint64_t lambda_s[HYPERIM_NSTRATA]);
+hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_host, int32_t k,
+                        uint64_t lambda_s[HYPERIM_NSTRATA]);
+
+// host arithmetic (plan.cpp)
+void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,
+                     uint64_t n_s[HYPERIM_NSTRATA]);
+double estimate(const hyperim_graph* g, int32_t root_mode, const uint64_t n_s[HYPERIM_NSTRATA],
+                const uint64_t lambda_s[HYPERIM_NSTRATA]);
+uint64_t stratum_weight(const hyperim_graph* g, int32_t root_mode, uint64_t n_s, int s);
+
+}  // namespace hyperim

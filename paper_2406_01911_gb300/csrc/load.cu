@@ -1,0 +1,621 @@
+// Incidence store and layer profile (Sec. 2.1 and Sec. 3.1.1), built on the device.
+//
+//   he -> members : hyperedges as sorted vertex sets (repeated ids collapsed)
+//   v  -> he      : hyperedges containing each vertex, ascending
+//   profile       : for every vertex mu, the layers of A(mu) keyed by w(mu,nu), L_1 = largest w,
+//                   with n(L_i), the activation threshold floor(p_i 2^32) and the h = 0 shortcut
+//   strata        : s(mu) = min(l_mu, 15); V_s lists in ascending id order
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_math.cuh"
+#include "internal.h"
+#include "mat.cuh"
+
+namespace hyperim {
+namespace {
+
+constexpr int kNormWarps = 8;   // warps per block of the per-hyperedge / per-vertex kernels
+constexpr int kProfThreads = 256;
+constexpr int kProfBuf = 8192;  // on-chip keys of the profile kernel (power of two)
+constexpr int kProfHist = 4096; // on-chip multiplicity histogram bins
+constexpr int kBucketsMax = 4096;
+
+__device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
+}
+
+// ---- validation -------------------------------------------------------------------------------
+__global__ void k_check_offsets(const int32_t* off, int32_t m, DevStatus* st) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (off[e + 1] < off[e]) dev_fail(st, kErrBadOffsets, (int32_t)e);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && off[0] != 0) dev_fail(st, kErrBadOffsets, 0);
+}
+
+// ---- normalisation: sort each hyperedge's members, drop repeats (a hyperedge is a set) -------
+// One warp per hyperedge. A member is kept at its first occurrence only; its position in the
+// sorted set is the number of distinct values below it.
+__global__ void k_normalise(const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                            int32_t m, int32_t n, int32_t* __restrict__ out,
+                            uint8_t* __restrict__ first, uint32_t* __restrict__ newsize,
+                            DevStatus* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = warp; e < m; e += nwarps) {
+        const int32_t b = off[e], len = off[e + 1] - b;
+        if (len <= 32) {
+            const int32_t x = lane < len ? mem[b + lane] : INT32_MAX;
+            if (lane < len && (x < 0 || x >= n)) dev_fail(st, kErrBadMember, (int32_t)e);
+            bool dup = false;
+            for (int j = 0; j < len; ++j) {
+                const int32_t y = __shfl_sync(0xFFFFFFFFu, x, j);
+                if (y == x && j < lane) dup = true;
+            }
+            int below = 0;
+            for (int j = 0; j < len; ++j) {
+                const int32_t y = __shfl_sync(0xFFFFFFFFu, x, j);
+                const int ydup = __shfl_sync(0xFFFFFFFFu, dup ? 1 : 0, j);
+                if (!ydup && y < x) ++below;
+            }
+            const bool keep = lane < len && !dup;
+            const uint32_t kb = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) out[b + below] = x;
+            if (lane == 0) newsize[e] = __popc(kb);
+        } else {
+            // first-occurrence flags, then positions among first occurrences
+            for (int i = lane; i < len; i += 32) {
+                const int32_t x = mem[b + i];
+                if (x < 0 || x >= n) dev_fail(st, kErrBadMember, (int32_t)e);
+                bool dup = false;
+                for (int j = 0; j < i && !dup; ++j) dup = mem[b + j] == x;
+                first[b + i] = dup ? 0 : 1;
+            }
+            __syncwarp();
+            int keep = 0;
+            for (int i = lane; i < len; i += 32) {
+                if (!first[b + i]) continue;
+                const int32_t x = mem[b + i];
+                int below = 0;
+                for (int j = 0; j < len; ++j) below += (first[b + j] && mem[b + j] < x) ? 1 : 0;
+                out[b + below] = x;
+                ++keep;
+            }
+            for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xFFFFFFFFu, keep, o);
+            if (lane == 0) newsize[e] = keep;
+        }
+    }
+}
+
+__global__ void k_compact_he(const int32_t* __restrict__ off_in, const int32_t* __restrict__ tmp,
+                             const int64_t* __restrict__ off_new, int32_t m,
+                             int32_t* __restrict__ he_off, int32_t* __restrict__ he_mem) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = warp; e < m; e += nwarps) {
+        const int32_t src = off_in[e];
+        const int64_t dst = off_new[e], len = off_new[e + 1] - dst;
+        for (int64_t i = lane; i < len; i += 32) he_mem[dst + i] = tmp[src + i];
+        if (lane == 0) he_off[e] = (int32_t)dst;
+        if (lane == 0 && e == m - 1) he_off[m] = (int32_t)off_new[m];
+    }
+}
+
+// ---- vertex -> hyperedge lists ------------------------------------------------------------------
+__global__ void k_count_dh(const int32_t* __restrict__ he_mem, int64_t nnz, uint32_t* cnt) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[he_mem[x]], 1u);
+}
+
+__global__ void k_scatter_vhe(const int32_t* __restrict__ he_off, const int32_t* __restrict__ he_mem,
+                              int32_t m, const int64_t* __restrict__ v_off64, uint32_t* cur,
+                              int32_t* __restrict__ v_he, int32_t* __restrict__ tsum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = warp; e < m; e += nwarps) {
+        const int32_t b = he_off[e], len = he_off[e + 1] - b;
+        for (int i = lane; i < len; i += 32) {
+            const int32_t v = he_mem[b + i];
+            const uint32_t pos = atomicAdd(&cur[v], 1u);
+            v_he[v_off64[v] + pos] = (int32_t)e;
+            atomicAdd(&tsum[v], len);
+        }
+    }
+}
+
+// sort each vertex's hyperedge list (distinct ids): position = number of smaller ids
+__global__ void k_sort_vhe(const int64_t* __restrict__ v_off64, int32_t n,
+                           const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                           int32_t* __restrict__ v_off32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const int64_t b = v_off64[v], len = v_off64[v + 1] - b;
+        for (int64_t i = lane; i < len; i += 32) {
+            const int32_t x = in[b + i];
+            int below = 0;
+            for (int64_t j = 0; j < len; ++j) below += in[b + j] < x ? 1 : 0;
+            out[b + below] = x;
+        }
+        if (lane == 0) v_off32[v] = (int32_t)b;
+        if (lane == 0 && v == n - 1) v_off32[n] = (int32_t)v_off64[n];
+    }
+}
+
+// ---- layer profile: pass 1 ----------------------------------------------------------------------
+// For each vertex mu: the multiplicities w(mu,nu) over its distinct neighbours nu, histogrammed by
+// w; the distinct w values in descending order with their counts n_i are written to
+// pairs[v_off[mu] ...] (at most d_H(mu) of them). Also l_mu and deg(mu).
+struct ProfScratch {
+    uint32_t* big;       // per block: bucketed members (big_cap entries)
+    uint32_t* hist;      // per block: multiplicity histogram when d_H exceeds kProfHist
+    int64_t big_cap;
+    int64_t hist_cap;
+};
+
+__global__ void __launch_bounds__(kProfThreads)
+k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
+          uint2* __restrict__ pairs, uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
+          int* __restrict__ next_vertex, ProfScratch S, DevStatus* st,
+          unsigned long long* __restrict__ maxima /* [max_l, max_deg, max_layer_n] */) {
+    extern __shared__ uint32_t smem[];
+    uint32_t* buf = smem;                                  // kProfBuf
+    uint32_t* hist_s = buf + kProfBuf;                     // kProfHist
+    int* bucket_cnt = (int*)(hist_s + kProfHist);          // kBucketsMax
+    int* ctrl = bucket_cnt + kBucketsMax;                  // small control block
+    using Gr = Group<kProfThreads>;
+    uint32_t* big = S.big + (int64_t)blockIdx.x * S.big_cap;
+    uint32_t* hist_g = S.hist + (int64_t)blockIdx.x * S.hist_cap;
+
+    for (;;) {
+        if (threadIdx.x == 0) ctrl[0] = atomicAdd(next_vertex, 1);
+        __syncthreads();
+        const int32_t mu = ctrl[0];
+        __syncthreads();
+        if (mu >= n) break;
+        const int32_t e0 = I.v_off[mu], dh = I.v_off[mu + 1] - e0;
+        if (dh == 0) {
+            if (threadIdx.x == 0) { nlayers[mu] = 0; deg[mu] = 0; }
+            continue;
+        }
+        if (dh == 1) {
+            if (threadIdx.x == 0) {
+                const int32_t he = I.v_he[e0];
+                const uint32_t nb = (uint32_t)(I.he_off[he + 1] - I.he_off[he] - 1);
+                nlayers[mu] = nb > 0 ? 1 : 0;
+                deg[mu] = nb;
+                if (nb > 0) pairs[e0] = make_uint2(1u, nb);
+                if (nb > 0) {
+                    atomicMax(&maxima[0], 1ull);
+                    atomicMax(&maxima[1], (unsigned long long)nb);
+                    atomicMax(&maxima[2], (unsigned long long)nb);
+                }
+            }
+            continue;
+        }
+        // histogram of multiplicities, indexed by w in [1, dh]
+        uint32_t* hist = dh < kProfHist ? hist_s : hist_g;
+        if (dh >= kProfHist && (int64_t)dh + 1 > S.hist_cap) {
+            if (threadIdx.x == 0) dev_fail(st, kErrCapacity, mu);
+            continue;
+        }
+        for (int w = threadIdx.x; w <= dh; w += kProfThreads) hist[w] = 0;
+        __syncthreads();
+        auto count_runs = [&](bool start, uint32_t, int mult) -> bool {
+            if (start) atomicAdd(&hist[mult], 1u);
+            return false;
+        };
+        const int T = tsum[mu] - dh;  // members other than mu
+        if (T <= kProfBuf) {
+            const int got = gather_nbhd<kProfThreads>(I, mu, buf, &ctrl[1]);
+            group_sort<kProfThreads>(buf, got);
+            walk_runs<kProfThreads>(buf, got, count_runs);
+        } else {
+            // bucket the members by their top id bits so each bucket fits on chip
+            if ((int64_t)T > S.big_cap) {
+                if (threadIdx.x == 0) dev_fail(st, kErrCapacity, mu);
+                continue;
+            }
+            int b = 0;
+            while ((int64_t)(kProfBuf / 4) << b < (int64_t)T && b < id_bits && (1 << (b + 1)) <= kBucketsMax) ++b;
+            bool ok = false;
+            for (;;) {
+                const int nb = 1 << b;
+                const int shift = id_bits - b;
+                for (int i = threadIdx.x; i < nb; i += kProfThreads) bucket_cnt[i] = 0;
+                __syncthreads();
+                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                for (int e = e0 + wid; e < e0 + dh; e += kProfThreads / 32) {
+                    const int he = I.v_he[e];
+                    const int hb = I.he_off[he], len = I.he_off[he + 1] - hb;
+                    for (int i = lane; i < len; i += 32) {
+                        const uint32_t x = (uint32_t)I.he_mem[hb + i];
+                        if (x != (uint32_t)mu) atomicAdd(&bucket_cnt[x >> shift], 1);
+                    }
+                }
+                __syncthreads();
+                int mx = 0;
+                for (int i = threadIdx.x; i < nb; i += kProfThreads) mx = max(mx, bucket_cnt[i]);
+                const int bmax = __reduce_max_sync(0xFFFFFFFFu, mx);
+                if ((threadIdx.x & 31) == 0) ctrl[8 + (threadIdx.x >> 5)] = bmax;
+                __syncthreads();
+                int all_max = 0;
+                for (int w = 0; w < kProfThreads / 32; ++w) all_max = max(all_max, ctrl[8 + w]);
+                __syncthreads();
+                if (all_max <= kProfBuf) { ok = true; break; }
+                if (b >= id_bits || (1 << (b + 1)) > kBucketsMax) break;
+                ++b;
+            }
+            if (!ok) {
+                if (threadIdx.x == 0) dev_fail(st, kErrBucket, mu);
+                __syncthreads();
+                continue;
+            }
+            const int nb = 1 << b;
+            const int shift = id_bits - b;
+            // exclusive scan of bucket counts (single warp, nb <= 4096)
+            if (threadIdx.x < 32) {
+                int carry = 0;
+                for (int base = 0; base < nb; base += 32) {
+                    const int i = base + threadIdx.x;
+                    const int v = i < nb ? bucket_cnt[i] : 0;
+                    int inc = v;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                        if ((int)threadIdx.x >= o) inc += t;
+                    }
+                    if (i < nb) bucket_cnt[i] = carry + inc - v;
+                    carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+                }
+            }
+            __syncthreads();
+            // scatter into the global bucket area; bucket_cnt becomes the running end
+            {
+                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                for (int e = e0 + wid; e < e0 + dh; e += kProfThreads / 32) {
+                    const int he = I.v_he[e];
+                    const int hb = I.he_off[he], len = I.he_off[he + 1] - hb;
+                    for (int i = lane; i < len; i += 32) {
+                        const uint32_t x = (uint32_t)I.he_mem[hb + i];
+                        if (x != (uint32_t)mu) big[atomicAdd(&bucket_cnt[x >> shift], 1)] = x;
+                    }
+                }
+            }
+            __syncthreads();
+            int begin = 0;
+            for (int q = 0; q < nb; ++q) {
+                const int end = bucket_cnt[q];
+                const int cnt = end - begin;
+                if (cnt > 0) {
+                    for (int i = threadIdx.x; i < cnt; i += kProfThreads) buf[i] = big[begin + i];
+                    __syncthreads();
+                    group_sort<kProfThreads>(buf, cnt);
+                    walk_runs<kProfThreads>(buf, cnt, count_runs);
+                    __syncthreads();
+                }
+                begin = end;
+            }
+        }
+        __syncthreads();
+        // distinct multiplicities in descending order -> (w_i, n_i); single warp
+        if (threadIdx.x < 32) {
+            int carry = 0;
+            uint32_t dsum = 0, nmax = 0;
+            for (int top = dh; top >= 1; top -= 32) {
+                const int w = top - (int)threadIdx.x;
+                const uint32_t c = w >= 1 ? hist[w] : 0u;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, c > 0);
+                const int pos = carry + __popc(bal & lanemask_lt());
+                if (c > 0) pairs[e0 + pos] = make_uint2((uint32_t)w, c);
+                carry += __popc(bal);
+                dsum += c;
+                nmax = max(nmax, c);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, o);
+                nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, o));
+            }
+            if (threadIdx.x == 0) {
+                nlayers[mu] = (uint32_t)carry;
+                deg[mu] = dsum;
+                atomicMax(&maxima[0], (unsigned long long)carry);
+                atomicMax(&maxima[1], (unsigned long long)dsum);
+                atomicMax(&maxima[2], (unsigned long long)nmax);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- layer profile: pass 2 (thresholds and the h = 0 shortcut) ---------------------------------
+__global__ void k_profile_write(int32_t n, const int32_t* __restrict__ v_off,
+                                const uint2* __restrict__ pairs, const int64_t* __restrict__ poff64,
+                                const uint32_t* __restrict__ deg, int32_t model, uint64_t uthr,
+                                const double* __restrict__ ln_l1, uint4* __restrict__ prof,
+                                int32_t* __restrict__ prof_off, uint8_t* __restrict__ stratum) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pb = poff64[v];
+        const int l = (int)(poff64[v + 1] - pb);
+        prof_off[v] = (int32_t)pb;
+        if (v == n - 1) prof_off[n] = (int32_t)poff64[n];
+        stratum[v] = (uint8_t)(l < HYPERIM_NSTRATA - 1 ? l : HYPERIM_NSTRATA - 1);
+        const uint32_t dg = deg[v];
+        for (int i = 0; i < l; ++i) {
+            const uint2 wn = pairs[v_off[v] + i];
+            const uint32_t n_i = wn.y;
+            uint64_t thr;
+            if (model == HYPERIM_P_UNIFORM_PAIR) {
+                thr = uthr;
+            } else if (model == HYPERIM_P_WC) {
+                thr = dg <= 1 ? kPOne : (kPOne / (uint64_t)dg);
+            } else {
+                // P(L_i) = 1/(i ln(l+1)) (Sec. 3.1.1); per member P(L_i)/n_i, clamped to 1
+                const double PL = __ddiv_rn(1.0, __dmul_rn((double)(i + 1), ln_l1[l]));
+                const double pd = __ddiv_rn(PL, (double)n_i);
+                thr = pd >= 1.0 ? kPOne : __double2ull_rz(__dmul_rn(pd, 4294967296.0));
+            }
+            uint32_t flags = 0, t0 = 0;
+            if (thr >= kPOne) {
+                flags = kPOneFlag;
+            } else if (thr > 0) {
+                uint64_t T0;
+                if (n_i <= 20) {
+                    T0 = binomial_t0(n_i, thr);
+                } else {
+                    const double lam = poisson_lambda(n_i, thr);
+                    T0 = poisson_parts(lam) == 1 ? cdf_thr(exp_neg(lam)) : 0;
+                }
+                t0 = (uint32_t)(T0 > 0xFFFFFFFFull ? 0xFFFFFFFFull : T0);
+            }
+            prof[pb + i] = make_uint4(wn.x | flags, n_i, thr >= kPOne ? 0u : (uint32_t)thr, t0);
+        }
+    }
+}
+
+__global__ void k_stratum_flags(const uint8_t* __restrict__ stratum, int32_t n, int s,
+                                uint32_t* __restrict__ flags) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        flags[v] = stratum[v] == s ? 1u : 0u;
+}
+
+__global__ void k_stratum_scatter(const uint32_t* __restrict__ flags, const int64_t* __restrict__ pos,
+                                  int32_t n, int32_t base, int32_t* __restrict__ vs_list) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (flags[v]) vs_list[base + pos[v]] = (int32_t)v;
+}
+
+__global__ void k_hist_layers(const int64_t* __restrict__ poff64, int32_t n,
+                              unsigned long long* __restrict__ hist, int hmax) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = poff64[v + 1] - poff64[v];
+        atomicAdd(&hist[l < hmax ? l : hmax], 1ull);
+    }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, unsigned long long* out) {
+    unsigned long long mx = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned long long)a[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+__global__ void k_vhe_len(const int64_t* __restrict__ v_off64, int32_t n, int32_t* __restrict__ dh) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        dh[v] = (int32_t)(v_off64[v + 1] - v_off64[v]);
+}
+
+int grid_for(int64_t items, int threads, int sm) {
+    int64_t b = (items + threads - 1) / threads;
+    int64_t cap = (int64_t)sm * 32;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int32_t* he_mem_in,
+                           int32_t nnz_in, bool on_device) {
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n, m = g->m;
+    const int sm = g->sm_count;
+    hyperim_status st;
+    // --- upload
+    int32_t *d_off_in = nullptr, *d_mem_in = nullptr, *d_tmp = nullptr;
+    const size_t nnz_alloc = (size_t)(nnz_in > 0 ? nnz_in : 1);
+    if ((st = dev_alloc(g, (void**)&d_off_in, sizeof(int32_t) * ((size_t)m + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&d_mem_in, sizeof(int32_t) * nnz_alloc))) return st;
+    if ((st = dev_alloc(g, (void**)&d_tmp, sizeof(int32_t) * nnz_alloc))) return st;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HYP_CUDA(cudaMemcpyAsync(d_off_in, he_off_in, sizeof(int32_t) * ((size_t)m + 1), kind, s));
+    if (nnz_in > 0)
+        HYP_CUDA(cudaMemcpyAsync(d_mem_in, he_mem_in, sizeof(int32_t) * (size_t)nnz_in, kind, s));
+    if (m > 0) k_check_offsets<<<grid_for(m, 256, sm), 256, 0, s>>>(d_off_in, m, g->d_status);
+    if ((st = check_device_status(g, "hyperedge offsets"))) return st;
+
+    // --- normalise hyperedges
+    uint32_t* d_newsize = nullptr;
+    int64_t* d_off_new = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_newsize, sizeof(uint32_t) * ((size_t)m + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&d_off_new, sizeof(int64_t) * ((size_t)m + 1)))) return st;
+    uint8_t* d_first = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_first, nnz_alloc))) return st;
+    if (m > 0)
+        k_normalise<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_mem_in, m, n,
+                                                                       d_tmp, d_first, d_newsize,
+                                                                       g->d_status);
+    if ((st = check_device_status(g, "hyperedge members"))) return st;
+    if ((st = exclusive_scan_u32_to_i64(g, d_newsize, d_off_new, m))) return st;
+    int64_t nnz = 0;
+    HYP_CUDA(cudaMemcpyAsync(&nnz, d_off_new + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    g->nnz = nnz;
+    const size_t nnz_a = (size_t)(nnz > 0 ? nnz : 1);
+    if ((st = dev_alloc(g, (void**)&g->he_off, sizeof(int32_t) * ((size_t)m + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->he_mem, sizeof(int32_t) * nnz_a))) return st;
+    if (m > 0)
+        k_compact_he<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_tmp, d_off_new,
+                                                                        m, g->he_off, g->he_mem);
+    else
+        HYP_CUDA(cudaMemsetAsync(g->he_off, 0, sizeof(int32_t), s));
+
+    // --- vertex -> hyperedge lists
+    uint32_t* d_cnt = nullptr;
+    int64_t* d_voff64 = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_cnt, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&d_voff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->v_off, sizeof(int32_t) * ((size_t)n + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->v_he, sizeof(int32_t) * nnz_a))) return st;
+    if ((st = dev_alloc(g, (void**)&g->tsum, sizeof(int32_t) * (size_t)n))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
+    HYP_CUDA(cudaMemsetAsync(g->tsum, 0, sizeof(int32_t) * (size_t)n, s));
+    if (nnz > 0) k_count_dh<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->he_mem, nnz, d_cnt);
+    if ((st = exclusive_scan_u32_to_i64(g, d_cnt, d_voff64, n))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
+    if (m > 0)
+        k_scatter_vhe<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(
+            g->he_off, g->he_mem, m, d_voff64, d_cnt, d_tmp, g->tsum);
+    k_sort_vhe<<<grid_for((int64_t)n * 32, 256, sm), 256, 0, s>>>(d_voff64, n, d_tmp, g->v_he,
+                                                                   g->v_off);
+
+    // --- maxima of d_H and T
+    unsigned long long* d_max = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_max, sizeof(unsigned long long) * 8))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long) * 8, s));
+    int32_t* d_dh = (int32_t*)d_cnt;  // reuse
+    k_vhe_len<<<grid_for(n, 256, sm), 256, 0, s>>>(d_voff64, n, d_dh);
+    k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(d_dh, n, d_max + 3);
+    k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(g->tsum, n, d_max + 4);
+    unsigned long long hmax[8];
+    HYP_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    g->max_dh = (int32_t)hmax[3];
+    g->max_tsum = (int64_t)hmax[4];
+
+    // --- layer profile pass 1
+    uint2* d_pairs = nullptr;
+    uint32_t *d_nl = nullptr, *d_deg = nullptr;
+    int* d_next = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_pairs, sizeof(uint2) * nnz_a))) return st;
+    if ((st = dev_alloc(g, (void**)&d_nl, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->deg, sizeof(int32_t) * (size_t)n))) return st;
+    d_deg = (uint32_t*)g->deg;
+    if ((st = dev_alloc(g, (void**)&d_next, sizeof(int)))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+    const size_t prof_smem = sizeof(uint32_t) * (kProfBuf + kProfHist) + sizeof(int) * (kBucketsMax + 8 + kProfThreads / 32);
+    HYP_CUDA(cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)prof_smem));
+    int per_sm = 0;
+    HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_profile, kProfThreads,
+                                                           prof_smem));
+    if (per_sm < 1) per_sm = 1;
+    const int pblocks = sm * per_sm;
+    ProfScratch PS;
+    PS.big_cap = g->max_tsum > kProfBuf ? g->max_tsum : 1;
+    PS.hist_cap = g->max_dh >= kProfHist ? (int64_t)g->max_dh + 1 : 1;
+    if ((st = dev_alloc(g, (void**)&PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks)))
+        return st;
+    if ((st = dev_alloc(g, (void**)&PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks)))
+        return st;
+    Incidence I{g->he_off, g->he_mem, g->v_off, g->v_he};
+    k_profile<<<pblocks, kProfThreads, prof_smem, s>>>(I, n, g->id_bits, g->tsum, d_pairs, d_nl,
+                                                       d_deg, d_next, PS, g->d_status, d_max);
+    if ((st = check_device_status(g, "layer profile"))) return st;
+    dev_free(g, PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks);
+    dev_free(g, PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks);
+    HYP_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    g->max_layers = (int32_t)hmax[0];
+    g->max_deg = (int64_t)hmax[1];
+    g->max_layer_n = (int64_t)hmax[2];
+
+    // --- profile offsets + pass 2
+    int64_t* d_poff64 = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_poff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = exclusive_scan_u32_to_i64(g, d_nl, d_poff64, n))) return st;
+    int64_t L = 0;
+    HYP_CUDA(cudaMemcpyAsync(&L, d_poff64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    g->profile_entries = L;
+    if ((st = dev_alloc(g, (void**)&g->prof, sizeof(uint4) * (size_t)(L > 0 ? L : 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->prof_off, sizeof(int32_t) * ((size_t)n + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->stratum, (size_t)n))) return st;
+    // ln(l + 1) for the paper's layer probabilities, computed once on the host
+    std::vector<double> ln_l1((size_t)g->max_layers + 2);
+    for (size_t l = 0; l < ln_l1.size(); ++l) ln_l1[l] = std::log((double)l + 1.0);
+    double* d_ln = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_ln, sizeof(double) * ln_l1.size()))) return st;
+    HYP_CUDA(cudaMemcpyAsync(d_ln, ln_l1.data(), sizeof(double) * ln_l1.size(),
+                             cudaMemcpyHostToDevice, s));
+    k_profile_write<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, d_pairs, d_poff64, d_deg,
+                                                         g->model, g->uniform_thr, d_ln, g->prof,
+                                                         g->prof_off, g->stratum);
+
+    // --- theta(l*) from the histogram of l (Thm 2)
+    const int hcap = g->max_layers + 1;
+    unsigned long long* d_lh = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1)))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_lh, 0, sizeof(unsigned long long) * ((size_t)hcap + 1), s));
+    k_hist_layers<<<grid_for(n, 256, sm), 256, 0, s>>>(d_poff64, n, d_lh, hcap);
+    std::vector<unsigned long long> lh((size_t)hcap + 1);
+    HYP_CUDA(cudaMemcpyAsync(lh.data(), d_lh, sizeof(unsigned long long) * lh.size(),
+                             cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    double lsum = 0.0;
+    for (int l = 1; l < hcap; ++l)
+        if (lh[l]) lsum += (double)lh[l] * ((double)l / std::log((double)l + 1.0));
+    g->theta_lstar = lsum / (double)n;
+    for (int s2 = 0; s2 < HYPERIM_NSTRATA; ++s2) g->stratum_size[s2] = 0;
+    for (int l = 0; l < hcap; ++l)
+        g->stratum_size[l < HYPERIM_NSTRATA - 1 ? l : HYPERIM_NSTRATA - 1] += (int64_t)lh[l];
+
+    // --- strata lists V_s (ascending ids)
+    if ((st = dev_alloc(g, (void**)&g->vs_off, sizeof(int32_t) * (HYPERIM_NSTRATA + 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->vs_list, sizeof(int32_t) * (size_t)n))) return st;
+    int32_t hvs[HYPERIM_NSTRATA + 1];
+    hvs[0] = 0;
+    for (int s2 = 0; s2 < HYPERIM_NSTRATA; ++s2) hvs[s2 + 1] = hvs[s2] + (int32_t)g->stratum_size[s2];
+    HYP_CUDA(cudaMemcpyAsync(g->vs_off, hvs, sizeof(hvs), cudaMemcpyHostToDevice, s));
+    uint32_t* d_flags = d_cnt;
+    for (int s2 = 0; s2 < HYPERIM_NSTRATA; ++s2) {
+        if (g->stratum_size[s2] == 0) continue;
+        k_stratum_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(g->stratum, n, s2, d_flags);
+        if ((st = exclusive_scan_u32_to_i64(g, d_flags, d_voff64, n))) return st;
+        k_stratum_scatter<<<grid_for(n, 256, sm), 256, 0, s>>>(d_flags, d_voff64, n, hvs[s2],
+                                                               g->vs_list);
+    }
+    HYP_CUDA(cudaGetLastError());
+    if ((st = check_device_status(g, "profile write"))) return st;
+    // temporaries
+    dev_free(g, d_off_in, sizeof(int32_t) * ((size_t)m + 1));
+    dev_free(g, d_mem_in, sizeof(int32_t) * nnz_alloc);
+    dev_free(g, d_tmp, sizeof(int32_t) * nnz_alloc);
+    dev_free(g, d_newsize, sizeof(uint32_t) * ((size_t)m + 1));
+    dev_free(g, d_first, nnz_alloc);
+    dev_free(g, d_off_new, sizeof(int64_t) * ((size_t)m + 1));
+    dev_free(g, d_cnt, sizeof(uint32_t) * ((size_t)n + 1));
+    dev_free(g, d_voff64, sizeof(int64_t) * ((size_t)n + 1));
+    dev_free(g, d_max, sizeof(unsigned long long) * 8);
+    dev_free(g, d_pairs, sizeof(uint2) * nnz_a);
+    dev_free(g, d_nl, sizeof(uint32_t) * ((size_t)n + 1));
+    dev_free(g, d_next, sizeof(int));
+    dev_free(g, d_poff64, sizeof(int64_t) * ((size_t)n + 1));
+    dev_free(g, d_ln, sizeof(double) * ln_l1.size());
+    dev_free(g, d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    return check_device_status(g, "load");
+}
+
+}  // namespace hyperim

@@ -1,0 +1,913 @@
+// Stratified random RR sets on a hypergraph (Algorithm 3) and their compaction to CSR.
+//
+// One block builds one RR set at a time (persistent grid over the batch). The reverse BFS runs
+// level by level: the warps of the block pop the vertices of the current level in parallel.
+// For a popped mu each lane draws h_i for one layer of A(mu) (Binomial if n(L_i) <= 20, else
+// Poisson; Sec. 3.1.3) from the keyed Philox stream (RR, mu, layer); if some h_i > 0, the layer
+// members at the picked positions are found by materialising A(mu) on chip:
+//   - d_H(mu) = 1: A(mu) is the one hyperedge minus mu, already sorted -> direct indexing;
+//   - small neighbourhoods: the warp sorts the members of mu's hyperedges in shared memory;
+//   - large ones are deferred to the end of the level and processed by the whole block, on chip
+//     or, past the on-chip buffer, bucketed by id through a global scratch area.
+// Draws are keyed by (RR, vertex, layer), so the set does not depend on the pop order and the
+// parallel pops are deterministic. Picks already in R are skipped (visited bitmap).
+#include <algorithm>
+#include <cstring>
+
+#include "device_math.cuh"
+#include "internal.h"
+#include "mat.cuh"
+
+namespace hyperim {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kWCap = 1024;      // per-warp on-chip neighbourhood keys (power of two)
+constexpr int kPCap = 256;       // per-warp picks
+constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the warp path
+constexpr int kBCap = 8192;      // block on-chip keys (power of two)
+constexpr int kBLQ = 64;         // layers with h > 0 per block round
+constexpr int kDCap = 512;       // deferred pops per level round
+constexpr int kBuckets = 4096;
+constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
+
+struct RRJobMap {
+    int64_t job_base[HYPERIM_NSTRATA + 1];
+    uint32_t j_base[HYPERIM_NSTRATA];
+};
+
+struct RRParams {
+    Incidence I;
+    const int32_t* prof_off;
+    const uint4* prof;
+    const int32_t* tsum;
+    const int32_t* vs_off;
+    const int32_t* vs_list;
+    int32_t n;
+    int id_bits;
+    uint64_t seed;
+    uint32_t tag;
+    int root_mode;
+    int strategy;
+    int64_t job_base[HYPERIM_NSTRATA + 1];
+    uint32_t j_base[HYPERIM_NSTRATA];
+    int32_t* list;            // per block: list_cap entries
+    int64_t list_cap;
+    uint32_t* gvis;           // per block: vis_words (when not on chip)
+    int vis_smem;             // 1 if the visited bitmap lives in shared memory
+    int64_t vis_words;
+    uint32_t* picks;          // per block: pick_cap entries
+    int64_t pick_cap;
+    uint32_t* big;            // per block: big_cap entries
+    int64_t big_cap;
+    int32_t* arena;
+    uint64_t arena_cap;
+    unsigned long long* arena_used;
+    int64_t* out_pos;
+    int32_t* out_size;
+    int* next_job;
+    DevStatus* st;
+    RRCounters* counters;
+};
+
+struct Need {                    // a layer with h > 0 at the current pop
+    uint32_t w, n, h, ksel, layer;
+};
+
+struct Shared {
+    int ctrl[16];
+    int tmp[kWarps + 2];
+    unsigned long long stat[8];
+    int32_t deferred[kDCap];
+    uint32_t wbuf[kWarps][kWCap];
+    uint32_t wpick[kWarps][kPCap];
+    Need wneed[kWarps][kLQ];
+    int wcursor[kWarps];
+    uint32_t wpoff[kWarps][kLQ + 1];
+    unsigned long long out_pos;
+    int wcnt[kWarps][kBLQ];     // per-warp per-layer counts (block ranks)
+    int lcnt[kBLQ];             // running rank per needed layer (block path)
+    Need bneed[kBLQ];
+    uint32_t bpick_off[kBLQ + 1];
+    uint32_t bbuf[kBCap];
+    int bucket[kBuckets];
+};
+// ctrl slots
+enum { C_JOB = 0, C_HEAD, C_TAIL, C_LEVEL_END, C_NEXT, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP,
+       C_BITS, C_OK };
+// stat slots
+enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL };
+
+__device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
+}
+
+// h for one layer (lane-level). Returns whether a draw was made (0 < p < 1).
+__device__ __forceinline__ bool layer_draw(const uint4 e, int strategy, WordStream& ws,
+                                          uint32_t& h, uint32_t& ksel) {
+    const uint32_t n_i = e.y, thr = e.z, T0 = e.w;
+    ksel = 0;
+    if (e.x & kPOneFlag) { h = n_i; return false; }
+    if (thr == 0) { h = 0; return false; }
+    const uint32_t w0 = ws.word(0);
+    const bool binom = n_i <= 20 || strategy == HYPERIM_STRAT_BINOMIAL_ONLY;
+    const bool fast = T0 != 0 && (n_i <= 20 || strategy == HYPERIM_STRAT_PAPER);
+    if (fast && w0 < T0) { h = 0; ksel = 1; return true; }
+    if (binom) {
+        h = binomial_h(n_i, thr, w0);
+        ksel = 1;
+        return true;
+    }
+    const double lam = poisson_lambda(n_i, thr);
+    const uint32_t c = poisson_parts(lam);
+    const double part = poisson_part_lambda(lam, c);
+    uint64_t sum = 0;
+    for (uint32_t t = 0; t < c; ++t) sum += poisson_part(part, n_i, t == 0 ? w0 : ws.word(t));
+    h = sum > n_i ? n_i : (uint32_t)sum;
+    ksel = c;
+    return true;
+}
+
+// Picks of one layer (warp-cooperative, all lanes pass identical arguments): for r = 0..h-1,
+// a = floor(x_r (n - r) / 2^32) from word ksel + r, and the pick is the a-th (0-based) position
+// of [0, n) not picked yet (Sec. 3.1.3: one uniform choice from the remainder per step).
+// sel[0, h) receives the picked positions in ascending order.
+__device__ void gen_picks(WordStream& ws, uint32_t n, uint32_t h, uint32_t ksel, uint32_t* sel) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t r = 0; r < h; ++r) {
+        const uint32_t x = ws.word(ksel + r);
+        const uint32_t a = (uint32_t)(((uint64_t)x * (uint64_t)(n - r)) >> 32);
+        uint32_t idx = a, c = 0;
+        for (;;) {
+            uint32_t cnt = 0;
+            for (uint32_t t = lane; t < r; t += 32) cnt += sel[t] <= idx ? 1u : 0u;
+            cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+            const uint32_t nid = a + cnt;
+            c = cnt;
+            if (nid == idx) break;
+            idx = nid;
+        }
+        // insert idx at position c (shift sel[c, r) up by one, top chunk first)
+        if (r > c) {
+            for (int64_t top = (int64_t)r - 1; top >= (int64_t)c; top -= 32) {
+                const int64_t t = top - lane;
+                uint32_t v = 0;
+                const bool act = t >= (int64_t)c;
+                if (act) v = sel[t];
+                __syncwarp();
+                if (act) sel[t + 1] = v;
+                __syncwarp();
+            }
+        }
+        if (lane == 0) sel[c] = idx;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ bool in_sorted(const uint32_t* a, uint32_t len, uint32_t x) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t v = a[mid];
+        if (v == x) return true;
+        if (v < x) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+// Add nu to R if it is not there yet.
+__device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
+                                     uint32_t nu) {
+    const uint32_t bit = 1u << (nu & 31);
+    const uint32_t old = atomicOr(&vis[nu >> 5], bit);
+    if (!(old & bit)) {
+        const int pos = atomicAdd(&S.ctrl[C_TAIL], 1);
+        list[pos] = (int32_t)nu;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// warp path
+// ------------------------------------------------------------------------------------------
+// Returns true when the pop must be handed to the block path.
+__device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
+                         uint32_t ybase, int32_t mu, bool count_stats) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t pb = P.prof_off[mu], l = P.prof_off[mu + 1] - pb;
+    Need* need = S.wneed[wid];
+    uint32_t nneed = 0, ndraw = 0;
+    for (int c0 = 0; c0 < l; c0 += 32) {
+        const int i = c0 + lane;
+        uint32_t h = 0, ksel = 0;
+        uint4 e = make_uint4(0, 0, 0, 0);
+        bool drew = false;
+        if (i < l) {
+            e = P.prof[pb + i];
+            WordStream ws;
+            ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
+            drew = layer_draw(e, P.strategy, ws, h, ksel);
+        }
+        const bool flag = h > 0;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
+        const uint32_t pos = nneed + __popc(bal & lanemask_lt());
+        if (flag && pos < kLQ) need[pos] = Need{e.x & ~kPOneFlag, e.y, h, ksel, (uint32_t)(i + 1)};
+        if (flag && count_stats) atomicAdd(&S.stat[S_SEL], (unsigned long long)h);
+        nneed += __popc(bal);
+        ndraw += __popc(__ballot_sync(0xFFFFFFFFu, drew));
+    }
+    __syncwarp();
+    if (count_stats && lane == 0) {
+        atomicAdd(&S.stat[S_POPS], 1ull);
+        atomicAdd(&S.stat[S_LAYERS], (unsigned long long)l);
+        atomicAdd(&S.stat[S_DRAWS], (unsigned long long)ndraw);
+    }
+    if (nneed == 0) return false;
+    const int32_t e0 = P.I.v_off[mu], dh = P.I.v_off[mu + 1] - e0;
+    if (count_stats && lane == 0) {
+        atomicAdd(&S.stat[S_MATS], 1ull);
+        atomicAdd(&S.stat[S_MAT_HE], (unsigned long long)dh);
+        atomicAdd(&S.stat[S_MAT_MEM], (unsigned long long)P.tsum[mu]);
+    }
+    if (nneed > kLQ) return true;
+    // picks for every needed layer (none when h = n)
+    uint32_t total_picks = 0;
+    for (uint32_t q = 0; q < nneed; ++q) {
+        const Need nd = need[q];
+        if (nd.h < nd.n) total_picks += nd.h;
+        if (total_picks > kPCap) return true;
+    }
+    const int T = P.tsum[mu] - dh;
+    if (dh != 1 && T > kWCap) return true;
+    uint32_t* picks = S.wpick[wid];
+    uint32_t* poff = S.wpoff[wid];
+    uint32_t acc = 0;
+    for (uint32_t q = 0; q < nneed; ++q) {
+        const Need nd = need[q];
+        if (lane == 0) poff[q] = acc;
+        if (nd.h < nd.n) {
+            if ((uint64_t)nd.ksel + nd.h > (1ull << 18)) {
+                if (lane == 0) dev_fail(P.st, kErrWords, mu);
+                return false;
+            }
+            WordStream ws;
+            ws.init(P.seed, j, ybase, (uint32_t)mu, nd.layer);
+            gen_picks(ws, nd.n, nd.h, nd.ksel, picks + acc);
+            acc += nd.h;
+        }
+    }
+    if (lane == 0) poff[nneed] = acc;
+    __syncwarp();
+    if (dh == 1) {
+        // A(mu) = the single hyperedge minus mu, sorted: position x maps to member x or x + 1
+        const int32_t he = P.I.v_he[e0];
+        const int32_t hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
+        // position of mu
+        int pmu = 0;
+        for (int b = 0; b < len; b += 32) {
+            const bool lt = b + lane < len && (uint32_t)P.I.he_mem[hb + b + lane] < (uint32_t)mu;
+            pmu += __popc(__ballot_sync(0xFFFFFFFFu, lt));
+        }
+        const Need nd = need[0];
+        if (nd.h >= nd.n) {
+            for (int x = lane; x < len - 1; x += 32)
+                push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+        } else {
+            for (uint32_t r = lane; r < nd.h; r += 32) {
+                const uint32_t x = picks[r];
+                push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+            }
+        }
+        __syncwarp();
+        return false;
+    }
+    // materialise A(mu) in shared memory, sorted by id
+    uint32_t* buf = S.wbuf[wid];
+    const int got = gather_nbhd<32>(P.I, mu, buf, &S.wcursor[wid]);
+    group_sort<32>(buf, got);
+    // walk runs; rank members of each needed layer in id order
+    int* cnt = S.wcnt[wid];
+    for (uint32_t q = lane; q < nneed; q += 32) cnt[q] = 0;
+    __syncwarp();
+    uint32_t done_mask = 0, want_mask = (nneed >= 32 ? 0xFFFFFFFFu : ((1u << nneed) - 1));
+    for (int base = 0; base < got; base += 32) {
+        const int p = base + lane;
+        bool start = false;
+        uint32_t x = kSentinel;
+        int mult = 0;
+        if (p < got) {
+            x = buf[p];
+            start = (p == 0) || (buf[p - 1] != x);
+            if (start) {
+                mult = 1;
+                while (p + mult < got && buf[p + mult] == x) ++mult;
+            }
+        }
+        for (uint32_t q = 0; q < nneed; ++q) {
+            const Need nd = need[q];
+            const bool f = start && (uint32_t)mult == nd.w;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
+            const uint32_t before = (uint32_t)cnt[q];
+            if (f) {
+                const uint32_t rank = before + __popc(bal & lanemask_lt());
+                const bool take = nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank);
+                if (take) push(P, S, vis, list, x);
+            }
+            const uint32_t after = before + __popc(bal);
+            __syncwarp();
+            if (lane == 0) cnt[q] = (int)after;
+            __syncwarp();
+            if (nd.h < nd.n && after > picks[poff[q] + nd.h - 1]) done_mask |= 1u << q;
+        }
+        if ((done_mask & want_mask) == want_mask) break;
+    }
+    __syncwarp();
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// block path (all threads of the block)
+// ------------------------------------------------------------------------------------------
+__device__ void rank_chunk_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
+                                 bool start, uint32_t x, int mult, uint32_t nq,
+                                 const uint32_t* picks) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int q = -1;
+    if (start)
+        for (uint32_t t = 0; t < nq; ++t)
+            if (S.bneed[t].w == (uint32_t)mult) { q = (int)t; break; }
+    const uint32_t mask = __match_any_sync(0xFFFFFFFFu, q);
+    const int rin = __popc(mask & lanemask_lt());
+    for (uint32_t t = lane; t < nq; t += 32) S.wcnt[wid][t] = 0;
+    __syncwarp();
+    if (q >= 0 && rin == 0) S.wcnt[wid][q] = __popc(mask);
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < nq; t += kThreads) {
+        int run = S.lcnt[t];
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = S.wcnt[w][t];
+            S.wcnt[w][t] = run;
+            run += c;
+        }
+        S.lcnt[t] = run;
+    }
+    __syncthreads();
+    if (q >= 0) {
+        const Need nd = S.bneed[q];
+        const uint32_t rank = (uint32_t)(S.wcnt[wid][q] + rin);
+        const bool take = nd.h >= nd.n || in_sorted(picks + S.bpick_off[q], nd.h, rank);
+        if (take) push(P, S, vis, list, x);
+    }
+    __syncthreads();
+}
+
+// true when every needed layer with a strict subset of picks has ranked past its largest pick
+__device__ __forceinline__ bool block_done(const Shared& S, uint32_t nq, const uint32_t* picks) {
+    for (uint32_t t = 0; t < nq; ++t) {
+        const Need nd = S.bneed[t];
+        if (nd.h >= nd.n) return false;
+        if ((uint32_t)S.lcnt[t] <= picks[S.bpick_off[t] + nd.h - 1]) return false;
+    }
+    return true;
+}
+
+__device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
+                          uint32_t ybase, int32_t mu, uint32_t* picks_g, uint32_t* big) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t pb = P.prof_off[mu], l = P.prof_off[mu + 1] - pb;
+    const int32_t e0 = P.I.v_off[mu], dh = P.I.v_off[mu + 1] - e0;
+    // needed layers are processed kBLQ at a time; draws are recomputed per round
+    for (uint32_t round_lo = 0;; round_lo += kBLQ) {
+        if (wid == 0) {
+            uint32_t nneed = 0;
+            for (int c0 = 0; c0 < l; c0 += 32) {
+                const int i = c0 + lane;
+                uint32_t h = 0, ksel = 0;
+                uint4 e = make_uint4(0, 0, 0, 0);
+                if (i < l) {
+                    e = P.prof[pb + i];
+                    WordStream ws;
+                    ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
+                    layer_draw(e, P.strategy, ws, h, ksel);
+                }
+                const bool flag = h > 0;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
+                const uint32_t pos = nneed + __popc(bal & lanemask_lt());
+                if (flag && pos >= round_lo && pos < round_lo + kBLQ)
+                    S.bneed[pos - round_lo] = Need{e.x & ~kPOneFlag, e.y, h, ksel, (uint32_t)(i + 1)};
+                nneed += __popc(bal);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t nq = nneed > round_lo ? min(nneed - round_lo, (uint32_t)kBLQ) : 0u;
+                S.ctrl[C_NNEED] = (int)nq;
+                S.ctrl[C_STOP] = nneed > round_lo + kBLQ ? 0 : 1;
+                uint32_t acc = 0;
+                for (uint32_t q = 0; q < nq; ++q) {
+                    S.bpick_off[q] = acc;
+                    if (S.bneed[q].h < S.bneed[q].n) acc += S.bneed[q].h;
+                    S.lcnt[q] = 0;
+                }
+                S.bpick_off[nq] = acc;
+                S.ctrl[C_OK] = (int64_t)acc <= P.pick_cap ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        const uint32_t nq = (uint32_t)S.ctrl[C_NNEED];
+        const bool last_round = S.ctrl[C_STOP] != 0;
+        if (!S.ctrl[C_OK]) {
+            if (threadIdx.x == 0) dev_fail(P.st, kErrCapacity, mu);
+            __syncthreads();
+            return;
+        }
+        if (nq > 0) {
+            // picks: warp q % kWarps generates layer q
+            for (uint32_t q = wid; q < nq; q += kWarps) {
+                const Need nd = S.bneed[q];
+                if (nd.h < nd.n) {
+                    if ((uint64_t)nd.ksel + nd.h > (1ull << 18)) {
+                        if (lane == 0) dev_fail(P.st, kErrWords, mu);
+                        continue;
+                    }
+                    WordStream ws;
+                    ws.init(P.seed, j, ybase, (uint32_t)mu, nd.layer);
+                    gen_picks(ws, nd.n, nd.h, nd.ksel, picks_g + S.bpick_off[q]);
+                }
+            }
+            __threadfence_block();
+            __syncthreads();
+            if (dh == 1) {
+                const int32_t he = P.I.v_he[e0];
+                const int32_t hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
+                if (threadIdx.x == 0) S.ctrl[C_CURSOR] = 0;
+                __syncthreads();
+                for (int b = threadIdx.x; b < len; b += kThreads)
+                    if ((uint32_t)P.I.he_mem[hb + b] < (uint32_t)mu) atomicAdd(&S.ctrl[C_CURSOR], 1);
+                __syncthreads();
+                const int pmu = S.ctrl[C_CURSOR];
+                const Need nd = S.bneed[0];
+                if (nd.h >= nd.n) {
+                    for (int x = threadIdx.x; x < len - 1; x += kThreads)
+                        push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+                } else {
+                    for (uint32_t r = threadIdx.x; r < nd.h; r += kThreads) {
+                        const uint32_t x = picks_g[r];
+                        push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+                    }
+                }
+                __syncthreads();
+            } else {
+                const int T = P.tsum[mu] - dh;
+                auto consume = [&](bool start, uint32_t x, int mult) -> bool {
+                    rank_chunk_block(P, S, vis, list, start, x, mult, nq, picks_g);
+                    return block_done(S, nq, picks_g);
+                };
+                if (T <= kBCap) {
+                    const int got = gather_nbhd<kThreads>(P.I, mu, S.bbuf, &S.ctrl[C_CURSOR]);
+                    group_sort<kThreads>(S.bbuf, got);
+                    walk_runs<kThreads>(S.bbuf, got, consume);
+                } else if ((int64_t)T > P.big_cap) {
+                    if (threadIdx.x == 0) dev_fail(P.st, kErrCapacity, mu);
+                } else {
+                    // bucket by the top id bits so that every bucket fits on chip
+                    int b = 0;
+                    while (((int64_t)(kBCap / 4) << b) < (int64_t)T && b < P.id_bits &&
+                           (2 << b) <= kBuckets)
+                        ++b;
+                    bool ok = false;
+                    for (;;) {
+                        const int nb = 1 << b, shift = P.id_bits - b;
+                        for (int i = threadIdx.x; i < nb; i += kThreads) S.bucket[i] = 0;
+                        __syncthreads();
+                        for (int e = e0 + wid; e < e0 + dh; e += kWarps) {
+                            const int he = P.I.v_he[e];
+                            const int hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
+                            for (int i = lane; i < len; i += 32) {
+                                const uint32_t x = (uint32_t)P.I.he_mem[hb + i];
+                                if (x != (uint32_t)mu) atomicAdd(&S.bucket[x >> shift], 1);
+                            }
+                        }
+                        __syncthreads();
+                        int mx = 0;
+                        for (int i = threadIdx.x; i < nb; i += kThreads) mx = max(mx, S.bucket[i]);
+                        mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+                        if (lane == 0) S.tmp[wid] = mx;
+                        __syncthreads();
+                        int allmx = 0;
+                        for (int w = 0; w < kWarps; ++w) allmx = max(allmx, S.tmp[w]);
+                        __syncthreads();
+                        if (allmx <= kBCap) { ok = true; break; }
+                        if (b >= P.id_bits || (2 << b) > kBuckets) break;
+                        ++b;
+                    }
+                    if (!ok) {
+                        if (threadIdx.x == 0) dev_fail(P.st, kErrBucket, mu);
+                    } else {
+                        const int nb = 1 << b, shift = P.id_bits - b;
+                        if (wid == 0) {
+                            int carry = 0;
+                            for (int base = 0; base < nb; base += 32) {
+                                const int i = base + lane;
+                                const int v = i < nb ? S.bucket[i] : 0;
+                                int inc = v;
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                                    if (lane >= o) inc += t;
+                                }
+                                if (i < nb) S.bucket[i] = carry + inc - v;
+                                carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+                            }
+                        }
+                        __syncthreads();
+                        for (int e = e0 + wid; e < e0 + dh; e += kWarps) {
+                            const int he = P.I.v_he[e];
+                            const int hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
+                            for (int i = lane; i < len; i += 32) {
+                                const uint32_t x = (uint32_t)P.I.he_mem[hb + i];
+                                if (x != (uint32_t)mu) big[atomicAdd(&S.bucket[x >> shift], 1)] = x;
+                            }
+                        }
+                        __threadfence_block();
+                        __syncthreads();
+                        int begin = 0;
+                        for (int qb = 0; qb < nb; ++qb) {
+                            const int end = S.bucket[qb];
+                            const int cnt = end - begin;
+                            if (cnt > 0) {
+                                for (int i = threadIdx.x; i < cnt; i += kThreads) S.bbuf[i] = big[begin + i];
+                                __syncthreads();
+                                group_sort<kThreads>(S.bbuf, cnt);
+                                const bool stop = walk_runs<kThreads>(S.bbuf, cnt, consume);
+                                __syncthreads();
+                                if (stop) break;
+                            }
+                            begin = end;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        if (last_round) break;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// the kernel
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+    uint32_t* vis = P.vis_smem ? reinterpret_cast<uint32_t*>(smem_raw + sizeof(Shared))
+                               : P.gvis + (int64_t)blockIdx.x * P.vis_words;
+    int32_t* list = P.list + (int64_t)blockIdx.x * P.list_cap;
+    uint32_t* picks_g = P.picks + (int64_t)blockIdx.x * P.pick_cap;
+    uint32_t* big = P.big + (int64_t)blockIdx.x * P.big_cap;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t njobs = P.job_base[HYPERIM_NSTRATA];
+    if (threadIdx.x < 8) S.stat[threadIdx.x] = 0;
+    for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job, 1);
+        __syncthreads();
+        const int64_t job = S.ctrl[C_JOB];
+        if (job >= njobs) break;
+        int s = 0;
+        while (s < HYPERIM_NSTRATA - 1 && job >= P.job_base[s + 1]) ++s;
+        const uint32_t j = P.j_base[s] + (uint32_t)(job - P.job_base[s]);
+        const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)s;
+        const uint32_t ybase = stream_ybase(P.tag, sfield);
+        if (threadIdx.x == 0) {
+            // root: uniform over the stratum (multiply-shift of one word)
+            WordStream ws;
+            ws.init(P.seed, j, ybase, 0xFFFFFFFFu, 0u);
+            const uint32_t w0 = ws.word(0);
+            int32_t root;
+            if (P.root_mode == HYPERIM_ROOTS_PLAIN) {
+                root = (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)P.n) >> 32);
+            } else {
+                const int32_t b = P.vs_off[s], size = P.vs_off[s + 1] - b;
+                root = P.vs_list[b + (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)size) >> 32)];
+            }
+            list[0] = root;
+            vis[root >> 5] |= 1u << (root & 31);
+            S.ctrl[C_HEAD] = 0;
+            S.ctrl[C_TAIL] = 1;
+        }
+        __syncthreads();
+        // level-synchronous reverse BFS
+        while (S.ctrl[C_HEAD] < S.ctrl[C_TAIL]) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.ctrl[C_LEVEL_END] = S.ctrl[C_TAIL];
+                S.ctrl[C_NEXT] = S.ctrl[C_HEAD];
+                S.ctrl[C_NDEF] = 0;
+            }
+            __syncthreads();
+            const int level_end = S.ctrl[C_LEVEL_END];
+            for (;;) {
+                // phase 1: warps pop vertices of this level
+                for (;;) {
+                    int idx = 0;
+                    if (lane == 0)
+                        idx = (*(volatile int*)&S.ctrl[C_NDEF] > kDCap - kWarps)
+                                  ? level_end
+                                  : atomicAdd(&S.ctrl[C_NEXT], 1);
+                    idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+                    if (idx >= level_end) break;
+                    const int32_t mu = list[idx];
+                    const bool defer = pop_warp(P, S, vis, list, j, ybase, mu, true);
+                    if (defer && lane == 0) S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
+                    __syncwarp();
+                }
+                __syncthreads();
+                // phase 2: the block materialises the deferred pops
+                const int ndef = S.ctrl[C_NDEF];
+                for (int d = 0; d < ndef; ++d) pop_block(P, S, vis, list, j, ybase, S.deferred[d], picks_g, big);
+                __syncthreads();
+                if (threadIdx.x == 0) S.ctrl[C_NDEF] = 0;
+                const bool more = S.ctrl[C_NEXT] < level_end;
+                __syncthreads();
+                if (!more) break;
+            }
+            if (threadIdx.x == 0) S.ctrl[C_HEAD] = level_end;
+            __syncthreads();
+        }
+        // output: members in ascending order
+        const int size = S.ctrl[C_TAIL];
+        if (threadIdx.x == 0) {
+            const unsigned long long pos = atomicAdd(P.arena_used, (unsigned long long)size);
+            P.out_pos[job] = (int64_t)pos;
+            P.out_size[job] = size;
+            S.ctrl[C_ROOT] = pos + (unsigned long long)size <= P.arena_cap ? 1 : 0;
+            S.out_pos = pos;
+        }
+        __syncthreads();
+        const bool fits = S.ctrl[C_ROOT] != 0;
+        const unsigned long long pos = S.out_pos;
+        if (size <= kBCap) {
+            for (int i = threadIdx.x; i < size; i += kThreads) S.bbuf[i] = (uint32_t)list[i];
+            __syncthreads();
+            group_sort<kThreads>(S.bbuf, size);
+            if (fits)
+                for (int i = threadIdx.x; i < size; i += kThreads) P.arena[pos + i] = (int32_t)S.bbuf[i];
+            __syncthreads();
+            for (int i = threadIdx.x; i < size; i += kThreads) vis[S.bbuf[i] >> 5] = 0;
+        } else {
+            // R is large: read it off the visited bitmap in id order
+            const int64_t nwords = ((int64_t)P.n + 31) >> 5;
+            int64_t carry = 0;
+            for (int64_t b0 = 0; b0 < nwords; b0 += kThreads) {
+                const int64_t wi = b0 + threadIdx.x;
+                const uint32_t word = wi < nwords ? vis[wi] : 0u;
+                int total;
+                // exclusive sum of popcounts across the block
+                const int c = __popc(word);
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (lane == 31) S.tmp[wid] = incl;
+                __syncthreads();
+                int woff = 0;
+                total = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    woff += w < wid ? S.tmp[w] : 0;
+                    total += S.tmp[w];
+                }
+                __syncthreads();
+                int64_t o = carry + woff + incl - c;
+                uint32_t bits = word;
+                while (bits) {
+                    const int bpos = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (fits) P.arena[pos + o] = (int32_t)(wi * 32 + bpos);
+                    ++o;
+                }
+                carry += total;
+            }
+            __syncthreads();
+            for (int64_t w = threadIdx.x; w < nwords; w += kThreads) vis[w] = 0;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&P.counters->pops, S.stat[S_POPS]);
+        atomicAdd(&P.counters->layers_seen, S.stat[S_LAYERS]);
+        atomicAdd(&P.counters->draws, S.stat[S_DRAWS]);
+        atomicAdd(&P.counters->mats, S.stat[S_MATS]);
+        atomicAdd(&P.counters->mat_he, S.stat[S_MAT_HE]);
+        atomicAdd(&P.counters->mat_members, S.stat[S_MAT_MEM]);
+        atomicAdd(&P.counters->selected, S.stat[S_SEL]);
+    }
+}
+
+}  // namespace
+}  // namespace hyperim
+
+namespace hyperim {
+namespace {
+
+// Copy each RR set of the batch from the arena to its CSR slot; record stratum and index.
+__global__ void k_compact_rr(const int32_t* __restrict__ arena, const int64_t* __restrict__ out_pos,
+                             const int64_t* __restrict__ boff, int64_t njobs, int64_t base_count,
+                             int64_t base_total, RRJobMap jm, int64_t* __restrict__ rr_off,
+                             int32_t* __restrict__ rr_mem, uint8_t* __restrict__ rr_stratum,
+                             uint32_t* __restrict__ rr_j) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < njobs; r += nwarps) {
+        const int64_t src = out_pos[r], dst = base_total + boff[r], len = boff[r + 1] - boff[r];
+        for (int64_t i = lane; i < len; i += 32) rr_mem[dst + i] = arena[src + i];
+        if (lane == 0) {
+            int s = 0;
+            while (s < HYPERIM_NSTRATA - 1 && r >= jm.job_base[s + 1]) ++s;
+            rr_off[base_count + r] = dst;
+            rr_stratum[base_count + r] = (uint8_t)s;
+            rr_j[base_count + r] = jm.j_base[s] + (uint32_t)(r - jm.job_base[s]);
+            if (r == njobs - 1) rr_off[base_count + njobs] = base_total + boff[njobs];
+        }
+    }
+}
+
+template <typename T>
+hyperim_status grow_array(hyperim_graph* g, T** arr, size_t used, size_t* cap, size_t need) {
+    if (need <= *cap) return HYPERIM_OK;
+    size_t nc = *cap ? *cap : 1024;
+    while (nc < need) nc *= 2;
+    T* na = nullptr;
+    hyperim_status st = dev_alloc(g, (void**)&na, sizeof(T) * nc);
+    if (st != HYPERIM_OK) return st;
+    if (used) HYP_CUDA(cudaMemcpyAsync(na, *arr, sizeof(T) * used, cudaMemcpyDeviceToDevice, g->stream));
+    if (*arr) dev_free(g, *arr, sizeof(T) * *cap);
+    *arr = na;
+    *cap = nc;
+    return HYPERIM_OK;
+}
+
+hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
+    Scratch& S = g->scratch;
+    const size_t list_cap = (size_t)g->n;
+    const size_t vis_words = vis_smem ? 0 : ((size_t)g->n + 31) / 32;
+    const size_t pick_cap = (size_t)std::max<int64_t>(g->max_deg, 1);  // picks of one pop
+    const size_t big_cap = (size_t)std::max<int64_t>(g->max_tsum, 1);
+    if (S.blocks >= blocks && S.list_cap >= list_cap && S.bitmap_words >= vis_words &&
+        S.pick_cap >= pick_cap && S.big_cap >= big_cap)
+        return HYPERIM_OK;
+    if (S.list) dev_free(g, S.list, sizeof(int32_t) * S.list_cap * S.blocks);
+    if (S.bitmap) dev_free(g, S.bitmap, sizeof(uint32_t) * S.bitmap_words * S.blocks);
+    if (S.picks) dev_free(g, S.picks, sizeof(uint32_t) * S.pick_cap * S.blocks);
+    if (S.big) dev_free(g, S.big, sizeof(uint32_t) * S.big_cap * S.blocks);
+    S = Scratch{0, 0, 0, 0, 0, nullptr, nullptr, nullptr, nullptr, S.arena, S.arena_cap};
+    hyperim_status st;
+    if ((st = dev_alloc(g, (void**)&S.list, sizeof(int32_t) * list_cap * blocks))) return st;
+    if (vis_words) {
+        if ((st = dev_alloc(g, (void**)&S.bitmap, sizeof(uint32_t) * vis_words * blocks))) return st;
+        HYP_CUDA(cudaMemsetAsync(S.bitmap, 0, sizeof(uint32_t) * vis_words * blocks, g->stream));
+    }
+    if ((st = dev_alloc(g, (void**)&S.picks, sizeof(uint32_t) * pick_cap * blocks))) return st;
+    if ((st = dev_alloc(g, (void**)&S.big, sizeof(uint32_t) * big_cap * blocks))) return st;
+    S.blocks = blocks;
+    S.list_cap = list_cap;
+    S.bitmap_words = vis_words;
+    S.pick_cap = pick_cap;
+    S.big_cap = big_cap;
+    return HYPERIM_OK;
+}
+
+}  // namespace
+
+hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]) {
+    RRJobMap jm;
+    jm.job_base[0] = 0;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+        const uint64_t old = p->n_s[s];
+        const uint64_t add = new_ns[s] > old ? new_ns[s] - old : 0;
+        if (new_ns[s] > 0xFFFFFFFFull)
+            return set_error(HYPERIM_EOVERFLOW, "an RR index within a stratum would reach 2^32");
+        jm.j_base[s] = (uint32_t)old;
+        jm.job_base[s + 1] = jm.job_base[s] + (int64_t)add;
+    }
+    const int64_t njobs = jm.job_base[HYPERIM_NSTRATA];
+    if (njobs == 0) return HYPERIM_OK;
+    cudaStream_t s = g->stream;
+    hyperim_status st;
+
+    const bool vis_smem = (int64_t)g->n <= kVisSmemBits;
+    const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
+    const size_t smem = sizeof(Shared) + vis_bytes;
+    HYP_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr, kThreads, smem));
+    if (per_sm < 1) return set_error(HYPERIM_ECUDA, "RR kernel does not fit on an SM");
+    int blocks = g->sm_count * per_sm;
+    if ((int64_t)blocks > njobs) blocks = (int)njobs;
+    if ((st = ensure_scratch(g, blocks, vis_smem))) return st;
+
+    // output arena sized from the pool's running mean set size, grown and relaunched on overflow
+    double hint = p->mean_size_hint > 0 ? p->mean_size_hint : 8.0;
+    uint64_t want = (uint64_t)((double)njobs * hint * 1.25) + 4096;
+    int64_t* d_pos = nullptr;
+    int32_t* d_size = nullptr;
+    int* d_next = nullptr;
+    unsigned long long* d_used = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_pos, sizeof(int64_t) * (size_t)njobs))) return st;
+    if ((st = dev_alloc(g, (void**)&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
+    if ((st = dev_alloc(g, (void**)&d_next, sizeof(int) + sizeof(unsigned long long) * 2))) return st;
+    d_used = reinterpret_cast<unsigned long long*>(d_next + 2);
+    RRParams P;
+    P.I = Incidence{g->he_off, g->he_mem, g->v_off, g->v_he};
+    P.prof_off = g->prof_off;
+    P.prof = g->prof;
+    P.tsum = g->tsum;
+    P.vs_off = g->vs_off;
+    P.vs_list = g->vs_list;
+    P.n = g->n;
+    P.id_bits = g->id_bits;
+    P.seed = g->seed;
+    P.tag = p->tag;
+    P.root_mode = p->root_mode;
+    P.strategy = p->strategy;
+    for (int i = 0; i <= HYPERIM_NSTRATA; ++i) P.job_base[i] = jm.job_base[i];
+    for (int i = 0; i < HYPERIM_NSTRATA; ++i) P.j_base[i] = jm.j_base[i];
+    P.list = g->scratch.list;
+    P.list_cap = (int64_t)g->scratch.list_cap;
+    P.gvis = g->scratch.bitmap;
+    P.vis_smem = vis_smem ? 1 : 0;
+    P.vis_words = vis_smem ? (int64_t)(((size_t)g->n + 31) / 32) : (int64_t)g->scratch.bitmap_words;
+    P.picks = g->scratch.picks;
+    P.pick_cap = (int64_t)g->scratch.pick_cap;
+    P.big = g->scratch.big;
+    P.big_cap = (int64_t)g->scratch.big_cap;
+    P.out_pos = d_pos;
+    P.out_size = d_size;
+    P.next_job = d_next;
+    P.arena_used = d_used;
+    P.st = g->d_status;
+    P.counters = g->d_counters;
+    unsigned long long used = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if (g->scratch.arena_cap < want) {
+            if (g->scratch.arena) dev_free(g, g->scratch.arena, sizeof(int32_t) * g->scratch.arena_cap);
+            g->scratch.arena = nullptr;
+            g->scratch.arena_cap = 0;
+            if ((st = dev_alloc(g, (void**)&g->scratch.arena, sizeof(int32_t) * want))) return st;
+            g->scratch.arena_cap = want;
+        }
+        P.arena = g->scratch.arena;
+        P.arena_cap = g->scratch.arena_cap;
+        HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int) + sizeof(unsigned long long) * 2, s));
+        HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters), s));
+        k_rr<<<blocks, kThreads, smem, s>>>(P);
+        HYP_CUDA(cudaGetLastError());
+        HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
+        if ((st = check_device_status(g, "RR generation"))) return st;
+        if (used <= g->scratch.arena_cap) break;
+        want = used + used / 8 + 4096;
+    }
+    if (used > g->scratch.arena_cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
+    RRCounters c;
+    HYP_CUDA(cudaMemcpyAsync(&c, g->d_counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+    // compaction: CSR offsets by an exclusive scan of the sizes
+    int64_t* d_boff = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
+    if ((st = exclusive_scan_u32_to_i64(g, reinterpret_cast<const uint32_t*>(d_size), d_boff, njobs)))
+        return st;
+    int64_t btotal = 0;
+    HYP_CUDA(cudaMemcpyAsync(&btotal, d_boff + njobs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    const size_t new_count = (size_t)(p->count + njobs), new_total = (size_t)(p->total + btotal);
+    if ((st = grow_array(g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
+        return st;
+    if ((st = grow_array(g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
+    if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
+    if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
+    const int grid = (int)std::min<int64_t>((njobs * 32 + 255) / 256, (int64_t)g->sm_count * 32);
+    k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos, d_boff, njobs, p->count, p->total, jm,
+                                      p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j);
+    HYP_CUDA(cudaGetLastError());
+    dev_free(g, d_boff, sizeof(int64_t) * ((size_t)njobs + 1));
+    dev_free(g, d_pos, sizeof(int64_t) * (size_t)njobs);
+    dev_free(g, d_size, sizeof(int32_t) * (size_t)njobs);
+    dev_free(g, d_next, sizeof(int) + sizeof(unsigned long long) * 2);
+    for (int i = 0; i < HYPERIM_NSTRATA; ++i)
+        if (new_ns[i] > p->n_s[i]) p->n_s[i] = new_ns[i];
+    p->count = (int64_t)new_count;
+    p->total = (int64_t)new_total;
+    p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
+    p->counters.pops += c.pops;
+    p->counters.layers_seen += c.layers_seen;
+    p->counters.draws += c.draws;
+    p->counters.mats += c.mats;
+    p->counters.mat_he += c.mat_he;
+    p->counters.mat_members += c.mat_members;
+    p->counters.selected += c.selected;
+    return check_device_status(g, "RR compaction");
+}
+
+}  // namespace hyperim

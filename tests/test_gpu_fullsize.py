@@ -1,0 +1,97 @@
+"""GPU parity at the benchmark workloads' full sizes, in the benchmark's launch configuration.
+
+* 1,000 vertices / 500 hyperedges, p = 0.05, fixed theta = 10,000, plain roots, k = 10: every RR
+  set, the seed set and the coverage against the oracle.
+* 100,000 vertices / 50,000 Zipf(2.1) hyperedges, p = 0.01, stratified roots: the layer profile
+  of every vertex, the first BRR round's pools (theta_0 = 49 per pool) set by set, and greedy on
+  them (the oracle spends ~0.15 s per RR set here: the sets hold a third of the graph).
+* 2,000,000 vertices / 1,000,000 Zipf(1.9) hyperedges, weighted cascade, stratified roots: the
+  profile of a sample of vertices and the theta_0 = 75 RR sets of the first BRR round.
+"""
+import numpy as np
+import pytest
+
+from tests import gpu_cases as gc
+from workloads import make_hypergraph, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_01911_gb300 import build
+    build.build()
+    import paper_2406_01911_gb300 as H
+    return H
+
+
+def _both(H, oracle, name):
+    w = workload(name)
+    off, mem = make_hypergraph(w.graph)
+    q = w.query
+    g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=q.seed)
+    og = oracle.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold)
+    return w, g, og
+
+
+def _profile_sample(g, og, verts):
+    prof = g.profile()
+    for v in verts:
+        v = int(v)
+        assert prof["deg"][v] == og.deg(v) and prof["nlayers"][v] == og.nlayers(v)
+        b = prof["prof_off"][v]
+        lay = og.layers(v)
+        got = list(zip(prof["layer_w"][b:b + len(lay)].tolist(), prof["layer_n"][b:b + len(lay)].tolist(),
+                       prof["layer_thr"][b:b + len(lay)].tolist()))
+        assert got == lay, v
+    assert g.stats()["stratum_size"] == [og.stratum_size(s) for s in range(16)]
+
+
+def test_tiny_fixed_theta(H, oracle):
+    w, g, og = _both(H, oracle, "tiny-1k-u2to6-p005")
+    q = w.query
+    _profile_sample(g, og, range(w.graph.n))
+    p = g.pool(tag=0, roots=q.roots).sample(q.theta)
+    op = oracle.Pool(og, seed=q.seed, tag=0, roots=q.roots)
+    op.grow_theta(q.theta)
+    gc.assert_same_pool(p, op)
+    gc.assert_same_counters(p, op)
+    seeds, res = g.select_seeds(p, None, q.k, mode="fixed")
+    oseeds, olam, _ = op.greedy(q.k)
+    assert seeds.tolist() == oseeds.tolist()
+    assert res["lambda_r1"].tolist() == olam.tolist()
+
+
+def test_zipf_100k_first_round(H, oracle):
+    w, g, og = _both(H, oracle, "zipf-100k-50k-p001")
+    q = w.query
+    _profile_sample(g, og, range(w.graph.n))
+    plan = g.plan_theta(q.k, q.eps, q.ell)
+    assert plan == pytest.approx(oracle.plan_theta(w.graph.n, q.k, q.eps, q.ell), rel=1e-12)
+    for tag in (0, 1):
+        p = g.pool(tag=tag, roots=q.roots).sample(plan["theta0"])
+        op = oracle.Pool(og, seed=q.seed, tag=tag, roots=q.roots)
+        op.grow_theta(plan["theta0"])
+        gc.assert_same_pool(p, op)
+        gc.assert_same_counters(p, op)
+        if tag == 0:
+            seeds, res = g.select_seeds(p, None, q.k, mode="fixed")
+            oseeds, olam, _ = op.greedy(q.k)
+            assert seeds.tolist() == oseeds.tolist()
+            assert res["lambda_r1"].tolist() == olam.tolist()
+
+
+def test_zipf_2m_first_round(H, oracle):
+    w, g, og = _both(H, oracle, "zipf-2m-1m-wc")
+    q = w.query
+    rng = np.random.default_rng(0)
+    _profile_sample(g, og, rng.integers(0, w.graph.n, size=3000))
+    plan = g.plan_theta(q.k, q.eps, q.ell)
+    p = g.pool(tag=0, roots=q.roots).sample(plan["theta0"])
+    op = oracle.Pool(og, seed=q.seed, tag=0, roots=q.roots)
+    op.grow_theta(plan["theta0"])
+    gc.assert_same_pool(p, op)
+    gc.assert_same_counters(p, op)
