@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of HyperIM's hot path on GB300.
+
+One step = one whole influence-maximisation query through the C ABI: load the hypergraph
+(incidence store + layer profile), plan theta, then HyperIM_BRR (grow the R1/R2 RR pools round
+by round, greedy max coverage on R1, coverage on R2, bounds) until the stop test passes -- or, for
+workloads with a fixed theta, one pool of theta RR sets and greedy. The metric is RR sets
+generated per second over the whole job; seed-selection seconds are reported beside it.
+
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the stream
+the library launches on; L2 is flushed (256 MiB write) before every step, outside the events.
+The inputs (CSR) are resident in HBM before the timed region; the e2e figure repeats the steps
+from pinned host buffers (host->device copy inside the timed call, seeds copied back).
+
+With torchrun (N > 1) every rank runs its own query (its own seed) on its GPU: the queries are
+independent problems, so there is no collective on the data path (weak scaling); rank 0 prints.
+``--impl reference`` times the CPU oracle (single core) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import make_hypergraph, workload  # noqa: E402
+
+DEFAULT_WORKLOAD = "zipf-100k-50k-p001"
+METRIC = "RR sets/sec + seed-selection seconds at fixed eps vs plain GPU form; % HBM roofline"
+UNIT = "RR sets/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def rr_algorithmic_bytes(v):
+    """Bytes the RR generator must move, from its work counters (layout of the incidence store):
+    per pop the profile offsets (8) and 16-byte layer entries; per materialising pop the v->he
+    offsets (8), 4 + 8 bytes per hyperedge (id, offsets) and 4 per member read, plus tsum (4);
+    per RR set the root (4); per member of R its queue write and read and its output write (12)."""
+    return (8 * v["pops"] + 16 * v["layers_seen"] + 12 * v["mats"] + 12 * v["mat_he"]
+            + 4 * v["mat_members"] + 12 * v["total"] + 4 * v["count"])
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("rr.cu", "mat.cuh", "device_math.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2406_01911_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(name):
+    """Per-launch DRAM bytes of the RR kernel from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_rr_{name}.json")
+    try:
+        d = json.load(open(path))
+    except OSError:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        else:
+            self.lines = []
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_query(H, torch, w, off, mem, seed, host_inputs=False):
+    """One whole IM query through the C ABI; returns counters of the work done."""
+    q = w.query
+    g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=seed)
+    r1 = g.pool(tag=0, roots=q.roots)
+    r2 = g.pool(tag=1, roots=q.roots)
+    if q.theta is not None:
+        r1.sample(q.theta)
+        seeds, res = g.select_seeds(r1, None, q.k, mode="fixed")
+    else:
+        seeds, res = g.select_seeds(r1, r2, q.k, mode="brr", eps=q.eps, ell=q.ell)
+    v1, v2 = r1.view(), r2.view()
+    out = {"rr_sets": v1["count"] + v2["count"], "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
+           "rr_launches": v1["rr_launches"] + v2["rr_launches"],
+           "bytes": rr_algorithmic_bytes(v1) + rr_algorithmic_bytes(v2),
+           "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
+           "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
+           "seeds": seeds}
+    r1.close()
+    r2.close()
+    g.close()
+    return out
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2406_01911_gb300 as H
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2406_01911_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+        build.build()
+
+    w = workload(args.workload)
+    off, mem = make_hypergraph(w.graph)
+    d_off = torch.as_tensor(off).cuda()
+    d_mem = torch.as_tensor(mem).cuda()
+    p_off = torch.as_tensor(off).pin_memory()
+    p_mem = torch.as_tensor(mem).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    seed = w.query.seed + 1000 * rank
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        run_query(H, torch, w, d_off, d_mem, seed)
+    stream = torch.cuda.current_stream()
+    times, stats = [], []
+    launches0 = H.hyperim_kernel_launches()
+    sync_all()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats.append(run_query(H, torch, w, d_off, d_mem, seed))
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        sync_all()
+        t_wall = time.perf_counter() - t_wall
+    launches = H.hyperim_kernel_launches() - launches0
+    # end to end from pinned host buffers
+    e2e_times = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = run_query(H, torch, w, p_off, p_mem, seed)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    rr_local = sum(s["rr_sets"] for s in stats)
+    t_local = sum(times)
+    e2e_local = sum(e2e_times)
+    vals = torch.tensor([t_local, e2e_local, float(rr_local)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = vals[:2].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tot = vals[2:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        t_all, e2e_all, rr_all = float(tmax[0]), float(tmax[1]), float(tot[0])
+    else:
+        t_all, e2e_all, rr_all = t_local, e2e_local, float(rr_local)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    kbytes = sum(s["bytes"] for s in stats)
+    ksec = sum(s["rr_kernel_seconds"] for s in stats)
+    klaunch = sum(s["rr_launches"] for s in stats)
+    achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
+    traffic = traffic_for(args.workload)
+    line = {
+        "metric": METRIC,
+        "value": rr_all / t_all,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "n": w.graph.n, "m": w.graph.m,
+                   "k": w.query.k, "eps": w.query.eps, "ell": w.query.ell, "roots": w.query.roots,
+                   "theta": w.query.theta or "adaptive (HyperIM_BRR)",
+                   "rr_sets_per_step": rr_local / args.steps,
+                   "brr_rounds": stats[-1]["rounds"], "theta_final": stats[-1]["theta"],
+                   "parallelism": f"replicas x{world} (independent queries)",
+                   "l2": "flushed between steps (256 MiB write), inputs resident in HBM"},
+        "seed_selection_seconds": sum(s["select_seconds"] for s in stats) / args.steps,
+        "rr_sampling_seconds": sum(s["sample_seconds"] for s in stats) / args.steps,
+        "wall_seconds_timed_region": t_wall,
+        "e2e": {"value": rr_all / e2e_all, "unit": UNIT,
+                "h2d_bytes_per_step": int(off.nbytes + mem.nbytes),
+                "d2h_bytes_per_step": int(4 * w.query.k)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_rr (RR generation)", "achieved": achieved,
+                     "peak": hbm, "peak_source": peak_note, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": kbytes / max(klaunch, 1),
+                     "launches": klaunch, "kernel_seconds": ksec},
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, off, mem, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_rate(w, off, mem, seconds, seed, tag=0):
+    """RR sets per second of the CPU oracle on the same graph: grows a pool of the workload's root
+    mode set by set until `seconds` have passed (graph build excluded)."""
+    import oracle as O
+    q = w.query
+    og = O.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold)
+    pool = O.Pool(og, seed=seed, tag=tag, roots=q.roots)
+    t0 = time.perf_counter()
+    theta = 1
+    while True:
+        pool.grow_theta(theta)
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+        theta += max(1, pool.count() // 8)
+    return pool.count(), el
+
+
+def cpu_baseline(w, off, mem, seconds):
+    count, el = oracle_rate(w, off, mem, seconds, w.query.seed)
+    return {"value": count / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {count} RR sets of pool tag 0 ({w.query.roots} roots) on the same "
+                      f"graph, {el:.1f} s of single-threaded oracle work; graph build excluded"}
+
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    off, mem = make_hypergraph(w.graph)
+    per_step = args.reference_seconds
+    for i in range(args.warmup):
+        oracle_rate(w, off, mem, per_step / 4, w.query.seed + 7 + i, tag=3)
+    counts, times = [], []
+    for i in range(args.steps):
+        c, el = oracle_rate(w, off, mem, per_step, w.query.seed + 100 + i)
+        counts.append(c)
+        times.append(el)
+    value = sum(counts) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "n": w.graph.n, "m": w.graph.m,
+                   "k": w.query.k, "eps": w.query.eps, "roots": w.query.roots},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of ~{per_step:.0f} s each: RR sets of "
+                                   f"fresh pools ({w.query.roots} roots) on the same graph, "
+                                   "graph build excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

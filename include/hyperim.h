@@ -177,8 +177,12 @@ typedef struct {
     uint64_t n_s[HYPERIM_NSTRATA];         /* sets per stratum */
     uint32_t pool_tag;
     int32_t root_mode, strategy;
-    /* work counters of all generation launches so far (see hyperim_rr_stats) */
+    /* work counters of all generation launches so far: vertices popped, profile entries read,
+       layer draws with 0 < p < 1, pops that materialised A(mu), hyperedges and members read by
+       those materialisations, activations drawn (sum of h) */
     uint64_t pops, layers_seen, draws, mats, mat_he, mat_members, selected;
+    uint64_t rr_launches;     /* RR-generation kernel launches */
+    double rr_kernel_seconds; /* their summed duration, CUDA events on the graph's stream */
 } hyperim_pool_view_t;
 
 hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out);
@@ -241,6 +245,9 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
  * ------------------------------------------------------------------------------------------ */
 hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k,
                               hyperim_pool_t pool, double* sigma_hat, double* std_err);
+
+/* Number of CUDA kernels this library has launched in this process (all threads, all graphs). */
+uint64_t hyperim_kernel_launches(void);
 
 /* Thread-local message describing the last non-OK status returned on this thread. */
 const char* hyperim_last_error(void);

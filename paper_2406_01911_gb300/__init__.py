@@ -62,7 +62,8 @@ class PoolView(C.Structure):
                 ("n_s", C.c_uint64 * NSTRATA), ("pool_tag", C.c_uint32), ("root_mode", C.c_int32),
                 ("strategy", C.c_int32), ("pops", C.c_uint64), ("layers_seen", C.c_uint64),
                 ("draws", C.c_uint64), ("mats", C.c_uint64), ("mat_he", C.c_uint64),
-                ("mat_members", C.c_uint64), ("selected", C.c_uint64)]
+                ("mat_members", C.c_uint64), ("selected", C.c_uint64),
+                ("rr_launches", C.c_uint64), ("rr_kernel_seconds", C.c_double)]
 
 
 class SelectOpts(C.Structure):
@@ -96,6 +97,7 @@ _SIGNATURES = {
                                        C.POINTER(SelectResult)]),
     "hyperim_spread": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
+    "hyperim_kernel_launches": (C.c_uint64, []),
     "hyperim_last_error": (C.c_char_p, []),
 }
 
@@ -162,6 +164,10 @@ def hyperim_load(n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, s
     h = C.c_void_p()
     _check(lib().hyperim_load(C.byref(args), C.byref(h)))
     return h
+
+
+def hyperim_kernel_launches():
+    return int(lib().hyperim_kernel_launches())
 
 
 def hyperim_graph_free(h):

@@ -2,6 +2,7 @@
 // the RR budget of Sec. 4.3, root allocation per stratum, the Eq. 1 estimate, and the
 // HyperIM_BRR doubling driver (Algorithm 4). Device work lives in load.cu, rr.cu, greedy.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -14,6 +15,9 @@
 namespace hyperim {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 hyperim_status set_error(hyperim_status st, const std::string& msg) {
     g_last_error = msg;
@@ -160,6 +164,8 @@ using namespace hyperim;
 extern "C" {
 
 const char* hyperim_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t hyperim_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
     if (!a || !out) return set_error(HYPERIM_EINVAL, "null argument");
@@ -360,6 +366,8 @@ hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
     out->mat_he = p->counters.mat_he;
     out->mat_members = p->counters.mat_members;
     out->selected = p->counters.selected;
+    out->rr_launches = p->rr_launches;
+    out->rr_kernel_seconds = p->rr_kernel_seconds;
     return HYPERIM_OK;
 }
 

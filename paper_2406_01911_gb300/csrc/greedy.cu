@@ -207,18 +207,18 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
     HYP_CUDA(cudaMemsetAsync(covered, 0, bytes_cov, s));
     HYP_CUDA(cudaMemsetAsync(lam, 0, sizeof(unsigned long long) * HYPERIM_NSTRATA, s));
     HYP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(uint32_t) * 2, s));
-    if (T > 0) k_count_occ<<<grid_cap(T, 256, sm, 32), 256, 0, s>>>(p->rr_mem, T, cnt);
+    if (T > 0) { k_count_occ<<<grid_cap(T, 256, sm, 32), 256, 0, s>>>(p->rr_mem, T, cnt); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, cnt, inv_off, n))) return st;
     HYP_CUDA(cudaMemsetAsync(cnt, 0, bytes_cnt, s));
     if (N > 0)
-        k_scatter_inv<<<grid_cap(N * 32, 256, sm, 32), 256, 0, s>>>(p->rr_off, p->rr_mem, p->rr_stratum,
-                                                                    N, inv_off, cnt, inv, score, W);
+        { k_scatter_inv<<<grid_cap(N * 32, 256, sm, 32), 256, 0, s>>>(p->rr_off, p->rr_mem, p->rr_stratum,
+                                                                    N, inv_off, cnt, inv, score, W); count_launch(); }
     const int rblocks = sm * 8;
     for (int32_t round = 0; round < k; ++round) {
-        k_argmax<<<ablocks, kArgThreads, 0, s>>>(score, picked, n, bscore, bid, ticket, best, seeds_d,
-                                                 round);
-        k_retire<<<rblocks, 256, 0, s>>>(best, inv_off, inv, p->rr_off, p->rr_mem, p->rr_stratum,
-                                         covered, score, lam, W);
+        { k_argmax<<<ablocks, kArgThreads, 0, s>>>(score, picked, n, bscore, bid, ticket, best, seeds_d,
+                                                 round); count_launch(); }
+        { k_retire<<<rblocks, 256, 0, s>>>(best, inv_off, inv, p->rr_off, p->rr_mem, p->rr_stratum,
+                                         covered, score, lam, W); count_launch(); }
     }
     HYP_CUDA(cudaGetLastError());
     unsigned long long hl[HYPERIM_NSTRATA];
@@ -257,11 +257,11 @@ hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_
     HYP_CUDA(cudaMemsetAsync(lam, 0, sizeof(unsigned long long) * HYPERIM_NSTRATA, s));
     if (k > 0) {
         HYP_CUDA(cudaMemcpyAsync(sd, seeds_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
-        k_mark<<<grid_cap(k, 256, g->sm_count, 4), 256, 0, s>>>(sd, k, in_s);
+        { k_mark<<<grid_cap(k, 256, g->sm_count, 4), 256, 0, s>>>(sd, k, in_s); count_launch(); }
     }
     if (N > 0)
-        k_coverage<<<grid_cap(N * 32, 256, g->sm_count, 32), 256, 0, s>>>(p->rr_off, p->rr_mem,
-                                                                          p->rr_stratum, N, in_s, lam);
+        { k_coverage<<<grid_cap(N * 32, 256, g->sm_count, 32), 256, 0, s>>>(p->rr_off, p->rr_mem,
+                                                                          p->rr_stratum, N, in_s, lam); count_launch(); }
     HYP_CUDA(cudaGetLastError());
     unsigned long long hl[HYPERIM_NSTRATA];
     HYP_CUDA(cudaMemcpyAsync(hl, lam, sizeof(hl), cudaMemcpyDeviceToHost, s));

@@ -106,10 +106,15 @@ struct hyperim_pool {
     uint8_t* rr_stratum = nullptr;  // count
     uint32_t* rr_j = nullptr;       // count
     hyperim::RRCounters counters = {};
+    uint64_t rr_launches = 0;
+    double rr_kernel_seconds = 0.0;
     double mean_size_hint = 0.0;
 };
 
 namespace hyperim {
+
+// launch accounting (capi.cu): every kernel launch of the library goes through count_launch()
+void count_launch(uint64_t k = 1);
 
 // error handling (capi.cu)
 hyperim_status set_error(hyperim_status st, const std::string& msg);

@@ -442,7 +442,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     HYP_CUDA(cudaMemcpyAsync(d_off_in, he_off_in, sizeof(int32_t) * ((size_t)m + 1), kind, s));
     if (nnz_in > 0)
         HYP_CUDA(cudaMemcpyAsync(d_mem_in, he_mem_in, sizeof(int32_t) * (size_t)nnz_in, kind, s));
-    if (m > 0) k_check_offsets<<<grid_for(m, 256, sm), 256, 0, s>>>(d_off_in, m, g->d_status);
+    if (m > 0) { k_check_offsets<<<grid_for(m, 256, sm), 256, 0, s>>>(d_off_in, m, g->d_status); count_launch(); }
     if ((st = check_device_status(g, "hyperedge offsets"))) return st;
 
     // --- normalise hyperedges
@@ -453,9 +453,9 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     uint8_t* d_first = nullptr;
     if ((st = dev_alloc(g, (void**)&d_first, nnz_alloc))) return st;
     if (m > 0)
-        k_normalise<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_mem_in, m, n,
+        { k_normalise<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_mem_in, m, n,
                                                                        d_tmp, d_first, d_newsize,
-                                                                       g->d_status);
+                                                                       g->d_status); count_launch(); }
     if ((st = check_device_status(g, "hyperedge members"))) return st;
     if ((st = exclusive_scan_u32_to_i64(g, d_newsize, d_off_new, m))) return st;
     int64_t nnz = 0;
@@ -466,8 +466,8 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&g->he_off, sizeof(int32_t) * ((size_t)m + 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->he_mem, sizeof(int32_t) * nnz_a))) return st;
     if (m > 0)
-        k_compact_he<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_tmp, d_off_new,
-                                                                        m, g->he_off, g->he_mem);
+        { k_compact_he<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_tmp, d_off_new,
+                                                                        m, g->he_off, g->he_mem); count_launch(); }
     else
         HYP_CUDA(cudaMemsetAsync(g->he_off, 0, sizeof(int32_t), s));
 
@@ -481,23 +481,23 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&g->tsum, sizeof(int32_t) * (size_t)n))) return st;
     HYP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
     HYP_CUDA(cudaMemsetAsync(g->tsum, 0, sizeof(int32_t) * (size_t)n, s));
-    if (nnz > 0) k_count_dh<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->he_mem, nnz, d_cnt);
+    if (nnz > 0) { k_count_dh<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->he_mem, nnz, d_cnt); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_cnt, d_voff64, n))) return st;
     HYP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
     if (m > 0)
-        k_scatter_vhe<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(
-            g->he_off, g->he_mem, m, d_voff64, d_cnt, d_tmp, g->tsum);
-    k_sort_vhe<<<grid_for((int64_t)n * 32, 256, sm), 256, 0, s>>>(d_voff64, n, d_tmp, g->v_he,
-                                                                   g->v_off);
+        { k_scatter_vhe<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(
+            g->he_off, g->he_mem, m, d_voff64, d_cnt, d_tmp, g->tsum); count_launch(); }
+    { k_sort_vhe<<<grid_for((int64_t)n * 32, 256, sm), 256, 0, s>>>(d_voff64, n, d_tmp, g->v_he,
+                                                                   g->v_off); count_launch(); }
 
     // --- maxima of d_H and T
     unsigned long long* d_max = nullptr;
     if ((st = dev_alloc(g, (void**)&d_max, sizeof(unsigned long long) * 8))) return st;
     HYP_CUDA(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long) * 8, s));
     int32_t* d_dh = (int32_t*)d_cnt;  // reuse
-    k_vhe_len<<<grid_for(n, 256, sm), 256, 0, s>>>(d_voff64, n, d_dh);
-    k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(d_dh, n, d_max + 3);
-    k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(g->tsum, n, d_max + 4);
+    { k_vhe_len<<<grid_for(n, 256, sm), 256, 0, s>>>(d_voff64, n, d_dh); count_launch(); }
+    { k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(d_dh, n, d_max + 3); count_launch(); }
+    { k_max_i32<<<grid_for(n, 256, sm), 256, 0, s>>>(g->tsum, n, d_max + 4); count_launch(); }
     unsigned long long hmax[8];
     HYP_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
@@ -530,8 +530,8 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks)))
         return st;
     Incidence I{g->he_off, g->he_mem, g->v_off, g->v_he};
-    k_profile<<<pblocks, kProfThreads, prof_smem, s>>>(I, n, g->id_bits, g->tsum, d_pairs, d_nl,
-                                                       d_deg, d_next, PS, g->d_status, d_max);
+    { k_profile<<<pblocks, kProfThreads, prof_smem, s>>>(I, n, g->id_bits, g->tsum, d_pairs, d_nl,
+                                                       d_deg, d_next, PS, g->d_status, d_max); count_launch(); }
     if ((st = check_device_status(g, "layer profile"))) return st;
     dev_free(g, PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks);
     dev_free(g, PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks);
@@ -559,16 +559,16 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&d_ln, sizeof(double) * ln_l1.size()))) return st;
     HYP_CUDA(cudaMemcpyAsync(d_ln, ln_l1.data(), sizeof(double) * ln_l1.size(),
                              cudaMemcpyHostToDevice, s));
-    k_profile_write<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, d_pairs, d_poff64, d_deg,
+    { k_profile_write<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, d_pairs, d_poff64, d_deg,
                                                          g->model, g->uniform_thr, d_ln, g->prof,
-                                                         g->prof_off, g->stratum);
+                                                         g->prof_off, g->stratum); count_launch(); }
 
     // --- theta(l*) from the histogram of l (Thm 2)
     const int hcap = g->max_layers + 1;
     unsigned long long* d_lh = nullptr;
     if ((st = dev_alloc(g, (void**)&d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1)))) return st;
     HYP_CUDA(cudaMemsetAsync(d_lh, 0, sizeof(unsigned long long) * ((size_t)hcap + 1), s));
-    k_hist_layers<<<grid_for(n, 256, sm), 256, 0, s>>>(d_poff64, n, d_lh, hcap);
+    { k_hist_layers<<<grid_for(n, 256, sm), 256, 0, s>>>(d_poff64, n, d_lh, hcap); count_launch(); }
     std::vector<unsigned long long> lh((size_t)hcap + 1);
     HYP_CUDA(cudaMemcpyAsync(lh.data(), d_lh, sizeof(unsigned long long) * lh.size(),
                              cudaMemcpyDeviceToHost, s));
@@ -591,10 +591,10 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     uint32_t* d_flags = d_cnt;
     for (int s2 = 0; s2 < HYPERIM_NSTRATA; ++s2) {
         if (g->stratum_size[s2] == 0) continue;
-        k_stratum_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(g->stratum, n, s2, d_flags);
+        { k_stratum_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(g->stratum, n, s2, d_flags); count_launch(); }
         if ((st = exclusive_scan_u32_to_i64(g, d_flags, d_voff64, n))) return st;
-        k_stratum_scatter<<<grid_for(n, 256, sm), 256, 0, s>>>(d_flags, d_voff64, n, hvs[s2],
-                                                               g->vs_list);
+        { k_stratum_scatter<<<grid_for(n, 256, sm), 256, 0, s>>>(d_flags, d_voff64, n, hvs[s2],
+                                                               g->vs_list); count_launch(); }
     }
     HYP_CUDA(cudaGetLastError());
     if ((st = check_device_status(g, "profile write"))) return st;

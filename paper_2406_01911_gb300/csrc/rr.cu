@@ -851,6 +851,9 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     P.st = g->d_status;
     P.counters = g->d_counters;
     unsigned long long used = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    HYP_CUDA(cudaEventCreate(&ev0));
+    HYP_CUDA(cudaEventCreate(&ev1));
     for (int attempt = 0; attempt < 3; ++attempt) {
         if (g->scratch.arena_cap < want) {
             if (g->scratch.arena) dev_free(g, g->scratch.arena, sizeof(int32_t) * g->scratch.arena_cap);
@@ -863,13 +866,21 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
         P.arena_cap = g->scratch.arena_cap;
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int) + sizeof(unsigned long long) * 2, s));
         HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters), s));
-        k_rr<<<blocks, kThreads, smem, s>>>(P);
+        HYP_CUDA(cudaEventRecord(ev0, s));
+        { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
         HYP_CUDA(cudaGetLastError());
+        HYP_CUDA(cudaEventRecord(ev1, s));
         HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
         if ((st = check_device_status(g, "RR generation"))) return st;
+        float ms = 0.f;
+        HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        p->rr_kernel_seconds += 1e-3 * (double)ms;
+        p->rr_launches += 1;
         if (used <= g->scratch.arena_cap) break;
         want = used + used / 8 + 4096;
     }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
     if (used > g->scratch.arena_cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
     RRCounters c;
     HYP_CUDA(cudaMemcpyAsync(&c, g->d_counters, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -888,8 +899,8 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
     if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
     const int grid = (int)std::min<int64_t>((njobs * 32 + 255) / 256, (int64_t)g->sm_count * 32);
-    k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos, d_boff, njobs, p->count, p->total, jm,
-                                      p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j);
+    { k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos, d_boff, njobs, p->count, p->total, jm,
+                                      p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
     HYP_CUDA(cudaGetLastError());
     dev_free(g, d_boff, sizeof(int64_t) * ((size_t)njobs + 1));
     dev_free(g, d_pos, sizeof(int64_t) * (size_t)njobs);

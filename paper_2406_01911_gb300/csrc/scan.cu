@@ -98,9 +98,9 @@ hyperim_status scan_impl(hyperim_graph* g, const T* in, int64_t* out, int64_t n)
     int64_t* sums = nullptr;
     hyperim_status st = dev_alloc(g, (void**)&sums, sizeof(int64_t) * (size_t)ntiles);
     if (st != HYPERIM_OK) return st;
-    k_tile_sums<T><<<(unsigned)ntiles, kScanThreads, 0, g->stream>>>(in, n, sums);
-    k_scan_sums<<<1, 1024, 0, g->stream>>>(sums, ntiles, out + n);
-    k_tile_scan<T><<<(unsigned)ntiles, kScanThreads, 0, g->stream>>>(in, n, sums, out);
+    { k_tile_sums<T><<<(unsigned)ntiles, kScanThreads, 0, g->stream>>>(in, n, sums); count_launch(); }
+    { k_scan_sums<<<1, 1024, 0, g->stream>>>(sums, ntiles, out + n); count_launch(); }
+    { k_tile_scan<T><<<(unsigned)ntiles, kScanThreads, 0, g->stream>>>(in, n, sums, out); count_launch(); }
     cudaError_t e = cudaGetLastError();
     dev_free(g, sums, sizeof(int64_t) * (size_t)ntiles);
     if (e != cudaSuccess) return cuda_fail(e, "scan kernels");

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared():
     src = open(os.path.join(ROOT, "include", "hyperim.h")).read()
-    return sorted(set(re.findall(r"^(?:hyperim_status|void|const char\*)\s+(hyperim_\w+)\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:hyperim_status|void|uint64_t|const char\*)\s+(hyperim_\w+)\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")

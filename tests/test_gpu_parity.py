@@ -117,7 +117,7 @@ def test_hub_paths(H, oracle):
     n, hes = gc.hub_graph()
     g, og = load_both(H, oracle, n, hes, "uniform_pair", 85899345, seed=11)  # p = 0.02
     check_profile(g, og, n)
-    assert og.dh(0) == 60
+    assert og.dh(0) >= 60 and og.dh(1) >= 10
     check_pool(H, oracle, g, og, 12, "plain", seed=11)
     g2, og2 = load_both(H, oracle, n, hes, "wc", 0, seed=11)
     check_pool(H, oracle, g2, og2, 3000, "stratified", seed=11)
