@@ -45,11 +45,12 @@ def peaks():
 
 
 def rr_algorithmic_bytes(v):
-    """Bytes the RR generator must move, from its work counters (layout of the incidence store):
-    per pop the profile offsets (8) and 16-byte layer entries; per materialising pop the v->he
-    offsets (8), 4 + 8 bytes per hyperedge (id, offsets) and 4 per member read, plus tsum (4);
-    per RR set the root (4); per member of R its queue write and read and its output write (12)."""
-    return (8 * v["pops"] + 16 * v["layers_seen"] + 12 * v["mats"] + 12 * v["mat_he"]
+    """Bytes the RR generator must move, from its work counters and the device layout: per pop
+    the per-vertex record (8) and one 32-byte entry per layer of A(mu); per materialising pop the
+    hyperedge spans (8 + 4 per hyperedge), the record and sum of sizes (12) and every member of
+    mu's hyperedges (4 each); per member of R its queue write, queue read and output write (12);
+    per RR set its root (4)."""
+    return (8 * v["pops"] + 32 * v["layers_seen"] + 12 * v["mats"] + 12 * v["mat_he"]
             + 4 * v["mat_members"] + 12 * v["total"] + 4 * v["count"])
 
 

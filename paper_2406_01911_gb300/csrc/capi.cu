@@ -231,7 +231,7 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
 void hyperim_graph_free(hyperim_graph_t g) {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
-    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->prof_off, g->prof, g->deg,
+    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off, g->prof, g->deg,
                     g->stratum, g->vs_off, g->vs_list, g->d_status, g->d_counters, g->scratch.list,
                     g->scratch.bitmap, g->scratch.big, g->scratch.picks, g->scratch.arena};
     for (void* p : ptrs)
@@ -262,10 +262,10 @@ hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* n
     const size_t n = (size_t)g->n, L = (size_t)g->profile_entries;
     std::vector<int32_t> off(n + 1);
     std::vector<uint8_t> strat(n);
-    std::vector<uint4> prof(L);
+    std::vector<uint4> prof(2 * L);
     HYP_CUDA(cudaMemcpyAsync(off.data(), g->prof_off, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, g->stream));
     HYP_CUDA(cudaMemcpyAsync(strat.data(), g->stratum, n, cudaMemcpyDeviceToHost, g->stream));
-    if (L) HYP_CUDA(cudaMemcpyAsync(prof.data(), g->prof, sizeof(uint4) * L, cudaMemcpyDeviceToHost, g->stream));
+    if (L) HYP_CUDA(cudaMemcpyAsync(prof.data(), g->prof, 2 * sizeof(uint4) * L, cudaMemcpyDeviceToHost, g->stream));
     if (deg) HYP_CUDA(cudaMemcpyAsync(deg, g->deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, g->stream));
     HYP_CUDA(cudaStreamSynchronize(g->stream));
     for (size_t v = 0; v < n; ++v) {
@@ -275,9 +275,10 @@ hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* n
     if (prof_off)
         for (size_t v = 0; v <= n; ++v) prof_off[v] = off[v];
     for (size_t x = 0; x < L; ++x) {
-        if (layer_w) layer_w[x] = prof[x].x & ~kPOneFlag;
-        if (layer_n) layer_n[x] = prof[x].y;
-        if (layer_thr) layer_thr[x] = (prof[x].x & kPOneFlag) ? HYPERIM_P_ONE : (uint64_t)prof[x].z;
+        const uint4 e = prof[2 * x];
+        if (layer_w) layer_w[x] = e.x & ~kPOneFlag;
+        if (layer_n) layer_n[x] = e.y;
+        if (layer_thr) layer_thr[x] = (e.x & kPOneFlag) ? HYPERIM_P_ONE : (uint64_t)e.z;
     }
     return HYPERIM_OK;
 }

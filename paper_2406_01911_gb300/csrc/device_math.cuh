@@ -143,6 +143,41 @@ static __device__ __noinline__ uint32_t poisson_part(double lam, uint32_t n, uin
     return n;
 }
 
+// The first four thresholds T_0..T_3 of the inversion computed by binomial_h (poisson = false) or
+// by a single-part poisson_part (poisson = true), by the same IEEE operation sequence, each capped
+// at 2^32 - 1. Where a pmf term underflows the CDF stops moving and later thresholds repeat the
+// last one. A draw w < T_k (least such k < min(4, n)) has h = k exactly; otherwise the full
+// inversion decides.
+__device__ __forceinline__ void cdf_first4(uint32_t n, uint64_t thr, bool poisson, uint32_t T[4]) {
+    double P, cum, r = 0.0, lam = 0.0;
+    if (poisson) {
+        lam = poisson_lambda(n, thr);
+        P = exp_neg(lam);
+    } else {
+        const double p = __dmul_rn((double)thr, 0x1p-32);
+        const double q = __dsub_rn(1.0, p);
+        P = 1.0;
+        for (uint32_t i = 0; i < n; ++i) P = __dmul_rn(P, q);
+        r = __ddiv_rn(p, q);
+    }
+    cum = P;
+    bool dead = false;
+    for (uint32_t k = 0; k < 4; ++k) {
+        if (k > 0 && !dead) {
+            if (poisson) {
+                P = __ddiv_rn(__dmul_rn(P, lam), (double)k);
+            } else {
+                const uint32_t h = k - 1;
+                P = __dmul_rn(__ddiv_rn(__dmul_rn(P, (double)(n - h)), (double)(h + 1)), r);
+            }
+            if (P == 0.0) dead = true;
+            else cum = __dadd_rn(cum, P);
+        }
+        const uint64_t t = cdf_thr(cum);
+        T[k] = (uint32_t)(t > 0xFFFFFFFFull ? 0xFFFFFFFFull : t);
+    }
+}
+
 // P(h = 0) threshold for the (unsplit or first split) Poisson strategy: the whole draw is 0 iff
 // every part draws 0; with one part this is w0 < floor(exp(-lam) 2^32).
 __device__ __forceinline__ uint64_t poisson_t0(uint32_t n, uint64_t thr) {

@@ -32,12 +32,14 @@ struct RRCounters {
     unsigned long long pops, layers_seen, draws, mats, mat_he, mat_members, selected;
 };
 
-// Profile entry of layer i of A(mu): 16 bytes.
-//   x: w_i | (p == 1 ? 1u << 31 : 0)
-//   y: n_i
-//   z: floor(p 2^32) for 0 <= p < 1
-//   w: T0 -- the draw is h = 0 whenever word 0 < T0 (0 disables this shortcut); it equals the
-//      first CDF threshold of the Binomial or single-part Poisson inversion, capped at 2^32 - 1.
+// Profile entry of layer i of A(mu): 32 bytes, two uint4.
+//   [0].x: w_i | (p == 1 ? 1u << 31 : 0)
+//   [0].y: n_i
+//   [0].z: floor(p 2^32) for 0 <= p < 1
+//   [0].w: T_0     [1].x, .y, .z: T_1, T_2, T_3     [1].w: 1 if T_0..T_3 are valid
+// T_k is the k-th CDF threshold of the layer's inversion under the paper's strategy (Binomial if
+// n_i <= 20, single-part Poisson if n_i > 20 and lambda <= 64), capped at 2^32 - 1: a draw whose
+// first word lies below T_k (least k < min(4, n_i)) has h = k without any floating point.
 constexpr uint32_t kPOneFlag = 0x80000000u;
 
 struct Scratch {
@@ -74,9 +76,11 @@ struct hyperim_graph {
     int32_t* v_off = nullptr;    // n + 1
     int32_t* v_he = nullptr;     // nnz, ascending hyperedge ids per vertex
     int32_t* tsum = nullptr;     // n: sum of |he| over he containing v
+    int2* v_span = nullptr;      // nnz: {he_off[he], |he|} for each incidence, in v_he order
+    int4* vinfo = nullptr;       // n: {profile begin, l, incidence begin, d_H}
     // layer profile
     int32_t* prof_off = nullptr; // n + 1
-    uint4* prof = nullptr;       // profile entries
+    uint4* prof = nullptr;       // profile entries (two uint4 per layer)
     int32_t* deg = nullptr;      // n
     uint8_t* stratum = nullptr;  // n
     int32_t* vs_off = nullptr;   // 17

@@ -361,20 +361,21 @@ __global__ void k_profile_write(int32_t n, const int32_t* __restrict__ v_off,
                 const double pd = __ddiv_rn(PL, (double)n_i);
                 thr = pd >= 1.0 ? kPOne : __double2ull_rz(__dmul_rn(pd, 4294967296.0));
             }
-            uint32_t flags = 0, t0 = 0;
+            uint32_t flags = 0, valid = 0;
+            uint32_t T[4] = {0, 0, 0, 0};
             if (thr >= kPOne) {
                 flags = kPOneFlag;
             } else if (thr > 0) {
-                uint64_t T0;
                 if (n_i <= 20) {
-                    T0 = binomial_t0(n_i, thr);
-                } else {
-                    const double lam = poisson_lambda(n_i, thr);
-                    T0 = poisson_parts(lam) == 1 ? cdf_thr(exp_neg(lam)) : 0;
+                    cdf_first4(n_i, thr, false, T);
+                    valid = 1;
+                } else if (poisson_parts(poisson_lambda(n_i, thr)) == 1) {
+                    cdf_first4(n_i, thr, true, T);
+                    valid = 1;
                 }
-                t0 = (uint32_t)(T0 > 0xFFFFFFFFull ? 0xFFFFFFFFull : T0);
             }
-            prof[pb + i] = make_uint4(wn.x | flags, n_i, thr >= kPOne ? 0u : (uint32_t)thr, t0);
+            prof[2 * (pb + i)] = make_uint4(wn.x | flags, n_i, thr >= kPOne ? 0u : (uint32_t)thr, T[0]);
+            prof[2 * (pb + i) + 1] = make_uint4(T[1], T[2], T[3], valid);
         }
     }
 }
@@ -415,6 +416,23 @@ __global__ void k_vhe_len(const int64_t* __restrict__ v_off64, int32_t n, int32_
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
         dh[v] = (int32_t)(v_off64[v + 1] - v_off64[v]);
+}
+
+// per-incidence spans and per-vertex records read by the RR kernel (fewer dependent loads)
+__global__ void k_build_spans(const int32_t* __restrict__ v_he, int64_t nnz,
+                              const int32_t* __restrict__ he_off, int2* __restrict__ v_span) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t he = v_he[x];
+        v_span[x] = make_int2(he_off[he], he_off[he + 1] - he_off[he]);
+    }
+}
+
+__global__ void k_build_vinfo(int32_t n, const int32_t* __restrict__ prof_off,
+                              const int32_t* __restrict__ v_off, int4* __restrict__ vinfo) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        vinfo[v] = make_int4(prof_off[v], prof_off[v + 1] - prof_off[v], v_off[v], v_off[v + 1] - v_off[v]);
 }
 
 int grid_for(int64_t items, int threads, int sm) {
@@ -549,7 +567,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     HYP_CUDA(cudaMemcpyAsync(&L, d_poff64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
     g->profile_entries = L;
-    if ((st = dev_alloc(g, (void**)&g->prof, sizeof(uint4) * (size_t)(L > 0 ? L : 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&g->prof, 2 * sizeof(uint4) * (size_t)(L > 0 ? L : 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->prof_off, sizeof(int32_t) * ((size_t)n + 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->stratum, (size_t)n))) return st;
     // ln(l + 1) for the paper's layer probabilities, computed once on the host
@@ -580,6 +598,13 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     for (int s2 = 0; s2 < HYPERIM_NSTRATA; ++s2) g->stratum_size[s2] = 0;
     for (int l = 0; l < hcap; ++l)
         g->stratum_size[l < HYPERIM_NSTRATA - 1 ? l : HYPERIM_NSTRATA - 1] += (int64_t)lh[l];
+
+    // --- spans and per-vertex records for the RR kernel
+    if ((st = dev_alloc(g, (void**)&g->v_span, sizeof(int2) * nnz_a))) return st;
+    if ((st = dev_alloc(g, (void**)&g->vinfo, sizeof(int4) * (size_t)n))) return st;
+    if (nnz > 0)
+        { k_build_spans<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->v_span); count_launch(); }
+    { k_build_vinfo<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->prof_off, g->v_off, g->vinfo); count_launch(); }
 
     // --- strata lists V_s (ascending ids)
     if ((st = dev_alloc(g, (void**)&g->vs_off, sizeof(int32_t) * (HYPERIM_NSTRATA + 1)))) return st;

@@ -159,3 +159,245 @@ __device__ bool walk_runs(const uint32_t* buf, int count, F&& consume) {
 }
 
 }  // namespace hyperim
+
+namespace hyperim {
+
+// ------------------------------------------------------------------------------------------
+// Flattened neighbourhood gather. Hyperedge spans (start, length into he_mem) of mu's
+// incidences are read G at a time; their lengths are prefix-summed in shared memory and every
+// thread then walks member positions p = rank, rank + G, ... of the group, locating its
+// hyperedge by binary search in the prefix: all member loads of a group are independent.
+// f(x) is called for every member x != mu (duplicates across hyperedges included).
+// pre: 2 G + 1 ints of shared memory (prefix and starts).
+// ------------------------------------------------------------------------------------------
+template <int G, typename F>
+__device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
+                                                const int32_t* __restrict__ he_mem, int32_t mu,
+                                                int32_t v_begin, int32_t dh, int* pre, F&& f) {
+    using Gr = Group<G>;
+    const int r = Gr::rank();
+    const int lane = threadIdx.x & 31;
+    int* start = pre + G + 1;  // G starts follow the G + 1 prefix entries
+    for (int c0 = 0; c0 < dh; c0 += G) {
+        const int cnt = min(G, dh - c0);
+        int2 sp = make_int2(0, 0);
+        if (r < cnt) sp = v_span[v_begin + c0 + r];
+        int inc = sp.y;  // inclusive prefix of the lengths across the group
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if constexpr (G > 32) {
+            const int wid = r >> 5;
+            if (lane == 31) start[wid] = inc;  // warp totals, before the starts are written
+            __syncthreads();
+            int off = 0;
+            for (int w = 0; w < wid; ++w) off += start[w];
+            __syncthreads();
+            inc += off;
+        }
+        if (r == 0) pre[0] = 0;
+        if (r < cnt) {
+            pre[r + 1] = inc;
+            start[r] = sp.x;
+        }
+        Gr::sync();
+        const int total = pre[cnt];
+        for (int p = r; p < total; p += G) {
+            int lo = 0, hi = cnt;  // j with pre[j] <= p < pre[j + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] <= p) lo = mid; else hi = mid;
+            }
+            const uint32_t x = (uint32_t)he_mem[start[lo] + (p - pre[lo])];
+            if (x != (uint32_t)mu) f(x);
+        }
+        Gr::sync();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sorted neighbourhood multiset by MSD bucketing: count members per bucket of their top id bits,
+// scan, scatter (second read of the members), then sort every bucket by insertion. With the
+// random vertex ids of real and synthetic hypergraphs buckets hold a handful of keys; if one
+// holds more than kBucketSortMax the whole buffer is sorted by the bitonic network instead
+// (capacity must then be a power of two >= count). Returns the number of keys (members != mu).
+// bkt: nb ints of shared memory; pre: 2 G + 1 ints; scratch: G / 32 ints; buf: capacity keys.
+// ------------------------------------------------------------------------------------------
+constexpr int kBucketSortMax = 48;
+
+// Number of bucket bits for count keys: about two keys per bucket, between 5 and max_bits.
+__device__ __forceinline__ int bucket_bits(int count, int max_bits) {
+    int b = 5;
+    while (b < max_bits && (2 << b) < count) ++b;
+    return b;
+}
+
+template <int G>
+__device__ int sorted_nbhd(const int2* __restrict__ v_span, const int32_t* __restrict__ he_mem,
+                           int32_t mu, int32_t v_begin, int32_t dh, int expected, int id_bits,
+                           uint32_t* buf, int* bkt, int max_bits, int* pre, int* scratch) {
+    using Gr = Group<G>;
+    const int r = Gr::rank();
+    const int nbits = bucket_bits(expected, max_bits);
+    const int nb = 1 << nbits;
+    const int shift = id_bits > nbits ? id_bits - nbits : 0;
+    const uint32_t key_mask = (uint32_t)nb - 1;
+    for (int b = r; b < nb; b += G) bkt[b] = 0;
+    Gr::sync();
+    for_each_member<G>(v_span, he_mem, mu, v_begin, dh, pre,
+                       [&](uint32_t x) { atomicAdd(&bkt[(x >> shift) & key_mask], 1); });
+    // exclusive scan of the bucket counts (chunks of G, carried)
+    int carry = 0;
+    int maxb = 0;
+    for (int c0 = 0; c0 < nb; c0 += G) {
+        const int b = c0 + r;
+        const int v = b < nb ? bkt[b] : 0;
+        maxb = max(maxb, v);
+        int inc = v;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int total;
+        if constexpr (G > 32) {
+            const int wid = r >> 5;
+            if (lane == 31) scratch[wid] = inc;
+            __syncthreads();
+            int off = 0;
+            total = 0;
+            for (int w = 0; w < G / 32; ++w) {
+                const int c = scratch[w];
+                off += w < wid ? c : 0;
+                total += c;
+            }
+            __syncthreads();
+            inc += off;
+        } else {
+            total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+        if (b < nb) bkt[b] = carry + inc - v;
+        carry += total;
+    }
+    // largest bucket across the group
+    maxb = __reduce_max_sync(0xFFFFFFFFu, maxb);
+    if constexpr (G > 32) {
+        if ((threadIdx.x & 31) == 0) scratch[r >> 5] = maxb;
+        __syncthreads();
+        int m = 0;
+        for (int w = 0; w < G / 32; ++w) m = max(m, scratch[w]);
+        __syncthreads();
+        maxb = m;
+    }
+    const int count = carry;
+    Gr::sync();
+    for_each_member<G>(v_span, he_mem, mu, v_begin, dh, pre, [&](uint32_t x) {
+        buf[atomicAdd(&bkt[(x >> shift) & key_mask], 1)] = x;
+    });
+    // bkt[b] is now the end of bucket b
+    if (maxb > kBucketSortMax) {
+        group_sort<G>(buf, count);
+        return count;
+    }
+    for (int b = r; b < nb; b += G) {
+        const int e = bkt[b], s = b ? bkt[b - 1] : 0;
+        for (int i = s + 1; i < e; ++i) {
+            const uint32_t x = buf[i];
+            int j = i - 1;
+            while (j >= s && buf[j] > x) {
+                buf[j + 1] = buf[j];
+                --j;
+            }
+            buf[j + 1] = x;
+        }
+    }
+    Gr::sync();
+    return count;
+}
+
+// Sort keys already in buf[0, count) (one id-range chunk) by the same bucketing, reading the
+// keys from src (global) instead of the incidence lists.
+// (key bits below the chunk's common prefix: rem_bits; the next bucket bits of them key the buckets)
+template <int G>
+__device__ void sort_chunk(const uint32_t* __restrict__ src, int count, int rem_bits, uint32_t* buf,
+                           int* bkt, int max_bits, int* scratch) {
+    using Gr = Group<G>;
+    const int r = Gr::rank();
+    const int nbits = bucket_bits(count, max_bits);
+    const int nb = 1 << nbits;
+    const int shift = rem_bits > nbits ? rem_bits - nbits : 0;
+    const uint32_t key_mask = (uint32_t)nb - 1;
+    for (int b = r; b < nb; b += G) bkt[b] = 0;
+    Gr::sync();
+    for (int i = r; i < count; i += G) atomicAdd(&bkt[(src[i] >> shift) & key_mask], 1);
+    Gr::sync();
+    int carry = 0, maxb = 0;
+    for (int c0 = 0; c0 < nb; c0 += G) {
+        const int b = c0 + r;
+        const int v = b < nb ? bkt[b] : 0;
+        maxb = max(maxb, v);
+        int inc = v;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int total;
+        if constexpr (G > 32) {
+            const int wid = r >> 5;
+            if (lane == 31) scratch[wid] = inc;
+            __syncthreads();
+            int off = 0;
+            total = 0;
+            for (int w = 0; w < G / 32; ++w) {
+                const int c = scratch[w];
+                off += w < wid ? c : 0;
+                total += c;
+            }
+            __syncthreads();
+            inc += off;
+        } else {
+            total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+        if (b < nb) bkt[b] = carry + inc - v;
+        carry += total;
+    }
+    maxb = __reduce_max_sync(0xFFFFFFFFu, maxb);
+    if constexpr (G > 32) {
+        if ((threadIdx.x & 31) == 0) scratch[r >> 5] = maxb;
+        __syncthreads();
+        int m = 0;
+        for (int w = 0; w < G / 32; ++w) m = max(m, scratch[w]);
+        __syncthreads();
+        maxb = m;
+    }
+    Gr::sync();
+    for (int i = r; i < count; i += G) {
+        const uint32_t x = src[i];
+        buf[atomicAdd(&bkt[(x >> shift) & key_mask], 1)] = x;
+    }
+    Gr::sync();
+    if (maxb > kBucketSortMax) {
+        group_sort<G>(buf, count);
+        return;
+    }
+    for (int b = r; b < nb; b += G) {
+        const int e = bkt[b], s = b ? bkt[b - 1] : 0;
+        for (int i = s + 1; i < e; ++i) {
+            const uint32_t x = buf[i];
+            int j = i - 1;
+            while (j >= s && buf[j] > x) {
+                buf[j + 1] = buf[j];
+                --j;
+            }
+            buf[j + 1] = x;
+        }
+    }
+    Gr::sync();
+}
+
+}  // namespace hyperim

@@ -29,7 +29,11 @@ constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the wa
 constexpr int kBCap = 8192;      // block on-chip keys (power of two)
 constexpr int kBLQ = 64;         // layers with h > 0 per block round
 constexpr int kDCap = 512;       // deferred pops per level round
-constexpr int kBuckets = 4096;
+constexpr int kBucketBits = 12;
+constexpr int kBuckets = 1 << kBucketBits;    // block-path buckets
+constexpr int kWBucketBits = 8;
+constexpr int kWBuckets = 1 << kWBucketBits;  // warp-path buckets
+constexpr int kChunks = 1024;        // first-level id chunks of the largest neighbourhoods
 constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
 
 struct RRJobMap {
@@ -38,7 +42,9 @@ struct RRJobMap {
 };
 
 struct RRParams {
-    Incidence I;
+    const int4* vinfo;        // per vertex: {profile begin, l, incidence begin, d_H}
+    const int2* v_span;       // per incidence: {member begin, |he|}
+    const int32_t* he_mem;
     const int32_t* prof_off;
     const uint4* prof;
     const int32_t* tsum;
@@ -75,23 +81,38 @@ struct Need {                    // a layer with h > 0 at the current pop
     uint32_t w, n, h, ksel, layer;
 };
 
+// Buffers of phase 1 (warps pop independently) and of phase 2 / output (the whole block works on
+// one deferred pop, or on the finished set) never live at the same time: they share storage.
+struct WarpArea {
+    uint32_t wbuf[kWarps][kWCap];
+    int wbkt[kWarps][kWBuckets];
+    uint32_t wpick[kWarps][kPCap];
+};
+struct BlockArea {
+    uint32_t bbuf[kBCap];
+    int bucket[kBuckets];
+    int chunk_end[kChunks];
+};
+
 struct Shared {
     int ctrl[16];
     int tmp[kWarps + 2];
     unsigned long long stat[8];
+    unsigned long long out_pos;
     int32_t deferred[kDCap];
-    uint32_t wbuf[kWarps][kWCap];
-    uint32_t wpick[kWarps][kPCap];
     Need wneed[kWarps][kLQ];
     int wcursor[kWarps];
+    int wpre[kWarps][2 * 32 + 1];
+    int bpre[2 * kThreads + 1];
     uint32_t wpoff[kWarps][kLQ + 1];
-    unsigned long long out_pos;
-    int wcnt[kWarps][kBLQ];     // per-warp per-layer counts (block ranks)
+    int wcnt[kWarps][kBLQ];     // per-warp per-layer counts (ranks)
     int lcnt[kBLQ];             // running rank per needed layer (block path)
     Need bneed[kBLQ];
     uint32_t bpick_off[kBLQ + 1];
-    uint32_t bbuf[kBCap];
-    int bucket[kBuckets];
+    union {
+        WarpArea w;
+        BlockArea b;
+    } u;
 };
 // ctrl slots
 enum { C_JOB = 0, C_HEAD, C_TAIL, C_LEVEL_END, C_NEXT, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP,
@@ -103,17 +124,24 @@ __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t de
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
 }
 
-// h for one layer (lane-level). Returns whether a draw was made (0 < p < 1).
-__device__ __forceinline__ bool layer_draw(const uint4 e, int strategy, WordStream& ws,
+// h for one layer (lane-level) from its two profile words. Returns whether a draw was made
+// (0 < p < 1). Draws below one of the layer's first four CDF thresholds are decided by integer
+// compares; the rest run the double-precision inversion.
+__device__ __forceinline__ bool layer_draw(const uint4 e, const uint4 f, int strategy, WordStream& ws,
                                           uint32_t& h, uint32_t& ksel) {
-    const uint32_t n_i = e.y, thr = e.z, T0 = e.w;
+    const uint32_t n_i = e.y, thr = e.z;
     ksel = 0;
     if (e.x & kPOneFlag) { h = n_i; return false; }
     if (thr == 0) { h = 0; return false; }
     const uint32_t w0 = ws.word(0);
     const bool binom = n_i <= 20 || strategy == HYPERIM_STRAT_BINOMIAL_ONLY;
-    const bool fast = T0 != 0 && (n_i <= 20 || strategy == HYPERIM_STRAT_PAPER);
-    if (fast && w0 < T0) { h = 0; ksel = 1; return true; }
+    if (f.w != 0 && (n_i <= 20 || strategy == HYPERIM_STRAT_PAPER)) {
+        // least k < min(4, n_i) with w0 < T_k (thresholds are non-decreasing)
+        const uint32_t k = (w0 >= e.w) + (n_i > 1 && w0 >= f.x) + (n_i > 2 && w0 >= f.y) +
+                           (n_i > 3 && w0 >= f.z);
+        if (k < 4 && k < n_i) { h = k; ksel = 1; return true; }
+        if (n_i <= 4) { h = n_i; ksel = 1; return true; }
+    }
     if (binom) {
         h = binomial_h(n_i, thr, w0);
         ksel = 1;
@@ -194,7 +222,8 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
 __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
                          uint32_t ybase, int32_t mu, bool count_stats) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t pb = P.prof_off[mu], l = P.prof_off[mu + 1] - pb;
+    const int4 vi = P.vinfo[mu];
+    const int32_t pb = vi.x, l = vi.y, v_begin = vi.z, dh = vi.w;
     Need* need = S.wneed[wid];
     uint32_t nneed = 0, ndraw = 0;
     for (int c0 = 0; c0 < l; c0 += 32) {
@@ -203,10 +232,11 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         uint4 e = make_uint4(0, 0, 0, 0);
         bool drew = false;
         if (i < l) {
-            e = P.prof[pb + i];
+            e = P.prof[2 * (pb + i)];
+            const uint4 f = P.prof[2 * (pb + i) + 1];
             WordStream ws;
             ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
-            drew = layer_draw(e, P.strategy, ws, h, ksel);
+            drew = layer_draw(e, f, P.strategy, ws, h, ksel);
         }
         const bool flag = h > 0;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
@@ -223,11 +253,11 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         atomicAdd(&S.stat[S_DRAWS], (unsigned long long)ndraw);
     }
     if (nneed == 0) return false;
-    const int32_t e0 = P.I.v_off[mu], dh = P.I.v_off[mu + 1] - e0;
+    const int32_t tsum = P.tsum[mu];
     if (count_stats && lane == 0) {
         atomicAdd(&S.stat[S_MATS], 1ull);
         atomicAdd(&S.stat[S_MAT_HE], (unsigned long long)dh);
-        atomicAdd(&S.stat[S_MAT_MEM], (unsigned long long)P.tsum[mu]);
+        atomicAdd(&S.stat[S_MAT_MEM], (unsigned long long)tsum);
     }
     if (nneed > kLQ) return true;
     // picks for every needed layer (none when h = n)
@@ -237,9 +267,9 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         if (nd.h < nd.n) total_picks += nd.h;
         if (total_picks > kPCap) return true;
     }
-    const int T = P.tsum[mu] - dh;
+    const int T = tsum - dh;
     if (dh != 1 && T > kWCap) return true;
-    uint32_t* picks = S.wpick[wid];
+    uint32_t* picks = S.u.w.wpick[wid];
     uint32_t* poff = S.wpoff[wid];
     uint32_t acc = 0;
     for (uint32_t q = 0; q < nneed; ++q) {
@@ -260,31 +290,30 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     __syncwarp();
     if (dh == 1) {
         // A(mu) = the single hyperedge minus mu, sorted: position x maps to member x or x + 1
-        const int32_t he = P.I.v_he[e0];
-        const int32_t hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
-        // position of mu
+        const int2 sp = P.v_span[v_begin];
+        const int32_t hb = sp.x, len = sp.y;
         int pmu = 0;
         for (int b = 0; b < len; b += 32) {
-            const bool lt = b + lane < len && (uint32_t)P.I.he_mem[hb + b + lane] < (uint32_t)mu;
+            const bool lt = b + lane < len && (uint32_t)P.he_mem[hb + b + lane] < (uint32_t)mu;
             pmu += __popc(__ballot_sync(0xFFFFFFFFu, lt));
         }
         const Need nd = need[0];
         if (nd.h >= nd.n) {
             for (int x = lane; x < len - 1; x += 32)
-                push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+                push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
         } else {
             for (uint32_t r = lane; r < nd.h; r += 32) {
                 const uint32_t x = picks[r];
-                push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+                push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
             }
         }
         __syncwarp();
         return false;
     }
-    // materialise A(mu) in shared memory, sorted by id
-    uint32_t* buf = S.wbuf[wid];
-    const int got = gather_nbhd<32>(P.I, mu, buf, &S.wcursor[wid]);
-    group_sort<32>(buf, got);
+    // materialise A(mu) in shared memory, sorted by id (bucketed by the top 8 id bits)
+    uint32_t* buf = S.u.w.wbuf[wid];
+    const int got = sorted_nbhd<32>(P.v_span, P.he_mem, mu, v_begin, dh, T, P.id_bits, buf,
+                                    S.u.w.wbkt[wid], kWBucketBits, S.wpre[wid], nullptr);
     // walk runs; rank members of each needed layer in id order
     int* cnt = S.wcnt[wid];
     for (uint32_t q = lane; q < nneed; q += 32) cnt[q] = 0;
@@ -328,37 +357,11 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
 // ------------------------------------------------------------------------------------------
 // block path (all threads of the block)
 // ------------------------------------------------------------------------------------------
-__device__ void rank_chunk_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
-                                 bool start, uint32_t x, int mult, uint32_t nq,
-                                 const uint32_t* picks) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int q = -1;
-    if (start)
-        for (uint32_t t = 0; t < nq; ++t)
-            if (S.bneed[t].w == (uint32_t)mult) { q = (int)t; break; }
-    const uint32_t mask = __match_any_sync(0xFFFFFFFFu, q);
-    const int rin = __popc(mask & lanemask_lt());
-    for (uint32_t t = lane; t < nq; t += 32) S.wcnt[wid][t] = 0;
-    __syncwarp();
-    if (q >= 0 && rin == 0) S.wcnt[wid][q] = __popc(mask);
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < nq; t += kThreads) {
-        int run = S.lcnt[t];
-        for (int w = 0; w < kWarps; ++w) {
-            const int c = S.wcnt[w][t];
-            S.wcnt[w][t] = run;
-            run += c;
-        }
-        S.lcnt[t] = run;
-    }
-    __syncthreads();
-    if (q >= 0) {
-        const Need nd = S.bneed[q];
-        const uint32_t rank = (uint32_t)(S.wcnt[wid][q] + rin);
-        const bool take = nd.h >= nd.n || in_sorted(picks + S.bpick_off[q], nd.h, rank);
-        if (take) push(P, S, vis, list, x);
-    }
-    __syncthreads();
+// layer index (among the needed layers of this round) of a run of multiplicity mult, or -1
+__device__ __forceinline__ int needed_layer(const Shared& S, uint32_t nq, int mult) {
+    for (uint32_t t = 0; t < nq; ++t)
+        if (S.bneed[t].w == (uint32_t)mult) return (int)t;
+    return -1;
 }
 
 // true when every needed layer with a strict subset of picks has ranked past its largest pick
@@ -371,11 +374,72 @@ __device__ __forceinline__ bool block_done(const Shared& S, uint32_t nq, const u
     return true;
 }
 
+// Ranked walk of a sorted block buffer: warp w owns positions [w L, (w + 1) L) and every run
+// that starts there. Pass A counts the runs of each needed layer per warp, the counts are
+// prefix-summed across warps (on top of the running layer ranks), pass B re-walks and pushes
+// the runs whose rank is a pick. Returns (uniformly) whether all picks have been passed.
+__device__ bool block_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
+                           const uint32_t* buf, int count, uint32_t nq, const uint32_t* picks) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int L = (count + kWarps - 1) / kWarps;
+    const int s0 = min(count, wid * L), s1 = min(count, s0 + L);
+    for (uint32_t t = lane; t < nq; t += 32) S.wcnt[wid][t] = 0;
+    __syncwarp();
+    for (int base = s0; base < s1; base += 32) {
+        const int p = base + lane;
+        if (p < s1) {
+            const uint32_t x = buf[p];
+            if (p == 0 || buf[p - 1] != x) {
+                int mult = 1;
+                while (p + mult < count && buf[p + mult] == x) ++mult;
+                const int q = needed_layer(S, nq, mult);
+                if (q >= 0) atomicAdd(&S.wcnt[wid][q], 1);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < nq; t += kThreads) {
+        int run = S.lcnt[t];
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = S.wcnt[w][t];
+            S.wcnt[w][t] = run;
+            run += c;
+        }
+        S.lcnt[t] = run;
+    }
+    __syncthreads();
+    for (int base = s0; base < s1; base += 32) {
+        const int p = base + lane;
+        int q = -1;
+        uint32_t x = 0;
+        if (p < s1) {
+            x = buf[p];
+            if (p == 0 || buf[p - 1] != x) {
+                int mult = 1;
+                while (p + mult < count && buf[p + mult] == x) ++mult;
+                q = needed_layer(S, nq, mult);
+            }
+        }
+        const uint32_t mask = __match_any_sync(0xFFFFFFFFu, q);
+        const int rin = __popc(mask & lanemask_lt());
+        if (q >= 0) {
+            const Need nd = S.bneed[q];
+            const uint32_t rank = (uint32_t)(S.wcnt[wid][q] + rin);
+            if (nd.h >= nd.n || in_sorted(picks + S.bpick_off[q], nd.h, rank)) push(P, S, vis, list, x);
+        }
+        __syncwarp();
+        if (q >= 0 && rin == 0) S.wcnt[wid][q] += __popc(mask);
+        __syncwarp();
+    }
+    __syncthreads();
+    return block_done(S, nq, picks);
+}
+
 __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
                           uint32_t ybase, int32_t mu, uint32_t* picks_g, uint32_t* big) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t pb = P.prof_off[mu], l = P.prof_off[mu + 1] - pb;
-    const int32_t e0 = P.I.v_off[mu], dh = P.I.v_off[mu + 1] - e0;
+    const int4 vi = P.vinfo[mu];
+    const int32_t pb = vi.x, l = vi.y, v_begin = vi.z, dh = vi.w;
     // needed layers are processed kBLQ at a time; draws are recomputed per round
     for (uint32_t round_lo = 0;; round_lo += kBLQ) {
         if (wid == 0) {
@@ -385,10 +449,11 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
                 uint32_t h = 0, ksel = 0;
                 uint4 e = make_uint4(0, 0, 0, 0);
                 if (i < l) {
-                    e = P.prof[pb + i];
+                    e = P.prof[2 * (pb + i)];
+                    const uint4 f = P.prof[2 * (pb + i) + 1];
                     WordStream ws;
                     ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
-                    layer_draw(e, P.strategy, ws, h, ksel);
+                    layer_draw(e, f, P.strategy, ws, h, ksel);
                 }
                 const bool flag = h > 0;
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
@@ -437,59 +502,49 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
             __threadfence_block();
             __syncthreads();
             if (dh == 1) {
-                const int32_t he = P.I.v_he[e0];
-                const int32_t hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
+                const int2 sp = P.v_span[v_begin];
+                const int32_t hb = sp.x, len = sp.y;
                 if (threadIdx.x == 0) S.ctrl[C_CURSOR] = 0;
                 __syncthreads();
                 for (int b = threadIdx.x; b < len; b += kThreads)
-                    if ((uint32_t)P.I.he_mem[hb + b] < (uint32_t)mu) atomicAdd(&S.ctrl[C_CURSOR], 1);
+                    if ((uint32_t)P.he_mem[hb + b] < (uint32_t)mu) atomicAdd(&S.ctrl[C_CURSOR], 1);
                 __syncthreads();
                 const int pmu = S.ctrl[C_CURSOR];
                 const Need nd = S.bneed[0];
                 if (nd.h >= nd.n) {
                     for (int x = threadIdx.x; x < len - 1; x += kThreads)
-                        push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+                        push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
                 } else {
                     for (uint32_t r = threadIdx.x; r < nd.h; r += kThreads) {
                         const uint32_t x = picks_g[r];
-                        push(P, S, vis, list, (uint32_t)P.I.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+                        push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
                     }
                 }
                 __syncthreads();
             } else {
                 const int T = P.tsum[mu] - dh;
-                auto consume = [&](bool start, uint32_t x, int mult) -> bool {
-                    rank_chunk_block(P, S, vis, list, start, x, mult, nq, picks_g);
-                    return block_done(S, nq, picks_g);
-                };
                 if (T <= kBCap) {
-                    const int got = gather_nbhd<kThreads>(P.I, mu, S.bbuf, &S.ctrl[C_CURSOR]);
-                    group_sort<kThreads>(S.bbuf, got);
-                    walk_runs<kThreads>(S.bbuf, got, consume);
+                    const int got = sorted_nbhd<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, T,
+                                                          P.id_bits, S.u.b.bbuf, S.u.b.bucket,
+                                                          kBucketBits, S.bpre, S.tmp);
+                    block_walk(P, S, vis, list, S.u.b.bbuf, got, nq, picks_g);
                 } else if ((int64_t)T > P.big_cap) {
                     if (threadIdx.x == 0) dev_fail(P.st, kErrCapacity, mu);
                 } else {
-                    // bucket by the top id bits so that every bucket fits on chip
+                    // first level: chunk by the top b id bits so every chunk fits on chip
                     int b = 0;
-                    while (((int64_t)(kBCap / 4) << b) < (int64_t)T && b < P.id_bits &&
-                           (2 << b) <= kBuckets)
+                    while (((int64_t)(kBCap / 2) << b) < (int64_t)T && b < P.id_bits &&
+                           (2 << b) <= kChunks)
                         ++b;
                     bool ok = false;
                     for (;;) {
                         const int nb = 1 << b, shift = P.id_bits - b;
-                        for (int i = threadIdx.x; i < nb; i += kThreads) S.bucket[i] = 0;
+                        for (int i = threadIdx.x; i < nb; i += kThreads) S.u.b.chunk_end[i] = 0;
                         __syncthreads();
-                        for (int e = e0 + wid; e < e0 + dh; e += kWarps) {
-                            const int he = P.I.v_he[e];
-                            const int hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
-                            for (int i = lane; i < len; i += 32) {
-                                const uint32_t x = (uint32_t)P.I.he_mem[hb + i];
-                                if (x != (uint32_t)mu) atomicAdd(&S.bucket[x >> shift], 1);
-                            }
-                        }
-                        __syncthreads();
+                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.bpre,
+                                                  [&](uint32_t x) { atomicAdd(&S.u.b.chunk_end[x >> shift], 1); });
                         int mx = 0;
-                        for (int i = threadIdx.x; i < nb; i += kThreads) mx = max(mx, S.bucket[i]);
+                        for (int i = threadIdx.x; i < nb; i += kThreads) mx = max(mx, S.u.b.chunk_end[i]);
                         mx = __reduce_max_sync(0xFFFFFFFFu, mx);
                         if (lane == 0) S.tmp[wid] = mx;
                         __syncthreads();
@@ -497,7 +552,7 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
                         for (int w = 0; w < kWarps; ++w) allmx = max(allmx, S.tmp[w]);
                         __syncthreads();
                         if (allmx <= kBCap) { ok = true; break; }
-                        if (b >= P.id_bits || (2 << b) > kBuckets) break;
+                        if (b >= P.id_bits || (2 << b) > kChunks) break;
                         ++b;
                     }
                     if (!ok) {
@@ -508,37 +563,30 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
                             int carry = 0;
                             for (int base = 0; base < nb; base += 32) {
                                 const int i = base + lane;
-                                const int v = i < nb ? S.bucket[i] : 0;
+                                const int v = i < nb ? S.u.b.chunk_end[i] : 0;
                                 int inc = v;
                                 for (int o = 1; o < 32; o <<= 1) {
                                     const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
                                     if (lane >= o) inc += t;
                                 }
-                                if (i < nb) S.bucket[i] = carry + inc - v;
+                                if (i < nb) S.u.b.chunk_end[i] = carry + inc - v;
                                 carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
                             }
                         }
                         __syncthreads();
-                        for (int e = e0 + wid; e < e0 + dh; e += kWarps) {
-                            const int he = P.I.v_he[e];
-                            const int hb = P.I.he_off[he], len = P.I.he_off[he + 1] - hb;
-                            for (int i = lane; i < len; i += 32) {
-                                const uint32_t x = (uint32_t)P.I.he_mem[hb + i];
-                                if (x != (uint32_t)mu) big[atomicAdd(&S.bucket[x >> shift], 1)] = x;
-                            }
-                        }
+                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.bpre,
+                                                  [&](uint32_t x) { big[atomicAdd(&S.u.b.chunk_end[x >> shift], 1)] = x; });
                         __threadfence_block();
                         __syncthreads();
+                        // second level: each chunk bucketed on chip by the next id bits
                         int begin = 0;
                         for (int qb = 0; qb < nb; ++qb) {
-                            const int end = S.bucket[qb];
+                            const int end = S.u.b.chunk_end[qb];
                             const int cnt = end - begin;
                             if (cnt > 0) {
-                                for (int i = threadIdx.x; i < cnt; i += kThreads) S.bbuf[i] = big[begin + i];
-                                __syncthreads();
-                                group_sort<kThreads>(S.bbuf, cnt);
-                                const bool stop = walk_runs<kThreads>(S.bbuf, cnt, consume);
-                                __syncthreads();
+                                sort_chunk<kThreads>(big + begin, cnt, shift, S.u.b.bbuf, S.u.b.bucket,
+                                                     kBucketBits, S.tmp);
+                                const bool stop = block_walk(P, S, vis, list, S.u.b.bbuf, cnt, nq, picks_g);
                                 if (stop) break;
                             }
                             begin = end;
@@ -556,7 +604,7 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
 // ------------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
+__global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
     uint32_t* vis = P.vis_smem ? reinterpret_cast<uint32_t*>(smem_raw + sizeof(Shared))
@@ -648,13 +696,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
         const bool fits = S.ctrl[C_ROOT] != 0;
         const unsigned long long pos = S.out_pos;
         if (size <= kBCap) {
-            for (int i = threadIdx.x; i < size; i += kThreads) S.bbuf[i] = (uint32_t)list[i];
+            for (int i = threadIdx.x; i < size; i += kThreads) S.u.b.bbuf[i] = (uint32_t)list[i];
             __syncthreads();
-            group_sort<kThreads>(S.bbuf, size);
+            group_sort<kThreads>(S.u.b.bbuf, size);
             if (fits)
-                for (int i = threadIdx.x; i < size; i += kThreads) P.arena[pos + i] = (int32_t)S.bbuf[i];
+                for (int i = threadIdx.x; i < size; i += kThreads) P.arena[pos + i] = (int32_t)S.u.b.bbuf[i];
             __syncthreads();
-            for (int i = threadIdx.x; i < size; i += kThreads) vis[S.bbuf[i] >> 5] = 0;
+            for (int i = threadIdx.x; i < size; i += kThreads) vis[S.u.b.bbuf[i] >> 5] = 0;
         } else {
             // R is large: read it off the visited bitmap in id order
             const int64_t nwords = ((int64_t)P.n + 31) >> 5;
@@ -821,7 +869,9 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     if ((st = dev_alloc(g, (void**)&d_next, sizeof(int) + sizeof(unsigned long long) * 2))) return st;
     d_used = reinterpret_cast<unsigned long long*>(d_next + 2);
     RRParams P;
-    P.I = Incidence{g->he_off, g->he_mem, g->v_off, g->v_he};
+    P.vinfo = g->vinfo;
+    P.v_span = g->v_span;
+    P.he_mem = g->he_mem;
     P.prof_off = g->prof_off;
     P.prof = g->prof;
     P.tsum = g->tsum;
