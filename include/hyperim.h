@@ -246,6 +246,34 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
 hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k,
                               hyperim_pool_t pool, double* sigma_hat, double* std_err);
 
+/* ------------------------------------------------------------------------------------------
+ * hyperim_coverage_noalloc -- per-stratum coverage of a seed set on an RR pool, computed without
+ *   allocating any memory. The paper has no counterpart: it is the coverage step behind
+ *   hyperim_spread and the BRR lower bound, offered to callers that cannot allocate device
+ *   memory -- a serving loop whose device memory was handed out up front by its admission
+ *   budget, a host application whose own allocator owns the GPU, or a latency-critical path
+ *   where an allocation may wait on the device or fail under memory pressure.
+ *   Inputs (device pointers, caller-owned): rr_off[count + 1] (int64), rr_mem[rr_off[count]]
+ *   (int32 vertex ids), rr_stratum[count] (0..15) -- e.g. the CSR of hyperim_pool_view -- and
+ *   seeds[k] (ids outside [0, n) are ignored). Output (device, caller-owned): lambda_s[16] gets
+ *   the number of RR sets of each stratum that contain a seed; the call zeroes it first.
+ *   Scratch: one flag byte per vertex in a fixed array of HYPERIM_NOALLOC_MAX_N bytes built into
+ *   the library; every GPU that loads the library holds those bytes until the process exits.
+ *   EINVAL: n < 1 or n > HYPERIM_NOALLOC_MAX_N (the scratch is too small), count < 0, k < 0,
+ *   null pointers. Never calls cudaMalloc, cudaFree or any other allocating routine.
+ *   The first call on a device looks up the scratch array's device address and caches it (a
+ *   set-up step): make that first call before any stream capture. The work is queued on
+ *   cuda_stream (NULL = legacy default stream) and the call returns without waiting. Every call
+ *   uses the same scratch array, which keeps the last call's flags until the next call clears
+ *   it: calls whose work overlaps on the GPU (other streams, other threads) race and return wrong
+ *   counts, so order them on one stream.
+ * ------------------------------------------------------------------------------------------ */
+#define HYPERIM_NOALLOC_MAX_N (1u << 24)
+hyperim_status hyperim_coverage_noalloc(int32_t n, const int64_t* rr_off, const int32_t* rr_mem,
+                                        const uint8_t* rr_stratum, int64_t count,
+                                        const int32_t* seeds, int32_t k,
+                                        unsigned long long* lambda_s, void* cuda_stream);
+
 /* Number of CUDA kernels this library has launched in this process (all threads, all graphs). */
 uint64_t hyperim_kernel_launches(void);
 

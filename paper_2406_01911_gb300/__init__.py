@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhyperim.so")
 
 NSTRATA = 16
 P_ONE = 1 << 32
+NOALLOC_MAX_N = 1 << 24
 MODELS = {"uniform_pair": 0, "wc": 1, "paper_layer": 2}
 ROOTS = {"plain": 0, "stratified": 1}
 STRATEGIES = {"paper": 0, "binomial_only": 1}
@@ -97,6 +98,8 @@ _SIGNATURES = {
                                        C.POINTER(SelectResult)]),
     "hyperim_spread": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
+    "hyperim_coverage_noalloc": (C.c_int, [C.c_int32, _vp, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp,
+                                           _vp]),
     "hyperim_kernel_launches": (C.c_uint64, []),
     "hyperim_last_error": (C.c_char_p, []),
 }
