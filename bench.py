@@ -61,9 +61,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(name):
-    """Per-launch DRAM bytes of the RR kernel from the committed ncu summary, if it was taken on
-    the current kernel source."""
+def traffic_ratio_for(name):
+    """DRAM bytes per algorithmic byte of the RR kernel, from the committed ncu capture of one
+    launch of known size (``--profile-batch``), if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", f"k_rr_{name}.json")
     try:
         d = json.load(open(path))
@@ -71,7 +71,7 @@ def traffic_for(name):
         return None
     if d.get("source_hash") != source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_algorithmic_byte")
 
 
 class ClockSampler:
@@ -234,7 +234,8 @@ def bench_gpu(args):
     ksec = sum(s["rr_kernel_seconds"] for s in stats)
     klaunch = sum(s["rr_launches"] for s in stats)
     achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
-    traffic = traffic_for(args.workload)
+    ratio = traffic_ratio_for(args.workload)
+    traffic = ratio * kbytes / max(klaunch, 1) if ratio is not None else None
     line = {
         "metric": METRIC,
         "value": rr_all / t_all,
@@ -274,6 +275,36 @@ def bench_gpu(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def profile_batch(args):
+    """Grow four fresh pools by the same theta, one after the other; the last growth is a single
+    RR-kernel launch of known size. Prints its RR sets, algorithmic bytes and its index among the
+    RR-kernel launches of this process (the -s of an ncu capture filtered on k_rr)."""
+    import torch
+    import paper_2406_01911_gb300 as H
+    from paper_2406_01911_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    w = workload(args.workload)
+    q = w.query
+    off, mem = make_hypergraph(w.graph)
+    g = H.Graph(w.graph.n, torch.as_tensor(off).cuda(), torch.as_tensor(mem).cuda(), q.model,
+                q.uniform_threshold, seed=q.seed)
+    before = 0
+    for i in range(4):
+        p = g.pool(tag=10 + i, roots=q.roots)
+        p.sample(args.profile_batch)
+        v = p.view()
+        if i == 3:
+            print(json.dumps({"workload": w.name, "theta": args.profile_batch, "rr_sets": v["count"],
+                              "k_rr_launch_index": before, "k_rr_launches": v["rr_launches"],
+                              "algorithmic_bytes": rr_algorithmic_bytes(v),
+                              "kernel_seconds": v["rr_kernel_seconds"], "source_hash": source_hash()}),
+                  flush=True)
+        before += v["rr_launches"]
+        p.close()
+    torch.cuda.synchronize()
 
 
 def oracle_rate(w, off, mem, seconds, seed, tag=0):
@@ -343,10 +374,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling aid: one RR-kernel launch growing a fresh pool by this theta")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_batch:
+        profile_batch(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_gpu(args)

@@ -181,8 +181,10 @@ typedef struct {
        layer draws with 0 < p < 1, pops that materialised A(mu), hyperedges and members read by
        those materialisations, activations drawn (sum of h) */
     uint64_t pops, layers_seen, draws, mats, mat_he, mat_members, selected;
-    uint64_t rr_launches;     /* RR-generation kernel launches */
-    double rr_kernel_seconds; /* their summed duration, CUDA events on the graph's stream */
+    uint64_t rr_launches;     /* RR-generation kernel launches that grew this pool first (a launch
+                                 growing R1 and R2 of a BRR round together counts once, on R1) */
+    double rr_kernel_seconds; /* this pool's share (by RR sets) of those launches' duration,
+                                 CUDA events on the graph's stream */
 } hyperim_pool_view_t;
 
 hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out);

@@ -213,7 +213,7 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
         return set_error(HYPERIM_EINVAL, "bad member array");
     }
     hyperim_status st = dev_alloc(g, (void**)&g->d_status, sizeof(DevStatus));
-    if (st == HYPERIM_OK) st = dev_alloc(g, (void**)&g->d_counters, sizeof(RRCounters));
+    if (st == HYPERIM_OK) st = dev_alloc(g, (void**)&g->d_counters, 2 * sizeof(RRCounters));
     if (st == HYPERIM_OK) {
         cudaMemsetAsync(g->d_status, 0, sizeof(DevStatus), g->stream);
         st = build_graph(g, a->he_off, a->he_mem, nnz_in, a->ptrs_on_device != 0);
@@ -231,7 +231,7 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
 void hyperim_graph_free(hyperim_graph_t g) {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
-    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off, g->prof, g->deg,
+    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off, g->prof, g->cdf_tab, g->deg,
                     g->stratum, g->vs_off, g->vs_list, g->d_status, g->d_counters, g->scratch.list,
                     g->scratch.bitmap, g->scratch.big, g->scratch.picks, g->scratch.arena};
     for (void* p : ptrs)
@@ -304,6 +304,17 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
     p->strategy = strategy;
     *out = p;
     return HYPERIM_OK;
+}
+
+// R1 and R2 of a BRR round grow by the same allocation: one launch generates both
+static hyperim_status pool_grow_pair(hyperim_graph* g, hyperim_pool* r1, hyperim_pool* r2, uint64_t theta) {
+    uint64_t ns[2][HYPERIM_NSTRATA];
+    hyperim_pool* pools[2] = {r1, r2};
+    for (int q = 0; q < 2; ++q) {
+        allocate_strata(g, pools[q]->root_mode, theta, ns[q]);
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) ns[q][s] = std::max(ns[q][s], pools[q]->n_s[s]);
+    }
+    return sample_rr_multi(g, pools, 2, ns);
 }
 
 static hyperim_status pool_grow(hyperim_graph* g, hyperim_pool* p, uint64_t theta) {
@@ -427,8 +438,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         if (opts->theta_cap && theta > opts->theta_cap)
             return set_error(HYPERIM_EOVERFLOW, "theta_i = " + std::to_string(theta) + " exceeds theta_cap");
         auto t0 = clk::now();
-        if ((st = pool_grow(g, r1, theta))) return st;
-        if ((st = pool_grow(g, r2, theta))) return st;
+        if ((st = pool_grow_pair(g, r1, r2, theta))) return st;
         auto t1 = clk::now();
         if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1))) return st;
         if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;

@@ -143,15 +143,20 @@ static __device__ __noinline__ uint32_t poisson_part(double lam, uint32_t n, uin
     return n;
 }
 
-// The first four thresholds T_0..T_3 of the inversion computed by binomial_h (poisson = false) or
-// by a single-part poisson_part (poisson = true), by the same IEEE operation sequence, each capped
-// at 2^32 - 1. Where a pmf term underflows the CDF stops moving and later thresholds repeat the
-// last one. A draw w < T_k (least such k < min(4, n)) has h = k exactly; otherwise the full
-// inversion decides.
-__device__ __forceinline__ void cdf_first4(uint32_t n, uint64_t thr, bool poisson, uint32_t T[4]) {
-    double P, cum, r = 0.0, lam = 0.0;
+// Thresholds T_0, T_1, ... of one inversion -- Binomial(n, p) as in binomial_h, or one
+// Poisson(lam) part as in poisson_part -- computed by the same IEEE operation sequence and capped
+// at 2^32 - 1. The table stops after T_{n-1}, where a pmf term underflows (the CDF is constant
+// from there), once T_h >= kTailStop (the remaining mass is below 2^-16) or at cap entries.
+// Returns the number of entries; writes them to T unless T is null. A draw w with w < T_k for a
+// least k in the table has h = k; w >= the last entry means h = n if the table has n entries,
+// otherwise the inversion itself must decide.
+constexpr uint32_t kTailStop = 0xFFFF0000u;
+constexpr uint32_t kTableCap = 64;
+
+__device__ __forceinline__ uint32_t cdf_table(uint32_t n, uint64_t thr, bool poisson, double lam,
+                                              uint32_t cap, uint32_t* T) {
+    double P, r = 0.0;
     if (poisson) {
-        lam = poisson_lambda(n, thr);
         P = exp_neg(lam);
     } else {
         const double p = __dmul_rn((double)thr, 0x1p-32);
@@ -160,22 +165,32 @@ __device__ __forceinline__ void cdf_first4(uint32_t n, uint64_t thr, bool poisso
         for (uint32_t i = 0; i < n; ++i) P = __dmul_rn(P, q);
         r = __ddiv_rn(p, q);
     }
-    cum = P;
-    bool dead = false;
-    for (uint32_t k = 0; k < 4; ++k) {
-        if (k > 0 && !dead) {
-            if (poisson) {
-                P = __ddiv_rn(__dmul_rn(P, lam), (double)k);
-            } else {
-                const uint32_t h = k - 1;
-                P = __dmul_rn(__ddiv_rn(__dmul_rn(P, (double)(n - h)), (double)(h + 1)), r);
-            }
-            if (P == 0.0) dead = true;
-            else cum = __dadd_rn(cum, P);
+    double cum = P;
+    uint32_t L = 0;
+    for (uint32_t k = 0; k < n && L < cap; ++k) {
+        if (k > 0) {
+            P = poisson ? __ddiv_rn(__dmul_rn(P, lam), (double)k)
+                        : __dmul_rn(__ddiv_rn(__dmul_rn(P, (double)(n - (k - 1))), (double)k), r);
+            if (P == 0.0) break;
+            cum = __dadd_rn(cum, P);
         }
         const uint64_t t = cdf_thr(cum);
-        T[k] = (uint32_t)(t > 0xFFFFFFFFull ? 0xFFFFFFFFull : t);
+        const uint32_t tk = (uint32_t)(t > 0xFFFFFFFFull ? 0xFFFFFFFFull : t);
+        if (T) T[L] = tk;
+        ++L;
+        if (tk >= kTailStop) break;
     }
+    return L;
+}
+
+// least k < L with w < T[k] (T non-decreasing), or L
+__device__ __forceinline__ uint32_t table_find(const uint32_t* __restrict__ T, uint32_t L, uint32_t w) {
+    uint32_t lo = 0, hi = L;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (w < T[mid]) hi = mid; else lo = mid + 1;
+    }
+    return lo;
 }
 
 // P(h = 0) threshold for the (unsplit or first split) Poisson strategy: the whole draw is 0 iff

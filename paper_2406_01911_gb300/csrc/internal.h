@@ -33,13 +33,13 @@ struct RRCounters {
 };
 
 // Profile entry of layer i of A(mu): 32 bytes, two uint4.
-//   [0].x: w_i | (p == 1 ? 1u << 31 : 0)
-//   [0].y: n_i
-//   [0].z: floor(p 2^32) for 0 <= p < 1
-//   [0].w: T_0     [1].x, .y, .z: T_1, T_2, T_3     [1].w: 1 if T_0..T_3 are valid
-// T_k is the k-th CDF threshold of the layer's inversion under the paper's strategy (Binomial if
-// n_i <= 20, single-part Poisson if n_i > 20 and lambda <= 64), capped at 2^32 - 1: a draw whose
-// first word lies below T_k (least k < min(4, n_i)) has h = k without any floating point.
+//   [0] = {w_i | (p == 1 ? 1u << 31 : 0), n_i, floor(p 2^32) for 0 <= p < 1, T_0}
+//   [1] = {offset of the layer's CDF table, table length L, Poisson parts c, kind}
+// kind 0: no draw (p = 0 or p = 1); 1: Binomial (n_i <= 20); 2: Poisson with c parts of lambda/c
+// (the paper's strategy for n_i > 20). The table holds the inversion's thresholds T_0..T_{L-1}
+// (capped at 2^32 - 1), computed at load by the same IEEE sequence as the inversion: a draw below
+// some T_k is decided by a table search; only draws beyond the table's last entry (a tail of
+// probability < 2^-16) run the double-precision inversion.
 constexpr uint32_t kPOneFlag = 0x80000000u;
 
 struct Scratch {
@@ -81,6 +81,8 @@ struct hyperim_graph {
     // layer profile
     int32_t* prof_off = nullptr; // n + 1
     uint4* prof = nullptr;       // profile entries (two uint4 per layer)
+    uint32_t* cdf_tab = nullptr; // CDF threshold tables of all layers
+    int64_t table_entries = 0;
     int32_t* deg = nullptr;      // n
     uint8_t* stratum = nullptr;  // n
     int32_t* vs_off = nullptr;   // 17
@@ -143,8 +145,10 @@ hyperim_status exclusive_scan_u32_to_i64(hyperim_graph* g, const uint32_t* in, i
                                          int64_t n);
 hyperim_status exclusive_scan_i64(hyperim_graph* g, const int64_t* in, int64_t* out, int64_t n);
 
-// rr.cu
+// rr.cu: grow one pool, or several pools of the same root mode and strategy in one launch
 hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]);
+hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
+                               const uint64_t (*new_ns)[HYPERIM_NSTRATA]);
 
 // greedy.cu
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,

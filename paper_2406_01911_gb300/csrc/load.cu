@@ -333,12 +333,16 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
     }
 }
 
-// ---- layer profile: pass 2 (thresholds and the h = 0 shortcut) ---------------------------------
+// ---- layer profile: pass 2 (thresholds, inversion kind, CDF table lengths) ------------------
+// Entry [0] = {w_i | p = 1 flag, n_i, floor(p 2^32), T_0}; entry [1] = {table offset, table
+// length, Poisson parts c, kind}; kind 0: no draw (p = 0 or 1), 1: Binomial (n_i <= 20), 2:
+// Poisson with c parts of lambda / c each (Sec. 3.1.3). The table and T_0 are filled by pass 3.
 __global__ void k_profile_write(int32_t n, const int32_t* __restrict__ v_off,
                                 const uint2* __restrict__ pairs, const int64_t* __restrict__ poff64,
                                 const uint32_t* __restrict__ deg, int32_t model, uint64_t uthr,
                                 const double* __restrict__ ln_l1, uint4* __restrict__ prof,
-                                int32_t* __restrict__ prof_off, uint8_t* __restrict__ stratum) {
+                                uint32_t* __restrict__ tab_len, int32_t* __restrict__ prof_off,
+                                uint8_t* __restrict__ stratum) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pb = poff64[v];
@@ -361,22 +365,46 @@ __global__ void k_profile_write(int32_t n, const int32_t* __restrict__ v_off,
                 const double pd = __ddiv_rn(PL, (double)n_i);
                 thr = pd >= 1.0 ? kPOne : __double2ull_rz(__dmul_rn(pd, 4294967296.0));
             }
-            uint32_t flags = 0, valid = 0;
-            uint32_t T[4] = {0, 0, 0, 0};
+            uint32_t flags = 0, kind = 0, c = 0, L = 0;
             if (thr >= kPOne) {
                 flags = kPOneFlag;
             } else if (thr > 0) {
                 if (n_i <= 20) {
-                    cdf_first4(n_i, thr, false, T);
-                    valid = 1;
-                } else if (poisson_parts(poisson_lambda(n_i, thr)) == 1) {
-                    cdf_first4(n_i, thr, true, T);
-                    valid = 1;
+                    kind = 1;
+                    c = 1;
+                    L = cdf_table(n_i, thr, false, 0.0, kTableCap, nullptr);
+                } else {
+                    kind = 2;
+                    const double lam = poisson_lambda(n_i, thr);
+                    c = poisson_parts(lam);
+                    L = cdf_table(n_i, thr, true, poisson_part_lambda(lam, c), kTableCap, nullptr);
                 }
             }
-            prof[2 * (pb + i)] = make_uint4(wn.x | flags, n_i, thr >= kPOne ? 0u : (uint32_t)thr, T[0]);
-            prof[2 * (pb + i) + 1] = make_uint4(T[1], T[2], T[3], valid);
+            prof[2 * (pb + i)] = make_uint4(wn.x | flags, n_i, thr >= kPOne ? 0u : (uint32_t)thr, 0u);
+            prof[2 * (pb + i) + 1] = make_uint4(0u, L, c, kind);
+            tab_len[pb + i] = L;
         }
+    }
+}
+
+// ---- layer profile: pass 3 (CDF threshold tables) -----------------------------------------------
+__global__ void k_table_fill(int64_t layers, const int64_t* __restrict__ tab_off, uint4* __restrict__ prof,
+                             uint32_t* __restrict__ tab) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < layers;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        uint4 a = prof[2 * x], b = prof[2 * x + 1];
+        const uint32_t n_i = a.y, kind = b.w;
+        const uint32_t off = (uint32_t)tab_off[x];
+        b.x = off;
+        if (kind == 1) {
+            cdf_table(n_i, a.z, false, 0.0, kTableCap, tab + off);
+        } else if (kind == 2) {
+            const double lam = poisson_lambda(n_i, a.z);
+            cdf_table(n_i, a.z, true, poisson_part_lambda(lam, b.z), kTableCap, tab + off);
+        }
+        a.w = b.y > 0 ? tab[off] : 0u;  // T_0 beside the entry: the common h = 0 needs no table read
+        prof[2 * x] = a;
+        prof[2 * x + 1] = b;
     }
 }
 
@@ -577,9 +605,26 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&d_ln, sizeof(double) * ln_l1.size()))) return st;
     HYP_CUDA(cudaMemcpyAsync(d_ln, ln_l1.data(), sizeof(double) * ln_l1.size(),
                              cudaMemcpyHostToDevice, s));
+    uint32_t* d_tlen = nullptr;
+    int64_t* d_toff = nullptr;
+    const size_t Lalloc = (size_t)(L > 0 ? L : 1);
+    if ((st = dev_alloc(g, (void**)&d_tlen, sizeof(uint32_t) * Lalloc))) return st;
+    if ((st = dev_alloc(g, (void**)&d_toff, sizeof(int64_t) * (Lalloc + 1)))) return st;
     { k_profile_write<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, d_pairs, d_poff64, d_deg,
                                                          g->model, g->uniform_thr, d_ln, g->prof,
-                                                         g->prof_off, g->stratum); count_launch(); }
+                                                         d_tlen, g->prof_off, g->stratum); count_launch(); }
+    if ((st = exclusive_scan_u32_to_i64(g, d_tlen, d_toff, L))) return st;
+    int64_t tab_total = 0;
+    HYP_CUDA(cudaMemcpyAsync(&tab_total, d_toff + L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    if (tab_total >= (int64_t)0xFFFFFFFFll) return set_error(HYPERIM_EOVERFLOW, "CDF tables exceed 2^32 entries");
+    g->table_entries = tab_total;
+    if ((st = dev_alloc(g, (void**)&g->cdf_tab, sizeof(uint32_t) * (size_t)(tab_total > 0 ? tab_total : 1))))
+        return st;
+    if (L > 0)
+        { k_table_fill<<<grid_for(L, 256, sm), 256, 0, s>>>(L, d_toff, g->prof, g->cdf_tab); count_launch(); }
+    dev_free(g, d_tlen, sizeof(uint32_t) * Lalloc);
+    dev_free(g, d_toff, sizeof(int64_t) * (Lalloc + 1));
 
     // --- theta(l*) from the histogram of l (Thm 2)
     const int hcap = g->max_layers + 1;

@@ -204,13 +204,22 @@ __device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
         }
         Gr::sync();
         const int total = pre[cnt];
+        // positions of a thread increase by G: when hyperedges are long compared with G the
+        // hyperedge index is advanced step by step, otherwise found by binary search
+        const bool stepwise = total >= cnt * (G / 4);
+        int j = 0;
         for (int p = r; p < total; p += G) {
-            int lo = 0, hi = cnt;  // j with pre[j] <= p < pre[j + 1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pre[mid] <= p) lo = mid; else hi = mid;
+            if (stepwise && p != r) {
+                while (pre[j + 1] <= p) ++j;
+            } else {
+                int lo = 0, hi = cnt;  // j with pre[j] <= p < pre[j + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid] <= p) lo = mid; else hi = mid;
+                }
+                j = lo;
             }
-            const uint32_t x = (uint32_t)he_mem[start[lo] + (p - pre[lo])];
+            const uint32_t x = (uint32_t)he_mem[start[j] + (p - pre[j])];
             if (x != (uint32_t)mu) f(x);
         }
         Gr::sync();

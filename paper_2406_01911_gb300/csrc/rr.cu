@@ -35,6 +35,7 @@ constexpr int kWBucketBits = 8;
 constexpr int kWBuckets = 1 << kWBucketBits;  // warp-path buckets
 constexpr int kChunks = 1024;        // first-level id chunks of the largest neighbourhoods
 constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
+constexpr int kMaxPools = 2;           // pools grown by one launch (R1 and R2 of a BRR round)
 
 struct RRJobMap {
     int64_t job_base[HYPERIM_NSTRATA + 1];
@@ -47,17 +48,19 @@ struct RRParams {
     const int32_t* he_mem;
     const int32_t* prof_off;
     const uint4* prof;
+    const uint32_t* tab;      // CDF threshold tables
     const int32_t* tsum;
     const int32_t* vs_off;
     const int32_t* vs_list;
     int32_t n;
     int id_bits;
     uint64_t seed;
-    uint32_t tag;
     int root_mode;
     int strategy;
-    int64_t job_base[HYPERIM_NSTRATA + 1];
-    uint32_t j_base[HYPERIM_NSTRATA];
+    int npools;                              // pools grown by this launch (same root mode/strategy)
+    int64_t pool_start[kMaxPools + 1];       // jobs of pool q: [pool_start[q], pool_start[q + 1])
+    uint32_t tags[kMaxPools];
+    RRJobMap jm[kMaxPools];
     int32_t* list;            // per block: list_cap entries
     int64_t list_cap;
     uint32_t* gvis;           // per block: vis_words (when not on chip)
@@ -74,7 +77,7 @@ struct RRParams {
     int32_t* out_size;
     int* next_job;
     DevStatus* st;
-    RRCounters* counters;
+    RRCounters* counters;                    // kMaxPools entries
 };
 
 struct Need {                    // a layer with h > 0 at the current pop
@@ -97,7 +100,8 @@ struct BlockArea {
 struct Shared {
     int ctrl[16];
     int tmp[kWarps + 2];
-    unsigned long long stat[8];
+    unsigned long long stat[kMaxPools][8];  // per pool work counters of this block
+    unsigned long long wstat[kWarps][8];    // per-warp counters of the current RR set (lane 0)
     unsigned long long out_pos;
     int32_t deferred[kDCap];
     Need wneed[kWarps][kLQ];
@@ -124,36 +128,40 @@ __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t de
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
 }
 
-// h for one layer (lane-level) from its two profile words. Returns whether a draw was made
-// (0 < p < 1). Draws below one of the layer's first four CDF thresholds are decided by integer
-// compares; the rest run the double-precision inversion.
-__device__ __forceinline__ bool layer_draw(const uint4 e, const uint4 f, int strategy, WordStream& ws,
-                                          uint32_t& h, uint32_t& ksel) {
+// h for one layer (lane-level) from its two profile words and its CDF table. Returns whether a
+// draw was made (0 < p < 1). The draw is decided by integer compares against the layer's table
+// (T_0 first, which sits in the entry); only words beyond the table's last threshold run the
+// double-precision inversion.
+__device__ __forceinline__ bool layer_draw(const uint4 e, const uint4 f, const uint32_t* __restrict__ tab,
+                                          int strategy, WordStream& ws, uint32_t& h, uint32_t& ksel) {
     const uint32_t n_i = e.y, thr = e.z;
     ksel = 0;
     if (e.x & kPOneFlag) { h = n_i; return false; }
     if (thr == 0) { h = 0; return false; }
     const uint32_t w0 = ws.word(0);
-    const bool binom = n_i <= 20 || strategy == HYPERIM_STRAT_BINOMIAL_ONLY;
-    if (f.w != 0 && (n_i <= 20 || strategy == HYPERIM_STRAT_PAPER)) {
-        // least k < min(4, n_i) with w0 < T_k (thresholds are non-decreasing)
-        const uint32_t k = (w0 >= e.w) + (n_i > 1 && w0 >= f.x) + (n_i > 2 && w0 >= f.y) +
-                           (n_i > 3 && w0 >= f.z);
-        if (k < 4 && k < n_i) { h = k; ksel = 1; return true; }
-        if (n_i <= 4) { h = n_i; ksel = 1; return true; }
-    }
-    if (binom) {
-        h = binomial_h(n_i, thr, w0);
+    const uint32_t kind = f.w, L = f.y, c = f.z;
+    if (kind == 1) {  // Binomial table: the same draw under both strategies (n_i <= 20)
         ksel = 1;
+        if (w0 < e.w) { h = 0; return true; }
+        const uint32_t k = table_find(tab + f.x, L, w0);
+        h = k < L ? k : (L == n_i ? n_i : binomial_h(n_i, thr, w0));
         return true;
     }
-    const double lam = poisson_lambda(n_i, thr);
-    const uint32_t c = poisson_parts(lam);
-    const double part = poisson_part_lambda(lam, c);
-    uint64_t sum = 0;
-    for (uint32_t t = 0; t < c; ++t) sum += poisson_part(part, n_i, t == 0 ? w0 : ws.word(t));
-    h = sum > n_i ? n_i : (uint32_t)sum;
-    ksel = c;
+    if (strategy == HYPERIM_STRAT_PAPER) {  // Poisson, c parts (kind 2)
+        ksel = c;
+        if (c == 1 && w0 < e.w) { h = 0; return true; }
+        uint64_t sum = 0;
+        for (uint32_t t = 0; t < c; ++t) {
+            const uint32_t w = t == 0 ? w0 : ws.word(t);
+            const uint32_t k = table_find(tab + f.x, L, w);
+            sum += k < L ? k
+                 : (L == n_i ? n_i : poisson_part(poisson_part_lambda(poisson_lambda(n_i, thr), c), n_i, w));
+        }
+        h = sum > n_i ? n_i : (uint32_t)sum;
+        return true;
+    }
+    h = binomial_h(n_i, thr, w0);  // Binomial strategy on a layer the paper draws by Poisson
+    ksel = 1;
     return true;
 }
 
@@ -220,12 +228,13 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
 // ------------------------------------------------------------------------------------------
 // Returns true when the pop must be handed to the block path.
 __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
-                         uint32_t ybase, int32_t mu, bool count_stats) {
+                         uint32_t ybase, int32_t mu) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 vi = P.vinfo[mu];
     const int32_t pb = vi.x, l = vi.y, v_begin = vi.z, dh = vi.w;
     Need* need = S.wneed[wid];
     uint32_t nneed = 0, ndraw = 0;
+    uint32_t hsum = 0;  // sum of h over the layers <= deg(mu) < 2^31
     for (int c0 = 0; c0 < l; c0 += 32) {
         const int i = c0 + lane;
         uint32_t h = 0, ksel = 0;
@@ -236,28 +245,31 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
             const uint4 f = P.prof[2 * (pb + i) + 1];
             WordStream ws;
             ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
-            drew = layer_draw(e, f, P.strategy, ws, h, ksel);
+            drew = layer_draw(e, f, P.tab, P.strategy, ws, h, ksel);
         }
         const bool flag = h > 0;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
         const uint32_t pos = nneed + __popc(bal & lanemask_lt());
         if (flag && pos < kLQ) need[pos] = Need{e.x & ~kPOneFlag, e.y, h, ksel, (uint32_t)(i + 1)};
-        if (flag && count_stats) atomicAdd(&S.stat[S_SEL], (unsigned long long)h);
+        hsum += h;
         nneed += __popc(bal);
         ndraw += __popc(__ballot_sync(0xFFFFFFFFu, drew));
     }
     __syncwarp();
-    if (count_stats && lane == 0) {
-        atomicAdd(&S.stat[S_POPS], 1ull);
-        atomicAdd(&S.stat[S_LAYERS], (unsigned long long)l);
-        atomicAdd(&S.stat[S_DRAWS], (unsigned long long)ndraw);
+    unsigned long long* wst = S.wstat[wid];
+    if (lane == 0) {
+        wst[S_POPS] += 1;
+        wst[S_LAYERS] += (unsigned long long)l;
+        wst[S_DRAWS] += ndraw;
     }
     if (nneed == 0) return false;
+    hsum = __reduce_add_sync(0xFFFFFFFFu, hsum);
     const int32_t tsum = P.tsum[mu];
-    if (count_stats && lane == 0) {
-        atomicAdd(&S.stat[S_MATS], 1ull);
-        atomicAdd(&S.stat[S_MAT_HE], (unsigned long long)dh);
-        atomicAdd(&S.stat[S_MAT_MEM], (unsigned long long)tsum);
+    if (lane == 0) {
+        wst[S_SEL] += hsum;
+        wst[S_MATS] += 1;
+        wst[S_MAT_HE] += (unsigned long long)dh;
+        wst[S_MAT_MEM] += (unsigned long long)tsum;
     }
     if (nneed > kLQ) return true;
     // picks for every needed layer (none when h = n)
@@ -453,7 +465,7 @@ __device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
                     const uint4 f = P.prof[2 * (pb + i) + 1];
                     WordStream ws;
                     ws.init(P.seed, j, ybase, (uint32_t)mu, (uint32_t)(i + 1));
-                    layer_draw(e, f, P.strategy, ws, h, ksel);
+                    layer_draw(e, f, P.tab, P.strategy, ws, h, ksel);
                 }
                 const bool flag = h > 0;
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, flag);
@@ -613,20 +625,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     uint32_t* picks_g = P.picks + (int64_t)blockIdx.x * P.pick_cap;
     uint32_t* big = P.big + (int64_t)blockIdx.x * P.big_cap;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t njobs = P.job_base[HYPERIM_NSTRATA];
-    if (threadIdx.x < 8) S.stat[threadIdx.x] = 0;
+    const int64_t njobs = P.pool_start[P.npools];
+    if (threadIdx.x < kMaxPools * 8) (&S.stat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kWarps * 8) (&S.wstat[0][0])[threadIdx.x] = 0;
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
     for (;;) {
+        // jobs are handed out from the last one down: strata ascend with the job index, and the
+        // high strata (roots with many layers, usually the costliest sets) should start first so
+        // that cheap sets fill the end of the launch
         if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job, 1);
         __syncthreads();
-        const int64_t job = S.ctrl[C_JOB];
-        if (job >= njobs) break;
+        const int64_t ticket = S.ctrl[C_JOB];
+        if (ticket >= njobs) break;
+        const int64_t job = njobs - 1 - ticket;
+        int pi = 0;
+        while (pi + 1 < P.npools && job >= P.pool_start[pi + 1]) ++pi;
+        const RRJobMap& jm = P.jm[pi];
+        const int64_t local = job - P.pool_start[pi];
         int s = 0;
-        while (s < HYPERIM_NSTRATA - 1 && job >= P.job_base[s + 1]) ++s;
-        const uint32_t j = P.j_base[s] + (uint32_t)(job - P.job_base[s]);
+        while (s < HYPERIM_NSTRATA - 1 && local >= jm.job_base[s + 1]) ++s;
+        const uint32_t j = jm.j_base[s] + (uint32_t)(local - jm.job_base[s]);
         const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)s;
-        const uint32_t ybase = stream_ybase(P.tag, sfield);
+        const uint32_t ybase = stream_ybase(P.tags[pi], sfield);
         if (threadIdx.x == 0) {
             // root: uniform over the stratum (multiply-shift of one word)
             WordStream ws;
@@ -666,7 +687,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
                     idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
                     if (idx >= level_end) break;
                     const int32_t mu = list[idx];
-                    const bool defer = pop_warp(P, S, vis, list, j, ybase, mu, true);
+                    const bool defer = pop_warp(P, S, vis, list, j, ybase, mu);
                     if (defer && lane == 0) S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
                     __syncwarp();
                 }
@@ -682,6 +703,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
             }
             if (threadIdx.x == 0) S.ctrl[C_HEAD] = level_end;
             __syncthreads();
+        }
+        // work counters of this RR set go to its pool
+        if (threadIdx.x < 8) {
+            unsigned long long sum = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                sum += S.wstat[w][threadIdx.x];
+                S.wstat[w][threadIdx.x] = 0;
+            }
+            S.stat[pi][threadIdx.x] += sum;
         }
         // output: members in ascending order
         const int size = S.ctrl[C_TAIL];
@@ -743,14 +773,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
         __syncthreads();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&P.counters->pops, S.stat[S_POPS]);
-        atomicAdd(&P.counters->layers_seen, S.stat[S_LAYERS]);
-        atomicAdd(&P.counters->draws, S.stat[S_DRAWS]);
-        atomicAdd(&P.counters->mats, S.stat[S_MATS]);
-        atomicAdd(&P.counters->mat_he, S.stat[S_MAT_HE]);
-        atomicAdd(&P.counters->mat_members, S.stat[S_MAT_MEM]);
-        atomicAdd(&P.counters->selected, S.stat[S_SEL]);
+    if (threadIdx.x < P.npools) {
+        RRCounters* c = P.counters + threadIdx.x;
+        const unsigned long long* st = S.stat[threadIdx.x];
+        atomicAdd(&c->pops, st[S_POPS]);
+        atomicAdd(&c->layers_seen, st[S_LAYERS]);
+        atomicAdd(&c->draws, st[S_DRAWS]);
+        atomicAdd(&c->mats, st[S_MATS]);
+        atomicAdd(&c->mat_he, st[S_MAT_HE]);
+        atomicAdd(&c->mat_members, st[S_MAT_MEM]);
+        atomicAdd(&c->selected, st[S_SEL]);
     }
 }
 
@@ -830,19 +862,31 @@ hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
 
 }  // namespace
 
-hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]) {
-    RRJobMap jm;
-    jm.job_base[0] = 0;
-    for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
-        const uint64_t old = p->n_s[s];
-        const uint64_t add = new_ns[s] > old ? new_ns[s] - old : 0;
-        if (new_ns[s] > 0xFFFFFFFFull)
-            return set_error(HYPERIM_EOVERFLOW, "an RR index within a stratum would reach 2^32");
-        jm.j_base[s] = (uint32_t)old;
-        jm.job_base[s + 1] = jm.job_base[s] + (int64_t)add;
+hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
+                               const uint64_t (*new_ns)[HYPERIM_NSTRATA]) {
+    if (npools < 1 || npools > kMaxPools) return set_error(HYPERIM_EINVAL, "bad pool count");
+    for (int q = 1; q < npools; ++q)
+        if (pools[q]->root_mode != pools[0]->root_mode || pools[q]->strategy != pools[0]->strategy)
+            return set_error(HYPERIM_ESTATE, "pools grown together must share root mode and strategy");
+    RRJobMap jm[kMaxPools];
+    int64_t pool_start[kMaxPools + 1];
+    pool_start[0] = 0;
+    for (int q = 0; q < npools; ++q) {
+        hyperim_pool* p = pools[q];
+        jm[q].job_base[0] = 0;
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+            const uint64_t old = p->n_s[s];
+            const uint64_t add = new_ns[q][s] > old ? new_ns[q][s] - old : 0;
+            if (new_ns[q][s] > 0xFFFFFFFFull)
+                return set_error(HYPERIM_EOVERFLOW, "an RR index within a stratum would reach 2^32");
+            jm[q].j_base[s] = (uint32_t)old;
+            jm[q].job_base[s + 1] = jm[q].job_base[s] + (int64_t)add;
+        }
+        pool_start[q + 1] = pool_start[q] + jm[q].job_base[HYPERIM_NSTRATA];
     }
-    const int64_t njobs = jm.job_base[HYPERIM_NSTRATA];
+    const int64_t njobs = pool_start[npools];
     if (njobs == 0) return HYPERIM_OK;
+    if (njobs >= (int64_t)0x7FFFFFFF) return set_error(HYPERIM_EOVERFLOW, "too many RR sets in one growth step");
     cudaStream_t s = g->stream;
     hyperim_status st;
 
@@ -857,9 +901,13 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     if ((int64_t)blocks > njobs) blocks = (int)njobs;
     if ((st = ensure_scratch(g, blocks, vis_smem))) return st;
 
-    // output arena sized from the pool's running mean set size, grown and relaunched on overflow
-    double hint = p->mean_size_hint > 0 ? p->mean_size_hint : 8.0;
-    uint64_t want = (uint64_t)((double)njobs * hint * 1.25) + 4096;
+    // output arena sized from the pools' running mean set size, relaunched on overflow
+    double want_d = 4096.0;
+    for (int q = 0; q < npools; ++q) {
+        const double hint = pools[q]->mean_size_hint > 0 ? pools[q]->mean_size_hint : 8.0;
+        want_d += (double)(pool_start[q + 1] - pool_start[q]) * hint * 1.25;
+    }
+    uint64_t want = (uint64_t)want_d;
     int64_t* d_pos = nullptr;
     int32_t* d_size = nullptr;
     int* d_next = nullptr;
@@ -874,17 +922,21 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     P.he_mem = g->he_mem;
     P.prof_off = g->prof_off;
     P.prof = g->prof;
+    P.tab = g->cdf_tab;
     P.tsum = g->tsum;
     P.vs_off = g->vs_off;
     P.vs_list = g->vs_list;
     P.n = g->n;
     P.id_bits = g->id_bits;
     P.seed = g->seed;
-    P.tag = p->tag;
-    P.root_mode = p->root_mode;
-    P.strategy = p->strategy;
-    for (int i = 0; i <= HYPERIM_NSTRATA; ++i) P.job_base[i] = jm.job_base[i];
-    for (int i = 0; i < HYPERIM_NSTRATA; ++i) P.j_base[i] = jm.j_base[i];
+    P.root_mode = pools[0]->root_mode;
+    P.strategy = pools[0]->strategy;
+    P.npools = npools;
+    for (int q = 0; q <= npools; ++q) P.pool_start[q] = pool_start[q];
+    for (int q = 0; q < npools; ++q) {
+        P.tags[q] = pools[q]->tag;
+        P.jm[q] = jm[q];
+    }
     P.list = g->scratch.list;
     P.list_cap = (int64_t)g->scratch.list_cap;
     P.gvis = g->scratch.bitmap;
@@ -904,6 +956,8 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     HYP_CUDA(cudaEventCreate(&ev0));
     HYP_CUDA(cudaEventCreate(&ev1));
+    double seconds = 0.0;
+    int launches = 0;
     for (int attempt = 0; attempt < 3; ++attempt) {
         if (g->scratch.arena_cap < want) {
             if (g->scratch.arena) dev_free(g, g->scratch.arena, sizeof(int32_t) * g->scratch.arena_cap);
@@ -915,7 +969,7 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
         P.arena = g->scratch.arena;
         P.arena_cap = g->scratch.arena_cap;
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int) + sizeof(unsigned long long) * 2, s));
-        HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters), s));
+        HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
         HYP_CUDA(cudaEventRecord(ev0, s));
         { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
         HYP_CUDA(cudaGetLastError());
@@ -924,51 +978,67 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
         if ((st = check_device_status(g, "RR generation"))) return st;
         float ms = 0.f;
         HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-        p->rr_kernel_seconds += 1e-3 * (double)ms;
-        p->rr_launches += 1;
+        seconds += 1e-3 * (double)ms;
+        ++launches;
         if (used <= g->scratch.arena_cap) break;
         want = used + used / 8 + 4096;
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     if (used > g->scratch.arena_cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
-    RRCounters c;
-    HYP_CUDA(cudaMemcpyAsync(&c, g->d_counters, sizeof(c), cudaMemcpyDeviceToHost, s));
-    // compaction: CSR offsets by an exclusive scan of the sizes
+    RRCounters c[kMaxPools];
+    HYP_CUDA(cudaMemcpyAsync(c, g->d_counters, sizeof(RRCounters) * kMaxPools, cudaMemcpyDeviceToHost, s));
+    // compaction, pool by pool: CSR offsets by an exclusive scan of the sizes
     int64_t* d_boff = nullptr;
     if ((st = dev_alloc(g, (void**)&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
-    if ((st = exclusive_scan_u32_to_i64(g, reinterpret_cast<const uint32_t*>(d_size), d_boff, njobs)))
-        return st;
-    int64_t btotal = 0;
-    HYP_CUDA(cudaMemcpyAsync(&btotal, d_boff + njobs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    HYP_CUDA(cudaStreamSynchronize(s));
-    const size_t new_count = (size_t)(p->count + njobs), new_total = (size_t)(p->total + btotal);
-    if ((st = grow_array(g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
-        return st;
-    if ((st = grow_array(g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
-    if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
-    if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
-    const int grid = (int)std::min<int64_t>((njobs * 32 + 255) / 256, (int64_t)g->sm_count * 32);
-    { k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos, d_boff, njobs, p->count, p->total, jm,
-                                      p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
-    HYP_CUDA(cudaGetLastError());
+    for (int q = 0; q < npools; ++q) {
+        hyperim_pool* p = pools[q];
+        const int64_t b0 = pool_start[q], nq = pool_start[q + 1] - b0;
+        if (nq > 0) {
+            if ((st = exclusive_scan_u32_to_i64(g, reinterpret_cast<const uint32_t*>(d_size + b0), d_boff, nq)))
+                return st;
+            int64_t btotal = 0;
+            HYP_CUDA(cudaMemcpyAsync(&btotal, d_boff + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HYP_CUDA(cudaStreamSynchronize(s));
+            const size_t new_count = (size_t)(p->count + nq), new_total = (size_t)(p->total + btotal);
+            if ((st = grow_array(g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
+                return st;
+            if ((st = grow_array(g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
+            if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
+            if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
+            const int grid = (int)std::min<int64_t>((nq * 32 + 255) / 256, (int64_t)g->sm_count * 32);
+            { k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos + b0, d_boff, nq, p->count, p->total,
+                                                jm[q], p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
+            HYP_CUDA(cudaGetLastError());
+            for (int i = 0; i < HYPERIM_NSTRATA; ++i)
+                if (new_ns[q][i] > p->n_s[i]) p->n_s[i] = new_ns[q][i];
+            p->count = (int64_t)new_count;
+            p->total = (int64_t)new_total;
+            p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
+        }
+        p->counters.pops += c[q].pops;
+        p->counters.layers_seen += c[q].layers_seen;
+        p->counters.draws += c[q].draws;
+        p->counters.mats += c[q].mats;
+        p->counters.mat_he += c[q].mat_he;
+        p->counters.mat_members += c[q].mat_members;
+        p->counters.selected += c[q].selected;
+        // the launch's time and count are shared by the pools it grew, in proportion to their jobs
+        const double share = (double)nq / (double)njobs;
+        p->rr_kernel_seconds += seconds * share;
+        if (q == 0) p->rr_launches += (uint64_t)launches;
+    }
     dev_free(g, d_boff, sizeof(int64_t) * ((size_t)njobs + 1));
     dev_free(g, d_pos, sizeof(int64_t) * (size_t)njobs);
     dev_free(g, d_size, sizeof(int32_t) * (size_t)njobs);
     dev_free(g, d_next, sizeof(int) + sizeof(unsigned long long) * 2);
-    for (int i = 0; i < HYPERIM_NSTRATA; ++i)
-        if (new_ns[i] > p->n_s[i]) p->n_s[i] = new_ns[i];
-    p->count = (int64_t)new_count;
-    p->total = (int64_t)new_total;
-    p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
-    p->counters.pops += c.pops;
-    p->counters.layers_seen += c.layers_seen;
-    p->counters.draws += c.draws;
-    p->counters.mats += c.mats;
-    p->counters.mat_he += c.mat_he;
-    p->counters.mat_members += c.mat_members;
-    p->counters.selected += c.selected;
     return check_device_status(g, "RR compaction");
+}
+
+hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]) {
+    hyperim_pool* pools[1] = {p};
+    const uint64_t (*ns)[HYPERIM_NSTRATA] = reinterpret_cast<const uint64_t (*)[HYPERIM_NSTRATA]>(new_ns);
+    return sample_rr_multi(g, pools, 1, ns);
 }
 
 }  // namespace hyperim
