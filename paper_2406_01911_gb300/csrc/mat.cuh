@@ -208,19 +208,31 @@ __device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
         // hyperedge index is advanced step by step, otherwise found by binary search
         const bool stepwise = total >= cnt * (G / 4);
         int j = 0;
-        for (int p = r; p < total; p += G) {
-            if (stepwise && p != r) {
-                while (pre[j + 1] <= p) ++j;
-            } else {
-                int lo = 0, hi = cnt;  // j with pre[j] <= p < pre[j + 1]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (pre[mid] <= p) lo = mid; else hi = mid;
+        // four positions per round: their loads are all issued before any result is used
+        constexpr int U = 4;
+        for (int p0 = r; p0 < total; p0 += U * G) {
+            uint32_t xs[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * G;
+                xs[u] = (uint32_t)mu;
+                if (p < total) {
+                    if (stepwise && p != r) {
+                        while (pre[j + 1] <= p) ++j;
+                    } else {
+                        int lo = 0, hi = cnt;  // j with pre[j] <= p < pre[j + 1]
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (pre[mid] <= p) lo = mid; else hi = mid;
+                        }
+                        j = lo;
+                    }
+                    xs[u] = (uint32_t)he_mem[start[j] + (p - pre[j])];
                 }
-                j = lo;
             }
-            const uint32_t x = (uint32_t)he_mem[start[j] + (p - pre[j])];
-            if (x != (uint32_t)mu) f(x);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (xs[u] != (uint32_t)mu) f(xs[u]);
         }
         Gr::sync();
     }

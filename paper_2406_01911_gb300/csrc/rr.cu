@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kWCap = 1024;      // per-warp on-chip neighbourhood keys (power of two)
+constexpr int kWCap = 2048;      // per-warp on-chip neighbourhood keys (power of two)
 constexpr int kPCap = 256;       // per-warp picks
 constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the warp path
 constexpr int kBCap = 8192;      // block on-chip keys (power of two)
@@ -890,12 +890,18 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     cudaStream_t s = g->stream;
     hyperim_status st;
 
-    const bool vis_smem = (int64_t)g->n <= kVisSmemBits;
-    const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
-    const size_t smem = sizeof(Shared) + vis_bytes;
-    HYP_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the visited bitmap goes on chip only while two blocks still fit on an SM
+    bool vis_smem = (int64_t)g->n <= kVisSmemBits;
+    size_t smem = 0;
     int per_sm = 0;
-    HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr, kThreads, smem));
+    for (;;) {
+        const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
+        smem = sizeof(Shared) + vis_bytes;
+        HYP_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr, kThreads, smem));
+        if (per_sm >= 2 || !vis_smem) break;
+        vis_smem = false;
+    }
     if (per_sm < 1) return set_error(HYPERIM_ECUDA, "RR kernel does not fit on an SM");
     int blocks = g->sm_count * per_sm;
     if ((int64_t)blocks > njobs) blocks = (int)njobs;
