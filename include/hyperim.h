@@ -112,6 +112,8 @@ typedef struct {
     int64_t stratum_size[HYPERIM_NSTRATA]; /* |V_s| */
     double theta_lstar;
     size_t device_bytes;                   /* device memory held by the graph */
+    int32_t index_vertices;                /* vertices with a chunk index (hyperim_graph_chunk_index) */
+    int64_t index_entries;                 /* uint32 entries of all chunk-index tables */
 } hyperim_graph_stats_t;
 
 hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out);
@@ -127,6 +129,20 @@ hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out
 hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* nlayers,
                                      int32_t* stratum, int64_t* prof_off, uint32_t* layer_w,
                                      uint32_t* layer_n, uint64_t* layer_thr);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_graph_chunk_index -- copy one vertex's chunk index to host (a lookup structure of this
+ *   library over the layers of Sec. 3.1.1, not a quantity of the paper).
+ *   A vertex v whose hyperedges hold more than 2048 members other than v (repeats counted) may
+ *   have one: ids are split into C = 2^bits chunks by their top bits (chunk of u = u >> (B -
+ *   bits), B = ceil(log2 n), at least 1), and table[(i - 1) C + k] = number of members of layer
+ *   L_i of A(v) whose chunk is < k (i = 1..l_v, k = 0..C-1). *bits = 0 and *entries = 0 when v
+ *   has no index. table may be NULL (then only *bits and *entries are set); otherwise it must
+ *   hold cap >= *entries = l_v C entries (EINVAL if not). EINVAL: v outside [0, n).
+ *   Synchronises the stream.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* bits,
+                                         uint32_t* table, int64_t cap, int64_t* entries);
 
 /* ------------------------------------------------------------------------------------------
  * hyperim_plan_theta -- RR budget of Sec. 4.3 (host arithmetic, IEEE double).
@@ -181,6 +197,11 @@ typedef struct {
        layer draws with 0 < p < 1, pops that materialised A(mu), hyperedges and members read by
        those materialisations, activations drawn (sum of h) */
     uint64_t pops, layers_seen, draws, mats, mat_he, mat_members, selected;
+    /* member ids the library actually read for those materialisations (one pass: sum of |he|
+       over mu's hyperedges, or only the id ranges of the chunks that hold picks when mu has a
+       chunk index), and 4-byte words read to locate those ranges (span entries, binary-search
+       probes into hyperedges, chunk-index probes) */
+    uint64_t gathered, search_words;
     uint64_t rr_launches;     /* RR-generation kernel launches that grew this pool first (a launch
                                  growing R1 and R2 of a BRR round together counts once, on R1) */
     double rr_kernel_seconds; /* this pool's share (by RR sets) of those launches' duration,

@@ -49,7 +49,8 @@ class GraphStats(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64),
                 ("profile_entries", C.c_int64), ("max_layers", C.c_int32), ("max_dh", C.c_int32),
                 ("max_deg", C.c_int64), ("stratum_size", C.c_int64 * NSTRATA),
-                ("theta_lstar", C.c_double), ("device_bytes", C.c_size_t)]
+                ("theta_lstar", C.c_double), ("device_bytes", C.c_size_t),
+                ("index_vertices", C.c_int32), ("index_entries", C.c_int64)]
 
 
 class ThetaPlan(C.Structure):
@@ -64,6 +65,7 @@ class PoolView(C.Structure):
                 ("strategy", C.c_int32), ("pops", C.c_uint64), ("layers_seen", C.c_uint64),
                 ("draws", C.c_uint64), ("mats", C.c_uint64), ("mat_he", C.c_uint64),
                 ("mat_members", C.c_uint64), ("selected", C.c_uint64),
+                ("gathered", C.c_uint64), ("search_words", C.c_uint64),
                 ("rr_launches", C.c_uint64), ("rr_kernel_seconds", C.c_double)]
 
 
@@ -88,6 +90,8 @@ _SIGNATURES = {
     "hyperim_graph_free": (None, [_vp]),
     "hyperim_graph_stats": (C.c_int, [_vp, C.POINTER(GraphStats)]),
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hyperim_graph_chunk_index": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _vp, C.c_int64,
+                                            C.POINTER(C.c_int64)]),
     "hyperim_plan_theta": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.POINTER(ThetaPlan)]),
     "hyperim_sample_rr": (C.c_int, [_vp, C.c_uint32, C.c_uint64, C.c_int32, C.c_int32,
                                     C.POINTER(_vp)]),
@@ -262,6 +266,17 @@ class Graph:
                                            _ptr(lw), _ptr(ln), _ptr(lt)))
         return {"deg": deg, "nlayers": nl, "stratum": strat, "prof_off": poff,
                 "layer_w": lw[:L], "layer_n": ln[:L], "layer_thr": lt[:L]}
+
+    def chunk_index(self, v):
+        """(bits, table[l_v, 2^bits]) of vertex v's chunk index, or (0, None) if it has none."""
+        bits, entries = C.c_int32(), C.c_int64()
+        _check(lib().hyperim_graph_chunk_index(self._h, int(v), C.byref(bits), None, 0, C.byref(entries)))
+        if entries.value == 0:
+            return 0, None
+        tab = np.zeros(entries.value, np.uint32)
+        _check(lib().hyperim_graph_chunk_index(self._h, int(v), C.byref(bits), _ptr(tab), entries.value,
+                                               C.byref(entries)))
+        return bits.value, tab.reshape(-1, 1 << bits.value)
 
     def plan_theta(self, k, eps, ell=1.0):
         return hyperim_plan_theta(self._h, k, eps, ell)

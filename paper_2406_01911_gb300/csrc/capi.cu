@@ -232,7 +232,7 @@ void hyperim_graph_free(hyperim_graph_t g) {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off, g->prof, g->cdf_tab, g->deg,
-                    g->stratum, g->vs_off, g->vs_list, g->d_status, g->d_counters, g->scratch.list,
+                    g->stratum, g->vs_off, g->vs_list, g->idx, g->idx_tab, g->d_status, g->d_counters, g->scratch.list,
                     g->scratch.bitmap, g->scratch.big, g->scratch.picks, g->scratch.arena};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, g->stream);
@@ -252,6 +252,30 @@ hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out
     for (int s = 0; s < HYPERIM_NSTRATA; ++s) out->stratum_size[s] = g->stratum_size[s];
     out->theta_lstar = g->theta_lstar;
     out->device_bytes = g->device_bytes;
+    out->index_vertices = g->idx_vertices;
+    out->index_entries = g->idx_entries;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* bits, uint32_t* table,
+                                         int64_t cap, int64_t* entries) {
+    if (!g || !bits || !entries) return set_error(HYPERIM_EINVAL, "null argument");
+    if (v < 0 || v >= g->n) return set_error(HYPERIM_EINVAL, "vertex outside [0, n)");
+    uint64_t word = 0;
+    int4 vi = make_int4(0, 0, 0, 0);
+    HYP_CUDA(cudaMemcpyAsync(&word, g->idx + v, sizeof(word), cudaMemcpyDeviceToHost, g->stream));
+    HYP_CUDA(cudaMemcpyAsync(&vi, g->vinfo + v, sizeof(vi), cudaMemcpyDeviceToHost, g->stream));
+    HYP_CUDA(cudaStreamSynchronize(g->stream));
+    const int c = (int)(word >> kIdxBitsShift);
+    const int64_t e = word ? (int64_t)vi.y << c : 0;
+    *bits = word ? c : 0;
+    *entries = e;
+    if (!table || e == 0) return HYPERIM_OK;
+    if (cap < e) return set_error(HYPERIM_EINVAL, "table buffer smaller than the index");
+    const uint64_t off = word & ((1ull << kIdxBitsShift) - 1);
+    HYP_CUDA(cudaMemcpyAsync(table, g->idx_tab + off, sizeof(uint32_t) * (size_t)e, cudaMemcpyDeviceToHost,
+                             g->stream));
+    HYP_CUDA(cudaStreamSynchronize(g->stream));
     return HYPERIM_OK;
 }
 
@@ -378,6 +402,8 @@ hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
     out->mat_he = p->counters.mat_he;
     out->mat_members = p->counters.mat_members;
     out->selected = p->counters.selected;
+    out->gathered = p->counters.gathered;
+    out->search_words = p->counters.search_words;
     out->rr_launches = p->rr_launches;
     out->rr_kernel_seconds = p->rr_kernel_seconds;
     return HYPERIM_OK;

@@ -30,7 +30,23 @@ struct DevStatus {
 // Work counters of RR generation (same definitions as the pool view's counters).
 struct RRCounters {
     unsigned long long pops, layers_seen, draws, mats, mat_he, mat_members, selected;
+    unsigned long long gathered, search_words;
 };
+
+// Chunk index of large neighbourhoods. For a vertex mu whose hyperedges hold more than
+// kIdxMinT members other than mu (repeats counted), the ids are split into C = 2^c chunks by
+// their top c of id_bits bits, c the smallest value for which no chunk holds more than
+// kIdxTarget of those members, and the index stores, for every layer i of A(mu) and chunk k, the
+// number of members of L_i in chunks < k (l_mu x C uint32, layer-major). The position of a pick
+// in L_i then names the one chunk that holds it, and only that id range of mu's (sorted)
+// hyperedges is read. Vertices with more than kIdxMaxL layers, or whose members crowd one id
+// range beyond kIdxTarget even at 2^kIdxMaxBits chunks, are not indexed.
+constexpr int kIdxMinT = 2048;
+constexpr int kIdxTarget = 1024;
+constexpr int kIdxMaxBits = 12;
+constexpr int kIdxMaxL = 2048;
+// idx word of a vertex: 0 = no index, else (c << 56) | offset of its table
+constexpr int kIdxBitsShift = 56;
 
 // Profile entry of layer i of A(mu): 32 bytes, two uint4.
 //   [0] = {w_i | (p == 1 ? 1u << 31 : 0), n_i, floor(p 2^32) for 0 <= p < 1, T_0}
@@ -87,6 +103,11 @@ struct hyperim_graph {
     uint8_t* stratum = nullptr;  // n
     int32_t* vs_off = nullptr;   // 17
     int32_t* vs_list = nullptr;  // n (vertices grouped by stratum, ascending id)
+    // chunk index of large neighbourhoods
+    uint64_t* idx = nullptr;     // n: 0 or (chunk bits << 56) | table offset
+    uint32_t* idx_tab = nullptr; // per indexed vertex: l x 2^bits prefix counts, layer-major
+    int64_t idx_entries = 0;
+    int32_t idx_vertices = 0;
     // host copies of scalars
     int64_t profile_entries = 0;
     int32_t max_layers = 0, max_dh = 0;
@@ -139,6 +160,9 @@ hyperim_status check_device_status(hyperim_graph* g, const char* where);
 // load.cu
 hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off, const int32_t* he_mem,
                            int32_t nnz_in, bool on_device);
+
+// index.cu: chunk index of the vertices with large neighbourhoods (after the layer profile)
+hyperim_status build_chunk_index(hyperim_graph* g);
 
 // scan.cu: exclusive scan of n uint32/int32 counts into int64 (out has n + 1 entries)
 hyperim_status exclusive_scan_u32_to_i64(hyperim_graph* g, const uint32_t* in, int64_t* out,

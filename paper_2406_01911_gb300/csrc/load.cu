@@ -16,7 +16,6 @@
 namespace hyperim {
 namespace {
 
-constexpr int kNormWarps = 8;   // warps per block of the per-hyperedge / per-vertex kernels
 constexpr int kProfThreads = 256;
 constexpr int kProfBuf = 8192;  // on-chip keys of the profile kernel (power of two)
 constexpr int kProfHist = 4096; // on-chip multiplicity histogram bins
@@ -650,6 +649,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if (nnz > 0)
         { k_build_spans<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->v_span); count_launch(); }
     { k_build_vinfo<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->prof_off, g->v_off, g->vinfo); count_launch(); }
+    if ((st = build_chunk_index(g))) return st;
 
     // --- strata lists V_s (ascending ids)
     if ((st = dev_alloc(g, (void**)&g->vs_off, sizeof(int32_t) * (HYPERIM_NSTRATA + 1)))) return st;

@@ -167,17 +167,19 @@ namespace hyperim {
 // incidences are read G at a time; their lengths are prefix-summed in shared memory and every
 // thread then walks member positions p = rank, rank + G, ... of the group, locating its
 // hyperedge by binary search in the prefix: all member loads of a group are independent.
-// f(x) is called for every member x != mu (duplicates across hyperedges included).
+// f(pos, x) is called for every position pos in [0, sum of the hyperedge sizes) of the
+// concatenation of mu's hyperedges (in incidence order), x the member there (mu included).
 // pre: 2 G + 1 ints of shared memory (prefix and starts).
 // ------------------------------------------------------------------------------------------
 template <int G, typename F>
-__device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
-                                                const int32_t* __restrict__ he_mem, int32_t mu,
-                                                int32_t v_begin, int32_t dh, int* pre, F&& f) {
+__device__ __forceinline__ void for_each_position(const int2* __restrict__ v_span,
+                                                  const int32_t* __restrict__ he_mem,
+                                                  int32_t v_begin, int32_t dh, int* pre, F&& f) {
     using Gr = Group<G>;
     const int r = Gr::rank();
     const int lane = threadIdx.x & 31;
     int* start = pre + G + 1;  // G starts follow the G + 1 prefix entries
+    int base = 0;              // positions of the earlier groups of incidences
     for (int c0 = 0; c0 < dh; c0 += G) {
         const int cnt = min(G, dh - c0);
         int2 sp = make_int2(0, 0);
@@ -211,11 +213,10 @@ __device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
         // four positions per round: their loads are all issued before any result is used
         constexpr int U = 4;
         for (int p0 = r; p0 < total; p0 += U * G) {
-            uint32_t xs[U];
+            uint32_t xs[U] = {};
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int p = p0 + u * G;
-                xs[u] = (uint32_t)mu;
                 if (p < total) {
                     if (stepwise && p != r) {
                         while (pre[j + 1] <= p) ++j;
@@ -232,10 +233,21 @@ __device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (xs[u] != (uint32_t)mu) f(xs[u]);
+                if (p0 + u * G < total) f(base + p0 + u * G, xs[u]);
         }
+        base += total;
         Gr::sync();
     }
+}
+
+// f(x) for every member x != mu of mu's hyperedges (duplicates across hyperedges included).
+template <int G, typename F>
+__device__ __forceinline__ void for_each_member(const int2* __restrict__ v_span,
+                                                const int32_t* __restrict__ he_mem, int32_t mu,
+                                                int32_t v_begin, int32_t dh, int* pre, F&& f) {
+    for_each_position<G>(v_span, he_mem, v_begin, dh, pre, [&](int, uint32_t x) {
+        if (x != (uint32_t)mu) f(x);
+    });
 }
 
 // ------------------------------------------------------------------------------------------

@@ -24,6 +24,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWCap = 2048;      // per-warp on-chip neighbourhood keys (power of two)
+constexpr int kWHalf = kWCap / 2;  // raw copy + sorted copy of neighbourhoods up to this size
+constexpr int kCollCap = kWHalf / 2;  // members collected for a direct selection
 constexpr int kPCap = 256;       // per-warp picks
 constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the warp path
 constexpr int kBCap = 8192;      // block on-chip keys (power of two)
@@ -36,6 +38,7 @@ constexpr int kWBuckets = 1 << kWBucketBits;  // warp-path buckets
 constexpr int kChunks = 1024;        // first-level id chunks of the largest neighbourhoods
 constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
 constexpr int kMaxPools = 2;           // pools grown by one launch (R1 and R2 of a BRR round)
+constexpr int kNStat = 9;              // work counters (stat slots below)
 
 struct RRJobMap {
     int64_t job_base[HYPERIM_NSTRATA + 1];
@@ -52,6 +55,8 @@ struct RRParams {
     const int32_t* tsum;
     const int32_t* vs_off;
     const int32_t* vs_list;
+    const uint64_t* idx;      // per vertex: 0 or (chunk bits << 56) | offset into idx_tab
+    const uint32_t* idx_tab;
     int32_t n;
     int id_bits;
     uint64_t seed;
@@ -100,13 +105,13 @@ struct BlockArea {
 struct Shared {
     int ctrl[16];
     int tmp[kWarps + 2];
-    unsigned long long stat[kMaxPools][8];  // per pool work counters of this block
-    unsigned long long wstat[kWarps][8];    // per-warp counters of the current RR set (lane 0)
+    unsigned long long stat[kMaxPools][kNStat];  // per pool work counters of this block
+    unsigned long long wstat[kWarps][kNStat];    // per-warp counters of the current RR set (lane 0)
     unsigned long long out_pos;
     int32_t deferred[kDCap];
     Need wneed[kWarps][kLQ];
     int wcursor[kWarps];
-    int wpre[kWarps][2 * 32 + 1];
+    int wpre[kWarps][3 * 32 + 1];   // span prefix, starts, holes (chunk path)
     int bpre[2 * kThreads + 1];
     uint32_t wpoff[kWarps][kLQ + 1];
     int wcnt[kWarps][kBLQ];     // per-warp per-layer counts (ranks)
@@ -122,7 +127,7 @@ struct Shared {
 enum { C_JOB = 0, C_HEAD, C_TAIL, C_LEVEL_END, C_NEXT, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP,
        C_BITS, C_OK };
 // stat slots
-enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL };
+enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL, S_GATH, S_SRCH };
 
 __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
@@ -226,6 +231,301 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
 // ------------------------------------------------------------------------------------------
 // warp path
 // ------------------------------------------------------------------------------------------
+// Exclusive scan of a warp's bucket counts bkt[0, nb) in place; returns the largest count.
+__device__ int warp_bucket_scan(int* bkt, int nb) {
+    const int lane = threadIdx.x & 31;
+    int carry = 0, maxb = 0;
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+        const int b = c0 + lane;
+        const int v = b < nb ? bkt[b] : 0;
+        maxb = max(maxb, v);
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (b < nb) bkt[b] = carry + inc - v;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    __syncwarp();
+    return __reduce_max_sync(0xFFFFFFFFu, maxb);
+}
+
+// Scatter raw[0, nraw) (entries equal to skip left out; count remain) into buf by the bucket
+// starts in bkt (key ((x - base) >> shift) & key_mask), then sort each bucket by insertion, or
+// the whole buffer by the bitonic network when the largest bucket exceeds kBucketSortMax.
+__device__ void warp_scatter_sort(const uint32_t* raw, int nraw, uint32_t skip, uint32_t* buf, int count,
+                                  int* bkt, int nb, uint32_t base, int shift, uint32_t key_mask, int maxb) {
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < nraw; p += 32) {
+        const uint32_t x = raw[p];
+        if (x != skip) buf[atomicAdd(&bkt[((x - base) >> shift) & key_mask], 1)] = x;
+    }
+    __syncwarp();
+    // bkt[b] is now the end of bucket b
+    if (maxb > kBucketSortMax) {
+        group_sort<32>(buf, count);
+        return;
+    }
+    for (int b = lane; b < nb; b += 32) {
+        const int e = bkt[b], s0 = b ? bkt[b - 1] : 0;
+        for (int i = s0 + 1; i < e; ++i) {
+            const uint32_t x = buf[i];
+            int k = i - 1;
+            while (k >= s0 && buf[k] > x) {
+                buf[k + 1] = buf[k];
+                --k;
+            }
+            buf[k + 1] = x;
+        }
+    }
+    __syncwarp();
+}
+
+// A(mu) with at most kWHalf incidence positions (tsum, mu's own included), by one pass over the
+// members: a raw copy goes to buf[kWHalf, kWHalf + tsum) and the members are counted into
+// buckets of their top id bits. Returns 1 if the pops of this vertex are already done: when no
+// member repeats (one layer, w = 1) the a-th member in id order lies in the bucket whose start
+// is the last one <= a, so only the buckets holding picks are collected and ranked. Otherwise
+// (returns 0) buf[0, T) receives the members sorted by id.
+__device__ int small_nbhd(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, int32_t mu,
+                          int32_t v_begin, int32_t dh, int tsum, int T, int l, const Need nd0,
+                          uint32_t* buf) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* bkt = S.u.w.wbkt[wid];
+    uint32_t* raw = buf + kWHalf;
+    const int nbits = bucket_bits(T, kWBucketBits);
+    const int nb = 1 << nbits;
+    const int shift = P.id_bits > nbits ? P.id_bits - nbits : 0;
+    const uint32_t key_mask = (uint32_t)nb - 1;
+    for (int b = lane; b < nb; b += 32) bkt[b] = 0;
+    __syncwarp();
+    for_each_position<32>(P.v_span, P.he_mem, v_begin, dh, S.wpre[wid], [&](int pos, uint32_t x) {
+        raw[pos] = x;
+        if (x != (uint32_t)mu) atomicAdd(&bkt[(x >> shift) & key_mask], 1);
+    });
+    const int maxb = warp_bucket_scan(bkt, nb);  // bucket starts
+    if (l == 1 && nd0.w == 1) {
+        if (nd0.h >= nd0.n) {  // every member is taken
+            for (int p = lane; p < tsum; p += 32) {
+                const uint32_t x = raw[p];
+                if (x != (uint32_t)mu) push(P, S, vis, list, x);
+            }
+            __syncwarp();
+            return 1;
+        }
+        if (nd0.h <= 32) {
+            uint32_t* marked = reinterpret_cast<uint32_t*>(S.wcnt[wid]);  // nb bits
+            for (int i = lane; i < (nb >> 5) + 1; i += 32) marked[i] = 0;
+            __syncwarp();
+            int pb = 0, po = 0;
+            if ((uint32_t)lane < nd0.h) {
+                const int a = (int)S.u.w.wpick[wid][lane];
+                int lo = 0, hi = nb;  // last bucket whose start is <= a
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (bkt[mid] <= a) lo = mid; else hi = mid;
+                }
+                pb = lo;
+                po = a - bkt[lo];
+                atomicOr(&marked[lo >> 5], 1u << (lo & 31));
+            }
+            __syncwarp();
+            uint32_t* coll = buf;
+            int cc = 0;
+            for (int p0 = 0; p0 < tsum; p0 += 32) {
+                const int p = p0 + lane;
+                bool f = false;
+                uint32_t x = 0;
+                if (p < tsum) {
+                    x = raw[p];
+                    const uint32_t b = (x >> shift) & key_mask;
+                    f = x != (uint32_t)mu && ((marked[b >> 5] >> (b & 31)) & 1u);
+                }
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
+                const int at = cc + __popc(bal & lanemask_lt());
+                if (f && at < kCollCap) coll[at] = x;
+                cc += __popc(bal);
+            }
+            __syncwarp();
+            if (cc <= kCollCap) {
+                uint32_t* srt = buf + kCollCap;  // the collected members in id order (all distinct)
+                for (int i = lane; i < cc; i += 32) {
+                    const uint32_t x = coll[i];
+                    int rk = 0;
+                    for (int k = 0; k < cc; ++k) rk += coll[k] < x ? 1 : 0;
+                    srt[rk] = x;
+                }
+                __syncwarp();
+                if ((uint32_t)lane < nd0.h) {
+                    const uint32_t lo_val = (uint32_t)pb << shift;  // smallest id of bucket pb
+                    int lo = 0, hi = cc;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (srt[mid] < lo_val) lo = mid + 1; else hi = mid;
+                    }
+                    push(P, S, vis, list, srt[lo + po]);
+                }
+                __syncwarp();
+                return 1;
+            }
+        }
+    }
+    warp_scatter_sort(raw, tsum, (uint32_t)mu, buf, T, bkt, nb, 0u, shift, key_mask, maxb);
+    return 0;
+}
+
+__device__ __forceinline__ int lower_bound_id(const int32_t* __restrict__ a, int len, uint32_t v,
+                                              uint32_t& probes) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        ++probes;
+        if ((uint32_t)a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The members != mu of mu's hyperedges whose ids lie in [lo, hi), sorted, in buf[0, count);
+// returns count, or -1 if they exceed kWHalf. Members of a hyperedge are sorted, so the range is
+// one slice found by two binary searches; when mu is in the range its own slot in every slice is
+// skipped (a hole at mu's offset). The slices are gathered with independent loads into the raw
+// half of buf and counted into buckets of the id offset within the range, then scattered and
+// sorted as in small_nbhd. probes counts the words read by the searches.
+__device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_begin, int32_t dh,
+                          uint32_t lo, int sh, uint32_t* buf, uint32_t& probes) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* pre = S.wpre[wid];
+    int* start = pre + 33;
+    int* hole = pre + 65;
+    uint32_t* raw = buf + kWHalf;
+    int* bkt = S.u.w.wbkt[wid];
+    constexpr int nb = kWBuckets;
+    const int shift = sh > kWBucketBits ? sh - kWBucketBits : 0;
+    const uint32_t key_mask = (uint32_t)nb - 1;
+    const uint32_t hi = lo + (1u << sh);
+    const bool mu_in = (uint32_t)mu >= lo && (uint32_t)mu < hi;
+    for (int b = lane; b < nb; b += 32) bkt[b] = 0;
+    int base = 0;
+    for (int c0 = 0; c0 < dh; c0 += 32) {
+        const int cnt = min(32, dh - c0);
+        int st = 0, len = 0, hl = 0x7FFFFFFF;
+        if (lane < cnt) {
+            const int2 sp = P.v_span[v_begin + c0 + lane];
+            const int32_t* e = P.he_mem + sp.x;
+            const int a = lower_bound_id(e, sp.y, lo, probes);
+            const int b = a + lower_bound_id(e + a, sp.y - a, hi, probes);
+            st = sp.x + a;
+            len = b - a;
+            if (mu_in) {
+                hl = lower_bound_id(e + a, len, (uint32_t)mu, probes);
+                len -= 1;
+            }
+        }
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        __syncwarp();  // the previous group's readers of pre / start / hole are done
+        if (lane == 0) pre[0] = 0;
+        if (lane < cnt) {
+            pre[lane + 1] = inc;
+            start[lane] = st;
+            hole[lane] = hl;
+        }
+        __syncwarp();
+        const int total = pre[cnt];
+        if (base + total > kWHalf) return -1;  // uniform
+        const bool stepwise = total >= cnt * 8;
+        int j = 0;
+        constexpr int U = 4;
+        for (int p0 = lane; p0 < total; p0 += U * 32) {
+            uint32_t xs[U] = {};
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * 32;
+                if (p < total) {
+                    if (stepwise && p != lane) {
+                        while (pre[j + 1] <= p) ++j;
+                    } else {
+                        int l2 = 0, h2 = cnt;
+                        while (h2 - l2 > 1) {
+                            const int mid = (l2 + h2) >> 1;
+                            if (pre[mid] <= p) l2 = mid; else h2 = mid;
+                        }
+                        j = l2;
+                    }
+                    int o = p - pre[j];
+                    o += o >= hole[j] ? 1 : 0;
+                    xs[u] = (uint32_t)P.he_mem[start[j] + o];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * 32;
+                if (p < total) {
+                    raw[base + p] = xs[u];
+                    atomicAdd(&bkt[((xs[u] - lo) >> shift) & key_mask], 1);
+                }
+            }
+        }
+        base += total;
+    }
+    __syncwarp();
+    const int maxb = warp_bucket_scan(bkt, nb);
+    warp_scatter_sort(raw, base, kSentinel, buf, base, bkt, nb, lo, shift, key_mask, maxb);
+    return base;
+}
+
+// Ranked walk of a sorted warp buffer buf[0, got): a run of multiplicity need[q].w is a member
+// of needed layer q, its rank in L_q is cnt[q] (the layer's members before the buffer) plus the
+// runs of that layer before it; members whose rank is a pick, or all of them when h = n, enter R.
+// Stops once every layer with picks has ranked past its last pick.
+__device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, const uint32_t* buf,
+                          int got, uint32_t nneed) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Need* need = S.wneed[wid];
+    const uint32_t* picks = S.u.w.wpick[wid];
+    const uint32_t* poff = S.wpoff[wid];
+    int* cnt = S.wcnt[wid];
+    uint32_t done_mask = 0, want_mask = (nneed >= 32 ? 0xFFFFFFFFu : ((1u << nneed) - 1));
+    for (int base = 0; base < got; base += 32) {
+        const int p = base + lane;
+        bool start = false;
+        uint32_t x = kSentinel;
+        int mult = 0;
+        if (p < got) {
+            x = buf[p];
+            start = (p == 0) || (buf[p - 1] != x);
+            if (start) {
+                mult = 1;
+                while (p + mult < got && buf[p + mult] == x) ++mult;
+            }
+        }
+        for (uint32_t q = 0; q < nneed; ++q) {
+            const Need nd = need[q];
+            const bool f = start && (uint32_t)mult == nd.w;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
+            const uint32_t before = (uint32_t)cnt[q];
+            if (f) {
+                const uint32_t rank = before + __popc(bal & lanemask_lt());
+                const bool take = nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank);
+                if (take) push(P, S, vis, list, x);
+            }
+            const uint32_t after = before + __popc(bal);
+            __syncwarp();
+            if (lane == 0) cnt[q] = (int)after;
+            __syncwarp();
+            if (nd.h < nd.n && after > picks[poff[q] + nd.h - 1]) done_mask |= 1u << q;
+        }
+        if ((done_mask & want_mask) == want_mask) break;
+    }
+    __syncwarp();
+}
+
 // Returns true when the pop must be handed to the block path.
 __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
                          uint32_t ybase, int32_t mu) {
@@ -270,17 +570,22 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         wst[S_MATS] += 1;
         wst[S_MAT_HE] += (unsigned long long)dh;
         wst[S_MAT_MEM] += (unsigned long long)tsum;
+        wst[S_GATH] += (unsigned long long)tsum;  // one pass over the members (the chunk path corrects it)
     }
     if (nneed > kLQ) return true;
     // picks for every needed layer (none when h = n)
     uint32_t total_picks = 0;
+    bool take_all = false;
     for (uint32_t q = 0; q < nneed; ++q) {
         const Need nd = need[q];
-        if (nd.h < nd.n) total_picks += nd.h;
+        if (nd.h < nd.n) total_picks += nd.h; else take_all = true;
         if (total_picks > kPCap) return true;
     }
     const int T = tsum - dh;
-    if (dh != 1 && T > kWCap) return true;
+    // a chunk index lets the warp read only the id ranges that hold the picks
+    uint64_t iw = 0;
+    if (dh != 1 && T > kIdxMinT && !take_all && total_picks <= 32) iw = P.idx[mu];
+    if (dh != 1 && iw == 0 && T > kWCap) return true;
     uint32_t* picks = S.u.w.wpick[wid];
     uint32_t* poff = S.wpoff[wid];
     uint32_t acc = 0;
@@ -322,47 +627,69 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         __syncwarp();
         return false;
     }
-    // materialise A(mu) in shared memory, sorted by id (bucketed by the top 8 id bits)
     uint32_t* buf = S.u.w.wbuf[wid];
-    const int got = sorted_nbhd<32>(P.v_span, P.he_mem, mu, v_begin, dh, T, P.id_bits, buf,
-                                    S.u.w.wbkt[wid], kWBucketBits, S.wpre[wid], nullptr);
-    // walk runs; rank members of each needed layer in id order
     int* cnt = S.wcnt[wid];
+    if (iw != 0) {
+        // chunk path: each pick's chunk from its layer's row of prefix counts, then the chunks
+        // that hold picks in ascending order, ranks starting from the row entries
+        const int c = (int)(iw >> kIdxBitsShift);
+        const uint64_t toff = iw & ((1ull << kIdxBitsShift) - 1);
+        const int sh = P.id_bits - c;
+        uint32_t probes = 0, my_chunk = 0xFFFFFFFFu;
+        unsigned long long gath = 0;
+        if ((uint32_t)lane < total_picks) {
+            uint32_t q = 0;
+            while (q + 1 < nneed && poff[q + 1] <= (uint32_t)lane) ++q;
+            const uint32_t a = picks[lane];
+            const uint32_t* row = P.idx_tab + toff + ((uint64_t)(need[q].layer - 1) << c);
+            int lo = 0, hi = 1 << c;  // last chunk whose prefix is <= a
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                ++probes;
+                if (row[mid] <= a) lo = mid; else hi = mid;
+            }
+            my_chunk = (uint32_t)lo;
+        }
+        uint32_t k = __reduce_min_sync(0xFFFFFFFFu, my_chunk);
+        int chunks = 0;
+        while (k != 0xFFFFFFFFu) {
+            for (uint32_t q = lane; q < nneed; q += 32) {
+                cnt[q] = (int)P.idx_tab[toff + ((uint64_t)(need[q].layer - 1) << c) + k];
+                ++probes;
+            }
+            __syncwarp();
+            const int got = chunk_nbhd(P, S, mu, v_begin, dh, k << sh, sh, buf, probes);
+            if (got < 0) {
+                if (lane == 0) dev_fail(P.st, kErrBucket, mu);
+                return false;
+            }
+            gath += (unsigned long long)got;
+            warp_walk(P, S, vis, list, buf, got, nneed);
+            ++chunks;
+            k = __reduce_min_sync(0xFFFFFFFFu, my_chunk > k ? my_chunk : 0xFFFFFFFFu);
+        }
+        probes = __reduce_add_sync(0xFFFFFFFFu, probes);
+        if (lane == 0) {
+            wst[S_GATH] += gath;
+            wst[S_GATH] -= (unsigned long long)tsum;
+            // span entries (2 words) of every chunk after the first are extra reads
+            wst[S_SRCH] += (unsigned long long)probes + 2ull * (unsigned long long)dh * (chunks - 1);
+        }
+        return false;
+    }
+    // materialise A(mu) in shared memory, sorted by id (bucketed by the top id bits)
+    int got;
+    if (tsum <= kWHalf) {
+        const int sel = small_nbhd(P, S, vis, list, mu, v_begin, dh, tsum, T, l, need[0], buf);
+        if (sel) return false;
+        got = T;
+    } else {
+        got = sorted_nbhd<32>(P.v_span, P.he_mem, mu, v_begin, dh, T, P.id_bits, buf,
+                              S.u.w.wbkt[wid], kWBucketBits, S.wpre[wid], nullptr);
+    }
     for (uint32_t q = lane; q < nneed; q += 32) cnt[q] = 0;
     __syncwarp();
-    uint32_t done_mask = 0, want_mask = (nneed >= 32 ? 0xFFFFFFFFu : ((1u << nneed) - 1));
-    for (int base = 0; base < got; base += 32) {
-        const int p = base + lane;
-        bool start = false;
-        uint32_t x = kSentinel;
-        int mult = 0;
-        if (p < got) {
-            x = buf[p];
-            start = (p == 0) || (buf[p - 1] != x);
-            if (start) {
-                mult = 1;
-                while (p + mult < got && buf[p + mult] == x) ++mult;
-            }
-        }
-        for (uint32_t q = 0; q < nneed; ++q) {
-            const Need nd = need[q];
-            const bool f = start && (uint32_t)mult == nd.w;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
-            const uint32_t before = (uint32_t)cnt[q];
-            if (f) {
-                const uint32_t rank = before + __popc(bal & lanemask_lt());
-                const bool take = nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank);
-                if (take) push(P, S, vis, list, x);
-            }
-            const uint32_t after = before + __popc(bal);
-            __syncwarp();
-            if (lane == 0) cnt[q] = (int)after;
-            __syncwarp();
-            if (nd.h < nd.n && after > picks[poff[q] + nd.h - 1]) done_mask |= 1u << q;
-        }
-        if ((done_mask & want_mask) == want_mask) break;
-    }
-    __syncwarp();
+    warp_walk(P, S, vis, list, buf, got, nneed);
     return false;
 }
 
@@ -626,8 +953,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     uint32_t* big = P.big + (int64_t)blockIdx.x * P.big_cap;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t njobs = P.pool_start[P.npools];
-    if (threadIdx.x < kMaxPools * 8) (&S.stat[0][0])[threadIdx.x] = 0;
-    if (threadIdx.x < kWarps * 8) (&S.wstat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
     for (;;) {
@@ -705,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
             __syncthreads();
         }
         // work counters of this RR set go to its pool
-        if (threadIdx.x < 8) {
+        if (threadIdx.x < kNStat) {
             unsigned long long sum = 0;
             for (int w = 0; w < kWarps; ++w) {
                 sum += S.wstat[w][threadIdx.x];
@@ -783,6 +1110,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
         atomicAdd(&c->mat_he, st[S_MAT_HE]);
         atomicAdd(&c->mat_members, st[S_MAT_MEM]);
         atomicAdd(&c->selected, st[S_SEL]);
+        atomicAdd(&c->gathered, st[S_GATH]);
+        atomicAdd(&c->search_words, st[S_SRCH]);
     }
 }
 
@@ -932,6 +1261,8 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.tsum = g->tsum;
     P.vs_off = g->vs_off;
     P.vs_list = g->vs_list;
+    P.idx = g->idx;
+    P.idx_tab = g->idx_tab;
     P.n = g->n;
     P.id_bits = g->id_bits;
     P.seed = g->seed;

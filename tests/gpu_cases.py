@@ -27,6 +27,25 @@ def hub_graph(seed=0, n=20000, hub_edges=60, hub_size=250, mid_edges=10, mid_siz
     return n, hes
 
 
+def layered_hub_graph(seed=0, n=30000, groups=12, group_edges=(1, 2, 3, 5, 8, 13), size=120,
+                      m_rest=4000):
+    """Vertices 0..3 share group_edges[i] hyperedges with groups of co-members of varying size, so
+    their neighbourhoods (several thousand members) have one layer per multiplicity in
+    group_edges, plus sparse random hyperedges: chunk index with several layers."""
+    rng = np.random.default_rng(seed)
+    hes = []
+    for hub in range(4):
+        for gi in range(groups):
+            w = group_edges[gi % len(group_edges)]
+            common = [int(x) for x in rng.integers(4, n, size=size)]
+            for _ in range(w):
+                extra = [int(x) for x in rng.integers(4, n, size=size // 4)]
+                hes.append([hub] + common + extra)
+    for _ in range(m_rest):
+        hes.append([int(x) for x in rng.integers(0, n, size=int(rng.integers(2, 6)))])
+    return n, hes
+
+
 def layered_graph(depth=40, pad=100):
     """Vertex 0 shares exactly i hyperedges with vertex i (i = 1..depth): depth distinct layers."""
     hes = []
@@ -46,6 +65,18 @@ def big_edge_graph(size=2000, n=2500):
 def degenerate_graph():
     """Empty, single-member and repeated-member hyperedges and isolated vertices."""
     return 12, [[], [3], [2, 2, 5], [5, 2, 7, 7], [1, 1], [9, 10, 11, 9], [], [0, 4]]
+
+
+def distinct_graph(seed=0, n=6000, edges=6, size=150, m_rest=2500):
+    """Vertex 0 sits in `edges` disjoint hyperedges of `size` members: its neighbourhood has no
+    repeated member (one layer of w = 1) and about (size - 1) * edges members; the rest is sparse
+    with distinct members per hyperedge, so many small neighbourhoods have one layer too."""
+    rng = np.random.default_rng(seed)
+    pool = rng.permutation(np.arange(1, n))
+    hes = [[0] + [int(x) for x in pool[i * (size - 1):(i + 1) * (size - 1)]] for i in range(edges)]
+    for _ in range(m_rest):
+        hes.append([int(x) + 1 for x in rng.choice(n - 1, size=int(rng.integers(2, 8)), replace=False)])
+    return n, hes
 
 
 def random_graph(seed, n, m, smax):

@@ -3,7 +3,8 @@
 Integer results (layer profiles, RR sets, coverage counts, seed sets, work counters) must be
 identical; double results (estimates, bounds, theta) agree to 1e-12 relative and integer theta
 is identical. Inputs are seeded and steer every kernel path: warp materialisation, block
-materialisation on chip, id-bucketed materialisation through global scratch, direct indexing of a
+materialisation on chip, id-bucketed materialisation through global scratch, selection in
+duplicate-free neighbourhoods by bucket starts, direct indexing of a
 single hyperedge, > 32 layers with draws, > 256 picks, split Poisson draws, p = 1, RR sets larger
 than the on-chip sort buffer, degenerate hyperedges.
 """
@@ -113,14 +114,97 @@ def test_big_single_hyperedge(H, oracle, uthr):
     check_pool(H, oracle, g, og, 40, "plain", seed=9)
 
 
-def test_hub_paths(H, oracle):
+@pytest.mark.parametrize("uthr,roots,theta", [(4294967, "stratified", 2000), (85899345, "plain", 12),
+                                              (P32, "plain", 12)])
+def test_hub_paths(H, oracle, uthr, roots, theta):
+    # p = 0.001: a few picks per hub pop (chunk index path; the hubs head high strata); p = 0.02:
+    # hundreds of picks on vertex 0 (block path, bucketed through global scratch); p = 1: every
+    # member (block path)
     n, hes = gc.hub_graph()
-    g, og = load_both(H, oracle, n, hes, "uniform_pair", 85899345, seed=11)  # p = 0.02
+    g, og = load_both(H, oracle, n, hes, "uniform_pair", uthr, seed=11)
     check_profile(g, og, n)
     assert og.dh(0) >= 60 and og.dh(1) >= 10
-    check_pool(H, oracle, g, og, 12, "plain", seed=11)
+    check_pool(H, oracle, g, og, theta, roots, seed=11)
+
+
+def test_hub_paths_wc(H, oracle):
+    n, hes = gc.hub_graph()
     g2, og2 = load_both(H, oracle, n, hes, "wc", 0, seed=11)
     check_pool(H, oracle, g2, og2, 3000, "stratified", seed=11)
+    n3, hes3 = gc.layered_hub_graph()
+    g3, og3 = load_both(H, oracle, n3, hes3, "wc", 0, seed=3)
+    check_pool(H, oracle, g3, og3, 2000, "stratified", seed=3)
+    g4, og4 = load_both(H, oracle, n3, hes3, "uniform_pair", 4294967, seed=3)  # p = 0.001
+    check_pool(H, oracle, g4, og4, 2000, "stratified", seed=3)
+
+
+@pytest.mark.parametrize("uthr", [128849018, 858993459, P32])
+def test_distinct_neighbourhoods(H, oracle, uthr):
+    # p = 0.03 draws ~27 picks from vertex 0's 894 distinct neighbours (selection by bucket
+    # starts), p = 0.2 ~180 (sorted path), p = 1 takes every member
+    n, hes = gc.distinct_graph()
+    g, og = load_both(H, oracle, n, hes, "uniform_pair", uthr, seed=13)
+    assert og.nlayers(0) == 1 and og.deg(0) == 894
+    check_pool(H, oracle, g, og, 300, "plain", seed=13)
+    g2, og2 = load_both(H, oracle, n, hes, "wc", 0, seed=13)
+    check_pool(H, oracle, g2, og2, 1500, "stratified", seed=13)
+
+
+def expected_chunk_index(og, v, id_bits):
+    """(bits, table) the chunk index of v must hold, from the oracle's layers (None: no index).
+    Candidates: d_H >= 2, more than 2048 members besides v (repeats counted), 1 <= l_v <= 2048;
+    bits = the fewest top id bits (at most 12) for which no chunk holds more than 1024 of those
+    members; table[i - 1, k] = members of L_i in chunks < k."""
+    lay = og.layers(v)
+    mem = [og.layer_members(v, i) for i in range(1, len(lay) + 1)]
+    T = sum(w * n_i for (w, n_i, _), m in zip(lay, mem))
+    if og.dh(v) < 2 or T <= 2048 or not 1 <= len(lay) <= 2048:
+        return None
+    hb = min(12, id_bits)
+    best = None
+    for c in range(1, hb + 1):
+        occ = np.zeros(1 << c, np.int64)
+        for (w, _, _), m in zip(lay, mem):
+            np.add.at(occ, m.astype(np.int64) >> (id_bits - c), w)
+        if occ.max() <= 1024:
+            best = c
+            break
+    if best is None:
+        return None
+    C = 1 << best
+    tab = np.zeros((len(lay), C), np.uint32)
+    for i, m in enumerate(mem):
+        per = np.bincount(m.astype(np.int64) >> (id_bits - best), minlength=C)
+        tab[i, 1:] = np.cumsum(per)[:-1]
+    return best, tab
+
+
+def check_chunk_index(g, og, n, vertices):
+    id_bits = max(1, int(n - 1).bit_length())
+    seen = 0
+    for v in vertices:
+        want = expected_chunk_index(og, v, id_bits)
+        bits, tab = g.chunk_index(v)
+        if want is None:
+            assert bits == 0 and tab is None, v
+        else:
+            assert bits == want[0], v
+            assert np.array_equal(tab, want[1]), v
+            seen += 1
+    return seen
+
+
+def test_chunk_index(H, oracle):
+    # vertex 0: 60 hyperedges of 250 (about 15K members, repeats across hyperedges); vertex 1:
+    # 10 of 300; the rest are small (no index)
+    n, hes = gc.hub_graph()
+    g, og = load_both(H, oracle, n, hes, "wc", 0, seed=11)
+    assert check_chunk_index(g, og, n, range(0, 40)) == 2
+    assert g.stats()["index_vertices"] == 2
+    # many layers on a large neighbourhood
+    n2, hes2 = gc.layered_hub_graph()
+    g2, og2 = load_both(H, oracle, n2, hes2, "wc", 0, seed=3)
+    assert check_chunk_index(g2, og2, n2, range(0, 8)) >= 1
 
 
 def test_greedy_and_spread(H, oracle):
