@@ -77,6 +77,9 @@ hyperim_status check_device_status(hyperim_graph* g, const char* where) {
     case kErrBucket:
         return set_error(HYPERIM_EOVERFLOW, msg + "scratch capacity exceeded at vertex " +
                                                 std::to_string(h.detail));
+    case kErrSpin:
+        return set_error(HYPERIM_ECUDA, msg + "a work-queue wait ran out in RR set job " +
+                                            std::to_string(h.detail));
     default:
         return set_error(HYPERIM_ECUDA, msg + "device error " + std::to_string(h.code));
     }

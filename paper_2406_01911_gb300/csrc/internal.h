@@ -19,6 +19,7 @@ enum DevErr : int32_t {
     kErrWords = 4,         // a layer draw needed more than 2^18 Philox words
     kErrCapacity = 5,      // a scratch capacity was exceeded
     kErrBucket = 6,        // id bucket larger than the on-chip buffer
+    kErrSpin = 7,          // a bounded wait of the RR kernel's work queue ran out
 };
 
 struct DevStatus {

@@ -124,8 +124,8 @@ struct Shared {
     } u;
 };
 // ctrl slots
-enum { C_JOB = 0, C_HEAD, C_TAIL, C_LEVEL_END, C_NEXT, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP,
-       C_BITS, C_OK };
+enum { C_JOB = 0, C_HEAD, C_TAIL, C_DONE, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP, C_BITS, C_OK,
+       C_FAIL };
 // stat slots
 enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL, S_GATH, S_SRCH };
 
@@ -217,15 +217,54 @@ __device__ __forceinline__ bool in_sorted(const uint32_t* a, uint32_t len, uint3
     return false;
 }
 
-// Add nu to R if it is not there yet.
+// Add nu to R if it is not there yet: reserve a queue slot, then store the id there (a reader
+// that claimed the slot waits until the id replaces the empty mark -1).
 __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
                                      uint32_t nu) {
     const uint32_t bit = 1u << (nu & 31);
     const uint32_t old = atomicOr(&vis[nu >> 5], bit);
     if (!(old & bit)) {
         const int pos = atomicAdd(&S.ctrl[C_TAIL], 1);
-        list[pos] = (int32_t)nu;
+        *(volatile int32_t*)&list[pos] = (int32_t)nu;
     }
+}
+
+// Work queue of one RR set (lane 0 of a warp). Slots [0, tail) are reserved, [0, head) claimed,
+// done pops are finished (their pushes are in), ndef claimed pops wait for the block path.
+// Returns a claimed slot, or -1 when this warp should go to the block barrier: no pop is in
+// flight (head - ndef == done) and either the queue is empty or the deferred list is nearly
+// full. done is read first and fenced: a pop publishes its pushes (tail, slots) before it counts
+// itself done, so the head and tail read afterwards include them, and a warp leaves only when
+// the queue is quiescent (a warp that left early would idle at the barrier for the rest of the
+// set). The wait is bounded (kErrSpin).
+constexpr int kSpinLimit = 1 << 24;
+__device__ int claim_slot(const RRParams& P, Shared& S, int64_t job) {
+    volatile int* ctrl = S.ctrl;
+    for (int it = 0; it < kSpinLimit; ++it) {
+        const int d = ctrl[C_DONE];
+        __threadfence_block();
+        const int h = ctrl[C_HEAD], t = ctrl[C_TAIL], nd = ctrl[C_NDEF];
+        if (h < t && nd <= kDCap - kWarps) {
+            if (atomicCAS(&S.ctrl[C_HEAD], h, h + 1) == h) return h;
+            continue;
+        }
+        if (h - nd == d) return -1;
+        __nanosleep(64);
+    }
+    dev_fail(P.st, kErrSpin, (int32_t)job);
+    return -1;
+}
+
+// The id in a claimed slot (its pusher may still be storing it); -1 if the bounded wait ran out.
+__device__ int32_t slot_value(const RRParams& P, const int32_t* list, int idx, int64_t job) {
+    const volatile int32_t* v = list + idx;
+    for (int it = 0; it < kSpinLimit; ++it) {
+        const int32_t x = *v;
+        if (x >= 0) return x;
+        __nanosleep(32);
+    }
+    dev_fail(P.st, kErrSpin, (int32_t)job);
+    return -1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -376,13 +415,14 @@ __device__ int small_nbhd(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
     return 0;
 }
 
-__device__ __forceinline__ int lower_bound_id(const int32_t* __restrict__ a, int len, uint32_t v,
-                                              uint32_t& probes) {
-    int lo = 0, hi = len;
-    while (lo < hi) {
+// Last chunk k in [k0, C) whose prefix row[k] is <= pos (row[k0] <= pos is given).
+__device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0, int C, uint32_t pos,
+                                        uint32_t& probes) {
+    int lo = k0, hi = C;
+    while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         ++probes;
-        if ((uint32_t)a[mid] < v) lo = mid + 1; else hi = mid;
+        if (row[mid] <= pos) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -414,12 +454,21 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
         if (lane < cnt) {
             const int2 sp = P.v_span[v_begin + c0 + lane];
             const int32_t* e = P.he_mem + sp.x;
-            const int a = lower_bound_id(e, sp.y, lo, probes);
-            const int b = a + lower_bound_id(e + a, sp.y - a, hi, probes);
-            st = sp.x + a;
-            len = b - a;
+            // three independent lower bounds (lo, hi, mu) advanced together: their loads overlap
+            int l1 = 0, h1 = sp.y, l2 = 0, h2 = sp.y, l3 = 0, h3 = mu_in ? sp.y : 0;
+            while (l1 < h1 || l2 < h2 || l3 < h3) {
+                const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1, m3 = (l3 + h3) >> 1;
+                const uint32_t v1 = l1 < h1 ? (uint32_t)e[m1] : 0u;
+                const uint32_t v2 = l2 < h2 ? (uint32_t)e[m2] : 0u;
+                const uint32_t v3 = l3 < h3 ? (uint32_t)e[m3] : 0u;
+                if (l1 < h1) { ++probes; if (v1 < lo) l1 = m1 + 1; else h1 = m1; }
+                if (l2 < h2) { ++probes; if (v2 < hi) l2 = m2 + 1; else h2 = m2; }
+                if (l3 < h3) { ++probes; if (v3 < (uint32_t)mu) l3 = m3 + 1; else h3 = m3; }
+            }
+            st = sp.x + l1;
+            len = l2 - l1;
             if (mu_in) {
-                hl = lower_bound_id(e + a, len, (uint32_t)mu, probes);
+                hl = l3 - l1;
                 len -= 1;
             }
         }
@@ -574,17 +623,17 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     }
     if (nneed > kLQ) return true;
     // picks for every needed layer (none when h = n)
-    uint32_t total_picks = 0;
-    bool take_all = false;
+    uint32_t total_picks = 0, take_all_n = 0;
     for (uint32_t q = 0; q < nneed; ++q) {
         const Need nd = need[q];
-        if (nd.h < nd.n) total_picks += nd.h; else take_all = true;
+        if (nd.h < nd.n) total_picks += nd.h; else take_all_n += nd.n;
         if (total_picks > kPCap) return true;
     }
     const int T = tsum - dh;
-    // a chunk index lets the warp read only the id ranges that hold the picks
+    // a chunk index lets the warp read only the id ranges that hold the picks (and the members
+    // of layers taken whole, when there are few of them)
     uint64_t iw = 0;
-    if (dh != 1 && T > kIdxMinT && !take_all && total_picks <= 32) iw = P.idx[mu];
+    if (dh != 1 && T > kIdxMinT && total_picks + take_all_n <= (uint32_t)kPCap) iw = P.idx[mu];
     if (dh != 1 && iw == 0 && T > kWCap) return true;
     uint32_t* picks = S.u.w.wpick[wid];
     uint32_t* poff = S.wpoff[wid];
@@ -630,31 +679,29 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     uint32_t* buf = S.u.w.wbuf[wid];
     int* cnt = S.wcnt[wid];
     if (iw != 0) {
-        // chunk path: each pick's chunk from its layer's row of prefix counts, then the chunks
-        // that hold picks in ascending order, ranks starting from the row entries
+        // chunk path: lane q follows needed layer q through its row of prefix counts: the next
+        // position it needs (its next pick, or for a layer taken whole its next member) and the
+        // chunk holding it; the warp visits those chunks in ascending order, each ranked from the
+        // row entries at that chunk
         const int c = (int)(iw >> kIdxBitsShift);
+        const int C = 1 << c;
         const uint64_t toff = iw & ((1ull << kIdxBitsShift) - 1);
         const int sh = P.id_bits - c;
-        uint32_t probes = 0, my_chunk = 0xFFFFFFFFu;
+        uint32_t probes = 0, cur = 0xFFFFFFFFu, cursor = 0;
         unsigned long long gath = 0;
-        if ((uint32_t)lane < total_picks) {
-            uint32_t q = 0;
-            while (q + 1 < nneed && poff[q + 1] <= (uint32_t)lane) ++q;
-            const uint32_t a = picks[lane];
-            const uint32_t* row = P.idx_tab + toff + ((uint64_t)(need[q].layer - 1) << c);
-            int lo = 0, hi = 1 << c;  // last chunk whose prefix is <= a
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                ++probes;
-                if (row[mid] <= a) lo = mid; else hi = mid;
-            }
-            my_chunk = (uint32_t)lo;
+        Need nd{};
+        const uint32_t* row = nullptr;
+        if ((uint32_t)lane < nneed) {
+            nd = need[lane];
+            row = P.idx_tab + toff + ((uint64_t)(nd.layer - 1) << c);
+            const uint32_t first = nd.h < nd.n ? picks[poff[lane]] : 0u;
+            cur = (uint32_t)chunk_of(row, 0, C, first, probes);
         }
-        uint32_t k = __reduce_min_sync(0xFFFFFFFFu, my_chunk);
+        uint32_t k = __reduce_min_sync(0xFFFFFFFFu, cur);
         int chunks = 0;
         while (k != 0xFFFFFFFFu) {
-            for (uint32_t q = lane; q < nneed; q += 32) {
-                cnt[q] = (int)P.idx_tab[toff + ((uint64_t)(need[q].layer - 1) << c) + k];
+            if ((uint32_t)lane < nneed) {
+                cnt[lane] = (int)row[k];
                 ++probes;
             }
             __syncwarp();
@@ -666,7 +713,20 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
             gath += (unsigned long long)got;
             warp_walk(P, S, vis, list, buf, got, nneed);
             ++chunks;
-            k = __reduce_min_sync(0xFFFFFFFFu, my_chunk > k ? my_chunk : 0xFFFFFFFFu);
+            if (cur == k) {
+                const uint32_t endk = (int)k + 1 < C ? row[k + 1] : nd.n;  // members of L_q before chunk k + 1
+                ++probes;
+                uint32_t nxt = 0xFFFFFFFFu;
+                if (nd.h < nd.n) {
+                    const uint32_t* pk = picks + poff[lane];
+                    while (cursor < nd.h && pk[cursor] < endk) ++cursor;
+                    if (cursor < nd.h) nxt = pk[cursor];
+                } else if (endk < nd.n) {
+                    nxt = endk;
+                }
+                cur = nxt != 0xFFFFFFFFu ? (uint32_t)chunk_of(row, (int)k + 1, C, nxt, probes) : 0xFFFFFFFFu;
+            }
+            k = __reduce_min_sync(0xFFFFFFFFu, cur);
         }
         probes = __reduce_add_sync(0xFFFFFFFFu, probes);
         if (lane == 0) {
@@ -774,7 +834,7 @@ __device__ bool block_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t*
     return block_done(S, nq, picks);
 }
 
-__device__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
+__device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
                           uint32_t ybase, int32_t mu, uint32_t* picks_g, uint32_t* big) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 vi = P.vinfo[mu];
@@ -991,44 +1051,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
             vis[root >> 5] |= 1u << (root & 31);
             S.ctrl[C_HEAD] = 0;
             S.ctrl[C_TAIL] = 1;
+            S.ctrl[C_DONE] = 0;
+            S.ctrl[C_NDEF] = 0;
         }
         __syncthreads();
-        // level-synchronous reverse BFS
-        while (S.ctrl[C_HEAD] < S.ctrl[C_TAIL]) {
+        // reverse BFS over an asynchronous queue: a warp pops any vertex already discovered
+        // (the draws are keyed by (RR, vertex, layer), so the order of pops does not change R);
+        // the block only meets when every pending pop needs the block path
+        for (;;) {
+            for (;;) {
+                int idx = 0;
+                if (lane == 0) idx = claim_slot(P, S, job);
+                idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+                if (idx < 0) break;
+                int32_t mu = 0;
+                if (lane == 0) mu = slot_value(P, list, idx, job);
+                mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
+                const bool defer = mu >= 0 && pop_warp(P, S, vis, list, j, ybase, mu);
+                __syncwarp();
+                if (lane == 0) {
+                    if (defer) {
+                        S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
+                    } else {
+                        __threadfence_block();  // this pop's pushes before its completion
+                        atomicAdd(&S.ctrl[C_DONE], 1);
+                    }
+                }
+            }
+            if (threadIdx.x == 0) S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0;
+            __syncthreads();
+            if (S.ctrl[C_DONE] == S.ctrl[C_TAIL] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
+            // the block materialises the deferred pops
+            const int ndef = S.ctrl[C_NDEF];
+            for (int d = 0; d < ndef; ++d) pop_block(P, S, vis, list, j, ybase, S.deferred[d], picks_g, big);
             __syncthreads();
             if (threadIdx.x == 0) {
-                S.ctrl[C_LEVEL_END] = S.ctrl[C_TAIL];
-                S.ctrl[C_NEXT] = S.ctrl[C_HEAD];
+                S.ctrl[C_DONE] += ndef;
                 S.ctrl[C_NDEF] = 0;
             }
-            __syncthreads();
-            const int level_end = S.ctrl[C_LEVEL_END];
-            for (;;) {
-                // phase 1: warps pop vertices of this level
-                for (;;) {
-                    int idx = 0;
-                    if (lane == 0)
-                        idx = (*(volatile int*)&S.ctrl[C_NDEF] > kDCap - kWarps)
-                                  ? level_end
-                                  : atomicAdd(&S.ctrl[C_NEXT], 1);
-                    idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-                    if (idx >= level_end) break;
-                    const int32_t mu = list[idx];
-                    const bool defer = pop_warp(P, S, vis, list, j, ybase, mu);
-                    if (defer && lane == 0) S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
-                    __syncwarp();
-                }
-                __syncthreads();
-                // phase 2: the block materialises the deferred pops
-                const int ndef = S.ctrl[C_NDEF];
-                for (int d = 0; d < ndef; ++d) pop_block(P, S, vis, list, j, ybase, S.deferred[d], picks_g, big);
-                __syncthreads();
-                if (threadIdx.x == 0) S.ctrl[C_NDEF] = 0;
-                const bool more = S.ctrl[C_NEXT] < level_end;
-                __syncthreads();
-                if (!more) break;
-            }
-            if (threadIdx.x == 0) S.ctrl[C_HEAD] = level_end;
             __syncthreads();
         }
         // work counters of this RR set go to its pool
@@ -1097,6 +1157,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
             __syncthreads();
             for (int64_t w = threadIdx.x; w < nwords; w += kThreads) vis[w] = 0;
         }
+        for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
         __syncthreads();
     }
     __syncthreads();
@@ -1175,6 +1236,7 @@ hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
     S = Scratch{0, 0, 0, 0, 0, nullptr, nullptr, nullptr, nullptr, S.arena, S.arena_cap};
     hyperim_status st;
     if ((st = dev_alloc(g, (void**)&S.list, sizeof(int32_t) * list_cap * blocks))) return st;
+    HYP_CUDA(cudaMemsetAsync(S.list, 0xFF, sizeof(int32_t) * list_cap * blocks, g->stream));  // empty slots
     if (vis_words) {
         if ((st = dev_alloc(g, (void**)&S.bitmap, sizeof(uint32_t) * vis_words * blocks))) return st;
         HYP_CUDA(cudaMemsetAsync(S.bitmap, 0, sizeof(uint32_t) * vis_words * blocks, g->stream));
@@ -1312,7 +1374,11 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         HYP_CUDA(cudaGetLastError());
         HYP_CUDA(cudaEventRecord(ev1, s));
         HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
-        if ((st = check_device_status(g, "RR generation"))) return st;
+        if ((st = check_device_status(g, "RR generation"))) {
+            // a failed launch may leave queue slots filled: empty them for the next one
+            cudaMemsetAsync(g->scratch.list, 0xFF, sizeof(int32_t) * g->scratch.list_cap * g->scratch.blocks, s);
+            return st;
+        }
         float ms = 0.f;
         HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
         seconds += 1e-3 * (double)ms;
