@@ -47,16 +47,18 @@ def peaks():
 def rr_algorithmic_bytes(v):
     """Bytes the RR generator must move, from its work counters and the device layout: per pop
     the per-vertex record (8) and one 32-byte entry per layer of A(mu); per materialising pop the
-    hyperedge spans (8 + 4 per hyperedge), the record and sum of sizes (12) and every member of
-    mu's hyperedges (4 each); per member of R its queue write, queue read and output write (12);
-    per RR set its root (4)."""
+    hyperedge spans (8 + 4 per hyperedge) and the record and sum of sizes (12); the member ids
+    the materialisations need (4 each: all of mu's hyperedges in one pass, or only the id slices
+    of the chunks that hold picks when mu has a chunk index) and the words read to locate those
+    slices (4 each: extra span reads, binary-search probes, chunk-index entries); per member of R
+    its queue write, queue read and output write (12); per RR set its root (4)."""
     return (8 * v["pops"] + 32 * v["layers_seen"] + 12 * v["mats"] + 12 * v["mat_he"]
-            + 4 * v["mat_members"] + 12 * v["total"] + 4 * v["count"])
+            + 4 * v["gathered"] + 4 * v["search_words"] + 12 * v["total"] + 4 * v["count"])
 
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("rr.cu", "mat.cuh", "device_math.cuh"):
+    for f in ("rr.cu", "mat.cuh", "device_math.cuh", "index.cu"):
         h.update(open(os.path.join(ROOT, "paper_2406_01911_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -124,18 +124,33 @@ __global__ void k_idx_word(const int32_t* __restrict__ list, int32_t nlist, cons
         if (entries[i]) idx[list[i]] = ((uint64_t)bits[i] << kIdxBitsShift) | (uint64_t)off[i];
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Per indexed vertex (one block): members bucketed by chunk through a global scratch area; the
+// warps then take chunks in turn, sort one on chip (warp bucket sort), count its runs per layer
+// (multiplicity w -> layer by search in the descending w list) and write the counts as column k;
+// finally every layer row becomes an exclusive prefix along the chunks.
+constexpr int kFillWarps = 4;
+constexpr int kFillThreads = kFillWarps * 32;
+constexpr size_t kFillSmem = sizeof(int) * kBins + sizeof(uint32_t) * kIdxMaxL +
+                             sizeof(int) * (2 * kFillThreads + 1) +
+                             kFillWarps * (sizeof(uint32_t) * (2 * kIdxTarget + kIdxMaxL) + sizeof(int) * 256);
+
+__global__ void __launch_bounds__(kFillThreads)
 k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __restrict__ bits_in,
            const uint32_t* __restrict__ entries, const int64_t* __restrict__ off,
            const int4* __restrict__ vinfo, const int2* __restrict__ v_span,
            const int32_t* __restrict__ he_mem, const uint4* __restrict__ prof, int id_bits,
            uint32_t* __restrict__ tab, uint32_t* __restrict__ scratch, int64_t scratch_cap,
            DevStatus* st) {
-    __shared__ int chunk_end[kBins];
-    __shared__ uint32_t lw[kIdxMaxL];
-    __shared__ int run[kIdxMaxL];
-    __shared__ uint32_t buf[kIdxTarget];
-    __shared__ int pre[2 * kThreads + 1];
+    extern __shared__ __align__(16) unsigned char fill_smem[];
+    int* chunk_end = reinterpret_cast<int*>(fill_smem);                 // kBins
+    uint32_t* lw = reinterpret_cast<uint32_t*>(chunk_end + kBins);      // kIdxMaxL
+    int* pre = reinterpret_cast<int*>(lw + kIdxMaxL);                   // 2 kFillThreads + 1
+    uint32_t* wbase = reinterpret_cast<uint32_t*>(pre + 2 * kFillThreads + 1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* raw = wbase + (size_t)wid * (2 * kIdxTarget + kIdxMaxL);
+    uint32_t* srt = raw + kIdxTarget;
+    uint32_t* wcnt = srt + kIdxTarget;                                  // kIdxMaxL per warp
+    int* bkt = reinterpret_cast<int*>(wbase + (size_t)kFillWarps * (2 * kIdxTarget + kIdxMaxL)) + wid * 256;
     uint32_t* big = scratch + (int64_t)blockIdx.x * scratch_cap;
     for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
         if (entries[i] == 0) continue;
@@ -144,53 +159,74 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
         const int l = vi.y, c = bits_in[i];
         const int C = 1 << c, shift = id_bits - c;
         uint32_t* t = tab + off[i];
-        for (int q = threadIdx.x; q < l; q += kThreads) {
-            lw[q] = prof[2 * ((int64_t)vi.x + q)].x & ~kPOneFlag;
-            run[q] = 0;
-        }
-        for (int k = threadIdx.x; k < C; k += kThreads) chunk_end[k] = 0;
+        for (int q = threadIdx.x; q < l; q += kFillThreads) lw[q] = prof[2 * ((int64_t)vi.x + q)].x & ~kPOneFlag;
+        for (int k = threadIdx.x; k < C; k += kFillThreads) chunk_end[k] = 0;
         __syncthreads();
-        for_each_member<kThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
-                                  [&](uint32_t x) { atomicAdd(&chunk_end[x >> shift], 1); });
+        for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
+                                      [&](uint32_t x) { atomicAdd(&chunk_end[x >> shift], 1); });
         __syncthreads();
         warp0_exclusive_scan(chunk_end, C);
         __syncthreads();
-        for_each_member<kThreads>(v_span, he_mem, mu, vi.z, vi.w, pre, [&](uint32_t x) {
+        for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre, [&](uint32_t x) {
             const int p = atomicAdd(&chunk_end[x >> shift], 1);
             if (p < scratch_cap) big[p] = x;
         });
         __threadfence_block();
         __syncthreads();
         // chunk_end[k] is now the end of chunk k
-        int begin = 0;
-        for (int k = 0; k < C; ++k) {
-            for (int q = threadIdx.x; q < l; q += kThreads) t[(int64_t)q * C + k] = (uint32_t)run[q];
-            const int end = chunk_end[k];
-            const int cnt = end - begin;
+        if (chunk_end[C - 1] > scratch_cap) {
+            if (threadIdx.x == 0) dev_fail(st, kErrCapacity, mu);
             __syncthreads();
-            if (cnt > kIdxTarget || end > scratch_cap) {
-                if (threadIdx.x == 0) dev_fail(st, kErrBucket, mu);
-                break;  // uniform
-            }
-            if (cnt > 0) {
-                for (int x = threadIdx.x; x < cnt; x += kThreads) buf[x] = big[begin + x];
-                __syncthreads();
-                group_sort<kThreads>(buf, cnt);
-                walk_runs<kThreads>(buf, cnt, [&](bool start, uint32_t, int mult) -> bool {
+            continue;
+        }
+        for (int k = wid; k < C; k += kFillWarps) {
+            const int begin = k ? chunk_end[k - 1] : 0;
+            const int cnt = chunk_end[k] - begin;
+            for (int q = lane; q < l; q += 32) wcnt[q] = 0;
+            if (cnt > kIdxTarget) {
+                if (lane == 0) dev_fail(st, kErrBucket, mu);
+            } else if (cnt > 0) {
+                const int nbits = bucket_bits(cnt, 8);
+                const int nb = 1 << nbits;
+                const int bshift = shift > nbits ? shift - nbits : 0;
+                const uint32_t key_mask = (uint32_t)nb - 1;
+                for (int b = lane; b < nb; b += 32) bkt[b] = 0;
+                __syncwarp();
+                for (int x = lane; x < cnt; x += 32) {
+                    const uint32_t v = big[begin + x];
+                    raw[x] = v;
+                    atomicAdd(&bkt[(v >> bshift) & key_mask], 1);
+                }
+                __syncwarp();
+                const int maxb = warp_bucket_scan(bkt, nb);
+                warp_scatter_sort(raw, cnt, kSentinel, srt, cnt, bkt, nb, 0u, bshift, key_mask, maxb);
+                walk_runs<32>(srt, cnt, [&](bool start, uint32_t, int mult) -> bool {
                     if (start) {
                         int lo = 0, hi = l;  // lw descends: first q with lw[q] <= mult
                         while (lo < hi) {
                             const int mid = (lo + hi) >> 1;
                             if (lw[mid] > (uint32_t)mult) lo = mid + 1; else hi = mid;
                         }
-                        if (lo < l && lw[lo] == (uint32_t)mult) atomicAdd(&run[lo], 1);
+                        if (lo < l && lw[lo] == (uint32_t)mult) atomicAdd(&wcnt[lo], 1u);
                         else dev_fail(st, kErrProfile, mu);
                     }
                     return false;
                 });
-                __syncthreads();
             }
-            begin = end;
+            __syncwarp();
+            for (int q = lane; q < l; q += 32) t[(int64_t)q * C + k] = wcnt[q];
+            __syncwarp();
+        }
+        __syncthreads();
+        // counts -> exclusive prefix along the chunks, one layer row per thread
+        for (int q = threadIdx.x; q < l; q += kFillThreads) {
+            uint32_t* row = t + (int64_t)q * C;
+            uint32_t run = 0;
+            for (int k = 0; k < C; ++k) {
+                const uint32_t v = row[k];
+                row[k] = run;
+                run += v;
+            }
         }
         __syncthreads();
     }
@@ -253,8 +289,9 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         if ((st = dev_alloc(g, (void**)&g->idx_tab, sizeof(uint32_t) * (size_t)total))) return st;
         { k_idx_word<<<grid_for(ncand, 256, sm), 256, 0, s>>>(d_list, nl, d_bits, d_entries, d_off, g->idx); count_launch(); }
         // per resident block, room for the largest neighbourhood
+        HYP_CUDA(cudaFuncSetAttribute(k_idx_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFillSmem));
         int per_sm = 0;
-        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_idx_fill, kThreads, 0));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_idx_fill, kFillThreads, kFillSmem));
         if (per_sm < 1) per_sm = 1;
         const int64_t cap = g->max_tsum;
         int fblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * per_sm);
@@ -262,7 +299,7 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)1 << 30)) fblocks -= sm;
         uint32_t* d_scratch = nullptr;
         if ((st = dev_alloc(g, (void**)&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
-        { k_idx_fill<<<fblocks, kThreads, 0, s>>>(d_list, nl, d_bits, d_entries, d_off, g->vinfo, g->v_span,
+        { k_idx_fill<<<fblocks, kFillThreads, kFillSmem, s>>>(d_list, nl, d_bits, d_entries, d_off, g->vinfo, g->v_span,
                                                   g->he_mem, g->prof, g->id_bits, g->idx_tab, d_scratch, cap,
                                                   g->d_status); count_launch(); }
         if ((st = check_device_status(g, "chunk index"))) return st;

@@ -45,7 +45,7 @@ struct RRCounters {
 constexpr int kIdxMinT = 2048;
 constexpr int kIdxTarget = 1024;
 constexpr int kIdxMaxBits = 12;
-constexpr int kIdxMaxL = 2048;
+constexpr int kIdxMaxL = 1024;
 // idx word of a vertex: 0 = no index, else (c << 56) | offset of its table
 constexpr int kIdxBitsShift = 56;
 

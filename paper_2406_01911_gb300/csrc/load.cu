@@ -20,6 +20,9 @@ constexpr int kProfThreads = 256;
 constexpr int kProfBuf = 8192;  // on-chip keys of the profile kernel (power of two)
 constexpr int kProfHist = 4096; // on-chip multiplicity histogram bins
 constexpr int kBucketsMax = 4096;
+constexpr int kProfWarpT = 1024;  // vertices with at most this many positions: warp profile
+constexpr int kPWWarps = 4;
+constexpr int kPWThreads = kPWWarps * 32;
 
 __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
@@ -158,39 +161,67 @@ struct ProfScratch {
     int64_t hist_cap;
 };
 
-__global__ void __launch_bounds__(kProfThreads)
-k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
-          uint2* __restrict__ pairs, uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
-          int* __restrict__ next_vertex, ProfScratch S, DevStatus* st,
-          unsigned long long* __restrict__ maxima /* [max_l, max_deg, max_layer_n] */) {
-    extern __shared__ uint32_t smem[];
-    uint32_t* buf = smem;                                  // kProfBuf
-    uint32_t* hist_s = buf + kProfBuf;                     // kProfHist
-    int* bucket_cnt = (int*)(hist_s + kProfHist);          // kBucketsMax
-    int* ctrl = bucket_cnt + kBucketsMax;                  // small control block
-    using Gr = Group<kProfThreads>;
-    uint32_t* big = S.big + (int64_t)blockIdx.x * S.big_cap;
-    uint32_t* hist_g = S.hist + (int64_t)blockIdx.x * S.hist_cap;
+// Distinct multiplicities of hist[1..dh] in descending order -> pairs (w_i, n_i), l, deg and the
+// maxima; one warp (lanes 0..31).
+__device__ void emit_layers(const uint32_t* hist, int dh, int32_t mu, int32_t e0, uint2* __restrict__ pairs,
+                            uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
+                            unsigned long long* __restrict__ maxima) {
+    const int lane = threadIdx.x & 31;
+    int carry = 0;
+    uint32_t dsum = 0, nmax = 0;
+    for (int top = dh; top >= 1; top -= 32) {
+        const int w = top - lane;
+        const uint32_t c = w >= 1 ? hist[w] : 0u;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, c > 0);
+        const int pos = carry + __popc(bal & lanemask_lt());
+        if (c > 0) pairs[e0 + pos] = make_uint2((uint32_t)w, c);
+        carry += __popc(bal);
+        dsum += c;
+        nmax = max(nmax, c);
+    }
+    dsum = __reduce_add_sync(0xFFFFFFFFu, dsum);
+    nmax = __reduce_max_sync(0xFFFFFFFFu, nmax);
+    if (lane == 0) {
+        nlayers[mu] = (uint32_t)carry;
+        deg[mu] = dsum;
+        atomicMax(&maxima[0], (unsigned long long)carry);
+        atomicMax(&maxima[1], (unsigned long long)dsum);
+        atomicMax(&maxima[2], (unsigned long long)nmax);
+    }
+}
 
-    for (;;) {
-        if (threadIdx.x == 0) ctrl[0] = atomicAdd(next_vertex, 1);
-        __syncthreads();
-        const int32_t mu = ctrl[0];
-        __syncthreads();
-        if (mu >= n) break;
-        const int32_t e0 = I.v_off[mu], dh = I.v_off[mu + 1] - e0;
+// Layer profile, small vertices: one warp per vertex whose hyperedges hold at most kProfWarpT
+// positions (mu's own included), and every vertex with d_H <= 1. The members are gathered once
+// into a raw copy and counted into buckets of their top id bits, scattered into id order and
+// sorted per bucket (the RR kernel's warp sort), then the runs give the multiplicity histogram.
+__global__ void __launch_bounds__(kPWThreads)
+k_profile_warp(int32_t n, const int32_t* __restrict__ v_off, const int2* __restrict__ v_span,
+               const int32_t* __restrict__ he_mem, const int32_t* __restrict__ tsum, int id_bits,
+               uint2* __restrict__ pairs, uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
+               unsigned long long* __restrict__ maxima) {
+    __shared__ uint32_t raw_s[kPWWarps][kProfWarpT + 4];
+    __shared__ uint32_t buf_s[kPWWarps][kProfWarpT];
+    __shared__ int bkt_s[kPWWarps][256];
+    __shared__ int pre_s[kPWWarps][2 * 32 + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* raw = raw_s[wid];
+    uint32_t* buf = buf_s[wid];
+    int* bkt = bkt_s[wid];
+    const int64_t nw = (int64_t)gridDim.x * kPWWarps;
+    for (int64_t v = (int64_t)blockIdx.x * kPWWarps + wid; v < n; v += nw) {
+        const int32_t mu = (int32_t)v;
+        const int32_t e0 = v_off[mu], dh = v_off[mu + 1] - e0;
         if (dh == 0) {
-            if (threadIdx.x == 0) { nlayers[mu] = 0; deg[mu] = 0; }
+            if (lane == 0) { nlayers[mu] = 0; deg[mu] = 0; }
             continue;
         }
         if (dh == 1) {
-            if (threadIdx.x == 0) {
-                const int32_t he = I.v_he[e0];
-                const uint32_t nb = (uint32_t)(I.he_off[he + 1] - I.he_off[he] - 1);
+            if (lane == 0) {
+                const uint32_t nb = (uint32_t)(v_span[e0].y - 1);
                 nlayers[mu] = nb > 0 ? 1 : 0;
                 deg[mu] = nb;
-                if (nb > 0) pairs[e0] = make_uint2(1u, nb);
                 if (nb > 0) {
+                    pairs[e0] = make_uint2(1u, nb);
                     atomicMax(&maxima[0], 1ull);
                     atomicMax(&maxima[1], (unsigned long long)nb);
                     atomicMax(&maxima[2], (unsigned long long)nb);
@@ -198,6 +229,78 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
             }
             continue;
         }
+        const int ts = tsum[mu];
+        if (ts > kProfWarpT) continue;  // the block kernel's vertex
+        const int T = ts - dh;
+        const int nbits = bucket_bits(T, 8);
+        const int nb = 1 << nbits;
+        const int shift = id_bits > nbits ? id_bits - nbits : 0;
+        const uint32_t key_mask = (uint32_t)nb - 1;
+        for (int b = lane; b < nb; b += 32) bkt[b] = 0;
+        __syncwarp();
+        for_each_position<32>(v_span, he_mem, e0, dh, pre_s[wid], [&](int pos, uint32_t x) {
+            raw[pos] = x;
+            if (x != (uint32_t)mu) atomicAdd(&bkt[(x >> shift) & key_mask], 1);
+        });
+        const int maxb = warp_bucket_scan(bkt, nb);
+        warp_scatter_sort(raw, ts, (uint32_t)mu, buf, T, bkt, nb, 0u, shift, key_mask, maxb);
+        // multiplicity histogram over w in [1, dh] (the raw copy is free again)
+        uint32_t* hist = raw;
+        for (int w = lane; w <= dh; w += 32) hist[w] = 0;
+        __syncwarp();
+        walk_runs<32>(buf, T, [&](bool start, uint32_t, int mult) -> bool {
+            if (start) atomicAdd(&hist[mult], 1u);
+            return false;
+        });
+        __syncwarp();
+        emit_layers(hist, dh, mu, e0, pairs, nlayers, deg, maxima);
+        __syncwarp();
+    }
+}
+
+// Vertices for the block profile kernel: d_H >= 2 and more than kProfWarpT positions.
+__global__ void k_big_flags(int32_t n, const int32_t* __restrict__ v_off, const int32_t* __restrict__ tsum,
+                            uint32_t* __restrict__ flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        flag[v] = (v_off[v + 1] - v_off[v] >= 2 && tsum[v] > kProfWarpT) ? 1u : 0u;
+}
+
+__global__ void k_big_list(int32_t n, const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                           int32_t* __restrict__ list) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (flag[v]) list[pos[v]] = (int32_t)v;
+}
+
+// Layer profile, large vertices (more than kProfWarpT positions): one block per vertex. Up to
+// kProfBuf members are bucket-sorted on chip; larger neighbourhoods are first split into id
+// chunks through a global scratch area, and each chunk is bucket-sorted on chip in id order.
+__global__ void __launch_bounds__(kProfThreads)
+k_profile(Incidence I, const int2* __restrict__ v_span, const int32_t* __restrict__ big_list, int32_t nbig,
+          int id_bits, const int32_t* __restrict__ tsum,
+          uint2* __restrict__ pairs, uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
+          int* __restrict__ next_vertex, ProfScratch S, DevStatus* st,
+          unsigned long long* __restrict__ maxima /* [max_l, max_deg, max_layer_n] */) {
+    extern __shared__ uint32_t smem[];
+    uint32_t* buf = smem;                                  // kProfBuf
+    uint32_t* hist_s = buf + kProfBuf;                     // kProfHist
+    int* bucket_cnt = (int*)(hist_s + kProfHist);          // kBucketsMax (first-level chunks)
+    int* bkt = bucket_cnt + kBucketsMax;                   // kBucketsMax (on-chip sort)
+    int* pre = bkt + kBucketsMax;                          // 2 kProfThreads + 1
+    int* ctrl = pre + 2 * kProfThreads + 1;                // small control block
+    using Gr = Group<kProfThreads>;
+    uint32_t* big = S.big + (int64_t)blockIdx.x * S.big_cap;
+    uint32_t* hist_g = S.hist + (int64_t)blockIdx.x * S.hist_cap;
+
+    for (;;) {
+        if (threadIdx.x == 0) ctrl[0] = atomicAdd(next_vertex, 1);
+        __syncthreads();
+        const int bi = ctrl[0];
+        __syncthreads();
+        if (bi >= nbig) break;
+        const int32_t mu = big_list[bi];
+        const int32_t e0 = I.v_off[mu], dh = I.v_off[mu + 1] - e0;
         // histogram of multiplicities, indexed by w in [1, dh]
         uint32_t* hist = dh < kProfHist ? hist_s : hist_g;
         if (dh >= kProfHist && (int64_t)dh + 1 > S.hist_cap) {
@@ -212,8 +315,8 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
         };
         const int T = tsum[mu] - dh;  // members other than mu
         if (T <= kProfBuf) {
-            const int got = gather_nbhd<kProfThreads>(I, mu, buf, &ctrl[1]);
-            group_sort<kProfThreads>(buf, got);
+            const int got = sorted_nbhd<kProfThreads>(v_span, I.he_mem, mu, e0, dh, T, id_bits, buf, bkt, 12,
+                                                      pre, ctrl + 16);
             walk_runs<kProfThreads>(buf, got, count_runs);
         } else {
             // bucket the members by their top id bits so each bucket fits on chip
@@ -229,16 +332,8 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
                 const int shift = id_bits - b;
                 for (int i = threadIdx.x; i < nb; i += kProfThreads) bucket_cnt[i] = 0;
                 __syncthreads();
-                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                for (int e = e0 + wid; e < e0 + dh; e += kProfThreads / 32) {
-                    const int he = I.v_he[e];
-                    const int hb = I.he_off[he], len = I.he_off[he + 1] - hb;
-                    for (int i = lane; i < len; i += 32) {
-                        const uint32_t x = (uint32_t)I.he_mem[hb + i];
-                        if (x != (uint32_t)mu) atomicAdd(&bucket_cnt[x >> shift], 1);
-                    }
-                }
-                __syncthreads();
+                for_each_member<kProfThreads>(v_span, I.he_mem, mu, e0, dh, pre,
+                                              [&](uint32_t x) { atomicAdd(&bucket_cnt[x >> shift], 1); });
                 int mx = 0;
                 for (int i = threadIdx.x; i < nb; i += kProfThreads) mx = max(mx, bucket_cnt[i]);
                 const int bmax = __reduce_max_sync(0xFFFFFFFFu, mx);
@@ -275,26 +370,16 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
             }
             __syncthreads();
             // scatter into the global bucket area; bucket_cnt becomes the running end
-            {
-                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                for (int e = e0 + wid; e < e0 + dh; e += kProfThreads / 32) {
-                    const int he = I.v_he[e];
-                    const int hb = I.he_off[he], len = I.he_off[he + 1] - hb;
-                    for (int i = lane; i < len; i += 32) {
-                        const uint32_t x = (uint32_t)I.he_mem[hb + i];
-                        if (x != (uint32_t)mu) big[atomicAdd(&bucket_cnt[x >> shift], 1)] = x;
-                    }
-                }
-            }
+            for_each_member<kProfThreads>(v_span, I.he_mem, mu, e0, dh, pre,
+                                          [&](uint32_t x) { big[atomicAdd(&bucket_cnt[x >> shift], 1)] = x; });
+            __threadfence_block();
             __syncthreads();
             int begin = 0;
             for (int q = 0; q < nb; ++q) {
                 const int end = bucket_cnt[q];
                 const int cnt = end - begin;
                 if (cnt > 0) {
-                    for (int i = threadIdx.x; i < cnt; i += kProfThreads) buf[i] = big[begin + i];
-                    __syncthreads();
-                    group_sort<kProfThreads>(buf, cnt);
+                    sort_chunk<kProfThreads>(big + begin, cnt, shift, buf, bkt, 12, ctrl + 16);
                     walk_runs<kProfThreads>(buf, cnt, count_runs);
                     __syncthreads();
                 }
@@ -302,32 +387,7 @@ k_profile(Incidence I, int32_t n, int id_bits, const int32_t* __restrict__ tsum,
             }
         }
         __syncthreads();
-        // distinct multiplicities in descending order -> (w_i, n_i); single warp
-        if (threadIdx.x < 32) {
-            int carry = 0;
-            uint32_t dsum = 0, nmax = 0;
-            for (int top = dh; top >= 1; top -= 32) {
-                const int w = top - (int)threadIdx.x;
-                const uint32_t c = w >= 1 ? hist[w] : 0u;
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, c > 0);
-                const int pos = carry + __popc(bal & lanemask_lt());
-                if (c > 0) pairs[e0 + pos] = make_uint2((uint32_t)w, c);
-                carry += __popc(bal);
-                dsum += c;
-                nmax = max(nmax, c);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, o);
-                nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, o));
-            }
-            if (threadIdx.x == 0) {
-                nlayers[mu] = (uint32_t)carry;
-                deg[mu] = dsum;
-                atomicMax(&maxima[0], (unsigned long long)carry);
-                atomicMax(&maxima[1], (unsigned long long)dsum);
-                atomicMax(&maxima[2], (unsigned long long)nmax);
-            }
-        }
+        if (threadIdx.x < 32) emit_layers(hist, dh, mu, e0, pairs, nlayers, deg, maxima);
         __syncthreads();
     }
 }
@@ -559,7 +619,14 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     d_deg = (uint32_t*)g->deg;
     if ((st = dev_alloc(g, (void**)&d_next, sizeof(int)))) return st;
     HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
-    const size_t prof_smem = sizeof(uint32_t) * (kProfBuf + kProfHist) + sizeof(int) * (kBucketsMax + 8 + kProfThreads / 32);
+    // per-incidence spans first: both profile kernels gather through them
+    if ((st = dev_alloc(g, (void**)&g->v_span, sizeof(int2) * nnz_a))) return st;
+    if (nnz > 0)
+        { k_build_spans<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->v_span); count_launch(); }
+    { k_profile_warp<<<grid_for((int64_t)n * 32, kPWThreads, sm), kPWThreads, 0, s>>>(
+        n, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg, d_max); count_launch(); }
+    const size_t prof_smem = sizeof(uint32_t) * (kProfBuf + kProfHist) +
+                             sizeof(int) * (2 * kBucketsMax + 2 * kProfThreads + 1 + 32);
     HYP_CUDA(cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)prof_smem));
     int per_sm = 0;
@@ -575,9 +642,28 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks)))
         return st;
     Incidence I{g->he_off, g->he_mem, g->v_off, g->v_he};
-    { k_profile<<<pblocks, kProfThreads, prof_smem, s>>>(I, n, g->id_bits, g->tsum, d_pairs, d_nl,
-                                                       d_deg, d_next, PS, g->d_status, d_max); count_launch(); }
+    // the large vertices, listed
+    uint32_t* d_bflag = nullptr;
+    int64_t* d_bpos = nullptr;
+    int32_t* d_blist = nullptr;
+    if ((st = dev_alloc(g, (void**)&d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)))) return st;
+    if ((st = dev_alloc(g, (void**)&d_bpos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if (n > 0) { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, d_bflag); count_launch(); }
+    if ((st = exclusive_scan_u32_to_i64(g, d_bflag, d_bpos, n))) return st;
+    int64_t nbig = 0;
+    HYP_CUDA(cudaMemcpyAsync(&nbig, d_bpos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    if ((st = dev_alloc(g, (void**)&d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1)))) return st;
+    if (nbig > 0) {
+        { k_big_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_bflag, d_bpos, d_blist); count_launch(); }
+        { k_profile<<<(int)std::min<int64_t>(pblocks, nbig), kProfThreads, prof_smem, s>>>(
+            I, g->v_span, d_blist, (int32_t)nbig, g->id_bits, g->tsum, d_pairs, d_nl, d_deg, d_next, PS,
+            g->d_status, d_max); count_launch(); }
+    }
     if ((st = check_device_status(g, "layer profile"))) return st;
+    dev_free(g, d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    dev_free(g, d_bpos, sizeof(int64_t) * ((size_t)n + 1));
+    dev_free(g, d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1));
     dev_free(g, PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks);
     dev_free(g, PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks);
     HYP_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, s));
@@ -643,11 +729,8 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     for (int l = 0; l < hcap; ++l)
         g->stratum_size[l < HYPERIM_NSTRATA - 1 ? l : HYPERIM_NSTRATA - 1] += (int64_t)lh[l];
 
-    // --- spans and per-vertex records for the RR kernel
-    if ((st = dev_alloc(g, (void**)&g->v_span, sizeof(int2) * nnz_a))) return st;
+    // --- per-vertex records for the RR kernel
     if ((st = dev_alloc(g, (void**)&g->vinfo, sizeof(int4) * (size_t)n))) return st;
-    if (nnz > 0)
-        { k_build_spans<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->v_span); count_launch(); }
     { k_build_vinfo<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->prof_off, g->v_off, g->vinfo); count_launch(); }
     if ((st = build_chunk_index(g))) return st;
 

@@ -433,4 +433,59 @@ __device__ void sort_chunk(const uint32_t* __restrict__ src, int count, int rem_
     Gr::sync();
 }
 
+// ------------------------------------------------------------------------------------------
+// Warp bucket sort pieces shared by the RR kernel and the load-time profile and index kernels.
+// ------------------------------------------------------------------------------------------
+// Exclusive scan of a warp's bucket counts bkt[0, nb) in place; returns the largest count.
+static __device__ int warp_bucket_scan(int* bkt, int nb) {
+    const int lane = threadIdx.x & 31;
+    int carry = 0, maxb = 0;
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+        const int b = c0 + lane;
+        const int v = b < nb ? bkt[b] : 0;
+        maxb = max(maxb, v);
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (b < nb) bkt[b] = carry + inc - v;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    __syncwarp();
+    return __reduce_max_sync(0xFFFFFFFFu, maxb);
+}
+
+// Scatter raw[0, nraw) (entries equal to skip left out; count remain) into buf by the bucket
+// starts in bkt (key ((x - base) >> shift) & key_mask), then sort each bucket by insertion, or
+// the whole buffer by the bitonic network when the largest bucket exceeds kBucketSortMax.
+static __device__ void warp_scatter_sort(const uint32_t* raw, int nraw, uint32_t skip, uint32_t* buf, int count,
+                                  int* bkt, int nb, uint32_t base, int shift, uint32_t key_mask, int maxb) {
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < nraw; p += 32) {
+        const uint32_t x = raw[p];
+        if (x != skip) buf[atomicAdd(&bkt[((x - base) >> shift) & key_mask], 1)] = x;
+    }
+    __syncwarp();
+    // bkt[b] is now the end of bucket b
+    if (maxb > kBucketSortMax) {
+        group_sort<32>(buf, count);
+        return;
+    }
+    for (int b = lane; b < nb; b += 32) {
+        const int e = bkt[b], s0 = b ? bkt[b - 1] : 0;
+        for (int i = s0 + 1; i < e; ++i) {
+            const uint32_t x = buf[i];
+            int k = i - 1;
+            while (k >= s0 && buf[k] > x) {
+                buf[k + 1] = buf[k];
+                --k;
+            }
+            buf[k + 1] = x;
+        }
+    }
+    __syncwarp();
+}
+
 }  // namespace hyperim

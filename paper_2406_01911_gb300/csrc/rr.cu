@@ -176,6 +176,31 @@ __device__ __forceinline__ bool layer_draw(const uint4 e, const uint4 f, const u
 // sel[0, h) receives the picked positions in ascending order.
 __device__ void gen_picks(WordStream& ws, uint32_t n, uint32_t h, uint32_t ksel, uint32_t* sel) {
     const int lane = threadIdx.x & 31;
+    if (h <= 32) {
+        // lane r draws a_r from its own word; the picks so far stay sorted across the lanes
+        // (lane i holds the i-th smallest), so each step is a few ballots
+        uint32_t a = 0, mine = 0xFFFFFFFFu;
+        if ((uint32_t)lane < h) {
+            const uint32_t x = ws.word(ksel + (uint32_t)lane);
+            a = (uint32_t)(((uint64_t)x * (uint64_t)(n - (uint32_t)lane)) >> 32);
+        }
+        for (uint32_t r = 0; r < h; ++r) {
+            const uint32_t ar = __shfl_sync(0xFFFFFFFFu, a, (int)r);
+            uint32_t idx = ar;
+            for (;;) {  // idx = a_r + #{picks <= idx}
+                const uint32_t c = __popc(__ballot_sync(0xFFFFFFFFu, (uint32_t)lane < r && mine <= idx));
+                if (ar + c == idx) break;
+                idx = ar + c;
+            }
+            const uint32_t at = __popc(__ballot_sync(0xFFFFFFFFu, (uint32_t)lane < r && mine < idx));
+            const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, mine, 1);
+            if ((uint32_t)lane > at && (uint32_t)lane <= r) mine = up;
+            if ((uint32_t)lane == at) mine = idx;
+        }
+        if ((uint32_t)lane < h) sel[lane] = mine;
+        __syncwarp();
+        return;
+    }
     for (uint32_t r = 0; r < h; ++r) {
         const uint32_t x = ws.word(ksel + r);
         const uint32_t a = (uint32_t)(((uint64_t)x * (uint64_t)(n - r)) >> 32);
@@ -270,58 +295,6 @@ __device__ int32_t slot_value(const RRParams& P, const int32_t* list, int idx, i
 // ------------------------------------------------------------------------------------------
 // warp path
 // ------------------------------------------------------------------------------------------
-// Exclusive scan of a warp's bucket counts bkt[0, nb) in place; returns the largest count.
-__device__ int warp_bucket_scan(int* bkt, int nb) {
-    const int lane = threadIdx.x & 31;
-    int carry = 0, maxb = 0;
-    for (int c0 = 0; c0 < nb; c0 += 32) {
-        const int b = c0 + lane;
-        const int v = b < nb ? bkt[b] : 0;
-        maxb = max(maxb, v);
-        int inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (b < nb) bkt[b] = carry + inc - v;
-        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
-    }
-    __syncwarp();
-    return __reduce_max_sync(0xFFFFFFFFu, maxb);
-}
-
-// Scatter raw[0, nraw) (entries equal to skip left out; count remain) into buf by the bucket
-// starts in bkt (key ((x - base) >> shift) & key_mask), then sort each bucket by insertion, or
-// the whole buffer by the bitonic network when the largest bucket exceeds kBucketSortMax.
-__device__ void warp_scatter_sort(const uint32_t* raw, int nraw, uint32_t skip, uint32_t* buf, int count,
-                                  int* bkt, int nb, uint32_t base, int shift, uint32_t key_mask, int maxb) {
-    const int lane = threadIdx.x & 31;
-    for (int p = lane; p < nraw; p += 32) {
-        const uint32_t x = raw[p];
-        if (x != skip) buf[atomicAdd(&bkt[((x - base) >> shift) & key_mask], 1)] = x;
-    }
-    __syncwarp();
-    // bkt[b] is now the end of bucket b
-    if (maxb > kBucketSortMax) {
-        group_sort<32>(buf, count);
-        return;
-    }
-    for (int b = lane; b < nb; b += 32) {
-        const int e = bkt[b], s0 = b ? bkt[b - 1] : 0;
-        for (int i = s0 + 1; i < e; ++i) {
-            const uint32_t x = buf[i];
-            int k = i - 1;
-            while (k >= s0 && buf[k] > x) {
-                buf[k + 1] = buf[k];
-                --k;
-            }
-            buf[k + 1] = x;
-        }
-    }
-    __syncwarp();
-}
-
 // A(mu) with at most kWHalf incidence positions (tsum, mu's own included), by one pass over the
 // members: a raw copy goes to buf[kWHalf, kWHalf + tsum) and the members are counted into
 // buckets of their top id bits. Returns 1 if the pops of this vertex are already done: when no
@@ -532,15 +505,24 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
 // Ranked walk of a sorted warp buffer buf[0, got): a run of multiplicity need[q].w is a member
 // of needed layer q, its rank in L_q is cnt[q] (the layer's members before the buffer) plus the
 // runs of that layer before it; members whose rank is a pick, or all of them when h = n, enter R.
-// Stops once every layer with picks has ranked past its last pick.
+// The running rank of layer q lives in lane q's register; each 32 positions take one ballot per
+// needed layer. Stops once every layer with picks has ranked past its last pick.
 __device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, const uint32_t* buf,
                           int got, uint32_t nneed) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const Need* need = S.wneed[wid];
     const uint32_t* picks = S.u.w.wpick[wid];
     const uint32_t* poff = S.wpoff[wid];
-    int* cnt = S.wcnt[wid];
-    uint32_t done_mask = 0, want_mask = (nneed >= 32 ? 0xFFFFFFFFu : ((1u << nneed) - 1));
+    uint32_t mycnt = (uint32_t)lane < nneed ? (uint32_t)S.wcnt[wid][lane] : 0u;
+    // lane q's layer: its last pick (or none when the layer is taken whole)
+    uint32_t mylast = 0xFFFFFFFFu;
+    bool mypicks = false;
+    if ((uint32_t)lane < nneed) {
+        const Need nd = need[lane];
+        mypicks = nd.h < nd.n;
+        if (mypicks) mylast = picks[poff[lane] + nd.h - 1];
+    }
+    const uint32_t want_mask = nneed >= 32 ? 0xFFFFFFFFu : ((1u << nneed) - 1);
     for (int base = 0; base < got; base += 32) {
         const int p = base + lane;
         bool start = false;
@@ -555,22 +537,19 @@ __device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
             }
         }
         for (uint32_t q = 0; q < nneed; ++q) {
-            const Need nd = need[q];
-            const bool f = start && (uint32_t)mult == nd.w;
+            const bool f = start && (uint32_t)mult == need[q].w;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
-            const uint32_t before = (uint32_t)cnt[q];
+            if (bal == 0) continue;
+            const uint32_t before = __shfl_sync(0xFFFFFFFFu, mycnt, (int)q);
             if (f) {
+                const Need nd = need[q];
                 const uint32_t rank = before + __popc(bal & lanemask_lt());
-                const bool take = nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank);
-                if (take) push(P, S, vis, list, x);
+                if (nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank)) push(P, S, vis, list, x);
             }
-            const uint32_t after = before + __popc(bal);
-            __syncwarp();
-            if (lane == 0) cnt[q] = (int)after;
-            __syncwarp();
-            if (nd.h < nd.n && after > picks[poff[q] + nd.h - 1]) done_mask |= 1u << q;
+            if ((uint32_t)lane == q) mycnt = before + __popc(bal);
         }
-        if ((done_mask & want_mask) == want_mask) break;
+        const bool done = mypicks && mycnt > mylast;
+        if ((__ballot_sync(0xFFFFFFFFu, done) & want_mask) == want_mask) break;
     }
     __syncwarp();
 }

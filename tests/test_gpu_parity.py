@@ -152,13 +152,13 @@ def test_distinct_neighbourhoods(H, oracle, uthr):
 
 def expected_chunk_index(og, v, id_bits):
     """(bits, table) the chunk index of v must hold, from the oracle's layers (None: no index).
-    Candidates: d_H >= 2, more than 2048 members besides v (repeats counted), 1 <= l_v <= 2048;
+    Candidates: d_H >= 2, more than 2048 members besides v (repeats counted), 1 <= l_v <= 1024;
     bits = the fewest top id bits (at most 12) for which no chunk holds more than 1024 of those
     members; table[i - 1, k] = members of L_i in chunks < k."""
     lay = og.layers(v)
     mem = [og.layer_members(v, i) for i in range(1, len(lay) + 1)]
     T = sum(w * n_i for (w, n_i, _), m in zip(lay, mem))
-    if og.dh(v) < 2 or T <= 2048 or not 1 <= len(lay) <= 2048:
+    if og.dh(v) < 2 or T <= 2048 or not 1 <= len(lay) <= 1024:
         return None
     hb = min(12, id_bits)
     best = None
