@@ -1405,6 +1405,8 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         p->counters.mat_he += c[q].mat_he;
         p->counters.mat_members += c[q].mat_members;
         p->counters.selected += c[q].selected;
+        p->counters.gathered += c[q].gathered;
+        p->counters.search_words += c[q].search_words;
         // the launch's time and count are shared by the pools it grew, in proportion to their jobs
         const double share = (double)nq / (double)njobs;
         p->rr_kernel_seconds += seconds * share;

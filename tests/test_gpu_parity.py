@@ -207,6 +207,23 @@ def test_chunk_index(H, oracle):
     assert check_chunk_index(g2, og2, n2, range(0, 8)) >= 1
 
 
+def test_read_counters(H, oracle):
+    # the member ids a pool's materialisations read: one pass over mu's hyperedges when mu has no
+    # chunk index (then equal to the oracle's mat_members), only the chunks holding picks when it
+    # has one (then fewer, plus search words)
+    n, hes = gc.random_graph(3, 400, 300, 9)
+    g, og = load_both(H, oracle, n, hes, "uniform_pair", 214748364, seed=7)
+    p, op = check_pool(H, oracle, g, og, 500, "stratified", seed=7)
+    v = p.view()
+    assert g.stats()["index_vertices"] == 0
+    assert v["gathered"] == op.stats()["mat_members"] and v["search_words"] == 0
+    n2, hes2 = gc.hub_graph()
+    g2, og2 = load_both(H, oracle, n2, hes2, "wc", 0, seed=11)
+    p2, op2 = check_pool(H, oracle, g2, og2, 3000, "stratified", seed=11)
+    v2 = p2.view()
+    assert 0 < v2["gathered"] < op2.stats()["mat_members"] and v2["search_words"] > 0
+
+
 def test_greedy_and_spread(H, oracle):
     n, hes = gc.random_graph(4, 2000, 1500, 8)
     g, og = load_both(H, oracle, n, hes, "uniform_pair", 429496729, seed=13)
