@@ -25,7 +25,6 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWCap = 2048;      // per-warp on-chip neighbourhood keys (power of two)
 constexpr int kWHalf = kWCap / 2;  // raw copy + sorted copy of neighbourhoods up to this size
-constexpr int kCollCap = kWHalf / 2;  // members collected for a direct selection
 constexpr int kPCap = 256;       // per-warp picks
 constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the warp path
 constexpr int kBCap = 8192;      // block on-chip keys (power of two)
@@ -297,13 +296,10 @@ __device__ int32_t slot_value(const RRParams& P, const int32_t* list, int idx, i
 // ------------------------------------------------------------------------------------------
 // A(mu) with at most kWHalf incidence positions (tsum, mu's own included), by one pass over the
 // members: a raw copy goes to buf[kWHalf, kWHalf + tsum) and the members are counted into
-// buckets of their top id bits. Returns 1 if the pops of this vertex are already done: when no
-// member repeats (one layer, w = 1) the a-th member in id order lies in the bucket whose start
-// is the last one <= a, so only the buckets holding picks are collected and ranked. Otherwise
-// (returns 0) buf[0, T) receives the members sorted by id.
-__device__ int small_nbhd(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, int32_t mu,
-                          int32_t v_begin, int32_t dh, int tsum, int T, int l, const Need nd0,
-                          uint32_t* buf) {
+// buckets of their top id bits; the raw copy is then scattered into buf[0, T) in bucket order and
+// each bucket is sorted (members sorted by id).
+__device__ void small_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_begin, int32_t dh, int tsum,
+                           int T, uint32_t* buf) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* bkt = S.u.w.wbkt[wid];
     uint32_t* raw = buf + kWHalf;
@@ -318,74 +314,7 @@ __device__ int small_nbhd(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
         if (x != (uint32_t)mu) atomicAdd(&bkt[(x >> shift) & key_mask], 1);
     });
     const int maxb = warp_bucket_scan(bkt, nb);  // bucket starts
-    if (l == 1 && nd0.w == 1) {
-        if (nd0.h >= nd0.n) {  // every member is taken
-            for (int p = lane; p < tsum; p += 32) {
-                const uint32_t x = raw[p];
-                if (x != (uint32_t)mu) push(P, S, vis, list, x);
-            }
-            __syncwarp();
-            return 1;
-        }
-        if (nd0.h <= 32) {
-            uint32_t* marked = reinterpret_cast<uint32_t*>(S.wcnt[wid]);  // nb bits
-            for (int i = lane; i < (nb >> 5) + 1; i += 32) marked[i] = 0;
-            __syncwarp();
-            int pb = 0, po = 0;
-            if ((uint32_t)lane < nd0.h) {
-                const int a = (int)S.u.w.wpick[wid][lane];
-                int lo = 0, hi = nb;  // last bucket whose start is <= a
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (bkt[mid] <= a) lo = mid; else hi = mid;
-                }
-                pb = lo;
-                po = a - bkt[lo];
-                atomicOr(&marked[lo >> 5], 1u << (lo & 31));
-            }
-            __syncwarp();
-            uint32_t* coll = buf;
-            int cc = 0;
-            for (int p0 = 0; p0 < tsum; p0 += 32) {
-                const int p = p0 + lane;
-                bool f = false;
-                uint32_t x = 0;
-                if (p < tsum) {
-                    x = raw[p];
-                    const uint32_t b = (x >> shift) & key_mask;
-                    f = x != (uint32_t)mu && ((marked[b >> 5] >> (b & 31)) & 1u);
-                }
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
-                const int at = cc + __popc(bal & lanemask_lt());
-                if (f && at < kCollCap) coll[at] = x;
-                cc += __popc(bal);
-            }
-            __syncwarp();
-            if (cc <= kCollCap) {
-                uint32_t* srt = buf + kCollCap;  // the collected members in id order (all distinct)
-                for (int i = lane; i < cc; i += 32) {
-                    const uint32_t x = coll[i];
-                    int rk = 0;
-                    for (int k = 0; k < cc; ++k) rk += coll[k] < x ? 1 : 0;
-                    srt[rk] = x;
-                }
-                __syncwarp();
-                if ((uint32_t)lane < nd0.h) {
-                    const uint32_t lo_val = (uint32_t)pb << shift;  // smallest id of bucket pb
-                    int lo = 0, hi = cc;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (srt[mid] < lo_val) lo = mid + 1; else hi = mid;
-                    }
-                    push(P, S, vis, list, srt[lo + po]);
-                }
-                __syncwarp();
-                return 1;
-            }
-        }
-    }
     warp_scatter_sort(raw, tsum, (uint32_t)mu, buf, T, bkt, nb, 0u, shift, key_mask, maxb);
-    return 0;
 }
 
 // Last chunk k in [k0, C) whose prefix row[k] is <= pos (row[k0] <= pos is given).
@@ -719,8 +648,7 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     // materialise A(mu) in shared memory, sorted by id (bucketed by the top id bits)
     int got;
     if (tsum <= kWHalf) {
-        const int sel = small_nbhd(P, S, vis, list, mu, v_begin, dh, tsum, T, l, need[0], buf);
-        if (sel) return false;
+        small_nbhd(P, S, mu, v_begin, dh, tsum, T, buf);
         got = T;
     } else {
         got = sorted_nbhd<32>(P.v_span, P.he_mem, mu, v_begin, dh, T, P.id_bits, buf,

@@ -3,8 +3,8 @@
 Integer results (layer profiles, RR sets, coverage counts, seed sets, work counters) must be
 identical; double results (estimates, bounds, theta) agree to 1e-12 relative and integer theta
 is identical. Inputs are seeded and steer every kernel path: warp materialisation, block
-materialisation on chip, id-bucketed materialisation through global scratch, selection in
-duplicate-free neighbourhoods by bucket starts, direct indexing of a
+materialisation on chip, id-bucketed materialisation through global scratch, the chunk index
+path, duplicate-free neighbourhoods, direct indexing of a
 single hyperedge, > 32 layers with draws, > 256 picks, split Poisson draws, p = 1, RR sets larger
 than the on-chip sort buffer, degenerate hyperedges.
 """
@@ -140,8 +140,8 @@ def test_hub_paths_wc(H, oracle):
 
 @pytest.mark.parametrize("uthr", [128849018, 858993459, P32])
 def test_distinct_neighbourhoods(H, oracle, uthr):
-    # p = 0.03 draws ~27 picks from vertex 0's 894 distinct neighbours (selection by bucket
-    # starts), p = 0.2 ~180 (sorted path), p = 1 takes every member
+    # p = 0.03 draws ~27 picks from vertex 0's 894 distinct neighbours, p = 0.2 ~180, p = 1 takes
+    # every member
     n, hes = gc.distinct_graph()
     g, og = load_both(H, oracle, n, hes, "uniform_pair", uthr, seed=13)
     assert og.nlayers(0) == 1 and og.deg(0) == 894
