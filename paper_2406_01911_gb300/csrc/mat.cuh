@@ -210,8 +210,9 @@ __device__ __forceinline__ void for_each_position(const int2* __restrict__ v_spa
         // hyperedge index is advanced step by step, otherwise found by binary search
         const bool stepwise = total >= cnt * (G / 4);
         int j = 0;
-        // four positions per round: their loads are all issued before any result is used
-        constexpr int U = 4;
+        // two positions per round: both loads are issued before either result is used (more in
+        // flight measured slower: the unrolled copies cost more issue slots than they hide)
+        constexpr int U = 2;
         for (int p0 = r; p0 < total; p0 += U * G) {
             uint32_t xs[U] = {};
 #pragma unroll

@@ -392,7 +392,7 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
         if (base + total > kWHalf) return -1;  // uniform
         const bool stepwise = total >= cnt * 8;
         int j = 0;
-        constexpr int U = 4;
+        constexpr int U = 2;
         for (int p0 = lane; p0 < total; p0 += U * 32) {
             uint32_t xs[U] = {};
 #pragma unroll
