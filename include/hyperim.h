@@ -133,13 +133,16 @@ hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* n
 /* ------------------------------------------------------------------------------------------
  * hyperim_graph_chunk_index -- copy one vertex's chunk index to host (a lookup structure of this
  *   library over the layers of Sec. 3.1.1, not a quantity of the paper).
- *   A vertex v whose hyperedges hold more than 2048 members other than v (repeats counted) may
- *   have one: ids are split into C = 2^bits chunks by their top bits (chunk of u = u >> (B -
- *   bits), B = ceil(log2 n), at least 1), and table[(i - 1) C + k] = number of members of layer
- *   L_i of A(v) whose chunk is < k (i = 1..l_v, k = 0..C-1). *bits = 0 and *entries = 0 when v
- *   has no index. table may be NULL (then only *bits and *entries are set); otherwise it must
- *   hold cap >= *entries = l_v C entries (EINVAL if not). EINVAL: v outside [0, n).
- *   Synchronises the stream.
+ *   Ids are split into C = 2^bits chunks by their top bits (chunk of u = u >> (B - bits),
+ *   B = ceil(log2 n), at least 1), and table[(i - 1) C + k] = number of members of layer L_i of
+ *   A(v) whose chunk is < k (i = 1..l_v, k = 0..C-1). Which vertices have one: d_H(v) >= 2,
+ *   1 <= l_v <= 1024, and, with T = members of v's hyperedges other than v (repeats counted) and
+ *   lambda = sum_i n_i p_i the expected picks per pop (decided on the integers
+ *   sum_i n_i floor(p_i 2^32) against 4 2^32): T > 1024 if lambda < 4, else T > 2048; bits is the
+ *   fewest (1..min(12, B)) for which no chunk holds more than 512 (lambda < 4) or 1024 of those
+ *   members, and no index if none does. *bits = 0 and *entries = 0 when v has no index. table may
+ *   be NULL (then only *bits and *entries are set); otherwise it must hold cap >= *entries =
+ *   l_v C entries (EINVAL if not). EINVAL: v outside [0, n). Synchronises the stream.
  * ------------------------------------------------------------------------------------------ */
 hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* bits,
                                          uint32_t* table, int64_t cap, int64_t* entries);

@@ -10,9 +10,10 @@
 //
 // Build (after the layer profile):
 //   k_idx_candidates  vertices with d_H >= 2, more than kIdxMinT members besides mu, l <= kIdxMaxL
-//   k_idx_plan        per candidate: histogram of the members over 2^hb id bins (hb = min(12,
-//                     id bits)); c = the fewest bits for which no chunk holds more than
-//                     kIdxTarget members (0 bits: not indexed); entries = l 2^c
+//   k_idx_plan        per candidate: the expected picks per pop decide the chunk target (or
+//                     no index); histogram of the members over 2^hb id bins (hb = min(12, id
+//                     bits)); c = the fewest bits for which no chunk holds more than the target
+//                     (0 bits: not indexed); entries = l 2^c
 //   scan              table offsets
 //   k_idx_fill        per indexed vertex: members bucketed by chunk through a global scratch
 //                     area, each chunk sorted on chip, its runs (multiplicity w -> layer) counted;
@@ -72,17 +73,43 @@ __device__ void warp0_exclusive_scan(int* a, int count) {
 
 __global__ void __launch_bounds__(kThreads)
 k_idx_plan(const int32_t* __restrict__ list, int32_t nlist, const int4* __restrict__ vinfo,
-           const int2* __restrict__ v_span, const int32_t* __restrict__ he_mem, int id_bits,
+           const int2* __restrict__ v_span, const int32_t* __restrict__ he_mem,
+           const int32_t* __restrict__ tsum, const uint4* __restrict__ prof, int id_bits,
            uint8_t* __restrict__ bits_out, uint32_t* __restrict__ entries) {
     __shared__ int hist_a[kBins];
     __shared__ int hist_b[kBins / 2];
     __shared__ int pre[2 * kThreads + 1];
     __shared__ int wmax[kThreads / 32];
+    __shared__ int target_s;
     const int hb = id_bits < kIdxMaxBits ? id_bits : kIdxMaxBits;
     const int shift = id_bits - hb;
     for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
         const int32_t mu = list[i];
         const int4 vi = vinfo[mu];
+        if (threadIdx.x == 0) {
+            // expected picks per pop, sum_i n_i p_i, against kIdxFewPicks on the integers
+            // n_i floor(p_i 2^32) (p = 1 counts 2^32), stopping once the bound is reached
+            const unsigned long long cap = kIdxFewPicks << 32;
+            unsigned long long acc = 0;
+            for (int q = 0; q < vi.y && acc < cap; ++q) {
+                const uint4 e = prof[2 * ((int64_t)vi.x + q)];
+                const unsigned long long t = (e.x & kPOneFlag) ? (1ull << 32) : (unsigned long long)e.z;
+                acc += (unsigned long long)e.y * t;
+            }
+            const bool few = acc < cap;
+            const int T = tsum[mu] - vi.w;
+            target_s = few ? kIdxTargetFew : (T > kIdxMinTMany ? kIdxTargetMany : 0);
+        }
+        __syncthreads();
+        const int target = target_s;
+        __syncthreads();
+        if (target == 0) {  // many picks on a neighbourhood one warp sorts whole: no index
+            if (threadIdx.x == 0) {
+                bits_out[i] = 0;
+                entries[i] = 0;
+            }
+            continue;
+        }
         for (int b = threadIdx.x; b < (1 << hb); b += kThreads) hist_a[b] = 0;
         __syncthreads();
         for_each_member<kThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
@@ -101,7 +128,7 @@ k_idx_plan(const int32_t* __restrict__ list, int32_t nlist, const int4* __restri
             __syncthreads();
             int all = 0;
             for (int w = 0; w < kThreads / 32; ++w) all = max(all, wmax[w]);
-            if (all <= kIdxTarget) best = c;  // uniform: every thread saw the same maxima
+            if (all <= target) best = c;  // uniform: every thread saw the same maxima
             for (int b = threadIdx.x; b < nb / 2; b += kThreads) half[b] = hist[2 * b] + hist[2 * b + 1];
             __syncthreads();
             int* tmp = hist;
@@ -277,8 +304,8 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
     { k_idx_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_flag, d_pos, d_list); count_launch(); }
     const int nl = (int)ncand;
     const int pblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * 4);
-    { k_idx_plan<<<pblocks, kThreads, 0, s>>>(d_list, nl, g->vinfo, g->v_span, g->he_mem, g->id_bits,
-                                              d_bits, d_entries); count_launch(); }
+    { k_idx_plan<<<pblocks, kThreads, 0, s>>>(d_list, nl, g->vinfo, g->v_span, g->he_mem, g->tsum, g->prof,
+                                              g->id_bits, d_bits, d_entries); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_entries, d_off, ncand))) return st;
     int64_t total = 0;
     HYP_CUDA(cudaMemcpyAsync(&total, d_off + ncand, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -34,16 +34,27 @@ struct RRCounters {
     unsigned long long gathered, search_words;
 };
 
-// Chunk index of large neighbourhoods. For a vertex mu whose hyperedges hold more than
-// kIdxMinT members other than mu (repeats counted), the ids are split into C = 2^c chunks by
-// their top c of id_bits bits, c the smallest value for which no chunk holds more than
-// kIdxTarget of those members, and the index stores, for every layer i of A(mu) and chunk k, the
-// number of members of L_i in chunks < k (l_mu x C uint32, layer-major). The position of a pick
-// in L_i then names the one chunk that holds it, and only that id range of mu's (sorted)
-// hyperedges is read. Vertices with more than kIdxMaxL layers, or whose members crowd one id
-// range beyond kIdxTarget even at 2^kIdxMaxBits chunks, are not indexed.
-constexpr int kIdxMinT = 2048;
-constexpr int kIdxTarget = 1024;
+// Chunk index of large neighbourhoods. The ids are split into C = 2^c chunks by their top c of
+// id_bits bits, and the index stores, for every layer i of A(mu) and chunk k, the number of
+// members of L_i in chunks < k (l_mu x C uint32, layer-major). The position of a pick in L_i
+// then names the one chunk that holds it, and only that id range of mu's (sorted) hyperedges is
+// read. Which vertices get one, and how large their chunks are, depends on lambda_mu = sum_i
+// n_i p_i, the expected number of picks per pop (decided exactly on the integers
+// sum_i n_i floor(p_i 2^32) against kIdxFewPicks 2^32):
+//   lambda < kIdxFewPicks : indexed when mu's hyperedges hold more than kIdxMinT members besides
+//                           mu (repeats counted); chunks of at most kIdxTargetFew members;
+//   otherwise             : indexed above kIdxMinTMany members (below that one warp sorts the
+//                           whole neighbourhood more cheaply than it visits most of its chunks);
+//                           chunks of at most kIdxTargetMany members.
+// c is the fewest bits for which no chunk exceeds the target. Vertices with more than kIdxMaxL
+// layers, or whose members crowd one id range beyond the target even at 2^kIdxMaxBits chunks,
+// are not indexed.
+constexpr int kIdxMinT = 1024;
+constexpr int kIdxMinTMany = 2048;
+constexpr int kIdxTargetFew = 512;
+constexpr int kIdxTargetMany = 1024;
+constexpr int kIdxTarget = kIdxTargetMany;  // the largest chunk any index holds
+constexpr unsigned long long kIdxFewPicks = 4;
 constexpr int kIdxMaxBits = 12;
 constexpr int kIdxMaxL = 1024;
 // idx word of a vertex: 0 = no index, else (c << 56) | offset of its table

@@ -152,21 +152,27 @@ def test_distinct_neighbourhoods(H, oracle, uthr):
 
 def expected_chunk_index(og, v, id_bits):
     """(bits, table) the chunk index of v must hold, from the oracle's layers (None: no index).
-    Candidates: d_H >= 2, more than 2048 members besides v (repeats counted), 1 <= l_v <= 1024;
-    bits = the fewest top id bits (at most 12) for which no chunk holds more than 1024 of those
-    members; table[i - 1, k] = members of L_i in chunks < k."""
+    With T = members of v's hyperedges besides v (repeats counted) and the expected picks per pop
+    sum_i n_i p_i compared with 4 on the integers n_i floor(p_i 2^32): candidates have d_H >= 2,
+    1 <= l_v <= 1024 and T > 1024 (fewer than 4 expected picks; chunks of at most 512 members)
+    or T > 2048 (chunks of at most 1024); bits = the fewest top id bits (at most 12) for which no
+    chunk exceeds that; table[i - 1, k] = members of L_i in chunks < k."""
     lay = og.layers(v)
-    mem = [og.layer_members(v, i) for i in range(1, len(lay) + 1)]
-    T = sum(w * n_i for (w, n_i, _), m in zip(lay, mem))
-    if og.dh(v) < 2 or T <= 2048 or not 1 <= len(lay) <= 1024:
+    if og.dh(v) < 2 or not 1 <= len(lay) <= 1024:
         return None
+    T = sum(w * n_i for (w, n_i, _) in lay)
+    few = sum(n_i * thr for (_, n_i, thr) in lay) < 4 * P32
+    if T <= 1024 or (not few and T <= 2048):
+        return None
+    target = 512 if few else 1024
+    mem = [og.layer_members(v, i) for i in range(1, len(lay) + 1)]
     hb = min(12, id_bits)
     best = None
     for c in range(1, hb + 1):
         occ = np.zeros(1 << c, np.int64)
         for (w, _, _), m in zip(lay, mem):
             np.add.at(occ, m.astype(np.int64) >> (id_bits - c), w)
-        if occ.max() <= 1024:
+        if occ.max() <= target:
             best = c
             break
     if best is None:
@@ -179,12 +185,22 @@ def expected_chunk_index(og, v, id_bits):
     return best, tab
 
 
+def neighbourhood_sizes(n, hes):
+    """T(v): members of v's hyperedges other than v, repeats across hyperedges counted (after the
+    hyperedges are made sets)."""
+    T = np.zeros(n, np.int64)
+    for he in hes:
+        u = np.unique(np.asarray(he, dtype=np.int64))
+        T[u] += len(u) - 1
+    return T
+
+
 def check_chunk_index(g, og, n, vertices):
     id_bits = max(1, int(n - 1).bit_length())
     seen = 0
     for v in vertices:
-        want = expected_chunk_index(og, v, id_bits)
-        bits, tab = g.chunk_index(v)
+        want = expected_chunk_index(og, int(v), id_bits)
+        bits, tab = g.chunk_index(int(v))
         if want is None:
             assert bits == 0 and tab is None, v
         else:
@@ -194,34 +210,24 @@ def check_chunk_index(g, og, n, vertices):
     return seen
 
 
-def test_chunk_index(H, oracle):
+@pytest.mark.parametrize("model,uthr", [("wc", 0), ("uniform_pair", 85899345)])
+def test_chunk_index(H, oracle, model, uthr):
     # vertex 0: 60 hyperedges of 250 (about 15K members, repeats across hyperedges); vertex 1:
-    # 10 of 300; the rest are small (no index)
+    # 10 of 300; others sit in a few of those hyperedges. Under WC a pop expects about one pick
+    # (chunks of 512 from 1,024 members up); at p = 0.02 the hubs expect hundreds (chunks of 1,024,
+    # only above 2,048 members). Every vertex above 1,024 members is checked, plus the first 40.
     n, hes = gc.hub_graph()
-    g, og = load_both(H, oracle, n, hes, "wc", 0, seed=11)
-    assert check_chunk_index(g, og, n, range(0, 40)) == 2
-    assert g.stats()["index_vertices"] == 2
+    g, og = load_both(H, oracle, n, hes, model, uthr, seed=11)
+    T = neighbourhood_sizes(n, hes)
+    big = np.nonzero(T > 1024)[0]
+    seen = check_chunk_index(g, og, n, sorted(set(range(40)) | set(big.tolist())))
+    assert seen == g.stats()["index_vertices"] and seen >= 2
     # many layers on a large neighbourhood
     n2, hes2 = gc.layered_hub_graph()
     g2, og2 = load_both(H, oracle, n2, hes2, "wc", 0, seed=3)
-    assert check_chunk_index(g2, og2, n2, range(0, 8)) >= 1
-
-
-def test_read_counters(H, oracle):
-    # the member ids a pool's materialisations read: one pass over mu's hyperedges when mu has no
-    # chunk index (then equal to the oracle's mat_members), only the chunks holding picks when it
-    # has one (then fewer, plus search words)
-    n, hes = gc.random_graph(3, 400, 300, 9)
-    g, og = load_both(H, oracle, n, hes, "uniform_pair", 214748364, seed=7)
-    p, op = check_pool(H, oracle, g, og, 500, "stratified", seed=7)
-    v = p.view()
-    assert g.stats()["index_vertices"] == 0
-    assert v["gathered"] == op.stats()["mat_members"] and v["search_words"] == 0
-    n2, hes2 = gc.hub_graph()
-    g2, og2 = load_both(H, oracle, n2, hes2, "wc", 0, seed=11)
-    p2, op2 = check_pool(H, oracle, g2, og2, 3000, "stratified", seed=11)
-    v2 = p2.view()
-    assert 0 < v2["gathered"] < op2.stats()["mat_members"] and v2["search_words"] > 0
+    T2 = neighbourhood_sizes(n2, hes2)
+    seen2 = check_chunk_index(g2, og2, n2, sorted(set(range(8)) | set(np.nonzero(T2 > 1024)[0].tolist())))
+    assert seen2 == g2.stats()["index_vertices"] and seen2 >= 4
 
 
 def test_greedy_and_spread(H, oracle):
