@@ -7,6 +7,8 @@
   them (the oracle spends ~0.15 s per RR set here: the sets hold a third of the graph).
 * 2,000,000 vertices / 1,000,000 Zipf(1.9) hyperedges, weighted cascade, stratified roots: the
   profile of a sample of vertices and the theta_0 = 75 RR sets of the first BRR round.
+* the 100k graph under the paper's layer probabilities (p_i = 1/(i ln(l+1)) / n_i): the profile
+  of every vertex, two pools of theta = 500 set by set, and greedy on them.
 """
 import numpy as np
 import pytest
@@ -95,3 +97,20 @@ def test_zipf_2m_first_round(H, oracle):
     op.grow_theta(plan["theta0"])
     gc.assert_same_pool(p, op)
     gc.assert_same_counters(p, op)
+
+
+def test_zipf_100k_paper_layer(H, oracle):
+    w, g, og = _both(H, oracle, "zipf-100k-50k-paper")
+    q = w.query
+    _profile_sample(g, og, range(w.graph.n))
+    for tag in (0, 1):
+        p = g.pool(tag=tag, roots=q.roots).sample(500)
+        op = oracle.Pool(og, seed=q.seed, tag=tag, roots=q.roots)
+        op.grow_theta(500)
+        gc.assert_same_pool(p, op)
+        gc.assert_same_counters(p, op)
+        seeds, res = g.select_seeds(p, None, q.k, mode="fixed")
+        oseeds, olam, _ = op.greedy(q.k)
+        assert seeds.tolist() == oseeds.tolist()
+        assert res["lambda_r1"].tolist() == olam.tolist()
+

@@ -190,6 +190,16 @@ WORKLOADS = {
         description="100k vertices, 50k hyperedges, Zipf(2.1) sizes in [2,200], preferential "
                     "membership; IC with p=0.01; k=50; eps=0.1, delta=1/n; adaptive theta; "
                     "stratified roots"),
+    "zipf-100k-50k-paper": Workload(
+        name="zipf-100k-50k-paper",
+        graph=HypergraphSpec(n=100_000, m=50_000, size_law="zipf", size_lo=2, size_hi=200,
+                             zipf_alpha=2.1, membership="preferential", seed=1),
+        query=QuerySpec(model="paper_layer", uniform_threshold=0, k=50, theta=None,
+                        eps=0.1, ell=1.0, roots="stratified", seed=1),
+        description="100k vertices, 50k hyperedges, Zipf(2.1) sizes in [2,200], preferential "
+                    "membership (the zipf-100k-50k-p001 graph); the paper's layer probabilities "
+                    "p_i = 1/(i ln(l+1)) / n_i; k=50; eps=0.1, delta=1/n; adaptive theta; "
+                    "stratified roots"),
     "zipf-2m-1m-wc": Workload(
         name="zipf-2m-1m-wc",
         graph=HypergraphSpec(n=2_000_000, m=1_000_000, size_law="zipf", size_lo=2, size_hi=1000,
