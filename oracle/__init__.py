@@ -93,6 +93,8 @@ def lib():
             "or_greedy": (C.c_int, [vp, C.c_int32, i32p, u64p, u64p]),
             "or_coverage": (C.c_int, [vp, i32p, C.c_int32, u64p]),
             "or_estimate": (C.c_double, [vp, u64p]),
+            "or_forward_spread": (C.c_int, [vp, i32p, C.c_int32, C.c_uint64, C.c_uint64,
+                                            C.POINTER(C.c_uint32)]),
             "or_plan_theta": (C.c_int, [C.c_int64, C.c_int32, C.c_double, C.c_double,
                                         C.POINTER(Plan)]),
             "or_upper_bound": (C.c_double, [C.c_double, C.c_int32, C.c_int64, C.c_uint64]),
@@ -201,6 +203,14 @@ class Graph:
         if c < 0:
             raise OracleError(f"layer_members status {c}")
         return buf[:c].copy()
+
+    def forward_spread(self, seeds, sims, seed):
+        """Activated-vertex counts of `sims` forward IC cascades from `seeds` (Sec. 2.2)."""
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+        out = np.zeros(max(int(sims), 1), dtype=np.uint32)
+        _check(lib().or_forward_spread(self._h, _p(s, C.c_int32), len(s), int(sims), int(seed),
+                                       _p(out, C.c_uint32)))
+        return out[:int(sims)]
 
     def allocate(self, roots, theta):
         ns = np.zeros(NSTRATA, dtype=np.uint64)

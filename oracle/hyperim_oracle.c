@@ -637,6 +637,64 @@ int64_t or_rr_set(const or_graph* g, uint64_t seed, uint32_t tag, int root_mode,
     return len;
 }
 
+/* ============================== forward Monte-Carlo influence ===============================
+ * The discrete-time cascade of Sec. 2.2 under the IC model: at time 0 the seeds are active;
+ * a vertex u activated at time i gets one chance, at time i + 1, to activate each neighbour v
+ * (each nu sharing a hyperedge with u), with probability p(u, v); the cascade stops when no
+ * vertex is newly activated. p(u, v) is the probability the layer setting gives u in A(v) --
+ * the layer of A(v) keyed by w(u, v) (Sec. 3.1.1) -- i.e. the probability of the same live edge
+ * u -> v that the reverse sampler draws for a pop of v, so that the expected number of activated
+ * vertices equals sigma(S) of Eq. 1. Coins: one word per directed pair and simulation,
+ * Philox4x32-10 with key (seed_lo, seed_hi) and counter (r, u, v, 0xFFFFFFFE); the edge is live
+ * iff p = 1, or p > 0 and word < floor(p 2^32). counts[r] = vertices activated in simulation r. */
+static uint64_t pair_threshold(const or_graph* g, int32_t v, uint32_t w) {
+    for (int64_t x = g->prof_off[v]; x < g->prof_off[v + 1]; ++x)
+        if (g->lay_w[x] == w) return g->lay_thr[x];
+    return 0; /* unreachable: every w(u, v) > 0 keys a layer of A(v) */
+}
+
+int or_forward_spread(const or_graph* g_, const int32_t* seeds, int32_t k, uint64_t sims,
+                      uint64_t seed, uint32_t* counts) {
+    or_graph* g = (or_graph*)g_;
+    if (k < 0 || (k > 0 && !seeds) || (sims > 0 && !counts) || sims > 0x100000000ull)
+        return OR_EINVAL;
+    for (int32_t i = 0; i < k; ++i)
+        if (seeds[i] < 0 || seeds[i] >= g->n) return OR_EINVAL;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    ivec A = {0, 0, 0};
+    int rc = OR_OK;
+    for (uint64_t r = 0; r < sims && rc == OR_OK; ++r) {
+        A.len = 0;
+        for (int32_t i = 0; i < k && rc == OR_OK; ++i)
+            if (!g->seen[seeds[i]]) { g->seen[seeds[i]] = 1; rc = ivec_push(&A, seeds[i]); }
+        for (int64_t head = 0; rc == OR_OK && head < A.len; ++head) {
+            const int32_t u = A.v[head];
+            const int64_t kn = nbhd_count(g, u);
+            for (int64_t x = 0; x < kn && rc == OR_OK; ++x) {
+                const int32_t v = g->nb[x];
+                const uint64_t thr = pair_threshold(g, v, (uint32_t)g->cnt[v]);
+                int live;
+                if (thr >= OR_P_ONE) {
+                    live = 1;
+                } else if (thr == 0) {
+                    live = 0;
+                } else {
+                    const uint32_t ctr[4] = {(uint32_t)r, (uint32_t)u, (uint32_t)v, 0xFFFFFFFEu};
+                    uint32_t out[4];
+                    or_philox4x32_10(ctr, key, out);
+                    live = (uint64_t)out[0] < thr;
+                }
+                if (live && !g->seen[v]) { g->seen[v] = 1; rc = ivec_push(&A, v); }
+            }
+            nbhd_release(g, kn);
+        }
+        counts[r] = (uint32_t)A.len;
+        for (int64_t i = 0; i < A.len; ++i) g->seen[A.v[i]] = 0;
+    }
+    free(A.v);
+    return rc;
+}
+
 /* ======================================== RR pools ========================================== */
 struct or_pool {
     const or_graph* g;

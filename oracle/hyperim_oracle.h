@@ -95,6 +95,12 @@ int or_greedy(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_
 int or_coverage(const or_pool* p, const int32_t* seeds, int32_t k, uint64_t lambda_s[OR_NSTRATA]);
 double or_estimate(const or_pool* p, const uint64_t lambda_s[OR_NSTRATA]);
 
+/* Forward Monte-Carlo influence of a seed set (Sec. 2.2 cascade, IC model; keyed coins, see the
+ * definition in hyperim_oracle.c): counts[r] = vertices activated in simulation r, r < sims
+ * (sims <= 2^32). OR_EINVAL on a seed outside [0, n). */
+int or_forward_spread(const or_graph* g, const int32_t* seeds, int32_t k, uint64_t sims,
+                      uint64_t seed, uint32_t* counts);
+
 /* ---- theta plan + BRR ---- */
 typedef struct {
     double delta, ln_binom, theta_max;
