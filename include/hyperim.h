@@ -273,6 +273,26 @@ hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int3
                               hyperim_pool_t pool, double* sigma_hat, double* std_err);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_forward_spread -- forward Monte-Carlo estimate of the influence of a seed set: the
+ *   discrete-time cascade of Sec. 2.2 under the IC model, simulated `simulations` times.
+ *   Simulation r starts with the seeds active; a vertex u activated at step i tries once, at
+ *   step i + 1, each vertex v sharing a hyperedge with it; the pair u -> v is live with the
+ *   probability of u's layer in A(v) (the layer keyed by w(u, v), Sec. 3.1.1) -- the same live
+ *   edge the RR sampler draws for a pop of v, so E[activated] = sigma(S) of Eq. 1. Each pair
+ *   draws one coin: word 0 of Philox4x32-10 with key (seed_lo, seed_hi) and counter (r, u, v,
+ *   0xFFFFFFFE), live iff p = 1, or word < floor(p 2^32). Results do not depend on the order in
+ *   which the GPU processes activations.
+ *   seeds_host: k vertex ids (host; repeats allowed); counts_host: NULL or `simulations` entries
+ *   receiving each simulation's activated count; mean / std_err: NULL or the sample mean of the
+ *   counts and its standard error (sample standard deviation / sqrt(simulations); 0 when
+ *   simulations = 1). EINVAL: k < 0, a seed outside [0, n), simulations = 0 or > 2^32.
+ *   Synchronises the stream.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_forward_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k,
+                                      uint64_t simulations, uint64_t seed, uint32_t* counts_host,
+                                      double* mean, double* std_err);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_coverage_noalloc -- per-stratum coverage of a seed set on an RR pool, computed without
  *   allocating any memory. The paper has no counterpart: it is the coverage step behind
  *   hyperim_spread and the BRR lower bound, offered to callers that cannot allocate device

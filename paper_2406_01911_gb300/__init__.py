@@ -92,6 +92,8 @@ _SIGNATURES = {
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hyperim_graph_chunk_index": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _vp, C.c_int64,
                                             C.POINTER(C.c_int64)]),
+    "hyperim_forward_spread": (C.c_int, [_vp, _vp, C.c_int32, C.c_uint64, C.c_uint64, _vp,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hyperim_plan_theta": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.POINTER(ThetaPlan)]),
     "hyperim_sample_rr": (C.c_int, [_vp, C.c_uint32, C.c_uint64, C.c_int32, C.c_int32,
                                     C.POINTER(_vp)]),
@@ -277,6 +279,15 @@ class Graph:
         _check(lib().hyperim_graph_chunk_index(self._h, int(v), C.byref(bits), _ptr(tab), entries.value,
                                                C.byref(entries)))
         return bits.value, tab.reshape(-1, 1 << bits.value)
+
+    def forward_spread(self, seeds, simulations, seed):
+        """(counts[simulations], mean, std_err) of forward IC cascades from `seeds` (Sec. 2.2)."""
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+        counts = np.zeros(int(simulations), np.uint32)
+        mean, se = C.c_double(), C.c_double()
+        _check(lib().hyperim_forward_spread(self._h, _ptr(s), len(s), int(simulations), int(seed),
+                                            _ptr(counts), C.byref(mean), C.byref(se)))
+        return counts, mean.value, se.value
 
     def plan_theta(self, k, eps, ell=1.0):
         return hyperim_plan_theta(self._h, k, eps, ell)

@@ -260,6 +260,33 @@ hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out
     return HYPERIM_OK;
 }
 
+hyperim_status hyperim_forward_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k,
+                                      uint64_t simulations, uint64_t seed, uint32_t* counts_host,
+                                      double* mean, double* std_err) {
+    if (!g) return set_error(HYPERIM_EINVAL, "null graph");
+    if (k < 0 || (k > 0 && !seeds_host)) return set_error(HYPERIM_EINVAL, "bad seed list");
+    if (simulations == 0 || simulations > 0x100000000ull)
+        return set_error(HYPERIM_EINVAL, "simulations must be in [1, 2^32]");
+    for (int32_t i = 0; i < k; ++i)
+        if (seeds_host[i] < 0 || seeds_host[i] >= g->n) return set_error(HYPERIM_EINVAL, "seed outside [0, n)");
+    std::vector<uint32_t> counts((size_t)simulations);
+    hyperim_status st = forward_spread(g, seeds_host, k, simulations, seed, counts.data());
+    if (st != HYPERIM_OK) return st;
+    // mean and variance in one pass (Welford), in simulation order
+    double m = 0.0, m2 = 0.0;
+    for (uint64_t r = 0; r < simulations; ++r) {
+        const double x = (double)counts[(size_t)r];
+        const double d = x - m;
+        m += d / (double)(r + 1);
+        m2 += d * (x - m);
+    }
+    if (mean) *mean = m;
+    if (std_err)
+        *std_err = simulations > 1 ? std::sqrt(m2 / (double)(simulations - 1) / (double)simulations) : 0.0;
+    if (counts_host) std::memcpy(counts_host, counts.data(), sizeof(uint32_t) * (size_t)simulations);
+    return HYPERIM_OK;
+}
+
 hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* bits, uint32_t* table,
                                          int64_t cap, int64_t* entries) {
     if (!g || !bits || !entries) return set_error(HYPERIM_EINVAL, "null argument");

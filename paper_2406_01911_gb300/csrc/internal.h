@@ -186,6 +186,10 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
 hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
                                const uint64_t (*new_ns)[HYPERIM_NSTRATA]);
 
+// rr.cu: forward Monte-Carlo influence of a seed set (counts_host: nsims entries)
+hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32_t k, uint64_t nsims,
+                              uint64_t seed, uint32_t* counts_host);
+
 // greedy.cu
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
                       uint64_t lambda_s[HYPERIM_NSTRATA]);

@@ -908,6 +908,166 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
 }
 
 // ------------------------------------------------------------------------------------------
+// forward Monte-Carlo influence (the Sec. 2.2 cascade under the IC model)
+// ------------------------------------------------------------------------------------------
+// One coin per directed pair u -> v and simulation r: word 0 of Philox4x32-10 with the forward
+// key and counter (r, u, v, 0xFFFFFFFE) (no RR counter has that last word). The pair is live
+// with the probability of u's layer in A(v): the layer of v's profile keyed by w(u, v).
+struct FwdParams {
+    RRParams P;           // graph arrays, queue scratch, status (RR-only fields unused)
+    const int32_t* seeds;
+    int32_t k;
+    uint64_t nsims;
+    uint32_t key0, key1;
+    uint32_t* counts;
+};
+
+__device__ __forceinline__ bool fwd_live(const RRParams& P, uint32_t key0, uint32_t key1, uint32_t r,
+                                         uint32_t u, uint32_t v, uint32_t w) {
+    const int4 vv = P.vinfo[v];
+    int lo = 0, hi = vv.y;  // v's layers by descending w: the one keyed by w
+    uint4 e = make_uint4(0, 0, 0, 0);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        e = P.prof[2 * ((int64_t)vv.x + mid)];
+        const uint32_t wm = e.x & ~kPOneFlag;
+        if (wm == w) { lo = mid; break; }
+        if (wm > w) lo = mid + 1; else hi = mid;
+    }
+    if ((e.x & ~kPOneFlag) != w) return false;  // unreachable: w(u, v) keys a layer of A(v)
+    if (e.x & kPOneFlag) return true;
+    if (e.z == 0) return false;
+    const uint4 word = philox10(make_uint4(r, u, v, 0xFFFFFFFEu), key0, key1);
+    return word.x < e.z;
+}
+
+// runs of a sorted buffer of u's neighbours: each distinct v (multiplicity w(u, v)) flips its coin
+__device__ void fwd_walk(const FwdParams& F, Shared& S, uint32_t* vis, int32_t* list, const uint32_t* buf,
+                         int got, uint32_t r, uint32_t u) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < got; base += 32) {
+        const int p = base + lane;
+        if (p < got) {
+            const uint32_t x = buf[p];
+            if (p == 0 || buf[p - 1] != x) {
+                int mult = 1;
+                while (p + mult < got && buf[p + mult] == x) ++mult;
+                if (fwd_live(F.P, F.key0, F.key1, r, u, x, (uint32_t)mult)) push(F.P, S, vis, list, x);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// One activated vertex u: all of A(u) with multiplicities, in id order, then the coins. Large
+// neighbourhoods are taken id range by id range (ranges of expected 256 members; a range that
+// still exceeds the warp's buffer is split into 16).
+__device__ void fwd_pop_warp(const FwdParams& F, Shared& S, uint32_t* vis, int32_t* list, uint32_t r,
+                             int32_t u) {
+    const RRParams& P = F.P;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int4 vi = P.vinfo[u];
+    const int32_t v_begin = vi.z, dh = vi.w;
+    if (dh == 0) return;
+    const int32_t tsum = P.tsum[u];
+    const int T = tsum - dh;
+    if (T == 0) return;
+    uint32_t* buf = S.u.w.wbuf[wid];
+    if (dh == 1) {
+        const int2 sp = P.v_span[v_begin];
+        for (int x = lane; x < sp.y; x += 32) {
+            const uint32_t v = (uint32_t)P.he_mem[sp.x + x];
+            if (v != (uint32_t)u && fwd_live(P, F.key0, F.key1, r, (uint32_t)u, v, 1u)) push(P, S, vis, list, v);
+        }
+        __syncwarp();
+        return;
+    }
+    if (tsum <= kWHalf) {
+        small_nbhd(P, S, u, v_begin, dh, tsum, T, buf);
+        fwd_walk(F, S, vis, list, buf, T, r, (uint32_t)u);
+        return;
+    }
+    if (T <= kWCap) {
+        const int got = sorted_nbhd<32>(P.v_span, P.he_mem, u, v_begin, dh, T, P.id_bits, buf,
+                                        S.u.w.wbkt[wid], kWBucketBits, S.wpre[wid], nullptr);
+        fwd_walk(F, S, vis, list, buf, got, r, (uint32_t)u);
+        return;
+    }
+    int b = 0;
+    while (b < P.id_bits && (256 << b) < T) ++b;
+    const int sh = P.id_bits - b;
+    uint32_t probes = 0;
+    for (uint32_t k = 0; k < (1u << b); ++k) {
+        const int got = chunk_nbhd(P, S, u, v_begin, dh, k << sh, sh, buf, probes);
+        if (got >= 0) {
+            fwd_walk(F, S, vis, list, buf, got, r, (uint32_t)u);
+            continue;
+        }
+        const int sh2 = sh >= 4 ? sh - 4 : 0;
+        for (uint32_t k2 = 0; k2 < (1u << (sh - sh2)); ++k2) {
+            const int got2 = chunk_nbhd(P, S, u, v_begin, dh, (k << sh) + (k2 << sh2), sh2, buf, probes);
+            if (got2 < 0) {
+                if (lane == 0) dev_fail(P.st, kErrBucket, u);
+                return;
+            }
+            fwd_walk(F, S, vis, list, buf, got2, r, (uint32_t)u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_forward(FwdParams F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RRParams& P = F.P;
+    Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+    uint32_t* vis = P.vis_smem ? reinterpret_cast<uint32_t*>(smem_raw + sizeof(Shared))
+                               : P.gvis + (int64_t)blockIdx.x * P.vis_words;
+    int32_t* list = P.list + (int64_t)blockIdx.x * P.list_cap;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t = atomicAdd(reinterpret_cast<unsigned long long*>(P.next_job), 1ull);
+            S.ctrl[C_JOB] = t < F.nsims ? (int)(t & 0x7FFFFFFF) : -1;
+            S.out_pos = t;
+            S.ctrl[C_HEAD] = 0;
+            S.ctrl[C_TAIL] = 0;
+            S.ctrl[C_DONE] = 0;
+            S.ctrl[C_NDEF] = 0;
+        }
+        __syncthreads();
+        if (S.ctrl[C_JOB] < 0) break;
+        const uint32_t r = (uint32_t)S.out_pos;
+        for (int i = threadIdx.x; i < F.k; i += kThreads) push(P, S, vis, list, (uint32_t)F.seeds[i]);
+        __syncthreads();
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = claim_slot(P, S, (int64_t)r);
+            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+            if (idx < 0) break;
+            int32_t u = 0;
+            if (lane == 0) u = slot_value(P, list, idx, (int64_t)r);
+            u = __shfl_sync(0xFFFFFFFFu, u, 0);
+            if (u >= 0) fwd_pop_warp(F, S, vis, list, r, u);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();  // this pop's pushes before its completion
+                atomicAdd(&S.ctrl[C_DONE], 1);
+            }
+        }
+        __syncthreads();
+        const int size = S.ctrl[C_TAIL];
+        if (threadIdx.x == 0) F.counts[r] = (uint32_t)size;
+        for (int i = threadIdx.x; i < size; i += kThreads) {
+            const int32_t v = list[i];
+            if (v >= 0) vis[v >> 5] = 0;
+            list[i] = -1;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
@@ -1351,6 +1511,74 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
     hyperim_pool* pools[1] = {p};
     const uint64_t (*ns)[HYPERIM_NSTRATA] = reinterpret_cast<const uint64_t (*)[HYPERIM_NSTRATA]>(new_ns);
     return sample_rr_multi(g, pools, 1, ns);
+}
+
+
+hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32_t k, uint64_t nsims,
+                              uint64_t seed, uint32_t* counts_host) {
+    if (nsims == 0) return HYPERIM_OK;
+    cudaStream_t s = g->stream;
+    hyperim_status st;
+    bool vis_smem = (int64_t)g->n <= kVisSmemBits;
+    size_t smem = 0;
+    int per_sm = 0;
+    for (;;) {
+        const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
+        smem = sizeof(Shared) + vis_bytes;
+        HYP_CUDA(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kThreads, smem));
+        if (per_sm >= 2 || !vis_smem) break;
+        vis_smem = false;
+    }
+    if (per_sm < 1) return set_error(HYPERIM_ECUDA, "forward kernel does not fit on an SM");
+    int blocks = g->sm_count * per_sm;
+    if ((uint64_t)blocks > nsims) blocks = (int)nsims;
+    if ((st = ensure_scratch(g, blocks, vis_smem))) return st;
+    int32_t* d_seeds = nullptr;
+    uint32_t* d_counts = nullptr;
+    unsigned long long* d_next = nullptr;
+    const size_t kk = (size_t)(k > 0 ? k : 1);
+    if ((st = dev_alloc(g, (void**)&d_seeds, sizeof(int32_t) * kk))) return st;
+    if ((st = dev_alloc(g, (void**)&d_counts, sizeof(uint32_t) * (size_t)nsims))) return st;
+    if ((st = dev_alloc(g, (void**)&d_next, sizeof(unsigned long long)))) return st;
+    if (k > 0) HYP_CUDA(cudaMemcpyAsync(d_seeds, seeds_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+    HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
+    FwdParams F;
+    std::memset(&F, 0, sizeof(F));
+    RRParams& P = F.P;
+    P.vinfo = g->vinfo;
+    P.v_span = g->v_span;
+    P.he_mem = g->he_mem;
+    P.prof_off = g->prof_off;
+    P.prof = g->prof;
+    P.tsum = g->tsum;
+    P.n = g->n;
+    P.id_bits = g->id_bits;
+    P.list = g->scratch.list;
+    P.list_cap = (int64_t)g->scratch.list_cap;
+    P.gvis = g->scratch.bitmap;
+    P.vis_smem = vis_smem ? 1 : 0;
+    P.vis_words = vis_smem ? (int64_t)(((size_t)g->n + 31) / 32) : (int64_t)g->scratch.bitmap_words;
+    P.next_job = reinterpret_cast<int*>(d_next);
+    P.st = g->d_status;
+    F.seeds = d_seeds;
+    F.k = k;
+    F.nsims = nsims;
+    F.key0 = (uint32_t)seed;
+    F.key1 = (uint32_t)(seed >> 32);
+    F.counts = d_counts;
+    { k_forward<<<blocks, kThreads, smem, s>>>(F); count_launch(); }
+    HYP_CUDA(cudaGetLastError());
+    if ((st = check_device_status(g, "forward spread"))) {
+        cudaMemsetAsync(g->scratch.list, 0xFF, sizeof(int32_t) * g->scratch.list_cap * g->scratch.blocks, s);
+        return st;
+    }
+    HYP_CUDA(cudaMemcpyAsync(counts_host, d_counts, sizeof(uint32_t) * (size_t)nsims, cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    dev_free(g, d_seeds, sizeof(int32_t) * kk);
+    dev_free(g, d_counts, sizeof(uint32_t) * (size_t)nsims);
+    dev_free(g, d_next, sizeof(unsigned long long));
+    return HYPERIM_OK;
 }
 
 }  // namespace hyperim
