@@ -143,7 +143,7 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False):
            "bytes": rr_algorithmic_bytes(v1) + rr_algorithmic_bytes(v2),
            "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
            "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
-           "seeds": seeds}
+           "sigma_r2": res["sigma_r2"], "seeds": seeds}
     r1.close()
     r2.close()
     g.close()
@@ -272,11 +272,28 @@ def bench_gpu(args):
                      "launches": klaunch, "kernel_seconds": ksec},
         "clocks": clk.summary(),
     }
+    if args.forward_sims > 0:
+        line["forward_mc"] = forward_check(H, torch, w, d_off, d_mem, stats[-1], args.forward_sims)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, off, mem, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def forward_check(H, torch, w, off, mem, last, sims):
+    """Outside the timed region: forward Monte-Carlo influence (Sec. 2.2 cascade) of the last
+    query's seeds on the GPU, beside the RR estimates of that query (R1: the pool greedy chose
+    on, biased upward; R2: the independent pool of the lower bound)."""
+    q = w.query
+    g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=q.seed)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, mean, se = g.forward_spread(last["seeds"], sims, seed=0xF0F0 + q.seed)
+    dt = time.perf_counter() - t
+    g.close()
+    return {"simulations": sims, "seconds": dt, "simulations_per_s": sims / dt, "sigma": mean,
+            "std_err": se, "sigma_rr_r1": last["sigma"], "sigma_rr_r2": last["sigma_r2"]}
 
 
 def profile_batch(args):
@@ -374,6 +391,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--forward-sims", type=int, default=256,
+                    help="forward Monte-Carlo simulations of the last query's seeds (0: skip)")
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-batch", type=int, default=0,
