@@ -16,7 +16,7 @@ from . import build as _build
 
 MODELS = {"uniform_pair": 0, "wc": 1, "paper_layer": 2}
 ROOTS = {"plain": 0, "stratified": 1}
-STRATEGIES = {"paper": 0, "binomial_only": 1}
+STRATEGIES = {"paper": 0, "binomial_only": 1, "lt": 2}
 NSTRATA = 16
 P_ONE = 1 << 32
 

@@ -602,6 +602,62 @@ done:
     return rc;
 }
 
+/* LT cascade (Sec. 2.2, LT model) in its live-edge form: a popped mu keeps at most one
+ * in-neighbour, nu with probability p(nu, mu). With the layers of A(mu) and t_i = floor(p_i 2^32)
+ * (2^32 for p = 1): masses m_i = n_i t_i, cumulated C_i = m_1 + ... + m_i, total M = C_l (exact
+ * 128-bit integers). One word x of the (RR, mu, layer 0) stream: if M <= 2^32, y = x and no
+ * in-neighbour is kept when y >= M; otherwise (sum of p above 1, which standard LT forbids)
+ * y = floor(x M / 2^32) always lands, so the probabilities are normalised by M. The kept vertex
+ * is position a = floor((y - C_{i-1}) / t_i) of the layer L_i with C_{i-1} <= y < C_i (members
+ * in ascending id order): each member of L_i owns t_i consecutive values of y. */
+static int rr_pop_lt(or_graph* g, uint64_t seed, uint32_t j, uint32_t c1base, int32_t mu, ivec* R,
+                     or_stats* st) {
+    uint64_t reads = 0;
+    int64_t k = nbhd_build(g, mu, &reads);
+    int32_t l = 0;
+    for (int64_t i = 0; i < k; ++i)
+        if (i == 0 || g->cnt[g->nb[i]] != g->cnt[g->nb[i - 1]]) l++;
+    st->pops++;
+    st->layers_seen += (uint64_t)l;
+    int rc = OR_OK;
+    unsigned __int128 M = 0;
+    for (int64_t px = g->prof_off[mu]; px < g->prof_off[mu + 1]; ++px)
+        M += (unsigned __int128)g->lay_n[px] * (unsigned __int128)g->lay_thr[px];
+    if (M == 0) goto done;
+    {
+        word_stream ws;
+        ws_init(&ws, seed, j, c1base, (uint32_t)mu, 0u);
+        st->draws++;
+        const uint32_t x = ws_next(&ws);
+        unsigned __int128 y = x;
+        if (M > ((unsigned __int128)1 << 32)) y = ((unsigned __int128)x * M) >> 32;
+        else if (y >= M) goto done;
+        unsigned __int128 C = 0;
+        int64_t start = 0;
+        for (int32_t i = 1; i <= l; ++i) {
+            const int64_t px = g->prof_off[mu] + i - 1;
+            const uint32_t n_i = g->lay_n[px];
+            const uint64_t t_i = g->lay_thr[px];
+            const unsigned __int128 m_i = (unsigned __int128)n_i * t_i;
+            if (y < C + m_i) {
+                const uint64_t a = (uint64_t)((y - C) / t_i);
+                const int32_t nu = g->nb[start + (int64_t)a];
+                st->selected += 1;
+                st->mats++;
+                st->mat_he += (uint64_t)(g->v_off[mu + 1] - g->v_off[mu]);
+                st->mat_members += reads;
+                if (!g->seen[nu]) { g->seen[nu] = 1; rc = ivec_push(R, nu); }
+                break;
+            }
+            C += m_i;
+            start += n_i;
+        }
+    }
+done:
+    nbhd_release(g, k);
+    return rc;
+}
+
 static int rr_generate(or_graph* g, uint64_t seed, uint32_t tag, int root_mode, uint32_t stratum,
                        uint32_t j, int strategy, ivec* R, or_stats* st) {
     R->len = 0;
@@ -613,7 +669,8 @@ static int rr_generate(or_graph* g, uint64_t seed, uint32_t tag, int root_mode, 
     uint32_t* selbuf = NULL;
     uint32_t selcap = 0;
     for (int64_t head = 0; rc == OR_OK && head < R->len; ++head)
-        rc = rr_pop(g, seed, j, c1base, strategy, R->v[head], R, st, &selbuf, &selcap);
+        rc = strategy == OR_STRAT_LT ? rr_pop_lt(g, seed, j, c1base, R->v[head], R, st)
+                                     : rr_pop(g, seed, j, c1base, strategy, R->v[head], R, st, &selbuf, &selcap);
     free(selbuf);
     for (int64_t i = 0; i < R->len; ++i) g->seen[R->v[i]] = 0;
     if (rc != OR_OK) return rc;
@@ -711,6 +768,7 @@ struct or_pool {
 int or_pool_create(const or_graph* g, uint64_t seed, uint32_t tag, int root_mode, int strategy,
                    or_pool** out) {
     if (!g || !out || tag > 0xFF || (root_mode != 0 && root_mode != 1)) return OR_EINVAL;
+    if (strategy < OR_STRAT_PAPER || strategy > OR_STRAT_LT) return OR_EINVAL;
     or_pool* p = (or_pool*)calloc(1, sizeof(or_pool));
     if (!p) return OR_ENOMEM;
     p->g = g; p->seed = seed; p->tag = tag; p->root_mode = root_mode; p->strategy = strategy;

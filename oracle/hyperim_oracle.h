@@ -22,7 +22,9 @@ extern "C" {
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_EOVERFLOW = -3 };
 enum { OR_MODEL_UNIFORM_PAIR = 0, OR_MODEL_WC = 1, OR_MODEL_PAPER_LAYER = 2 };
 enum { OR_ROOTS_PLAIN = 0, OR_ROOTS_STRATIFIED = 1 };
-enum { OR_STRAT_PAPER = 0, OR_STRAT_BINOMIAL_ONLY = 1 };
+enum { OR_STRAT_PAPER = 0, OR_STRAT_BINOMIAL_ONLY = 1, OR_STRAT_LT = 2 };
+/* OR_STRAT_LT: the LT cascade's live-edge sampler instead of the IC one -- each popped vertex keeps
+ * at most one in-neighbour (see rr_pop_lt in hyperim_oracle.c). */
 
 #define OR_NSTRATA 16
 #define OR_P_ONE 4294967296ull /* threshold value meaning p = 1 */
