@@ -63,8 +63,15 @@ typedef enum {
 } hyperim_root_mode;
 
 typedef enum {
-    HYPERIM_STRAT_PAPER = 0,        /* Binomial if n(L_i) <= 20, else Poisson (Sec. 3.1.3) */
-    HYPERIM_STRAT_BINOMIAL_ONLY = 1 /* Binomial for every layer (exact IC semantics, Lemma 3) */
+    HYPERIM_STRAT_PAPER = 0,         /* Binomial if n(L_i) <= 20, else Poisson (Sec. 3.1.3) */
+    HYPERIM_STRAT_BINOMIAL_ONLY = 1, /* Binomial for every layer (exact IC semantics, Lemma 3) */
+    HYPERIM_STRAT_LT = 2             /* the LT cascade (Sec. 2.2) in live-edge form: a popped mu
+                                        keeps at most one in-neighbour; one word w against the
+                                        layers' masses n_i floor(p_i 2^32) cumulated as C_i (sum
+                                        M): y = w if M <= 2^32 (nothing kept when y >= M), else
+                                        floor(w M / 2^32); kept: position floor((y - C_{i-1}) /
+                                        t_i) of the layer with C_{i-1} <= y < C_i. Stream (RR, mu,
+                                        layer field 0). */
 } hyperim_strategy;
 
 typedef struct hyperim_graph* hyperim_graph_t;

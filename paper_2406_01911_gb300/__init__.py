@@ -26,7 +26,7 @@ P_ONE = 1 << 32
 NOALLOC_MAX_N = 1 << 24
 MODELS = {"uniform_pair": 0, "wc": 1, "paper_layer": 2}
 ROOTS = {"plain": 0, "stratified": 1}
-STRATEGIES = {"paper": 0, "binomial_only": 1}
+STRATEGIES = {"paper": 0, "binomial_only": 1, "lt": 2}
 SELECT_MODES = {"fixed": 0, "brr": 1}
 STATUS = {0: "HYPERIM_OK", -1: "HYPERIM_EINVAL", -2: "HYPERIM_ENOMEM", -3: "HYPERIM_EOVERFLOW",
           -4: "HYPERIM_ETIMEDOUT", -5: "HYPERIM_ECUDA", -6: "HYPERIM_ESTATE"}

@@ -348,7 +348,7 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
     if (tag > 0xFF) return set_error(HYPERIM_EINVAL, "pool_tag must be < 256");
     if (root_mode != HYPERIM_ROOTS_PLAIN && root_mode != HYPERIM_ROOTS_STRATIFIED)
         return set_error(HYPERIM_EINVAL, "unknown root mode");
-    if (strategy != HYPERIM_STRAT_PAPER && strategy != HYPERIM_STRAT_BINOMIAL_ONLY)
+    if (strategy != HYPERIM_STRAT_PAPER && strategy != HYPERIM_STRAT_BINOMIAL_ONLY && strategy != HYPERIM_STRAT_LT)
         return set_error(HYPERIM_EINVAL, "unknown strategy");
     hyperim_pool* p = new (std::nothrow) hyperim_pool();
     if (!p) return set_error(HYPERIM_ENOMEM, "host allocation failed");

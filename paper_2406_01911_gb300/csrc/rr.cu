@@ -230,6 +230,43 @@ __device__ void gen_picks(WordStream& ws, uint32_t n, uint32_t h, uint32_t ksel,
     }
 }
 
+// LT cascade (Sec. 2.2, LT model) in its live-edge form: the popped mu keeps at most one
+// in-neighbour. One thread. With t_i = floor(p_i 2^32) (2^32 for p = 1), masses m_i = n_i t_i
+// cumulated as C_i and M = C_l (exact 128-bit integers), one word x of the (RR, mu, layer 0)
+// stream gives y = x if M <= 2^32 (no vertex kept when y >= M), else y = floor(x M / 2^32); the
+// kept vertex is position floor((y - C_{i-1}) / t_i) of the layer with C_{i-1} <= y < C_i. Returns
+// whether a vertex is kept and, through nd, {w_i, n_i, h = 1, kept position, layer i}; *drew
+// tells whether a word was used (M > 0).
+__device__ bool lt_keep(const RRParams& P, int32_t pb, int32_t l, uint32_t j, uint32_t ybase, int32_t mu,
+                        Need& nd, bool* drew) {
+    unsigned __int128 M = 0;
+    for (int i = 0; i < l; ++i) {
+        const uint4 e = P.prof[2 * ((int64_t)pb + i)];
+        const uint64_t t = (e.x & kPOneFlag) ? (1ull << 32) : (uint64_t)e.z;
+        M += (unsigned __int128)e.y * t;
+    }
+    *drew = M > 0;
+    if (M == 0) return false;
+    WordStream ws;
+    ws.init(P.seed, j, ybase, (uint32_t)mu, 0u);
+    const uint32_t x = ws.word(0);
+    unsigned __int128 y = x;
+    if (M > ((unsigned __int128)1 << 32)) y = ((unsigned __int128)x * M) >> 32;
+    else if (y >= M) return false;
+    unsigned __int128 C = 0;
+    for (int i = 0; i < l; ++i) {
+        const uint4 e = P.prof[2 * ((int64_t)pb + i)];
+        const uint64_t t = (e.x & kPOneFlag) ? (1ull << 32) : (uint64_t)e.z;
+        const unsigned __int128 m = (unsigned __int128)e.y * t;
+        if (y < C + m) {
+            nd = Need{e.x & ~kPOneFlag, e.y, 1u, (uint32_t)((uint64_t)(y - C) / t), (uint32_t)(i + 1)};
+            return true;
+        }
+        C += m;
+    }
+    return false;  // unreachable: y < M
+}
+
 __device__ __forceinline__ bool in_sorted(const uint32_t* a, uint32_t len, uint32_t x) {
     uint32_t lo = 0, hi = len;
     while (lo < hi) {
@@ -492,7 +529,22 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     Need* need = S.wneed[wid];
     uint32_t nneed = 0, ndraw = 0;
     uint32_t hsum = 0;  // sum of h over the layers <= deg(mu) < 2^31
-    for (int c0 = 0; c0 < l; c0 += 32) {
+    const bool lt = P.strategy == HYPERIM_STRAT_LT;
+    if (lt) {  // one kept in-neighbour at most: one need of h = 1 (ksel holds its position)
+        int kept = 0, drew = 0;
+        if (lane == 0) {
+            Need nd;
+            bool dr = false;
+            kept = lt_keep(P, pb, l, j, ybase, mu, nd, &dr) ? 1 : 0;
+            drew = dr ? 1 : 0;
+            if (kept) need[0] = nd;
+        }
+        kept = __shfl_sync(0xFFFFFFFFu, kept, 0);
+        ndraw = (uint32_t)__shfl_sync(0xFFFFFFFFu, drew, 0);
+        nneed = (uint32_t)kept;
+        hsum = lane == 0 ? (uint32_t)kept : 0u;
+    }
+    for (int c0 = 0; c0 < (lt ? 0 : l); c0 += 32) {
         const int i = c0 + lane;
         uint32_t h = 0, ksel = 0;
         uint4 e = make_uint4(0, 0, 0, 0);
@@ -549,6 +601,13 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     for (uint32_t q = 0; q < nneed; ++q) {
         const Need nd = need[q];
         if (lane == 0) poff[q] = acc;
+        if (lt) {
+            if (nd.h < nd.n) {
+                if (lane == 0) picks[acc] = nd.ksel;
+                acc += 1;
+            }
+            continue;
+        }
         if (nd.h < nd.n) {
             if ((uint64_t)nd.ksel + nd.h > (1ull << 18)) {
                 if (lane == 0) dev_fail(P.st, kErrWords, mu);
@@ -750,7 +809,17 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
     for (uint32_t round_lo = 0;; round_lo += kBLQ) {
         if (wid == 0) {
             uint32_t nneed = 0;
-            for (int c0 = 0; c0 < l; c0 += 32) {
+            if (P.strategy == HYPERIM_STRAT_LT) {  // one need of h = 1, ksel = the kept position
+                int kept = 0;
+                if (lane == 0) {
+                    Need nd;
+                    bool dr = false;
+                    kept = lt_keep(P, pb, l, j, ybase, mu, nd, &dr) ? 1 : 0;
+                    if (kept) S.bneed[0] = nd;
+                }
+                nneed = (uint32_t)__shfl_sync(0xFFFFFFFFu, kept, 0);
+            }
+            for (int c0 = 0; c0 < (P.strategy == HYPERIM_STRAT_LT ? 0 : l); c0 += 32) {
                 const int i = c0 + lane;
                 uint32_t h = 0, ksel = 0;
                 uint4 e = make_uint4(0, 0, 0, 0);
@@ -795,6 +864,10 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
             // picks: warp q % kWarps generates layer q
             for (uint32_t q = wid; q < nq; q += kWarps) {
                 const Need nd = S.bneed[q];
+                if (P.strategy == HYPERIM_STRAT_LT) {
+                    if (nd.h < nd.n && lane == 0) picks_g[S.bpick_off[q]] = nd.ksel;
+                    continue;
+                }
                 if (nd.h < nd.n) {
                     if ((uint64_t)nd.ksel + nd.h > (1ull << 18)) {
                         if (lane == 0) dev_fail(P.st, kErrWords, mu);

@@ -230,6 +230,44 @@ def test_chunk_index(H, oracle, model, uthr):
     assert seen2 == g2.stats()["index_vertices"] and seen2 >= 4
 
 
+@pytest.mark.parametrize("model,uthr", [("uniform_pair", 858993459), ("wc", 0), ("paper_layer", 0),
+                                        ("uniform_pair", P32)])
+def test_lt_sampler(H, oracle, model, uthr):
+    # the LT cascade's live-edge sampler (one kept in-neighbour per pop); paper_layer and p = 1
+    # give layer masses above 2^32 (normalised)
+    n, hes = gc.random_graph(5, 500, 420, 9)
+    g, og = load_both(H, oracle, n, hes, model, uthr, seed=21)
+    for roots in ("plain", "stratified"):
+        check_pool(H, oracle, g, og, 3000, roots, "lt", seed=21, grow=[100])
+
+
+def test_lt_sampler_large_neighbourhoods(H, oracle):
+    # hubs (chunk index path), many layers, degenerate hyperedges
+    n, hes = gc.hub_graph()
+    for model, uthr in (("wc", 0), ("uniform_pair", 85899345)):
+        g, og = load_both(H, oracle, n, hes, model, uthr, seed=11)
+        check_pool(H, oracle, g, og, 3000, "stratified", "lt", seed=11)
+    n2, hes2 = gc.layered_hub_graph()
+    g2, og2 = load_both(H, oracle, n2, hes2, "paper_layer", 0, seed=3)
+    check_pool(H, oracle, g2, og2, 2000, "stratified", "lt", seed=3)
+    n3, hes3 = gc.degenerate_graph()
+    g3, og3 = load_both(H, oracle, n3, hes3, "uniform_pair", 1 << 31, seed=3)
+    check_pool(H, oracle, g3, og3, 400, "plain", "lt", seed=3)
+
+
+def test_lt_brr(H, oracle):
+    n, hes = gc.random_graph(8, 2000, 1700, 6)
+    g, og = load_both(H, oracle, n, hes, "wc", 0, seed=17)
+    r1 = g.pool(tag=0, roots="stratified", strategy="lt")
+    r2 = g.pool(tag=1, roots="stratified", strategy="lt")
+    seeds, res = g.select_seeds(r1, r2, 10, mode="brr", eps=0.2, ell=1.0)
+    oseeds, ores = oracle.brr(og, 17, 10, 0.2, 1.0, 0, "stratified", "lt")
+    assert seeds.tolist() == oseeds.tolist()
+    for key in ("rounds", "theta", "pool_r1", "pool_r2"):
+        assert res[key] == ores[key], key
+    assert res["lambda_r2"].tolist() == ores["lambda_r2"].tolist()
+
+
 def test_greedy_and_spread(H, oracle):
     n, hes = gc.random_graph(4, 2000, 1500, 8)
     g, og = load_both(H, oracle, n, hes, "uniform_pair", 429496729, seed=13)
