@@ -130,8 +130,8 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False):
     """One whole IM query through the C ABI; returns counters of the work done."""
     q = w.query
     g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=seed)
-    r1 = g.pool(tag=0, roots=q.roots)
-    r2 = g.pool(tag=1, roots=q.roots)
+    r1 = g.pool(tag=0, roots=q.roots, strategy=q.strategy)
+    r2 = g.pool(tag=1, roots=q.roots, strategy=q.strategy)
     if q.theta is not None:
         r1.sample(q.theta)
         seeds, res = g.select_seeds(r1, None, q.k, mode="fixed")
@@ -312,7 +312,7 @@ def profile_batch(args):
                 q.uniform_threshold, seed=q.seed)
     before = 0
     for i in range(4):
-        p = g.pool(tag=10 + i, roots=q.roots)
+        p = g.pool(tag=10 + i, roots=q.roots, strategy=q.strategy)
         p.sample(args.profile_batch)
         v = p.view()
         if i == 3:
@@ -332,7 +332,7 @@ def oracle_rate(w, off, mem, seconds, seed, tag=0):
     import oracle as O
     q = w.query
     og = O.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold)
-    pool = O.Pool(og, seed=seed, tag=tag, roots=q.roots)
+    pool = O.Pool(og, seed=seed, tag=tag, roots=q.roots, strategy=q.strategy)
     t0 = time.perf_counter()
     theta = 1
     while True:

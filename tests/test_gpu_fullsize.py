@@ -6,7 +6,8 @@
   of every vertex, the first BRR round's pools (theta_0 = 49 per pool) set by set, and greedy on
   them (the oracle spends ~0.15 s per RR set here: the sets hold a third of the graph).
 * 2,000,000 vertices / 1,000,000 Zipf(1.9) hyperedges, weighted cascade, stratified roots: the
-  profile of a sample of vertices and the theta_0 = 75 RR sets of the first BRR round.
+  profile of a sample of vertices and the theta_0 = 75 RR sets of the first BRR round, under the
+  IC and under the LT cascade.
 * the 100k graph under the paper's layer probabilities (p_i = 1/(i ln(l+1)) / n_i): the profile
   of every vertex, two pools of theta = 500 set by set, and greedy on them.
 """
@@ -97,6 +98,12 @@ def test_zipf_2m_first_round(H, oracle):
     op.grow_theta(plan["theta0"])
     gc.assert_same_pool(p, op)
     gc.assert_same_counters(p, op)
+    # the same graph under the LT cascade (zipf-2m-1m-lt): paths of ~400 pops through the hubs
+    lt = g.pool(tag=0, roots=q.roots, strategy="lt").sample(plan["theta0"])
+    olt = oracle.Pool(og, seed=q.seed, tag=0, roots=q.roots, strategy="lt")
+    olt.grow_theta(plan["theta0"])
+    gc.assert_same_pool(lt, olt)
+    gc.assert_same_counters(lt, olt)
 
 
 def test_zipf_100k_paper_layer(H, oracle):

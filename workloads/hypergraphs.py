@@ -86,6 +86,7 @@ class QuerySpec:
     ell: float
     roots: str                  # "plain" | "stratified"
     seed: int = 1
+    strategy: str = "paper"     # "paper" | "binomial_only" (IC) | "lt" (the LT cascade)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -200,6 +201,15 @@ WORKLOADS = {
                     "membership (the zipf-100k-50k-p001 graph); the paper's layer probabilities "
                     "p_i = 1/(i ln(l+1)) / n_i; k=50; eps=0.1, delta=1/n; adaptive theta; "
                     "stratified roots"),
+    "zipf-2m-1m-lt": Workload(
+        name="zipf-2m-1m-lt",
+        graph=HypergraphSpec(n=2_000_000, m=1_000_000, size_law="zipf", size_lo=2, size_hi=1000,
+                             zipf_alpha=1.9, membership="preferential", seed=1),
+        query=QuerySpec(model="wc", uniform_threshold=0, k=100, theta=None, eps=0.1, ell=1.0,
+                        roots="stratified", seed=1, strategy="lt"),
+        description="the zipf-2m-1m-wc graph under the LT cascade (live-edge form, one kept "
+                    "in-neighbour per pop) with weighted-cascade weights p=1/deg; k=100; eps=0.1, "
+                    "delta=1/n; adaptive theta; stratified roots"),
     "zipf-2m-1m-wc": Workload(
         name="zipf-2m-1m-wc",
         graph=HypergraphSpec(n=2_000_000, m=1_000_000, size_law="zipf", size_lo=2, size_hi=1000,
