@@ -91,6 +91,9 @@ def lib():
             "or_pool_copy": (C.c_int, [vp, i64p, i32p, C.POINTER(C.c_uint8), u32p]),
             "or_pool_stats": (None, [vp, C.POINTER(Stats)]),
             "or_greedy": (C.c_int, [vp, C.c_int32, i32p, u64p, u64p]),
+            "or_greedy_upper": (C.c_int, [vp, C.c_int32, i32p, u64p, u64p, u64p]),
+            "or_prefix_upper_sigma": (C.c_double, [C.c_uint64, C.c_uint64, C.c_int, C.c_int64,
+                                                   C.c_uint64]),
             "or_coverage": (C.c_int, [vp, i32p, C.c_int32, u64p]),
             "or_estimate": (C.c_double, [vp, u64p]),
             "or_forward_spread": (C.c_int, [vp, i32p, C.c_int32, C.c_uint64, C.c_uint64,
@@ -102,6 +105,9 @@ def lib():
             "or_brr": (C.c_int, [vp, C.c_uint64, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                  C.c_int, C.c_int, i32p, C.POINTER(BrrResult),
                                  C.POINTER(Stats)]),
+            "or_brr_upper": (C.c_int, [vp, C.c_uint64, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                       C.c_int, C.c_int, C.c_int, i32p, C.POINTER(BrrResult),
+                                       C.POINTER(Stats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -292,6 +298,16 @@ class Pool:
                                _p(gains, C.c_uint64)))
         return seeds[:k], lam, gains[:k]
 
+    def greedy_upper(self, k):
+        """greedy plus Eq. upper_2 (p_max = 1) as an exact integer in the greedy's weights."""
+        seeds = np.zeros(max(k, 1), dtype=np.int32)
+        lam = np.zeros(NSTRATA, dtype=np.uint64)
+        gains = np.zeros(max(k, 1), dtype=np.uint64)
+        pu = np.zeros(2, dtype=np.uint64)
+        _check(lib().or_greedy_upper(self._h, k, _p(seeds, C.c_int32), _p(lam, C.c_uint64),
+                                     _p(gains, C.c_uint64), _p(pu, C.c_uint64)))
+        return seeds[:k], lam, gains[:k], int(pu[0]) | (int(pu[1]) << 64)
+
     def coverage(self, seeds):
         s = np.ascontiguousarray(seeds, dtype=np.int32)
         lam = np.zeros(NSTRATA, dtype=np.uint64)
@@ -318,12 +334,19 @@ def lower_bound(lambda2, delta, n, theta):
     return lib().or_lower_bound(float(lambda2), float(delta), int(n), int(theta))
 
 
-def brr(graph: Graph, seed, k, eps, ell=1.0, cap=0, roots="stratified", strategy="paper"):
+UPPER = {"closed": 0, "prefix": 1}
+
+
+def prefix_upper_sigma(u, roots, n, N):
+    return lib().or_prefix_upper_sigma(u & ((1 << 64) - 1), u >> 64, ROOTS[roots], n, N)
+
+
+def brr(graph: Graph, seed, k, eps, ell=1.0, cap=0, roots="stratified", strategy="paper", upper="closed"):
     seeds = np.zeros(max(k, 1), dtype=np.int32)
     res = BrrResult()
     st = Stats()
-    _check(lib().or_brr(graph.handle, seed, k, eps, ell, cap, ROOTS[roots], STRATEGIES[strategy],
-                        _p(seeds, C.c_int32), C.byref(res), C.byref(st)))
+    _check(lib().or_brr_upper(graph.handle, seed, k, eps, ell, cap, ROOTS[roots], STRATEGIES[strategy],
+                              UPPER[upper], _p(seeds, C.c_int32), C.byref(res), C.byref(st)))
     out = {f: getattr(res, f) for f, _ in BrrResult._fields_
            if f not in ("alpha_round", "lambda_r1", "lambda_r2")}
     out["alpha_round"] = list(res.alpha_round)[:res.rounds]

@@ -865,8 +865,32 @@ static uint64_t stratum_weight(const or_pool* p, int s) {
  * containing it counts with its stratum weight -- ties to the lowest id, among vertices not yet
  * picked; add it to S and retire the RR sets it covers.
  */
+static int cmp_u64_desc(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x < y) - (x > y);
+}
+
+/* Eq. upper_2 with p_max = 1: min over the greedy prefixes S_i (0 <= i <= k) of the coverage of
+ * S_i plus the sum of the k largest marginal coverages given S_i (maxC(S_i, k)), all in the
+ * greedy's integer weights; the k largest are taken among the vertices not in S_i. */
+static unsigned __int128 topk_sum(const uint64_t* score, const uint8_t* picked, int32_t n, int32_t k,
+                                  uint64_t* tmp) {
+    int32_t c = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (!picked[v]) tmp[c++] = score[v];
+    qsort(tmp, (size_t)c, sizeof(uint64_t), cmp_u64_desc);
+    unsigned __int128 sum = 0;
+    for (int32_t i = 0; i < c && i < k; ++i) sum += tmp[i];
+    return sum;
+}
+
 int or_greedy(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_NSTRATA],
               uint64_t* gains) {
+    return or_greedy_upper(p, k, seeds, lambda_s, gains, NULL);
+}
+
+int or_greedy_upper(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_NSTRATA],
+                    uint64_t* gains, uint64_t prefix_upper[2]) {
     const int32_t n = p->g->n;
     if (k < 0 || k > n) return OR_EINVAL;
     int64_t N = or_pool_count(p);
@@ -897,7 +921,14 @@ int or_greedy(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_
             score[mem[x]] += W[sof[r]];
         }
     memset(lambda_s, 0, sizeof(uint64_t) * OR_NSTRATA);
-    for (int32_t round = 0; round < k; ++round) {
+    uint64_t* tmp = prefix_upper ? (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1)) : NULL;
+    unsigned __int128 cover = 0, best_u = ~(unsigned __int128)0;
+    for (int32_t round = 0; round <= k; ++round) {
+        if (prefix_upper) {
+            const unsigned __int128 u = cover + topk_sum(score, picked, n, k, tmp);
+            if (u < best_u) best_u = u;
+        }
+        if (round == k) break;
         int32_t best = -1;
         for (int32_t v = 0; v < n; ++v) {
             if (picked[v]) continue;
@@ -915,7 +946,13 @@ int or_greedy(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_
             for (int64_t x = off[r]; x < off[r + 1]; ++x) score[mem[x]] -= W[sof[r]];
         }
         if (gains) gains[round] = gain;
+        cover += gain;
     }
+    if (prefix_upper) {
+        prefix_upper[0] = (uint64_t)best_u;
+        prefix_upper[1] = (uint64_t)(best_u >> 64);
+    }
+    free(tmp);
     free(off); free(mem); free(sof); free(score); free(ioff); free(covered); free(picked);
     free(inv); free(cur);
     return OR_OK;
@@ -997,8 +1034,22 @@ double or_lower_bound(double lambda2, double delta, int64_t n, uint64_t theta) {
  * gives S_k; the upper bound comes from R1, the lower bound from S_k's coverage of R2; stop when
  * alpha = lower/upper >= 1 - 1/e - eps or after i_max doublings.
  */
+/* Eq. upper_2 (integer greedy weights, two 64-bit words) in the units of sigma: the weights
+ * are floor(|V_s| 2^32 / n_s) with stratified roots (scale 2^-32), 1 with plain roots (scale n/N). */
+double or_prefix_upper_sigma(uint64_t lo, uint64_t hi, int root_mode, int64_t n, uint64_t N) {
+    const double u = (double)(((unsigned __int128)hi << 64) | lo);
+    if (root_mode == 1) return u * 0x1p-32;
+    return (u * (double)n) / (double)N;
+}
+
 int or_brr(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
            int root_mode, int strategy, int32_t* seeds, or_brr_result* res, or_stats* st) {
+    return or_brr_upper(g, seed, k, eps, ell, cap, root_mode, strategy, 0, seeds, res, st);
+}
+
+int or_brr_upper(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
+                 int root_mode, int strategy, int upper_mode, int32_t* seeds, or_brr_result* res,
+                 or_stats* st) {
     or_plan plan;
     int rc = or_plan_theta(g->n, k, eps, ell, &plan);
     if (rc != OR_OK) return rc;
@@ -1015,13 +1066,15 @@ int or_brr(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, 
         if ((rc = or_pool_grow(r1, ns))) break;
         if ((rc = or_pool_grow(r2, ns))) break;
         uint64_t N1 = (uint64_t)or_pool_count(r1), N2 = (uint64_t)or_pool_count(r2);
-        if ((rc = or_greedy(r1, k, seeds, res->lambda_r1, NULL))) break;
+        uint64_t pu[2] = {0, 0};
+        if ((rc = or_greedy_upper(r1, k, seeds, res->lambda_r1, NULL, upper_mode ? pu : NULL))) break;
         if ((rc = or_coverage(r2, seeds, k, res->lambda_r2))) break;
         double s1 = or_estimate(r1, res->lambda_r1);
         double s2 = or_estimate(r2, res->lambda_r2);
         double lam1 = s1 * (double)N1 / (double)g->n;
         double lam2 = s2 * (double)N2 / (double)g->n;
-        double up = or_upper_bound(lam1, k, g->n, N1);
+        double up = upper_mode ? or_prefix_upper_sigma(pu[0], pu[1], root_mode, g->n, N1)
+                               : or_upper_bound(lam1, k, g->n, N1);
         double lo = or_lower_bound(lam2, plan.delta, g->n, N2);
         double alpha = lo / up;
         res->rounds = i + 1;

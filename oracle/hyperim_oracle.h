@@ -124,6 +124,18 @@ typedef struct {
 } or_brr_result;
 int or_brr(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
            int root_mode, int strategy, int32_t* seeds, or_brr_result* res, or_stats* st);
+/* Greedy that also returns Eq. upper_2 (p_max = 1): min over i in [0, k] of the weighted
+ * coverage of the first i seeds plus the k largest weighted marginal coverages of the vertices
+ * not among them, as an unsigned 128-bit integer {low, high} in the greedy's weights. */
+int or_greedy_upper(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_NSTRATA],
+                    uint64_t* gains, uint64_t prefix_upper[2]);
+/* that bound in the units of sigma (stratified: x 2^-32; plain: x n / N) */
+double or_prefix_upper_sigma(uint64_t lo, uint64_t hi, int root_mode, int64_t n, uint64_t N);
+/* BRR with the upper bound of Eq. upper_6 (upper_mode 0, the closed form Alg. 4 uses) or of
+ * Eq. upper_2 (upper_mode 1, its definition: the prefix minimum). */
+int or_brr_upper(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
+                 int root_mode, int strategy, int upper_mode, int32_t* seeds, or_brr_result* res,
+                 or_stats* st);
 
 #ifdef __cplusplus
 }

@@ -177,3 +177,74 @@ def test_brr_schedule(oracle):
     assert all(a < target for a in res["alpha_round"][:-1])
     assert res["pool_r1"] == res["pool_r2"] == int(g.allocate("stratified", res["theta"]).sum())
     assert abs(res["alpha"] - res["lower"] / res["upper"]) < 1e-12
+
+
+@pytest.mark.parametrize("roots", ["plain", "stratified"])
+@pytest.mark.parametrize("seed", range(3))
+def test_prefix_upper_bound_from_scratch(oracle, roots, seed):
+    # Eq. upper_2 with p_max = 1, recomputed from the weighted marginals of every greedy prefix
+    rng = np.random.default_rng(100 + seed)
+    n = 40
+    hes = [[int(x) for x in rng.integers(0, n, size=int(rng.integers(2, 5)))] for _ in range(30)]
+    g, pool, sets, a = make_pool(oracle, n, hes, "uniform_pair", 644245094, 2000, roots, seed)
+    ns = pool.counts()
+    W = [1] * 16 if roots == "plain" else [
+        ((g.stratum_size(s) << 32) // int(ns[s])) if ns[s] else 0 for s in range(16)]
+    k = 6
+    seeds, lam, gains, U = pool.greedy_upper(k)
+    best = None
+    for i in range(k + 1):
+        S = [int(x) for x in seeds[:i]]
+        cov = sum(int(W[s]) for R, s in zip(sets, a.stratum) if set(R) & set(S))
+        marg = sorted((weighted_marginal(sets, a.stratum, W, S, v) for v in range(n) if v not in S),
+                      reverse=True)
+        u = cov + sum(marg[:k])
+        best = u if best is None else min(best, u)
+    assert U == best
+    # never looser than the closed form of Lemma 5 (Eq. upper_6 with p_max = 1)
+    ck = sum(int(x) for x in gains)
+    assert U <= ck / (1 - (1 - 1 / k) ** k) + 1
+
+
+def test_prefix_upper_bounds_the_optimum(oracle):
+    # Lemma 4: the coverage of every k-set is at most the bound (exhaustive search, tiny pools)
+    rng = np.random.default_rng(11)
+    n = 12
+    for trial in range(4):
+        hes = [[int(x) for x in rng.integers(0, n, size=3)] for _ in range(10)]
+        _, pool, sets, _ = make_pool(oracle, n, hes, "uniform_pair", 1288490188, 300, "plain", trial)
+        for k in (1, 2, 3):
+            _, lam, _, U = pool.greedy_upper(k)
+            opt = bf.best_cover(sets, n, k)
+            assert opt <= U, (trial, k, opt, U)
+            assert int(lam.sum()) <= U
+
+
+def test_prefix_upper_in_sigma_units(oracle):
+    assert oracle.prefix_upper_sigma(3 << 32, "stratified", 100, 7) == 3.0
+    assert oracle.prefix_upper_sigma(21, "plain", 100, 7) == 300.0
+    assert oracle.prefix_upper_sigma((1 << 64) + (1 << 32), "stratified", 1, 1) == float(2 ** 32 + 1)
+
+
+@pytest.mark.parametrize("roots", ["plain", "stratified"])
+def test_brr_with_prefix_upper(oracle, roots):
+    # the same schedule with Eq. upper_2: every round's bound is at most the closed form's, so the
+    # prefix variant stops no later; its last round's bound is the greedy's prefix minimum
+    rng = np.random.default_rng(5)
+    n = 400
+    hes = [[int(x) for x in rng.integers(0, n, size=int(rng.integers(2, 6)))] for _ in range(300)]
+    off, mem = bf.to_csr(hes)
+    g = oracle.Graph(n, off, mem, "wc")
+    k, eps = 5, 0.3
+    _, closed = oracle.brr(g, 1, k, eps, 1.0, 0, roots)
+    seeds, pref = oracle.brr(g, 1, k, eps, 1.0, 0, roots, upper="prefix")
+    assert pref["rounds"] <= closed["rounds"]
+    for a_p, a_c in zip(pref["alpha_round"], closed["alpha_round"]):
+        # same R1 seeds and R2 lower bound in both: alpha_p / alpha_c = upper_c / upper_p >= 1
+        assert a_c == 0.0 or a_p / a_c >= 1 - 1e-12
+    # recompute the last round's bound from a pool grown the same way
+    p1 = oracle.Pool(g, seed=1, tag=0, roots=roots)
+    p1.grow_theta(pref["theta"])
+    s2, _, _, U = p1.greedy_upper(k)
+    assert s2.tolist() == seeds.tolist()
+    assert pref["upper"] == oracle.prefix_upper_sigma(U, roots, n, pref["pool_r1"])
