@@ -126,7 +126,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_query(H, torch, w, off, mem, seed, host_inputs=False):
+def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed"):
     """One whole IM query through the C ABI; returns counters of the work done."""
     q = w.query
     g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=seed)
@@ -136,7 +136,7 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False):
         r1.sample(q.theta)
         seeds, res = g.select_seeds(r1, None, q.k, mode="fixed")
     else:
-        seeds, res = g.select_seeds(r1, r2, q.k, mode="brr", eps=q.eps, ell=q.ell)
+        seeds, res = g.select_seeds(r1, r2, q.k, mode="brr", eps=q.eps, ell=q.ell, upper=upper)
     v1, v2 = r1.view(), r2.view()
     out = {"rr_sets": v1["count"] + v2["count"], "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
            "rr_launches": v1["rr_launches"] + v2["rr_launches"],
@@ -274,11 +274,35 @@ def bench_gpu(args):
     }
     if args.forward_sims > 0:
         line["forward_mc"] = forward_check(H, torch, w, d_off, d_mem, stats[-1], args.forward_sims)
+    if w.query.theta is None and not args.no_prefix_query:
+        line["brr_prefix_upper"] = prefix_query(H, torch, w, d_off, d_mem, seed, flush, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, off, mem, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def prefix_query(H, torch, w, off, mem, seed, flush, stream, steps=3):
+    """Outside the timed region: the same query with BRR's upper bound taken as Eq. upper_2
+    (the prefix minimum) instead of the closed form of Alg. 4; fewer rounds, same guarantee."""
+    run_query(H, torch, w, off, mem, seed, upper="prefix")
+    times, stats = [], []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(run_query(H, torch, w, off, mem, seed, upper="prefix"))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    last = stats[-1]
+    return {"ms_per_query": 1e3 * sum(times) / steps, "rr_sets_per_query": last["rr_sets"],
+            "rr_sets_per_s": sum(s["rr_sets"] for s in stats) / sum(times),
+            "brr_rounds": last["rounds"], "theta_final": last["theta"],
+            "seed_selection_seconds": sum(s["select_seconds"] for s in stats) / steps,
+            "sigma_rr_r2": last["sigma_r2"]}
 
 
 def forward_check(H, torch, w, off, mem, last, sims):
@@ -395,6 +419,8 @@ def main():
                     help="forward Monte-Carlo simulations of the last query's seeds (0: skip)")
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-prefix-query", action="store_true",
+                    help="skip the extra measurement of BRR with the Eq. upper_2 bound")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling aid: one RR-kernel launch growing a fresh pool by this theta")
     args = ap.parse_args()

@@ -237,6 +237,13 @@ hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_
  *          p_max = 1); lower bound ((sqrt(Lambda_R2 + 2 ln(1/delta)/9) - sqrt(ln(1/delta)/2))^2 -
  *          ln(1/delta)/18) n/|R2| (Sec. 4.2); stop once lower/upper >= 1 - 1/e - eps or after
  *          i_max doublings. theta_cap > 0 bounds theta_i (EOVERFLOW beyond it).
+ *          upper_mode HYPERIM_UPPER_PREFIX replaces the closed form (the one Alg. 4 uses) by
+ *          the bound it closes, Eq. upper_2 with p_max = 1: the minimum over the greedy's
+ *          prefixes S_i (0 <= i <= k) of the weighted coverage of S_i plus the k largest
+ *          weighted marginal coverages of the vertices not in S_i, computed exactly on the
+ *          integer greedy weights and scaled to sigma units (x 2^-32 with stratified roots,
+ *          x n/|R1| with plain roots); never larger than the closed form (Lemma 5), so BRR
+ *          stops no later. Also usable in FIXED mode (reported in `upper`).
  *          seconds_sample / seconds_select split the call's host wall time between growing
  *          the pools and running greedy + coverage.
  *   Greedy: marginal coverage (Eq. 2) weighted per stratum by floor(|V_s| 2^32 / n_s) (1 with
@@ -246,6 +253,7 @@ hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_
  *   EINVAL: k < 1, k > n, bad mode; ESTATE: pools of another graph or r1 == r2.
  * ------------------------------------------------------------------------------------------ */
 typedef enum { HYPERIM_SELECT_FIXED = 0, HYPERIM_SELECT_BRR = 1 } hyperim_select_mode;
+typedef enum { HYPERIM_UPPER_CLOSED = 0, HYPERIM_UPPER_PREFIX = 1 } hyperim_upper_mode;
 
 typedef struct {
     int32_t mode;        /* hyperim_select_mode */
@@ -253,6 +261,7 @@ typedef struct {
     uint64_t theta_cap;  /* BRR only; 0 = no cap (the i_max doublings bound theta) */
     int32_t root_mode;   /* BRR only: used when the pools are created empty */
     int32_t strategy;    /* BRR only */
+    int32_t upper_mode;  /* hyperim_upper_mode (0: Eq. upper_6, the default) */
 } hyperim_select_opts;
 
 typedef struct {

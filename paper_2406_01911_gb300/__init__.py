@@ -71,7 +71,8 @@ class PoolView(C.Structure):
 
 class SelectOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("eps", C.c_double), ("ell", C.c_double),
-                ("theta_cap", C.c_uint64), ("root_mode", C.c_int32), ("strategy", C.c_int32)]
+                ("theta_cap", C.c_uint64), ("root_mode", C.c_int32), ("strategy", C.c_int32),
+                ("upper_mode", C.c_int32)]
 
 
 class SelectResult(C.Structure):
@@ -196,10 +197,13 @@ def hyperim_sample_rr(h, pool_tag, theta, root_mode="plain", strategy="paper", p
     return ph
 
 
+UPPER_MODES = {"closed": 0, "prefix": 1}
+
+
 def hyperim_select_seeds(h, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap=0,
-                         root_mode="stratified", strategy="paper"):
+                         root_mode="stratified", strategy="paper", upper="closed"):
     opts = SelectOpts(SELECT_MODES[mode], float(eps), float(ell), int(theta_cap), ROOTS[root_mode],
-                      STRATEGIES[strategy])
+                      STRATEGIES[strategy], UPPER_MODES[upper])
     seeds = np.zeros(int(k), dtype=np.int32)
     res = SelectResult()
     _check(lib().hyperim_select_seeds(h, r1, r2, int(k), C.byref(opts), _ptr(seeds), C.byref(res)))
@@ -295,9 +299,9 @@ class Graph:
     def pool(self, tag=0, roots="plain", strategy="paper"):
         return Pool(self, tag, roots, strategy)
 
-    def select_seeds(self, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap=0):
+    def select_seeds(self, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap=0, upper="closed"):
         return hyperim_select_seeds(self._h, r1.handle, r2.handle if r2 is not None else None, k,
-                                    mode, eps, ell, theta_cap, r1.roots, r1.strategy)
+                                    mode, eps, ell, theta_cap, r1.roots, r1.strategy, upper)
 
     def spread(self, seeds, pool):
         return hyperim_spread(self._h, seeds, pool.handle)

@@ -102,6 +102,15 @@ void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,
 }
 
 // Eq. 1 per stratum: sigma = sum_s (|V_s| / n_s) Lambda_s, strata in ascending order.
+// Eq. upper_2 (integer greedy weights as {low, high} 64-bit words) in the units of sigma: the
+// weights are floor(|V_s| 2^32 / n_s) with stratified roots (scale 2^-32), 1 with plain roots
+// (scale n / N)
+double prefix_upper_sigma(const uint64_t u[2], int32_t root_mode, int64_t n, uint64_t N) {
+    const double x = (double)(((unsigned __int128)u[1] << 64) | u[0]);
+    if (root_mode == HYPERIM_ROOTS_STRATIFIED) return x * 0x1p-32;
+    return (x * (double)n) / (double)N;
+}
+
 double estimate(const hyperim_graph* g, int32_t root_mode, const uint64_t n_s[HYPERIM_NSTRATA],
                 const uint64_t lambda_s[HYPERIM_NSTRATA]) {
     double sigma = 0.0;
@@ -462,14 +471,19 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     if (k < 1 || k > g->n) return set_error(HYPERIM_EINVAL, "need 1 <= k <= n");
     if (r1->g != g || (r2 && r2->g != g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
     if (r1 == r2) return set_error(HYPERIM_ESTATE, "r1 and r2 must be distinct pools");
+    if (opts->upper_mode != HYPERIM_UPPER_CLOSED && opts->upper_mode != HYPERIM_UPPER_PREFIX)
+        return set_error(HYPERIM_EINVAL, "unknown upper bound mode");
     std::memset(out, 0, sizeof(*out));
     hyperim_status st;
     using clk = std::chrono::steady_clock;
     double t_sample = 0.0, t_select = 0.0;
+    const bool prefix = opts->upper_mode == HYPERIM_UPPER_PREFIX;
+    uint64_t pu[2] = {0, 0};
     if (opts->mode == HYPERIM_SELECT_FIXED) {
         auto t0 = clk::now();
-        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1))) return st;
+        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr))) return st;
         out->sigma_r1 = estimate(g, r1->root_mode, r1->n_s, out->lambda_r1);
+        if (prefix) out->upper = prefix_upper_sigma(pu, r1->root_mode, g->n, (uint64_t)r1->count);
         if (r2) {
             if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
             out->sigma_r2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
@@ -496,7 +510,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         auto t0 = clk::now();
         if ((st = pool_grow_pair(g, r1, r2, theta))) return st;
         auto t1 = clk::now();
-        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1))) return st;
+        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr))) return st;
         if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
         auto t2 = clk::now();
         t_sample += std::chrono::duration<double>(t1 - t0).count();
@@ -506,7 +520,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         const double s2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
         const double lam1 = s1 * (double)N1 / (double)g->n;
         const double lam2 = s2 * (double)N2 / (double)g->n;
-        const double up = upper_bound(lam1, k, g->n, N1);
+        const double up = prefix ? prefix_upper_sigma(pu, r1->root_mode, g->n, N1) : upper_bound(lam1, k, g->n, N1);
         const double lo = lower_bound(lam2, plan.delta, g->n, N2);
         const double alpha = lo / up;
         out->rounds = i + 1;

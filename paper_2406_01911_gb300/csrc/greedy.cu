@@ -7,6 +7,7 @@
 // subtracted from the score of every member. The k rounds run back to back on the stream; the
 // winner of a round is read on the device by the next launch.
 #include <algorithm>
+#include <cstddef>
 
 #include "internal.h"
 
@@ -53,11 +54,21 @@ __device__ __forceinline__ bool better(unsigned long long s1, uint32_t i1, unsig
 
 // argmax of score over unpicked vertices, lowest id on ties; the last block to finish reduces
 // the per-block winners, records the seed and marks it picked.
+// Eq. upper_2 state (see the top-k kernels below)
+struct TopK {
+    unsigned long long prefix;
+    unsigned int kleft, all;  // all: fewer unpicked vertices than k, so all of them count
+    unsigned long long cover;
+    unsigned long long best_lo, best_hi;
+    unsigned int ticket;
+    unsigned int first_pass;  // radix passes before it: every unpicked score's digit is 0 there
+};
+
 __global__ void __launch_bounds__(kArgThreads)
 k_argmax(const unsigned long long* __restrict__ score, uint8_t* __restrict__ picked, int32_t n,
          unsigned long long* __restrict__ bscore, uint32_t* __restrict__ bid,
          unsigned int* __restrict__ ticket, int32_t* __restrict__ best, int32_t* __restrict__ seeds,
-         int round) {
+         int round, TopK* __restrict__ tk) {
     __shared__ unsigned long long ss[kArgThreads / 32];
     __shared__ uint32_t si[kArgThreads / 32];
     __shared__ bool last;
@@ -109,8 +120,123 @@ k_argmax(const unsigned long long* __restrict__ score, uint8_t* __restrict__ pic
         *best = (int32_t)bi;
         seeds[round] = (int32_t)bi;
         picked[bi] = 1;
+        // the winner's marginal weight, before its sets are retired; no unpicked score exceeds
+        // it, now or later (scores only decrease), so the radix passes above its leading digit
+        // can be skipped from here on
+        tk->cover += bs;
+        const int lead = bs ? (63 - __clzll((long long)bs)) : 0;
+        tk->first_pass = (unsigned int)((56 - (lead & ~7)) / 8);
         *ticket = 0;
     }
+}
+
+// ---- Eq. upper_2 (p_max = 1): the k largest scores among the vertices not picked yet ---------
+// A radix select over 8-bit digits, most significant first, finds the k-th largest score T
+// (prefix) and how many of its copies belong to the top k (kleft); the top-k sum is then the sum
+// of the scores above T plus kleft T. Every round's bound, cover + top-k sum, enters a running
+// minimum; all of it stays on the device between the greedy's launches. 128-bit sums are kept
+// as (lo, hi) pairs of 64-bit words.
+
+__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi, unsigned long long a_lo,
+                                       unsigned long long a_hi) {
+    const unsigned long long l = lo + a_lo;
+    hi += a_hi + (l < lo ? 1ull : 0ull);
+    lo = l;
+}
+
+__global__ void k_topk_hist(const unsigned long long* __restrict__ score, const uint8_t* __restrict__ picked,
+                            int32_t n, const TopK* __restrict__ st, int pass, unsigned int* __restrict__ hist) {
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    // passes above the top bound's leading digit would find every candidate in digit 0: skipped
+    if (!st->all && pass >= (int)st->first_pass) {
+        const int sh = 56 - 8 * pass;
+        const unsigned long long prefix = st->prefix;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < n; v0 += stride) {
+            const int64_t v = v0 + threadIdx.x;
+            int d = -1;
+            if (v < n && !picked[v]) {
+                const unsigned long long x = score[v];
+                if (pass == 0 || (x >> (sh + 8)) == prefix) d = (int)((x >> sh) & 255u);
+            }
+            // one shared atomic per distinct digit of the warp
+            const unsigned int same = __match_any_sync(0xFFFFFFFFu, d);
+            if (d >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[d], (unsigned int)__popc(same));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// one thread: the digit of the k-th largest among the candidates; clears the histogram
+__global__ void k_topk_select(TopK* __restrict__ st, unsigned int* __restrict__ hist, int pass) {
+    if (!st->all && pass >= (int)st->first_pass) {
+        unsigned int cum = 0;
+        int d = 255;
+        for (; d >= 0; --d) {
+            if (cum + hist[d] >= st->kleft) break;
+            cum += hist[d];
+        }
+        if (d < 0) {  // fewer candidates than k (only on the first pass): take every unpicked vertex
+            st->all = 1;
+            st->prefix = 0;
+            st->kleft = 0;
+        } else {
+            st->prefix = (st->prefix << 8) | (unsigned long long)d;
+            st->kleft -= cum;
+        }
+    }
+    for (int i = 0; i < 256; ++i) hist[i] = 0;
+}
+
+// sum of the scores above T = prefix over the unpicked vertices (grid reduction, last block
+// finishes): K = sum + kleft T; bound = cover + K; running minimum; state reset for next round
+__global__ void __launch_bounds__(kArgThreads)
+k_topk_sum(const unsigned long long* __restrict__ score, const uint8_t* __restrict__ picked, int32_t n,
+           TopK* __restrict__ st, unsigned long long* __restrict__ part, unsigned int k) {
+    __shared__ unsigned long long slo[kArgThreads / 32], shi[kArgThreads / 32];
+    __shared__ bool last;
+    const unsigned long long T = st->prefix;
+    unsigned long long lo = 0, hi = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (picked[v]) continue;
+        const unsigned long long x = score[v];
+        if (x > T) add128(lo, hi, x, 0ull);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        add128(lo, hi, __shfl_xor_sync(0xFFFFFFFFu, lo, o), __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { slo[wid] = lo; shi[wid] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kArgThreads / 32; ++w) add128(lo, hi, slo[w], shi[w]);
+        part[2 * blockIdx.x] = lo;
+        part[2 * blockIdx.x + 1] = hi;
+        __threadfence();
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    lo = 0;
+    hi = 0;
+    for (unsigned int b = 0; b < gridDim.x; ++b)
+        add128(lo, hi, ((volatile unsigned long long*)part)[2 * b], ((volatile unsigned long long*)part)[2 * b + 1]);
+    const unsigned long long kl = st->kleft;
+    add128(lo, hi, kl * T, __umul64hi(kl, T));
+    add128(lo, hi, st->cover, 0ull);
+    if (hi < st->best_hi || (hi == st->best_hi && lo < st->best_lo)) {
+        st->best_lo = lo;
+        st->best_hi = hi;
+    }
+    st->prefix = 0;
+    st->kleft = k;
+    st->all = 0;
+    st->ticket = 0;
 }
 
 // retire the uncovered RR sets containing the round's winner; one warp per inverted entry
@@ -170,7 +296,7 @@ int grid_cap(int64_t items, int threads, int sm, int per_sm) {
 }  // namespace
 
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
-                      uint64_t lambda_s[HYPERIM_NSTRATA]) {
+                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper) {
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
     const int64_t N = p->count, T = p->total;
@@ -201,6 +327,29 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
     if ((st = dev_alloc(g, (void**)&ticket, sizeof(uint32_t) * 2))) return st;
     if ((st = dev_alloc(g, (void**)&best, sizeof(int32_t) * 2))) return st;
     if ((st = dev_alloc(g, (void**)&seeds_d, sizeof(int32_t) * (size_t)k))) return st;
+    TopK* tk = nullptr;
+    unsigned int* hist = nullptr;
+    unsigned long long* part = nullptr;
+    const int tblocks = ablocks;
+    if ((st = dev_alloc(g, (void**)&tk, sizeof(TopK)))) return st;
+    if ((st = dev_alloc(g, (void**)&hist, sizeof(unsigned int) * 256))) return st;
+    if ((st = dev_alloc(g, (void**)&part, sizeof(unsigned long long) * 2 * (size_t)tblocks))) return st;
+    {
+        TopK t0{};
+        t0.kleft = (unsigned int)k;
+        t0.best_lo = ~0ull;
+        t0.best_hi = ~0ull;
+        HYP_CUDA(cudaMemcpyAsync(tk, &t0, sizeof(TopK), cudaMemcpyHostToDevice, s));
+        HYP_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 256, s));
+    }
+    auto topk_round = [&]() -> hyperim_status {
+        for (int pass = 0; pass < 8; ++pass) {
+            { k_topk_hist<<<tblocks, kArgThreads, 0, s>>>(score, picked, n, tk, pass, hist); count_launch(); }
+            { k_topk_select<<<1, 1, 0, s>>>(tk, hist, pass); count_launch(); }
+        }
+        { k_topk_sum<<<tblocks, kArgThreads, 0, s>>>(score, picked, n, tk, part, (unsigned int)k); count_launch(); }
+        return HYPERIM_OK;
+    };
     HYP_CUDA(cudaMemsetAsync(cnt, 0, bytes_cnt, s));
     HYP_CUDA(cudaMemsetAsync(score, 0, sizeof(unsigned long long) * (size_t)n, s));
     HYP_CUDA(cudaMemsetAsync(picked, 0, (size_t)n, s));
@@ -215,17 +364,28 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
                                                                     N, inv_off, cnt, inv, score, W); count_launch(); }
     const int rblocks = sm * 8;
     for (int32_t round = 0; round < k; ++round) {
+        if (prefix_upper) topk_round();
         { k_argmax<<<ablocks, kArgThreads, 0, s>>>(score, picked, n, bscore, bid, ticket, best, seeds_d,
-                                                 round); count_launch(); }
+                                                 round, tk); count_launch(); }
         { k_retire<<<rblocks, 256, 0, s>>>(best, inv_off, inv, p->rr_off, p->rr_mem, p->rr_stratum,
                                          covered, score, lam, W); count_launch(); }
     }
+    if (prefix_upper) topk_round();  // i = k: the whole seed set
     HYP_CUDA(cudaGetLastError());
     unsigned long long hl[HYPERIM_NSTRATA];
+    TopK th{};
     HYP_CUDA(cudaMemcpyAsync(seeds_host, seeds_d, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaMemcpyAsync(hl, lam, sizeof(hl), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaMemcpyAsync(&th, tk, sizeof(TopK), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < HYPERIM_NSTRATA; ++i) lambda_s[i] = hl[i];
+    if (prefix_upper) {
+        prefix_upper[0] = th.best_lo;
+        prefix_upper[1] = th.best_hi;
+    }
+    dev_free(g, tk, sizeof(TopK));
+    dev_free(g, hist, sizeof(unsigned int) * 256);
+    dev_free(g, part, sizeof(unsigned long long) * 2 * (size_t)tblocks);
     dev_free(g, cnt, bytes_cnt);
     dev_free(g, inv_off, sizeof(int64_t) * ((size_t)n + 1));
     dev_free(g, inv, bytes_inv);

@@ -192,13 +192,15 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
 
 // greedy.cu
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
-                      uint64_t lambda_s[HYPERIM_NSTRATA]);
+                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper = nullptr);
 hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_host, int32_t k,
                         uint64_t lambda_s[HYPERIM_NSTRATA]);
 
 // host arithmetic (plan.cpp)
 void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,
                      uint64_t n_s[HYPERIM_NSTRATA]);
+// Eq. upper_2 bound {lo, hi} (greedy weights) in sigma units
+double prefix_upper_sigma(const uint64_t u[2], int32_t root_mode, int64_t n, uint64_t N);
 double estimate(const hyperim_graph* g, int32_t root_mode, const uint64_t n_s[HYPERIM_NSTRATA],
                 const uint64_t lambda_s[HYPERIM_NSTRATA]);
 uint64_t stratum_weight(const hyperim_graph* g, int32_t root_mode, uint64_t n_s, int s);

@@ -318,6 +318,41 @@ def test_brr(H, oracle, roots):
     assert len(res["alpha_round"]) == len(ores["alpha_round"])
 
 
+@pytest.mark.parametrize("roots", ["plain", "stratified"])
+def test_prefix_upper_fixed(H, oracle, roots):
+    # Eq. upper_2 on the device (radix select of the k largest marginals each round) equals the
+    # oracle's exact integer bound; includes rounds with fewer unpicked vertices than k
+    cases = [(gc.random_graph(12, 3000, 2500, 6), "wc", 0, 4000, 25),
+             (gc.random_graph(13, 12, 9, 4), "uniform_pair", 1 << 31, 300, 9),
+             (gc.hub_graph(), "wc", 0, 3000, 40)]
+    for (n, hes), model, uthr, theta, k in cases:
+        g, og = load_both(H, oracle, n, hes, model, uthr, seed=29)
+        p = g.pool(tag=0, roots=roots).sample(theta)
+        op = oracle.Pool(og, seed=29, tag=0, roots=roots)
+        op.grow_theta(theta)
+        seeds, res = g.select_seeds(p, None, k, mode="fixed", upper="prefix")
+        oseeds, olam, _, U = op.greedy_upper(k)
+        assert seeds.tolist() == oseeds.tolist()
+        assert res["upper"] == oracle.prefix_upper_sigma(U, roots, n, op.count()), (n, k)
+
+
+@pytest.mark.parametrize("roots", ["plain", "stratified"])
+def test_brr_prefix_upper(H, oracle, roots):
+    n, hes = gc.random_graph(6, 3000, 2500, 6)
+    g, og = load_both(H, oracle, n, hes, "wc", 0, seed=17)
+    k, eps = 20, 0.2
+    r1, r2 = g.pool(tag=0, roots=roots), g.pool(tag=1, roots=roots)
+    seeds, res = g.select_seeds(r1, r2, k, mode="brr", eps=eps, ell=1.0, upper="prefix")
+    oseeds, ores = oracle.brr(og, 17, k, eps, 1.0, 0, roots, upper="prefix")
+    assert seeds.tolist() == oseeds.tolist()
+    for key in ("rounds", "theta", "pool_r1", "pool_r2"):
+        assert res[key] == ores[key], key
+    for key in ("sigma_r1", "sigma_r2", "upper", "lower", "alpha"):
+        assert abs(res[key] - ores[key]) <= REL * max(1.0, abs(ores[key])), key
+    _, closed = oracle.brr(og, 17, k, eps, 1.0, 0, roots)
+    assert res["rounds"] <= closed["rounds"]
+
+
 def test_errors(H):
     off, mem = gc.csr([[0, 5]])
     with pytest.raises(H.HyperIMError) as e:
