@@ -15,9 +15,9 @@
 //                     bits)); c = the fewest bits for which no chunk holds more than the target
 //                     (0 bits: not indexed); entries = l 2^c
 //   scan              table offsets
-//   k_idx_fill        per indexed vertex: members bucketed by chunk through a global scratch
-//                     area, each chunk sorted on chip, its runs (multiplicity w -> layer) counted;
-//                     before chunk k the running per-layer counts are written as column k
+//   k_idx_fill        per indexed vertex: members sorted by id on chip (bucketed through a global
+//                     scratch area when large), runs (multiplicity w -> layer) counted per
+//                     (layer, chunk); each layer row becomes an exclusive prefix
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -151,108 +151,133 @@ __global__ void k_idx_word(const int32_t* __restrict__ list, int32_t nlist, cons
         if (entries[i]) idx[list[i]] = ((uint64_t)bits[i] << kIdxBitsShift) | (uint64_t)off[i];
 }
 
-// Per indexed vertex (one block): members bucketed by chunk through a global scratch area; the
-// warps then take chunks in turn, sort one on chip (warp bucket sort), count its runs per layer
-// (multiplicity w -> layer by search in the descending w list) and write the counts as column k;
-// finally every layer row becomes an exclusive prefix along the chunks.
-constexpr int kFillWarps = 4;
-constexpr int kFillThreads = kFillWarps * 32;
-constexpr size_t kFillSmem = sizeof(int) * kBins + sizeof(uint32_t) * kIdxMaxL +
-                             sizeof(int) * (2 * kFillThreads + 1) +
-                             kFillWarps * (sizeof(uint32_t) * (2 * kIdxTarget + kIdxMaxL) + sizeof(int) * 256);
+// Per indexed vertex (one block, vertices taken from a shared counter): the members of mu's
+// hyperedges in ascending id order -- sorted whole on chip when at most kFillBuf of them, else
+// bucketed by their top id bits (a bucket is 2^3 whole index chunks, so at most 8 x 1,024
+// members) through a global scratch area and sorted bucket by bucket -- are walked run by run:
+// each distinct neighbour (multiplicity w -> layer by search in the descending w list) adds one
+// to its (layer, chunk) count, kept on chip when the l x 2^c table fits, else in the table
+// itself. Every layer row then becomes an exclusive prefix along the chunks, one warp per row.
+constexpr int kFillThreads = 256;
+constexpr int kFillBuf = 8192;  // members sorted on chip at once (power of two)
+constexpr int kFillCnt = 8192;  // (layer, chunk) counts kept on chip
+constexpr int kFillBkt = kBins;
+constexpr int kFillCtrl = 64;
+constexpr size_t kFillSmem = sizeof(uint32_t) * (kFillBuf + kFillCnt + kIdxMaxL) +
+                             sizeof(int) * (2 * kFillBkt + 2 * kFillThreads + 1 + kFillCtrl);
 
 __global__ void __launch_bounds__(kFillThreads)
 k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __restrict__ bits_in,
            const uint32_t* __restrict__ entries, const int64_t* __restrict__ off,
            const int4* __restrict__ vinfo, const int2* __restrict__ v_span,
-           const int32_t* __restrict__ he_mem, const uint4* __restrict__ prof, int id_bits,
-           uint32_t* __restrict__ tab, uint32_t* __restrict__ scratch, int64_t scratch_cap,
-           DevStatus* st) {
+           const int32_t* __restrict__ he_mem, const int32_t* __restrict__ tsum,
+           const uint4* __restrict__ prof, int id_bits, uint32_t* __restrict__ tab,
+           uint32_t* __restrict__ scratch, int64_t scratch_cap, int* __restrict__ next, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char fill_smem[];
-    int* chunk_end = reinterpret_cast<int*>(fill_smem);                 // kBins
-    uint32_t* lw = reinterpret_cast<uint32_t*>(chunk_end + kBins);      // kIdxMaxL
-    int* pre = reinterpret_cast<int*>(lw + kIdxMaxL);                   // 2 kFillThreads + 1
-    uint32_t* wbase = reinterpret_cast<uint32_t*>(pre + 2 * kFillThreads + 1);
+    uint32_t* buf = reinterpret_cast<uint32_t*>(fill_smem);             // kFillBuf
+    uint32_t* cnt_s = buf + kFillBuf;                                   // kFillCnt
+    uint32_t* lw = cnt_s + kFillCnt;                                    // kIdxMaxL
+    int* bkt = reinterpret_cast<int*>(lw + kIdxMaxL);                   // kFillBkt (on-chip sorts)
+    int* bucket_end = bkt + kFillBkt;                                   // kFillBkt (top-bit buckets)
+    int* pre = bucket_end + kFillBkt;                                   // 2 kFillThreads + 1
+    int* ctrl = pre + 2 * kFillThreads + 1;                             // kFillCtrl
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t* raw = wbase + (size_t)wid * (2 * kIdxTarget + kIdxMaxL);
-    uint32_t* srt = raw + kIdxTarget;
-    uint32_t* wcnt = srt + kIdxTarget;                                  // kIdxMaxL per warp
-    int* bkt = reinterpret_cast<int*>(wbase + (size_t)kFillWarps * (2 * kIdxTarget + kIdxMaxL)) + wid * 256;
+    constexpr int kWarps = kFillThreads / 32;
     uint32_t* big = scratch + (int64_t)blockIdx.x * scratch_cap;
-    for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) ctrl[0] = atomicAdd(next, 1);
+        __syncthreads();
+        const int i = ctrl[0];
+        __syncthreads();
+        if (i >= nlist) break;
         if (entries[i] == 0) continue;
         const int32_t mu = list[i];
         const int4 vi = vinfo[mu];
         const int l = vi.y, c = bits_in[i];
         const int C = 1 << c, shift = id_bits - c;
+        const int T = tsum[mu] - vi.w;
         uint32_t* t = tab + off[i];
+        const int64_t cells = (int64_t)l * C;
+        uint32_t* cnt = cells <= kFillCnt ? cnt_s : t;
         for (int q = threadIdx.x; q < l; q += kFillThreads) lw[q] = prof[2 * ((int64_t)vi.x + q)].x & ~kPOneFlag;
-        for (int k = threadIdx.x; k < C; k += kFillThreads) chunk_end[k] = 0;
+        for (int64_t k = threadIdx.x; k < cells; k += kFillThreads) cnt[k] = 0;
         __syncthreads();
-        for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
-                                      [&](uint32_t x) { atomicAdd(&chunk_end[x >> shift], 1); });
-        __syncthreads();
-        warp0_exclusive_scan(chunk_end, C);
-        __syncthreads();
-        for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre, [&](uint32_t x) {
-            const int p = atomicAdd(&chunk_end[x >> shift], 1);
-            if (p < scratch_cap) big[p] = x;
-        });
-        __threadfence_block();
-        __syncthreads();
-        // chunk_end[k] is now the end of chunk k
-        if (chunk_end[C - 1] > scratch_cap) {
-            if (threadIdx.x == 0) dev_fail(st, kErrCapacity, mu);
-            __syncthreads();
-            continue;
-        }
-        for (int k = wid; k < C; k += kFillWarps) {
-            const int begin = k ? chunk_end[k - 1] : 0;
-            const int cnt = chunk_end[k] - begin;
-            for (int q = lane; q < l; q += 32) wcnt[q] = 0;
-            if (cnt > kIdxTarget) {
-                if (lane == 0) dev_fail(st, kErrBucket, mu);
-            } else if (cnt > 0) {
-                const int nbits = bucket_bits(cnt, 8);
-                const int nb = 1 << nbits;
-                const int bshift = shift > nbits ? shift - nbits : 0;
-                const uint32_t key_mask = (uint32_t)nb - 1;
-                for (int b = lane; b < nb; b += 32) bkt[b] = 0;
-                __syncwarp();
-                for (int x = lane; x < cnt; x += 32) {
-                    const uint32_t v = big[begin + x];
-                    raw[x] = v;
-                    atomicAdd(&bkt[(v >> bshift) & key_mask], 1);
+        auto count_run = [&](bool start, uint32_t x, int mult) -> bool {
+            if (start) {
+                int lo = 0, hi = l;  // lw descends: first q with lw[q] <= mult
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (lw[mid] > (uint32_t)mult) lo = mid + 1; else hi = mid;
                 }
-                __syncwarp();
-                const int maxb = warp_bucket_scan(bkt, nb);
-                warp_scatter_sort(raw, cnt, kSentinel, srt, cnt, bkt, nb, 0u, bshift, key_mask, maxb);
-                walk_runs<32>(srt, cnt, [&](bool start, uint32_t, int mult) -> bool {
-                    if (start) {
-                        int lo = 0, hi = l;  // lw descends: first q with lw[q] <= mult
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (lw[mid] > (uint32_t)mult) lo = mid + 1; else hi = mid;
-                        }
-                        if (lo < l && lw[lo] == (uint32_t)mult) atomicAdd(&wcnt[lo], 1u);
-                        else dev_fail(st, kErrProfile, mu);
-                    }
-                    return false;
-                });
+                if (lo < l && lw[lo] == (uint32_t)mult) atomicAdd(&cnt[(int64_t)lo * C + (x >> shift)], 1u);
+                else dev_fail(st, kErrProfile, mu);
             }
-            __syncwarp();
-            for (int q = lane; q < l; q += 32) t[(int64_t)q * C + k] = wcnt[q];
-            __syncwarp();
+            return false;
+        };
+        if (T <= kFillBuf) {
+            const int got = sorted_nbhd<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, T, id_bits, buf, bkt, 12,
+                                                      pre, ctrl + 16);
+            walk_runs<kFillThreads>(buf, got, count_run);
+        } else {
+            if ((int64_t)T > scratch_cap) {
+                if (threadIdx.x == 0) dev_fail(st, kErrCapacity, mu);
+                __syncthreads();
+                continue;
+            }
+            const int b = c > 3 ? c - 3 : 0;
+            const int nb = 1 << b, bshift = id_bits - b;
+            for (int q = threadIdx.x; q < nb; q += kFillThreads) bucket_end[q] = 0;
+            __syncthreads();
+            for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
+                                          [&](uint32_t x) { atomicAdd(&bucket_end[x >> bshift], 1); });
+            __syncthreads();
+            int mx = 0;
+            for (int q = threadIdx.x; q < nb; q += kFillThreads) mx = max(mx, bucket_end[q]);
+            mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+            if (lane == 0) ctrl[8 + wid] = mx;
+            __syncthreads();
+            int all = 0;
+            for (int w = 0; w < kWarps; ++w) all = max(all, ctrl[8 + w]);
+            if (all > kFillBuf) {  // uniform; the plan's chunk bound rules this out
+                if (threadIdx.x == 0) dev_fail(st, kErrBucket, mu);
+                __syncthreads();
+                continue;
+            }
+            warp0_exclusive_scan(bucket_end, nb);
+            __syncthreads();
+            for_each_member<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, pre,
+                                          [&](uint32_t x) { big[atomicAdd(&bucket_end[x >> bshift], 1)] = x; });
+            __threadfence_block();
+            __syncthreads();
+            // bucket_end[q] is now the end of bucket q
+            int begin = 0;
+            for (int q = 0; q < nb; ++q) {
+                const int end = bucket_end[q];
+                if (end > begin) {
+                    sort_chunk<kFillThreads>(big + begin, end - begin, bshift, buf, bkt, 12, ctrl + 16);
+                    walk_runs<kFillThreads>(buf, end - begin, count_run);
+                    __syncthreads();
+                }
+                begin = end;
+            }
         }
         __syncthreads();
-        // counts -> exclusive prefix along the chunks, one layer row per thread
-        for (int q = threadIdx.x; q < l; q += kFillThreads) {
-            uint32_t* row = t + (int64_t)q * C;
-            uint32_t run = 0;
-            for (int k = 0; k < C; ++k) {
-                const uint32_t v = row[k];
-                row[k] = run;
-                run += v;
+        // counts -> exclusive prefix along the chunks, one warp per layer row
+        for (int q = wid; q < l; q += kWarps) {
+            const uint32_t* src = cnt + (int64_t)q * C;
+            uint32_t* dst = t + (int64_t)q * C;
+            uint32_t carry = 0;
+            for (int k0 = 0; k0 < C; k0 += 32) {
+                const int k = k0 + lane;
+                const uint32_t v = k < C ? src[k] : 0u;
+                uint32_t inc = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                if (k < C) dst[k] = carry + inc - v;
+                carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
             }
         }
         __syncthreads();
@@ -325,12 +350,16 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         // keep the scratch area within 1 GiB
         while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)1 << 30)) fblocks -= sm;
         uint32_t* d_scratch = nullptr;
+        int* d_next = nullptr;
         if ((st = dev_alloc(g, (void**)&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
+        if ((st = dev_alloc(g, (void**)&d_next, sizeof(int)))) return st;
+        HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
         { k_idx_fill<<<fblocks, kFillThreads, kFillSmem, s>>>(d_list, nl, d_bits, d_entries, d_off, g->vinfo, g->v_span,
-                                                  g->he_mem, g->prof, g->id_bits, g->idx_tab, d_scratch, cap,
-                                                  g->d_status); count_launch(); }
+                                                  g->he_mem, g->tsum, g->prof, g->id_bits, g->idx_tab, d_scratch,
+                                                  cap, d_next, g->d_status); count_launch(); }
         if ((st = check_device_status(g, "chunk index"))) return st;
         dev_free(g, d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks);
+        dev_free(g, d_next, sizeof(int));
         // indexed vertices
         std::vector<uint32_t> e((size_t)ncand);
         HYP_CUDA(cudaMemcpyAsync(e.data(), d_entries, sizeof(uint32_t) * (size_t)ncand, cudaMemcpyDeviceToHost, s));

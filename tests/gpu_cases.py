@@ -46,6 +46,23 @@ def layered_hub_graph(seed=0, n=30000, groups=12, group_edges=(1, 2, 3, 5, 8, 13
     return n, hes
 
 
+def deep_layered_hub_graph(seed=0, n=40000, layers=150, per_layer=2, m_rest=3000):
+    """Vertex 0 sits in `layers` hyperedges; for w = 1..layers, `per_layer` random co-members sit
+    in exactly w of them (hyperedges 0..w-1), so A(0) has one layer per w and about
+    per_layer * layers^2 / 2 members (repeats counted): many layers times many chunks, more
+    (layer, chunk) counts than the index build keeps on chip. Plus sparse random hyperedges."""
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(np.arange(1, n), size=layers * per_layer, replace=False)
+    hes = [[0] for _ in range(layers)]
+    for w in range(1, layers + 1):
+        for v in ids[(w - 1) * per_layer:w * per_layer]:
+            for j in range(w):
+                hes[j].append(int(v))
+    for _ in range(m_rest):
+        hes.append([int(x) for x in rng.integers(0, n, size=int(rng.integers(2, 6)))])
+    return n, hes
+
+
 def layered_graph(depth=40, pad=100):
     """Vertex 0 shares exactly i hyperedges with vertex i (i = 1..depth): depth distinct layers."""
     hes = []
