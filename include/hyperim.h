@@ -155,6 +155,20 @@ hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* 
                                          uint32_t* table, int64_t cap, int64_t* entries);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_graph_set_schedule -- how RR generation (Alg. 3) is scheduled on the GPU for every
+ *   later hyperim_sample_rr / hyperim_select_seeds call on g. The RR sets are identical under
+ *   both (their draws are keyed by RR id, vertex and layer); only the time differs.
+ *   HYPERIM_SCHED_PERSISTENT (the default): one launch per growth step, a persistent grid whose
+ *     blocks take RR sets from a device counter until none is left.
+ *   HYPERIM_SCHED_PLAIN: the comparison form, one launch per batch of as many RR sets as blocks
+ *     fit on the GPU, one set per block, the next batch launched after the slowest set of the
+ *     previous one finishes.
+ *   EINVAL: g NULL or an unknown schedule. No device work.
+ * ------------------------------------------------------------------------------------------ */
+typedef enum { HYPERIM_SCHED_PERSISTENT = 0, HYPERIM_SCHED_PLAIN = 1 } hyperim_schedule;
+hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_plan_theta -- RR budget of Sec. 4.3 (host arithmetic, IEEE double).
  *   delta = n^-ell (Sec. 6: delta = 1/|V| for ell = 1); ln C(n,k) = sum_{i<=k'} ln((n-k'+i)/i)
  *   with k' = min(k, n-k);

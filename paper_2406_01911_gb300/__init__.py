@@ -26,6 +26,7 @@ P_ONE = 1 << 32
 NOALLOC_MAX_N = 1 << 24
 MODELS = {"uniform_pair": 0, "wc": 1, "paper_layer": 2}
 ROOTS = {"plain": 0, "stratified": 1}
+SCHEDULES = {"persistent": 0, "plain": 1}
 STRATEGIES = {"paper": 0, "binomial_only": 1, "lt": 2}
 SELECT_MODES = {"fixed": 0, "brr": 1}
 STATUS = {0: "HYPERIM_OK", -1: "HYPERIM_EINVAL", -2: "HYPERIM_ENOMEM", -3: "HYPERIM_EOVERFLOW",
@@ -91,6 +92,7 @@ _SIGNATURES = {
     "hyperim_graph_free": (None, [_vp]),
     "hyperim_graph_stats": (C.c_int, [_vp, C.POINTER(GraphStats)]),
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hyperim_graph_set_schedule": (C.c_int, [_vp, C.c_int32]),
     "hyperim_graph_chunk_index": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _vp, C.c_int64,
                                             C.POINTER(C.c_int64)]),
     "hyperim_forward_spread": (C.c_int, [_vp, _vp, C.c_int32, C.c_uint64, C.c_uint64, _vp,
@@ -283,6 +285,11 @@ class Graph:
         _check(lib().hyperim_graph_chunk_index(self._h, int(v), C.byref(bits), _ptr(tab), entries.value,
                                                C.byref(entries)))
         return bits.value, tab.reshape(-1, 1 << bits.value)
+
+    def set_schedule(self, schedule):
+        """RR generation schedule: "persistent" (default) or "plain" (one launch per batch of one
+        set per block, the comparison form); the RR sets are the same under both."""
+        _check(lib().hyperim_graph_set_schedule(self._h, SCHEDULES[schedule]))
 
     def forward_spread(self, seeds, simulations, seed):
         """(counts[simulations], mean, std_err) of forward IC cascades from `seeds` (Sec. 2.2)."""

@@ -318,6 +318,14 @@ hyperim_status hyperim_graph_chunk_index(hyperim_graph_t g, int32_t v, int32_t* 
     return HYPERIM_OK;
 }
 
+hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule) {
+    if (!g) return set_error(HYPERIM_EINVAL, "null graph");
+    if (schedule != HYPERIM_SCHED_PERSISTENT && schedule != HYPERIM_SCHED_PLAIN)
+        return set_error(HYPERIM_EINVAL, "unknown schedule");
+    g->schedule = schedule;
+    return HYPERIM_OK;
+}
+
 hyperim_status hyperim_graph_profile(hyperim_graph_t g, int32_t* deg, int32_t* nlayers, int32_t* stratum,
                                      int64_t* prof_off, uint32_t* layer_w, uint32_t* layer_n,
                                      uint64_t* layer_thr) {

@@ -131,6 +131,7 @@ struct hyperim_graph {
     hyperim::RRCounters* d_counters = nullptr;
     hyperim::Scratch scratch;
     int sm_count = 0;
+    int32_t schedule = 0;        // hyperim_schedule of RR generation
 };
 
 struct hyperim_pool {

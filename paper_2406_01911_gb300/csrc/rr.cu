@@ -80,6 +80,8 @@ struct RRParams {
     int64_t* out_pos;
     int32_t* out_size;
     int* next_job;
+    int plain;                // 1: this launch runs jobs [plain_base, plain_base + gridDim.x), one per block
+    int64_t plain_base;
     DevStatus* st;
     RRCounters* counters;                    // kMaxPools entries
 };
@@ -1157,11 +1159,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
+    int64_t plain_ticket = P.plain_base + blockIdx.x;  // the plain schedule's one job
     for (;;) {
         // jobs are handed out from the last one down: strata ascend with the job index, and the
         // high strata (roots with many layers, usually the costliest sets) should start first so
         // that cheap sets fill the end of the launch
-        if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job, 1);
+        if (threadIdx.x == 0) {
+            if (P.plain) {
+                S.ctrl[C_JOB] = (int)plain_ticket;
+                plain_ticket = njobs;
+            } else {
+                S.ctrl[C_JOB] = atomicAdd(P.next_job, 1);
+            }
+        }
         __syncthreads();
         const int64_t ticket = S.ctrl[C_JOB];
         if (ticket >= njobs) break;
@@ -1488,6 +1498,8 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.out_pos = d_pos;
     P.out_size = d_size;
     P.next_job = d_next;
+    P.plain = g->schedule == HYPERIM_SCHED_PLAIN ? 1 : 0;
+    P.plain_base = 0;
     P.arena_used = d_used;
     P.st = g->d_status;
     P.counters = g->d_counters;
@@ -1510,7 +1522,19 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int) + sizeof(unsigned long long) * 2, s));
         HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
         HYP_CUDA(cudaEventRecord(ev0, s));
-        { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+        if (P.plain) {
+            // the comparison form: one launch per batch of `blocks` sets, one set per block
+            for (int64_t base = 0; base < njobs; base += blocks) {
+                P.plain_base = base;
+                const int grid = (int)std::min<int64_t>(blocks, njobs - base);
+                { k_rr<<<grid, kThreads, smem, s>>>(P); count_launch(); }
+                HYP_CUDA(cudaGetLastError());
+                ++launches;
+            }
+        } else {
+            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+            ++launches;
+        }
         HYP_CUDA(cudaGetLastError());
         HYP_CUDA(cudaEventRecord(ev1, s));
         HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
@@ -1522,7 +1546,6 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         float ms = 0.f;
         HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
         seconds += 1e-3 * (double)ms;
-        ++launches;
         if (used <= g->scratch.arena_cap) break;
         want = used + used / 8 + 4096;
     }

@@ -230,6 +230,24 @@ def test_chunk_index(H, oracle, model, uthr):
     assert seen2 == g2.stats()["index_vertices"] and seen2 >= 4
 
 
+@pytest.mark.parametrize("case", ["layered_small", "deep"])
+def test_chunk_index_layers(H, oracle, case):
+    # layered_small: hubs of about 4,800 members with six layers (sorted whole on chip while the
+    # index is built); deep: a hub of about 22,650 members in 150 layers, so its l x 2^c counts
+    # exceed what the build keeps on chip (counted in the table itself, bucketed members)
+    if case == "layered_small":
+        n, hes = gc.layered_hub_graph(groups=6)
+    else:
+        n, hes = gc.deep_layered_hub_graph()
+    g, og = load_both(H, oracle, n, hes, "wc", 0, seed=5)
+    T = neighbourhood_sizes(n, hes)
+    seen = check_chunk_index(g, og, n, sorted(set(range(8)) | set(np.nonzero(T > 1024)[0].tolist())))
+    assert seen == g.stats()["index_vertices"] and seen >= 1
+    if case == "deep":
+        bits, tab = g.chunk_index(0)
+        assert tab.shape[0] >= 150 and tab.size > 8192
+
+
 @pytest.mark.parametrize("model,uthr", [("uniform_pair", 858993459), ("wc", 0), ("paper_layer", 0),
                                         ("uniform_pair", P32)])
 def test_lt_sampler(H, oracle, model, uthr):
@@ -381,3 +399,24 @@ def test_errors(H):
     with pytest.raises(H.HyperIMError) as e:
         H.Graph(3, off, mem, hbm_budget_bytes=64)
     assert e.value.status == -2
+
+
+@pytest.mark.parametrize("roots", ["plain", "stratified"])
+def test_plain_schedule(H, oracle, roots):
+    # the comparison form (one launch per batch, one RR set per block) draws the same sets: pools
+    # grown over several batches, and a whole BRR query
+    n, hes = gc.hub_graph()
+    g, og = load_both(H, oracle, n, hes, "uniform_pair", 85899345, seed=7)
+    g.set_schedule("plain")
+    check_pool(H, oracle, g, og, 2000, roots, seed=7, grow=[300])
+    assert H.lib().hyperim_graph_set_schedule(g._h, 7) == -1
+    n2, hes2 = gc.random_graph(6, 3000, 2500, 6)
+    g2, og2 = load_both(H, oracle, n2, hes2, "wc", 0, seed=17)
+    g2.set_schedule("plain")
+    r1, r2 = g2.pool(tag=0, roots=roots), g2.pool(tag=1, roots=roots)
+    seeds, res = g2.select_seeds(r1, r2, 20, mode="brr", eps=0.2, ell=1.0)
+    oseeds, ores = oracle.brr(og2, 17, 20, 0.2, 1.0, 0, roots)
+    assert seeds.tolist() == oseeds.tolist()
+    for key in ("rounds", "theta", "pool_r1", "pool_r2"):
+        assert res[key] == ores[key], key
+    assert res["lambda_r2"].tolist() == ores["lambda_r2"].tolist()
