@@ -14,7 +14,8 @@ from pinned host buffers (host->device copy inside the timed call, seeds copied 
 
 With torchrun (N > 1) every rank runs its own query (its own seed) on its GPU: the queries are
 independent problems, so there is no collective on the data path (weak scaling); rank 0 prints.
-``--impl reference`` times the CPU oracle (single core) on a bounded sample of the same workload.
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload, on every host
+core (one thread and one oracle graph per core, disjoint RR ids).
 """
 import argparse
 import hashlib
@@ -126,10 +127,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed"):
+def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", schedule="persistent"):
     """One whole IM query through the C ABI; returns counters of the work done."""
     q = w.query
     g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=seed)
+    if schedule != "persistent":
+        g.set_schedule(schedule)
     r1 = g.pool(tag=0, roots=q.roots, strategy=q.strategy)
     r2 = g.pool(tag=1, roots=q.roots, strategy=q.strategy)
     if q.theta is not None:
@@ -141,6 +144,7 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed"):
     out = {"rr_sets": v1["count"] + v2["count"], "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
            "rr_launches": v1["rr_launches"] + v2["rr_launches"],
            "bytes": rr_algorithmic_bytes(v1) + rr_algorithmic_bytes(v2),
+           "edges": sum(v["mat_he"] + v["gathered"] for v in (v1, v2)),
            "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
            "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
            "sigma_r2": res["sigma_r2"], "seeds": seeds}
@@ -148,6 +152,21 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed"):
     r2.close()
     g.close()
     return out
+
+
+def reduce_over_ranks(torch, dist, times, units, device):
+    """Whole-job figures of a multi-rank run: each timed duration is the slowest rank's (max over
+    ranks), each unit count the sum over ranks. Returns the reduced times followed by the sums."""
+    tmax = torch.tensor(times, dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tot = torch.tensor(units, dtype=torch.float64, device=device)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return [float(x) for x in tmax.tolist()] + [float(x) for x in tot.tolist()]
+
+
+def rank_seed(base, rank):
+    """Each rank's query seed: the ranks run independent queries (distinct Philox keys)."""
+    return base + 1000 * rank
 
 
 def bench_gpu(args):
@@ -175,7 +194,7 @@ def bench_gpu(args):
     p_off = torch.as_tensor(off).pin_memory()
     p_mem = torch.as_tensor(mem).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    seed = w.query.seed + 1000 * rank
+    seed = rank_seed(w.query.seed, rank)
 
     def sync_all():
         torch.cuda.synchronize()
@@ -215,13 +234,8 @@ def bench_gpu(args):
     rr_local = sum(s["rr_sets"] for s in stats)
     t_local = sum(times)
     e2e_local = sum(e2e_times)
-    vals = torch.tensor([t_local, e2e_local, float(rr_local)], dtype=torch.float64, device="cuda")
     if world > 1:
-        tmax = vals[:2].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tot = vals[2:].clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        t_all, e2e_all, rr_all = float(tmax[0]), float(tmax[1]), float(tot[0])
+        t_all, e2e_all, rr_all = reduce_over_ranks(torch, dist, [t_local, e2e_local], [float(rr_local)], "cuda")
     else:
         t_all, e2e_all, rr_all = t_local, e2e_local, float(rr_local)
     if rank != 0:
@@ -259,6 +273,9 @@ def bench_gpu(args):
                    "parallelism": f"replicas x{world} (independent queries)",
                    "l2": "flushed between steps (256 MiB write), inputs resident in HBM"},
         "seed_selection_seconds": sum(s["select_seconds"] for s in stats) / args.steps,
+        # incidence entries the RR generator read (hyperedge ids of materialising pops plus the
+        # member ids gathered), per second of the timed region (this rank)
+        "edge_traversals_per_s": sum(s["edges"] for s in stats) / t_local,
         "rr_sampling_seconds": sum(s["sample_seconds"] for s in stats) / args.steps,
         "wall_seconds_timed_region": t_wall,
         "e2e": {"value": rr_all / e2e_all, "unit": UNIT,
@@ -274,6 +291,8 @@ def bench_gpu(args):
     }
     if args.forward_sims > 0:
         line["forward_mc"] = forward_check(H, torch, w, d_off, d_mem, stats[-1], args.forward_sims)
+    if not args.no_plain_form:
+        line["plain_form"] = plain_form(H, torch, w, d_off, d_mem, seed, flush, stream, line["value"])
     if w.query.theta is None and not args.no_prefix_query:
         line["brr_prefix_upper"] = prefix_query(H, torch, w, d_off, d_mem, seed, flush, stream)
     if world == 1 and not args.no_cpu_baseline:
@@ -281,6 +300,30 @@ def bench_gpu(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def plain_form(H, torch, w, off, mem, seed, flush, stream, value, steps=2):
+    """Outside the timed region: the same query with RR generation in the plain form (one launch
+    per batch of as many sets as blocks fit, one set per block, instead of the persistent grid
+    with its device work counter); the RR sets, seeds and theta are identical."""
+    run_query(H, torch, w, off, mem, seed, schedule="plain")
+    times, stats = [], []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(run_query(H, torch, w, off, mem, seed, schedule="plain"))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    rr = sum(s["rr_sets"] for s in stats)
+    plain = rr / sum(times)
+    return {"value": plain, "unit": UNIT, "ms_per_query": 1e3 * sum(times) / steps,
+            "rr_kernel_seconds_per_query": sum(s["rr_kernel_seconds"] for s in stats) / steps,
+            "rr_kernel_launches_per_query": sum(s["rr_launches"] for s in stats) / steps,
+            "seed_selection_seconds": sum(s["select_seconds"] for s in stats) / steps,
+            "persistent_over_plain": value / plain}
 
 
 def prefix_query(H, torch, w, off, mem, seed, flush, stream, steps=3):
@@ -368,11 +411,59 @@ def oracle_rate(w, off, mem, seconds, seed, tag=0):
     return pool.count(), el
 
 
+def oracle_rate_threads(w, off, mem, seconds, seed, threads, tag=0):
+    """The oracle driven by `threads` host threads over disjoint RR ids of one pool (each thread
+    with its own oracle graph; the ctypes calls release the GIL). The (stratum, j) ids of a
+    stratified allocation are interleaved in proportion to the strata, so any prefix of the work
+    list has the pool's mix. Returns (sets done, wall seconds)."""
+    import threading
+    import oracle
+    q = w.query
+    graphs = [oracle.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold) for _ in range(threads)]
+    n_s = graphs[0].allocate(q.roots, 1 << 16)
+    work = sorted(((j + 0.5) / int(c), s, j) for s, c in enumerate(n_s) if c for j in range(int(c)))
+    lock = threading.Lock()
+    state = {"next": 0, "done": 0}
+    t0 = time.perf_counter()
+
+    def run(g):
+        while time.perf_counter() - t0 < seconds:
+            with lock:
+                i = state["next"]
+                state["next"] += 1
+            if i >= len(work):
+                return
+            _, s, j = work[i]
+            g.rr_set(seed, tag, q.roots, s, j, strategy=q.strategy)
+            with lock:
+                state["done"] += 1
+
+    ts = [threading.Thread(target=run, args=(g,)) for g in graphs]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return state["done"], time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(w, off, mem, seconds):
-    count, el = oracle_rate(w, off, mem, seconds, w.query.seed)
-    return {"value": count / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {count} RR sets of pool tag 0 ({w.query.roots} roots) on the same "
-                      f"graph, {el:.1f} s of single-threaded oracle work; graph build excluded"}
+    """The oracle on the host: every core (the baseline) and one core (beside it)."""
+    cores = host_cores()
+    count, el = oracle_rate_threads(w, off, mem, seconds, w.query.seed, cores)
+    c1, e1 = oracle_rate(w, off, mem, seconds, w.query.seed)
+    return {"value": count / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} RR sets of one pool (tag 0, {w.query.roots} roots, ids interleaved "
+                      f"across strata) on the same graph, {el:.1f} s of oracle work on {cores} "
+                      "threads, one oracle graph per thread; graph build excluded",
+            "single_core": {"value": c1 / e1, "cores": 1,
+                            "sample": f"first {c1} RR sets of pool tag 0, {e1:.1f} s on one thread"}}
 
 
 def bench_reference(args):
@@ -383,11 +474,12 @@ def bench_reference(args):
     w = workload(args.workload)
     off, mem = make_hypergraph(w.graph)
     per_step = args.reference_seconds
+    cores = host_cores()
     for i in range(args.warmup):
-        oracle_rate(w, off, mem, per_step / 4, w.query.seed + 7 + i, tag=3)
+        oracle_rate_threads(w, off, mem, min(per_step / 4, 2.0), w.query.seed + 7 + i, cores, tag=3)
     counts, times = [], []
     for i in range(args.steps):
-        c, el = oracle_rate(w, off, mem, per_step, w.query.seed + 100 + i)
+        c, el = oracle_rate_threads(w, off, mem, per_step, w.query.seed + 100 + i, cores)
         counts.append(c)
         times.append(el)
     value = sum(counts) / sum(times)
@@ -398,10 +490,11 @@ def bench_reference(args):
         "data": "synthetic",
         "config": {"workload": w.name, "description": w.description, "n": w.graph.n, "m": w.graph.m,
                    "k": w.query.k, "eps": w.query.eps, "roots": w.query.roots},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps of ~{per_step:.0f} s each: RR sets of "
-                                   f"fresh pools ({w.query.roots} roots) on the same graph, "
-                                   "graph build excluded"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of ~{per_step:.0f} s each: "
+                                   f"RR sets of one pool per step ({w.query.roots} roots, a new "
+                                   f"seed each step) on the same graph, {cores} threads with one "
+                                   "oracle graph each, graph build excluded"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -419,6 +512,8 @@ def main():
                     help="forward Monte-Carlo simulations of the last query's seeds (0: skip)")
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain-form", action="store_true",
+                    help="skip the plain-schedule comparison query (outside the timed region)")
     ap.add_argument("--no-prefix-query", action="store_true",
                     help="skip the extra measurement of BRR with the Eq. upper_2 bound")
     ap.add_argument("--profile-batch", type=int, default=0,

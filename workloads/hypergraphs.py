@@ -34,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "HypergraphSpec", "QuerySpec", "Workload", "make_hypergraph", "WORKLOADS", "workload",
-    "batch_workload", "serving_workload", "uniform01",
+    "batch_workload", "serving_workload", "serving_queries", "ServingQuery", "uniform01",
 ]
 
 _TWO_M53 = 2.0 ** -53
@@ -254,3 +254,27 @@ def serving_workload(count: int = 16, seed: int = 1):
                                   zipf_alpha=2.0, membership="preferential",
                                   seed=seed * 2000 + g))
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class ServingQuery:
+    arrival: float              # seconds from the start of the stream
+    graph: int                  # index into serving_workload()
+    k: int
+    eps: float
+
+
+def serving_queries(count: int = 2000, rate: float = 200.0, graphs: int = 16, seed: int = 1):
+    """A Poisson stream of IM queries over the resident graphs: exponential inter-arrival times
+    of mean 1/rate (inversion of seeded uniforms), graph uniform over `graphs`, k uniform in
+    [10, 200], eps uniform over {0.05, 0.1, 0.2}."""
+    st = _Stream(seed, 0x5F)
+    u = st.uniform(4 * count)
+    out, t = [], 0.0
+    for i in range(count):
+        t += -math.log1p(-float(u[4 * i])) / rate
+        out.append(ServingQuery(arrival=t, graph=min(int(u[4 * i + 1] * graphs), graphs - 1),
+                                k=10 + min(int(u[4 * i + 2] * 191), 190),
+                                eps=(0.05, 0.1, 0.2)[min(int(u[4 * i + 3] * 3), 2)]))
+    return out
+
