@@ -104,6 +104,25 @@ typedef struct {
 } hyperim_load_args;
 
 hyperim_status hyperim_load(const hyperim_load_args* args, hyperim_graph_t* out);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_graph_share -- a second handle on a loaded graph, for calls from another host thread
+ *   on another stream at the same time (a query server, one worker per handle). It reads g's
+ *   incidence store, layer profile and chunk index (never copied) and owns its own stream
+ *   (cuda_stream, may be NULL), RR-kernel scratch, device status word and counters. Handles of
+ *   one graph share its HBM budget, its seed and its RR schedule at the time of sharing, and
+ *   any of them may grow or read the pools created on any other: a pool is grown under an
+ *   exclusive lock and read (greedy, coverage, views, copies) under a shared one, so concurrent
+ *   calls see whole growth steps. The result of a call does not depend on other calls running
+ *   beside it (RR sets are keyed by (stratum, index); BRR rounds read the prefix of a pool that
+ *   their theta names). g may itself be a share; every share is freed with hyperim_graph_free.
+ *   EINVAL: g or out NULL. ESTATE: g already freed. ENOMEM: budget or allocation.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim_graph_t* out);
+
+/* hyperim_graph_free -- releases a handle. The loaded graph's device data stays until it and all
+ * of its shares are freed. Pools must be freed before the loaded graph (pools of a graph may be
+ * freed while shares remain). Synchronises the handle's stream. NULL is ignored. */
 void hyperim_graph_free(hyperim_graph_t g);
 
 /* ------------------------------------------------------------------------------------------
@@ -281,7 +300,10 @@ typedef struct {
 typedef struct {
     int32_t rounds;                          /* BRR rounds run (1 in FIXED mode) */
     uint64_t theta;                          /* target theta of the last round */
-    uint64_t pool_r1, pool_r2;               /* RR sets in r1 / r2 when the selection ended */
+    uint64_t pool_r1, pool_r2;               /* RR sets of r1 / r2 the last round used: all of
+                                                the pool in FIXED mode; in BRR the sets (s, j)
+                                                with j < n_s(theta) (a pool another query grew
+                                                further holds more) */
     uint64_t lambda_r1[HYPERIM_NSTRATA];     /* coverage of S_k in r1 per stratum */
     uint64_t lambda_r2[HYPERIM_NSTRATA];     /* coverage of S_k in r2 per stratum */
     double sigma_r1, sigma_r2;               /* Eq. 1 estimates on r1 and r2 */
@@ -349,6 +371,71 @@ hyperim_status hyperim_coverage_noalloc(int32_t n, const int64_t* rr_off, const 
                                         const uint8_t* rr_stratum, int64_t count,
                                         const int32_t* seeds, int32_t k,
                                         unsigned long long* lambda_s, void* cuda_stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Query server -- influence-maximisation queries (HyperIM_BRR, Alg. 4, stratified roots) on
+ *   graphs resident in HBM, served with continuous batching: `workers` host threads each run one
+ *   query at a time on their own CUDA stream and their own share of each graph
+ *   (hyperim_graph_share), so the kernels of up to `workers` queries overlap on the GPU; a worker
+ *   that finishes takes the next queued query at once. Queries on one graph use one R1/R2 pool
+ *   pair (tags 0 and 1), grown by whichever query needs more sets first; every query reads the
+ *   prefix its own theta names, so its seeds, theta and estimates equal those of the same query
+ *   run alone (hyperim_select_seeds on fresh pools).
+ *   Admission by HBM budget: before a query starts, if the device bytes held by the server's
+ *   graphs exceed hbm_budget_bytes (0 = no limit), the pools of graphs with no running query are
+ *   released (least recently used first; they are regrown on demand, with the same sets); if the
+ *   total is still above the budget the query waits until a running one finishes (it starts
+ *   anyway when nothing runs). Latency = submit to completion (host steady clock).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct hyperim_server* hyperim_server_t;
+
+typedef struct {
+    int32_t workers;              /* 1..64 */
+    size_t hbm_budget_bytes;      /* 0 = no admission limit */
+} hyperim_server_args;
+
+typedef struct {
+    int32_t graph_id;             /* from hyperim_server_add_graph */
+    int32_t k;                    /* 1 <= k <= n */
+    double eps, ell;              /* as in hyperim_select_opts (BRR) */
+    int32_t upper_mode;           /* hyperim_upper_mode */
+} hyperim_query;
+
+typedef struct {
+    hyperim_status status;        /* the query's own status (OK or the error it met) */
+    int32_t k;
+    hyperim_select_result result; /* as hyperim_select_seeds fills it */
+    double queued_seconds;        /* submit to start */
+    double run_seconds;           /* start to completion */
+    double latency_seconds;       /* submit to completion */
+    int32_t worker;
+} hyperim_query_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, evictions;
+    double p50_latency_seconds, p99_latency_seconds, mean_latency_seconds, max_latency_seconds;
+    double span_seconds;          /* first submit to last completion */
+    double queries_per_second;    /* completed / span_seconds */
+    uint64_t rr_sets_generated;   /* RR sets the server's pools generated (evicted pools included) */
+    size_t device_bytes;          /* held by the server's graphs now */
+    int32_t max_running;          /* most queries that ran at once */
+} hyperim_server_stats_t;
+
+/* EINVAL: args NULL or workers outside [1, 64]. Workers start at once. */
+hyperim_status hyperim_server_create(const hyperim_server_args* args, hyperim_server_t* out);
+/* Registers a loaded graph (not a share); it must outlive the server. *graph_id: 0, 1, ... */
+hyperim_status hyperim_server_add_graph(hyperim_server_t s, hyperim_graph_t g, int32_t* graph_id);
+/* Queues a query; returns at once. EINVAL: unknown graph_id, k outside [1, n], eps outside
+ * (0, 1), ell <= 0, unknown upper_mode. */
+hyperim_status hyperim_server_submit(hyperim_server_t s, const hyperim_query* q, uint64_t* ticket);
+/* Blocks until the ticket's query is done; seeds_host (k entries, may be NULL) receives S_k.
+ * Each ticket is waited for once. EINVAL: unknown or already collected ticket. The call
+ * returns OK when the result was collected; the query's own status is out->status. */
+hyperim_status hyperim_server_wait(hyperim_server_t s, uint64_t ticket, int32_t* seeds_host,
+                                   hyperim_query_result* out);
+hyperim_status hyperim_server_stats(hyperim_server_t s, hyperim_server_stats_t* out);
+/* Finishes the running queries, drops the queued ones, frees the pools and shares. */
+void hyperim_server_free(hyperim_server_t s);
 
 /* Number of CUDA kernels this library has launched in this process (all threads, all graphs). */
 uint64_t hyperim_kernel_launches(void);

@@ -85,6 +85,30 @@ class SelectResult(C.Structure):
                 ("seconds_sample", C.c_double), ("seconds_select", C.c_double)]
 
 
+class ServerArgs(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_size_t)]
+
+
+class Query(C.Structure):
+    _fields_ = [("graph_id", C.c_int32), ("k", C.c_int32), ("eps", C.c_double), ("ell", C.c_double),
+                ("upper_mode", C.c_int32)]
+
+
+class QueryResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("k", C.c_int32), ("result", SelectResult),
+                ("queued_seconds", C.c_double), ("run_seconds", C.c_double),
+                ("latency_seconds", C.c_double), ("worker", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("evictions", C.c_uint64), ("p50_latency_seconds", C.c_double),
+                ("p99_latency_seconds", C.c_double), ("mean_latency_seconds", C.c_double),
+                ("max_latency_seconds", C.c_double), ("span_seconds", C.c_double),
+                ("queries_per_second", C.c_double), ("rr_sets_generated", C.c_uint64),
+                ("device_bytes", C.c_size_t), ("max_running", C.c_int32)]
+
+
 _lib = None
 _vp = C.c_void_p
 _SIGNATURES = {
@@ -93,6 +117,13 @@ _SIGNATURES = {
     "hyperim_graph_stats": (C.c_int, [_vp, C.POINTER(GraphStats)]),
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hyperim_graph_set_schedule": (C.c_int, [_vp, C.c_int32]),
+    "hyperim_graph_share": (C.c_int, [_vp, _vp, C.POINTER(_vp)]),
+    "hyperim_server_create": (C.c_int, [C.POINTER(ServerArgs), C.POINTER(_vp)]),
+    "hyperim_server_add_graph": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
+    "hyperim_server_submit": (C.c_int, [_vp, C.POINTER(Query), C.POINTER(C.c_uint64)]),
+    "hyperim_server_wait": (C.c_int, [_vp, C.c_uint64, _vp, C.POINTER(QueryResult)]),
+    "hyperim_server_stats": (C.c_int, [_vp, C.POINTER(ServerStats)]),
+    "hyperim_server_free": (None, [_vp]),
     "hyperim_graph_chunk_index": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _vp, C.c_int64,
                                             C.POINTER(C.c_int64)]),
     "hyperim_forward_spread": (C.c_int, [_vp, _vp, C.c_int32, C.c_uint64, C.c_uint64, _vp,
@@ -209,12 +240,16 @@ def hyperim_select_seeds(h, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap
     seeds = np.zeros(int(k), dtype=np.int32)
     res = SelectResult()
     _check(lib().hyperim_select_seeds(h, r1, r2, int(k), C.byref(opts), _ptr(seeds), C.byref(res)))
+    return seeds, _select_result(res)
+
+
+def _select_result(res):
     out = {f: getattr(res, f) for f, _ in SelectResult._fields_
            if f not in ("lambda_r1", "lambda_r2", "alpha_round")}
     out["lambda_r1"] = np.array(res.lambda_r1, dtype=np.uint64)
     out["lambda_r2"] = np.array(res.lambda_r2, dtype=np.uint64)
     out["alpha_round"] = list(res.alpha_round)[: res.rounds]
-    return seeds, out
+    return out
 
 
 def hyperim_spread(h, seeds, pool):
@@ -285,6 +320,17 @@ class Graph:
         _check(lib().hyperim_graph_chunk_index(self._h, int(v), C.byref(bits), _ptr(tab), entries.value,
                                                C.byref(entries)))
         return bits.value, tab.reshape(-1, 1 << bits.value)
+
+    def share(self, stream=None):
+        """A second handle on this graph (hyperim_graph_share): same device data and pools, its own
+        stream (a cudaStream_t as int; default: the current torch stream) and scratch, for use
+        from another host thread at the same time."""
+        h = C.c_void_p()
+        _check(lib().hyperim_graph_share(self._h, stream if stream is not None else current_stream(),
+                                         C.byref(h)))
+        g = Graph.__new__(Graph)
+        g.n, g.model, g._h, g.parent = self.n, self.model, h, self
+        return g
 
     def set_schedule(self, schedule):
         """RR generation schedule: "persistent" (default) or "plain" (one launch per batch of one
@@ -367,3 +413,57 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Query server over resident graphs (hyperim_server_*): continuous batching of BRR queries
+    on `workers` host threads, each with its own CUDA stream; admission by HBM budget."""
+
+    def __init__(self, workers=4, hbm_budget_bytes=0):
+        self._h = C.c_void_p()
+        _check(lib().hyperim_server_create(C.byref(ServerArgs(int(workers), int(hbm_budget_bytes))),
+                                           C.byref(self._h)))
+        self.graphs = []
+        self._k = {}
+
+    def add_graph(self, graph):
+        gid = C.c_int32()
+        _check(lib().hyperim_server_add_graph(self._h, graph.handle, C.byref(gid)))
+        self.graphs.append(graph)
+        return gid.value
+
+    def submit(self, graph_id, k, eps=0.1, ell=1.0, upper="closed"):
+        t = C.c_uint64()
+        _check(lib().hyperim_server_submit(self._h, C.byref(Query(int(graph_id), int(k), float(eps), float(ell),
+                                                                  UPPER_MODES[upper])), C.byref(t)))
+        self._k[t.value] = int(k)
+        return t.value
+
+    def wait(self, ticket):
+        """(seeds, result dict with status, latency_seconds, ...) of a submitted query."""
+        seeds = np.zeros(self._k.pop(ticket, 1), np.int32)
+        r = QueryResult()
+        _check(lib().hyperim_server_wait(self._h, C.c_uint64(ticket), _ptr(seeds), C.byref(r)))
+        out = _select_result(r.result)
+        out.update(status=r.status, queued_seconds=r.queued_seconds, run_seconds=r.run_seconds,
+                   latency_seconds=r.latency_seconds, worker=r.worker)
+        if r.status != 0:
+            out["message"] = lib().hyperim_last_error().decode(errors="replace")
+        return seeds[:r.k], out
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().hyperim_server_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hyperim_server_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

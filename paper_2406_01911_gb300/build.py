@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhyperim.so")
-SOURCES = ["capi.cu", "load.cu", "rr.cu", "greedy.cu", "scan.cu", "noalloc.cu", "index.cu"]
+SOURCES = ["capi.cu", "load.cu", "rr.cu", "greedy.cu", "scan.cu", "noalloc.cu", "index.cu", "server.cu"]
 HEADERS = ["device_math.cuh", "mat.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

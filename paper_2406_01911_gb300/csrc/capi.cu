@@ -32,18 +32,21 @@ hyperim_status cuda_fail(cudaError_t e, const char* what) {
 hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (g->budget && g->device_bytes + bytes > g->budget)
-        return set_error(HYPERIM_ENOMEM, "device memory budget exceeded (" +
-                                             std::to_string(g->device_bytes + bytes) + " > " +
-                                             std::to_string(g->budget) + " bytes)");
+    hyperim_graph* r = graph_root(g);  // one budget for all handles of a graph
+    const size_t before = r->device_bytes.fetch_add(bytes);
+    if (r->budget && before + bytes > r->budget) {
+        r->device_bytes.fetch_sub(bytes);
+        return set_error(HYPERIM_ENOMEM, "device memory budget exceeded (" + std::to_string(before + bytes) +
+                                             " > " + std::to_string(r->budget) + " bytes)");
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, g->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
+        r->device_bytes.fetch_sub(bytes);
         return set_error(HYPERIM_ENOMEM, std::string("cudaMallocAsync(") + std::to_string(bytes) +
                                              "): " + cudaGetErrorString(e));
     }
-    g->device_bytes += bytes;
     return HYPERIM_OK;
 }
 
@@ -51,7 +54,12 @@ void dev_free(hyperim_graph* g, void* p, size_t bytes) {
     if (!p) return;
     if (bytes == 0) bytes = 16;
     cudaFreeAsync(p, g->stream);
-    g->device_bytes -= std::min(bytes, g->device_bytes);
+    graph_root(g)->device_bytes.fetch_sub(bytes);
+}
+
+std::mutex& graph_mutex() {
+    static std::mutex m;
+    return m;
 }
 
 hyperim_status check_device_status(hyperim_graph* g, const char* where) {
@@ -240,16 +248,124 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
     return HYPERIM_OK;
 }
 
+namespace {
+// frees what one handle owns: its status word, counters and RR-kernel scratch, and, for the
+// loaded graph, the graph data itself when `data` is set
+void free_handle(hyperim_graph* g, bool data) {
+    cudaStreamSynchronize(g->stream);
+    const Scratch& S = g->scratch;
+    dev_free(g, g->d_status, sizeof(DevStatus));
+    dev_free(g, g->d_counters, 2 * sizeof(RRCounters));
+    dev_free(g, S.list, sizeof(int32_t) * S.list_cap * S.blocks);
+    dev_free(g, S.bitmap, sizeof(uint32_t) * S.bitmap_words * S.blocks);
+    dev_free(g, S.picks, sizeof(uint32_t) * S.pick_cap * S.blocks);
+    dev_free(g, S.big, sizeof(uint32_t) * S.big_cap * S.blocks);
+    dev_free(g, S.arena, sizeof(int32_t) * S.arena_cap);
+    if (data) {
+        void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off,
+                        g->prof, g->cdf_tab, g->deg, g->stratum, g->vs_off, g->vs_list, g->idx, g->idx_tab};
+        for (void* p : ptrs)
+            if (p) cudaFreeAsync(p, g->stream);
+    }
+    cudaStreamSynchronize(g->stream);
+}
+}  // namespace
+
 void hyperim_graph_free(hyperim_graph_t g) {
     if (!g) return;
-    cudaStreamSynchronize(g->stream);
-    void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off, g->prof, g->cdf_tab, g->deg,
-                    g->stratum, g->vs_off, g->vs_list, g->idx, g->idx_tab, g->d_status, g->d_counters, g->scratch.list,
-                    g->scratch.bitmap, g->scratch.big, g->scratch.picks, g->scratch.arena};
-    for (void* p : ptrs)
-        if (p) cudaFreeAsync(p, g->stream);
-    cudaStreamSynchronize(g->stream);
+    if (g->owner) {
+        hyperim_graph* r = g->owner;
+        free_handle(g, false);
+        delete g;
+        bool last = false;
+        {
+            std::lock_guard<std::mutex> lk(graph_mutex());
+            last = --r->shares == 0 && r->freed;
+        }
+        if (last) {
+            free_handle(r, true);
+            delete r;
+        }
+        return;
+    }
+    bool keep = false;
+    {
+        std::lock_guard<std::mutex> lk(graph_mutex());
+        g->freed = true;
+        keep = g->shares > 0;
+    }
+    if (keep) return;  // the last share releases it
+    free_handle(g, true);
     delete g;
+}
+
+hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim_graph_t* out) {
+    if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    *out = nullptr;
+    hyperim_graph* r = graph_root(g);
+    hyperim_graph* h = new (std::nothrow) hyperim_graph();
+    if (!h) return set_error(HYPERIM_ENOMEM, "host allocation failed");
+    {
+        std::lock_guard<std::mutex> lk(graph_mutex());
+        if (r->freed) {
+            delete h;
+            return set_error(HYPERIM_ESTATE, "graph already freed");
+        }
+        ++r->shares;
+    }
+    h->owner = r;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->n = r->n;
+    h->m = r->m;
+    h->nnz = r->nnz;
+    h->model = r->model;
+    h->uniform_thr = r->uniform_thr;
+    h->seed = r->seed;
+    h->id_bits = r->id_bits;
+    h->he_off = r->he_off;
+    h->he_mem = r->he_mem;
+    h->v_off = r->v_off;
+    h->v_he = r->v_he;
+    h->tsum = r->tsum;
+    h->v_span = r->v_span;
+    h->vinfo = r->vinfo;
+    h->prof_off = r->prof_off;
+    h->prof = r->prof;
+    h->cdf_tab = r->cdf_tab;
+    h->table_entries = r->table_entries;
+    h->deg = r->deg;
+    h->stratum = r->stratum;
+    h->vs_off = r->vs_off;
+    h->vs_list = r->vs_list;
+    h->idx = r->idx;
+    h->idx_tab = r->idx_tab;
+    h->idx_entries = r->idx_entries;
+    h->idx_vertices = r->idx_vertices;
+    h->profile_entries = r->profile_entries;
+    h->max_layers = r->max_layers;
+    h->max_dh = r->max_dh;
+    h->max_deg = r->max_deg;
+    h->max_tsum = r->max_tsum;
+    h->max_layer_n = r->max_layer_n;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) h->stratum_size[s] = r->stratum_size[s];
+    h->theta_lstar = r->theta_lstar;
+    h->sm_count = r->sm_count;
+    h->schedule = r->schedule;
+    hyperim_status st = dev_alloc(h, (void**)&h->d_status, sizeof(DevStatus));
+    if (st == HYPERIM_OK) st = dev_alloc(h, (void**)&h->d_counters, 2 * sizeof(RRCounters));
+    if (st == HYPERIM_OK) {
+        cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "share status word");
+    }
+    if (st != HYPERIM_OK) {
+        std::string keep = g_last_error;
+        hyperim_graph_free(h);
+        g_last_error = keep;
+        return st;
+    }
+    *out = h;
+    return HYPERIM_OK;
 }
 
 hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out) {
@@ -263,7 +379,7 @@ hyperim_status hyperim_graph_stats(hyperim_graph_t g, hyperim_graph_stats_t* out
     out->max_deg = g->max_deg;
     for (int s = 0; s < HYPERIM_NSTRATA; ++s) out->stratum_size[s] = g->stratum_size[s];
     out->theta_lstar = g->theta_lstar;
-    out->device_bytes = g->device_bytes;
+    out->device_bytes = graph_root(g)->device_bytes.load();
     out->index_vertices = g->idx_vertices;
     out->index_entries = g->idx_entries;
     return HYPERIM_OK;
@@ -369,7 +485,7 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
         return set_error(HYPERIM_EINVAL, "unknown strategy");
     hyperim_pool* p = new (std::nothrow) hyperim_pool();
     if (!p) return set_error(HYPERIM_ENOMEM, "host allocation failed");
-    p->g = g;
+    p->g = graph_root(g);
     p->tag = tag;
     p->root_mode = root_mode;
     p->strategy = strategy;
@@ -381,10 +497,17 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
 static hyperim_status pool_grow_pair(hyperim_graph* g, hyperim_pool* r1, hyperim_pool* r2, uint64_t theta) {
     uint64_t ns[2][HYPERIM_NSTRATA];
     hyperim_pool* pools[2] = {r1, r2};
+    // growth is exclusive; the two locks are taken in address order
+    std::unique_lock<std::shared_mutex> la(r1 < r2 ? r1->mu : r2->mu), lb(r1 < r2 ? r2->mu : r1->mu);
+    bool need = false;
     for (int q = 0; q < 2; ++q) {
         allocate_strata(g, pools[q]->root_mode, theta, ns[q]);
-        for (int s = 0; s < HYPERIM_NSTRATA; ++s) ns[q][s] = std::max(ns[q][s], pools[q]->n_s[s]);
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+            need = need || ns[q][s] > pools[q]->n_s[s];
+            ns[q][s] = std::max(ns[q][s], pools[q]->n_s[s]);
+        }
     }
+    if (!need) return HYPERIM_OK;  // an earlier query grew both pools past theta
     return sample_rr_multi(g, pools, 2, ns);
 }
 
@@ -405,11 +528,14 @@ hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t 
         created = true;
     } else {
         hyperim_pool* p = *inout;
-        if (p->g != g) return set_error(HYPERIM_ESTATE, "pool belongs to another graph");
+        if (graph_root(p->g) != graph_root(g)) return set_error(HYPERIM_ESTATE, "pool belongs to another graph");
         if (p->tag != pool_tag || p->root_mode != root_mode || p->strategy != strategy)
             return set_error(HYPERIM_ESTATE, "pool was created with other tag/root mode/strategy");
     }
-    st = pool_grow(g, *inout, theta);
+    {
+        std::unique_lock<std::shared_mutex> lk((*inout)->mu);
+        st = pool_grow(g, *inout, theta);
+    }
     if (st != HYPERIM_OK && created) {
         std::string keep = g_last_error;
         hyperim_pool_free(*inout);
@@ -432,6 +558,7 @@ void hyperim_pool_free(hyperim_pool_t p) {
 
 hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
     if (!p || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    std::shared_lock<std::shared_mutex> lk(p->mu);
     out->count = p->count;
     out->total = p->total;
     out->rr_off = p->rr_off;
@@ -459,6 +586,7 @@ hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
 hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_mem, uint8_t* rr_stratum,
                                  uint32_t* rr_j) {
     if (!p) return set_error(HYPERIM_EINVAL, "null pool");
+    std::shared_lock<std::shared_mutex> lk(p->mu);
     cudaStream_t s = p->g->stream;
     const size_t N = (size_t)p->count, T = (size_t)p->total;
     if (rr_off) {
@@ -477,7 +605,8 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
                                     hyperim_select_result* out) {
     if (!g || !r1 || !opts || !seeds_host || !out) return set_error(HYPERIM_EINVAL, "null argument");
     if (k < 1 || k > g->n) return set_error(HYPERIM_EINVAL, "need 1 <= k <= n");
-    if (r1->g != g || (r2 && r2->g != g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    if (graph_root(r1->g) != graph_root(g) || (r2 && graph_root(r2->g) != graph_root(g)))
+        return set_error(HYPERIM_ESTATE, "pool of another graph");
     if (r1 == r2) return set_error(HYPERIM_ESTATE, "r1 and r2 must be distinct pools");
     if (opts->upper_mode != HYPERIM_UPPER_CLOSED && opts->upper_mode != HYPERIM_UPPER_PREFIX)
         return set_error(HYPERIM_EINVAL, "unknown upper bound mode");
@@ -489,10 +618,14 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     uint64_t pu[2] = {0, 0};
     if (opts->mode == HYPERIM_SELECT_FIXED) {
         auto t0 = clk::now();
-        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr))) return st;
+        {
+            std::shared_lock<std::shared_mutex> lk(r1->mu);
+            if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr))) return st;
+        }
         out->sigma_r1 = estimate(g, r1->root_mode, r1->n_s, out->lambda_r1);
         if (prefix) out->upper = prefix_upper_sigma(pu, r1->root_mode, g->n, (uint64_t)r1->count);
         if (r2) {
+            std::shared_lock<std::shared_mutex> lk(r2->mu);
             if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
             out->sigma_r2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
         }
@@ -515,17 +648,32 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         const uint64_t theta = plan.theta0 << i;
         if (opts->theta_cap && theta > opts->theta_cap)
             return set_error(HYPERIM_EOVERFLOW, "theta_i = " + std::to_string(theta) + " exceeds theta_cap");
+        // round i works on the sets a pool grown to theta_i holds (a prefix by (s, j) of pools
+        // that an earlier query grew further, so the result does not depend on that history)
+        uint64_t v1[HYPERIM_NSTRATA], v2[HYPERIM_NSTRATA];
+        allocate_strata(g, r1->root_mode, theta, v1);
+        allocate_strata(g, r2->root_mode, theta, v2);
         auto t0 = clk::now();
         if ((st = pool_grow_pair(g, r1, r2, theta))) return st;
         auto t1 = clk::now();
-        if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr))) return st;
-        if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2))) return st;
+        {
+            std::shared_lock<std::shared_mutex> lk(r1->mu);
+            if ((st = greedy(g, r1, k, seeds_host, out->lambda_r1, prefix ? pu : nullptr, v1))) return st;
+        }
+        {
+            std::shared_lock<std::shared_mutex> lk(r2->mu);
+            if ((st = coverage(g, r2, seeds_host, k, out->lambda_r2, v2))) return st;
+        }
         auto t2 = clk::now();
         t_sample += std::chrono::duration<double>(t1 - t0).count();
         t_select += std::chrono::duration<double>(t2 - t1).count();
-        const uint64_t N1 = (uint64_t)r1->count, N2 = (uint64_t)r2->count;
-        const double s1 = estimate(g, r1->root_mode, r1->n_s, out->lambda_r1);
-        const double s2 = estimate(g, r2->root_mode, r2->n_s, out->lambda_r2);
+        uint64_t N1 = 0, N2 = 0;
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+            N1 += v1[s];
+            N2 += v2[s];
+        }
+        const double s1 = estimate(g, r1->root_mode, v1, out->lambda_r1);
+        const double s2 = estimate(g, r2->root_mode, v2, out->lambda_r2);
         const double lam1 = s1 * (double)N1 / (double)g->n;
         const double lam2 = s2 * (double)N2 / (double)g->n;
         const double up = prefix ? prefix_upper_sigma(pu, r1->root_mode, g->n, N1) : upper_bound(lam1, k, g->n, N1);
@@ -551,11 +699,12 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
 hyperim_status hyperim_spread(hyperim_graph_t g, const int32_t* seeds_host, int32_t k, hyperim_pool_t pool,
                               double* sigma_hat, double* std_err) {
     if (!g || !pool || (k > 0 && !seeds_host)) return set_error(HYPERIM_EINVAL, "null argument");
-    if (pool->g != g) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    if (graph_root(pool->g) != graph_root(g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
     if (k < 0) return set_error(HYPERIM_EINVAL, "k must be >= 0");
     for (int32_t i = 0; i < k; ++i)
         if (seeds_host[i] < 0 || seeds_host[i] >= g->n) return set_error(HYPERIM_EINVAL, "seed outside [0, n)");
     uint64_t lam[HYPERIM_NSTRATA];
+    std::shared_lock<std::shared_mutex> lk(pool->mu);
     hyperim_status st = coverage(g, pool, seeds_host, k, lam);
     if (st) return st;
     const double sigma = estimate(g, pool->root_mode, pool->n_s, lam);

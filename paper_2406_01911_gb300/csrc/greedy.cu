@@ -20,6 +20,29 @@ struct Weights {
     unsigned long long w[HYPERIM_NSTRATA];
 };
 
+// A prefix view of a pool: only the RR sets (stratum s, index j) with j < lim[s] take part (the
+// sets a pool grown to a smaller theta would hold). on = 0: every set of the pool.
+struct Limits {
+    uint32_t lim[HYPERIM_NSTRATA];
+    int on;
+    __device__ __forceinline__ bool skip(const uint8_t* rr_stratum, const uint32_t* rr_j, int64_t r) const {
+        return on && rr_j[r] >= lim[rr_stratum[r]];
+    }
+};
+
+// occurrences of each vertex over the RR sets of a prefix view; one warp per RR set
+__global__ void k_count_occ_view(const int64_t* __restrict__ rr_off, const int32_t* __restrict__ mem,
+                                 const uint8_t* __restrict__ rr_stratum, const uint32_t* __restrict__ rr_j,
+                                 int64_t N, Limits L, uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < N; r += nwarps) {
+        if (L.skip(rr_stratum, rr_j, r)) continue;
+        for (int64_t x = rr_off[r] + lane; x < rr_off[r + 1]; x += 32) atomicAdd(&cnt[mem[x]], 1u);
+    }
+}
+
 __global__ void k_count_occ(const int32_t* __restrict__ mem, int64_t total, uint32_t* __restrict__ cnt) {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x)
@@ -28,14 +51,15 @@ __global__ void k_count_occ(const int32_t* __restrict__ mem, int64_t total, uint
 
 // inverted index (vertex -> RR ids) and initial weighted scores; one warp per RR set
 __global__ void k_scatter_inv(const int64_t* __restrict__ rr_off, const int32_t* __restrict__ mem,
-                              const uint8_t* __restrict__ rr_stratum, int64_t N,
-                              const int64_t* __restrict__ inv_off, uint32_t* __restrict__ cur,
-                              uint32_t* __restrict__ inv, unsigned long long* __restrict__ score,
-                              Weights W) {
+                              const uint8_t* __restrict__ rr_stratum, const uint32_t* __restrict__ rr_j,
+                              int64_t N, Limits L, const int64_t* __restrict__ inv_off,
+                              uint32_t* __restrict__ cur, uint32_t* __restrict__ inv,
+                              unsigned long long* __restrict__ score, Weights W) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < N; r += nwarps) {
+        if (L.skip(rr_stratum, rr_j, r)) continue;
         const int64_t b = rr_off[r], e = rr_off[r + 1];
         const unsigned long long w = W.w[rr_stratum[r]];
         for (int64_t x = b + lane; x < e; x += 32) {
@@ -265,12 +289,14 @@ __global__ void k_retire(const int32_t* __restrict__ best, const int64_t* __rest
 
 // coverage of a seed set: RR sets with at least one member in S, per stratum; one warp per set
 __global__ void k_coverage(const int64_t* __restrict__ rr_off, const int32_t* __restrict__ mem,
-                           const uint8_t* __restrict__ rr_stratum, int64_t N,
-                           const uint8_t* __restrict__ in_s, unsigned long long* __restrict__ lam) {
+                           const uint8_t* __restrict__ rr_stratum, const uint32_t* __restrict__ rr_j,
+                           int64_t N, Limits L, const uint8_t* __restrict__ in_s,
+                           unsigned long long* __restrict__ lam) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < N; r += nwarps) {
+        if (L.skip(rr_stratum, rr_j, r)) continue;
         const int64_t b = rr_off[r], e = rr_off[r + 1];
         bool hit = false;
         for (int64_t base = b; base < e; base += 32) {
@@ -295,16 +321,31 @@ int grid_cap(int64_t items, int threads, int sm, int per_sm) {
 
 }  // namespace
 
+namespace {
+// the view of p that lim names (nullptr: the whole pool); lim[s] <= p->n_s[s]
+Limits make_limits(const hyperim_pool* p, const uint64_t* lim, uint64_t view_ns[HYPERIM_NSTRATA]) {
+    Limits L{};
+    for (int i = 0; i < HYPERIM_NSTRATA; ++i) {
+        view_ns[i] = lim ? std::min<uint64_t>(lim[i], p->n_s[i]) : p->n_s[i];
+        L.lim[i] = (uint32_t)std::min<uint64_t>(view_ns[i], 0xFFFFFFFFull);
+        if (view_ns[i] < p->n_s[i]) L.on = 1;
+    }
+    return L;
+}
+}  // namespace
+
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
-                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper) {
+                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper, const uint64_t* lim) {
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
     const int64_t N = p->count, T = p->total;
     const int sm = g->sm_count;
     if (N >= (int64_t)0xFFFFFFFFll) return set_error(HYPERIM_EOVERFLOW, "more than 2^32 - 1 RR sets");
+    uint64_t view_ns[HYPERIM_NSTRATA];
+    const Limits L = make_limits(p, lim, view_ns);
     Weights W;
     for (int i = 0; i < HYPERIM_NSTRATA; ++i)
-        W.w[i] = stratum_weight(g, p->root_mode, p->n_s[i], i);
+        W.w[i] = stratum_weight(g, p->root_mode, view_ns[i], i);
     hyperim_status st;
     uint32_t *cnt = nullptr, *inv = nullptr, *covered = nullptr, *bid = nullptr, *ticket = nullptr;
     int64_t* inv_off = nullptr;
@@ -356,12 +397,16 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
     HYP_CUDA(cudaMemsetAsync(covered, 0, bytes_cov, s));
     HYP_CUDA(cudaMemsetAsync(lam, 0, sizeof(unsigned long long) * HYPERIM_NSTRATA, s));
     HYP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(uint32_t) * 2, s));
-    if (T > 0) { k_count_occ<<<grid_cap(T, 256, sm, 32), 256, 0, s>>>(p->rr_mem, T, cnt); count_launch(); }
+    if (T > 0 && !L.on) { k_count_occ<<<grid_cap(T, 256, sm, 32), 256, 0, s>>>(p->rr_mem, T, cnt); count_launch(); }
+    if (T > 0 && L.on)
+        { k_count_occ_view<<<grid_cap(N * 32, 256, sm, 32), 256, 0, s>>>(p->rr_off, p->rr_mem, p->rr_stratum,
+                                                                        p->rr_j, N, L, cnt); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, cnt, inv_off, n))) return st;
     HYP_CUDA(cudaMemsetAsync(cnt, 0, bytes_cnt, s));
     if (N > 0)
         { k_scatter_inv<<<grid_cap(N * 32, 256, sm, 32), 256, 0, s>>>(p->rr_off, p->rr_mem, p->rr_stratum,
-                                                                    N, inv_off, cnt, inv, score, W); count_launch(); }
+                                                                    p->rr_j, N, L, inv_off, cnt, inv, score,
+                                                                    W); count_launch(); }
     const int rblocks = sm * 8;
     for (int32_t round = 0; round < k; ++round) {
         if (prefix_upper) topk_round();
@@ -402,9 +447,11 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
 }
 
 hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_host, int32_t k,
-                        uint64_t lambda_s[HYPERIM_NSTRATA]) {
+                        uint64_t lambda_s[HYPERIM_NSTRATA], const uint64_t* lim) {
     cudaStream_t s = g->stream;
     const int64_t N = p->count;
+    uint64_t view_ns[HYPERIM_NSTRATA];
+    const Limits L = make_limits(p, lim, view_ns);
     hyperim_status st;
     uint8_t* in_s = nullptr;
     unsigned long long* lam = nullptr;
@@ -421,7 +468,8 @@ hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_
     }
     if (N > 0)
         { k_coverage<<<grid_cap(N * 32, 256, g->sm_count, 32), 256, 0, s>>>(p->rr_off, p->rr_mem,
-                                                                          p->rr_stratum, N, in_s, lam); count_launch(); }
+                                                                          p->rr_stratum, p->rr_j, N, L, in_s,
+                                                                          lam); count_launch(); }
     HYP_CUDA(cudaGetLastError());
     unsigned long long hl[HYPERIM_NSTRATA];
     HYP_CUDA(cudaMemcpyAsync(hl, lam, sizeof(hl), cudaMemcpyDeviceToHost, s));

@@ -2,7 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <vector>
 
@@ -96,7 +99,7 @@ struct hyperim_graph {
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     size_t budget = 0;
-    size_t device_bytes = 0;
+    std::atomic<size_t> device_bytes{0};  // on the loaded graph: all handles of it together
     int id_bits = 1;             // ceil(log2 n)
     // incidence store
     int32_t* he_off = nullptr;   // m + 1
@@ -132,6 +135,11 @@ struct hyperim_graph {
     hyperim::Scratch scratch;
     int sm_count = 0;
     int32_t schedule = 0;        // hyperim_schedule of RR generation
+    // handles made by hyperim_graph_share point at the loaded graph, whose device data they read;
+    // it is released once it has been freed and no share is left
+    hyperim_graph* owner = nullptr;
+    int shares = 0;              // on the loaded graph, under hyperim::graph_mutex()
+    bool freed = false;
 };
 
 struct hyperim_pool {
@@ -149,9 +157,17 @@ struct hyperim_pool {
     uint64_t rr_launches = 0;
     double rr_kernel_seconds = 0.0;
     double mean_size_hint = 0.0;
+    // growth takes it exclusively, readers (greedy, coverage, views) shared: handles of one graph
+    // may use a pool from several host threads
+    std::shared_mutex mu;
 };
 
 namespace hyperim {
+
+// the loaded graph behind a handle (itself, or the graph a share was made from)
+inline hyperim_graph* graph_root(hyperim_graph* g) { return g->owner ? g->owner : g; }
+inline const hyperim_graph* graph_root(const hyperim_graph* g) { return g->owner ? g->owner : g; }
+std::mutex& graph_mutex();
 
 // launch accounting (capi.cu): every kernel launch of the library goes through count_launch()
 void count_launch(uint64_t k = 1);
@@ -192,10 +208,12 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
                               uint64_t seed, uint32_t* counts_host);
 
 // greedy.cu
+// lim (optional): a prefix view, only the RR sets (s, j) with j < lim[s] take part
 hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* seeds_host,
-                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper = nullptr);
+                      uint64_t lambda_s[HYPERIM_NSTRATA], uint64_t* prefix_upper = nullptr,
+                      const uint64_t* lim = nullptr);
 hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_host, int32_t k,
-                        uint64_t lambda_s[HYPERIM_NSTRATA]);
+                        uint64_t lambda_s[HYPERIM_NSTRATA], const uint64_t* lim = nullptr);
 
 // host arithmetic (plan.cpp)
 void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,

@@ -1370,6 +1370,21 @@ hyperim_status grow_array(hyperim_graph* g, T** arr, size_t used, size_t* cap, s
     return HYPERIM_OK;
 }
 
+// The dynamic shared memory limit of a kernel is one value per function, not per launch: it is
+// raised once to the most any launch can ask for (an on-chip visited bitmap of kVisSmemBits), so
+// that launches from several host threads with different sizes never race on it.
+hyperim_status allow_rr_smem() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        const int most = (int)(sizeof(Shared) + kVisSmemBits / 8);
+        err = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    });
+    HYP_CUDA(err);
+    return HYPERIM_OK;
+}
+
 hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
     Scratch& S = g->scratch;
     const size_t list_cap = (size_t)g->n;
@@ -1432,13 +1447,13 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     hyperim_status st;
 
     // the visited bitmap goes on chip only while two blocks still fit on an SM
+    if ((st = allow_rr_smem())) return st;
     bool vis_smem = (int64_t)g->n <= kVisSmemBits;
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
         const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
         smem = sizeof(Shared) + vis_bytes;
-        HYP_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr, kThreads, smem));
         if (per_sm >= 2 || !vis_smem) break;
         vis_smem = false;
@@ -1615,13 +1630,13 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     if (nsims == 0) return HYPERIM_OK;
     cudaStream_t s = g->stream;
     hyperim_status st;
+    if ((st = allow_rr_smem())) return st;
     bool vis_smem = (int64_t)g->n <= kVisSmemBits;
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
         const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
         smem = sizeof(Shared) + vis_bytes;
-        HYP_CUDA(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kThreads, smem));
         if (per_sm >= 2 || !vis_smem) break;
         vis_smem = false;
