@@ -500,6 +500,145 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _sequential(H, torch, loaded, queries, schedule):
+    """Each query alone on fresh pools, one after the other (wall seconds, results)."""
+    out = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for gi, k, eps in queries:
+        g = loaded[gi]
+        g.set_schedule(schedule)
+        r1, r2 = g.pool(tag=0, roots="stratified"), g.pool(tag=1, roots="stratified")
+        seeds, res = g.select_seeds(r1, r2, k, mode="brr", eps=eps, ell=1.0)
+        out.append((time.perf_counter() - t0, seeds, res, r1.view()["count"] + r2.view()["count"]))
+        r1.close()
+        r2.close()
+    torch.cuda.synchronize()
+    for g in loaded:
+        g.set_schedule("persistent")
+    return time.perf_counter() - t0, out
+
+
+def _served(H, torch, loaded, queries, workers, budget, arrivals=None):
+    """The same queries through the server (continuous batching, shared pools); submitted all at
+    once, or at their arrival times (seconds from the start) when given."""
+    srv = H.Server(workers=workers, hbm_budget_bytes=budget)
+    ids = [srv.add_graph(g) for g in loaded]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (gi, k, eps) in enumerate(queries):
+        if arrivals is not None:
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+        tickets.append(srv.submit(ids[gi], k, eps))
+    res = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return wall, res, st
+
+
+def _same_seeds(a, b):
+    return all(x.tolist() == y.tolist() for x, y in zip(a, b))
+
+
+def bench_batched(args):
+    """The batched configuration: 64 hypergraphs of uneven size (n log-uniform in [1e3, 2e5],
+    Zipf(2.1) sizes in [2, 300]), each queried with k in {10, 50, 100} at eps = 0.1 (weighted
+    cascade, stratified roots), resident in HBM. Three forms, same GPU, same queries, identical
+    seeds: the plain form (one query at a time, fresh pools, RR sets one launch per batch of one
+    set per block), one query at a time with the persistent RR kernel, and the server (all 192
+    queries submitted at once to `--workers` workers; queries on one graph share its pools)."""
+    import torch
+    import paper_2406_01911_gb300 as H
+    from workloads import batch_workload
+    specs = batch_workload()
+    loaded = []
+    for sp in specs:
+        off, mem = make_hypergraph(sp)
+        loaded.append(H.Graph(sp.n, torch.as_tensor(off).cuda(), torch.as_tensor(mem).cuda(), "wc", 0, seed=1))
+    queries = [(gi, k, 0.1) for gi in range(len(specs)) for k in (10, 50, 100)]
+    _sequential(H, torch, loaded, queries[:6], "persistent")  # warm-up
+    t_plain, plain = _sequential(H, torch, loaded, queries, "plain")
+    t_seq, seq = _sequential(H, torch, loaded, queries, "persistent")
+    t_srv, srv, st = _served(H, torch, loaded, queries, args.workers, int(args.budget_gb * 2**30))
+    same = _same_seeds([x[1] for x in plain], [x[1] for x in seq]) and \
+        _same_seeds([x[1] for x in seq], [x[0] for x in srv])
+    sets_fresh = sum(x[3] for x in seq)
+    line = {"metric": "batched IM queries per second (64 graphs x k in {10, 50, 100}, eps = 0.1)",
+            "value": len(queries) / t_srv, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True,
+            "config": {"workload": "batched-64-graphs", "graphs": len(specs), "queries": len(queries),
+                       "workers": args.workers, "model": "wc", "roots": "stratified"},
+            "served": {"wall_seconds": t_srv, "queries_per_s": len(queries) / t_srv,
+                       "rr_sets_generated": st["rr_sets_generated"],
+                       "rr_sets_per_s": st["rr_sets_generated"] / t_srv,
+                       "p50_latency_seconds": st["p50_latency_seconds"],
+                       "p99_latency_seconds": st["p99_latency_seconds"], "max_running": st["max_running"]},
+            "sequential_persistent": {"wall_seconds": t_seq, "queries_per_s": len(queries) / t_seq,
+                                      "rr_sets": sets_fresh, "rr_sets_per_s": sets_fresh / t_seq},
+            "plain_form": {"wall_seconds": t_plain, "queries_per_s": len(queries) / t_plain,
+                           "rr_sets_per_s": sets_fresh / t_plain},
+            "served_over_plain": t_plain / t_srv, "served_over_sequential": t_seq / t_srv,
+            "identical_seeds": same, "failed": st["failed"]}
+    print(json.dumps(line), flush=True)
+    for g in loaded:
+        g.close()
+
+
+def bench_served(args):
+    """The served configuration: 16 resident hypergraphs (n log-uniform in [1e5, 5e6],
+    m = min(0.6 n, 3e6), Zipf(2.0) sizes in [2, 500]) and a Poisson stream of queries (mean 200
+    per second; k uniform in [10, 200]; eps in {0.05, 0.1, 0.2}); the first `--queries` of the
+    stream are submitted at their arrival times. Latency is submit to completion. The plain form
+    (one query at a time on fresh pools, RR sets one launch per batch) runs the first
+    `--plain-queries` of them; its latencies follow from its measured durations under the same
+    arrivals with one query in service at a time (FIFO)."""
+    import torch
+    import paper_2406_01911_gb300 as H
+    from workloads import serving_queries, serving_workload
+    specs = serving_workload()
+    loaded = []
+    t_load = time.perf_counter()
+    for sp in specs:
+        off, mem = make_hypergraph(sp)
+        loaded.append(H.Graph(sp.n, torch.as_tensor(off).cuda(), torch.as_tensor(mem).cuda(), "wc", 0, seed=1))
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t_load
+    stream = serving_queries()[:args.queries]
+    queries = [(q.graph, q.k, q.eps) for q in stream]
+    arrivals = [q.arrival for q in stream]
+    t_srv, srv, st = _served(H, torch, loaded, queries, args.workers, int(args.budget_gb * 2**30), arrivals)
+    npl = min(args.plain_queries, len(queries))
+    t_plain, plain = _sequential(H, torch, loaded, queries[:npl], "plain")
+    done, prev, lat = 0.0, 0.0, []
+    for i, (t_end, *_rest) in enumerate(plain):
+        dur = t_end - prev
+        prev = t_end
+        done = max(done, arrivals[i]) + dur
+        lat.append(done - arrivals[i])
+    lat.sort()
+    pct = lambda q: lat[max(0, min(len(lat), math.ceil(q * len(lat))) - 1)]
+    same = _same_seeds([x[1] for x in plain], [x[0] for x in srv[:npl]])
+    line = {"metric": "served IM queries: throughput and p50/p99 latency", "value": st["queries_per_second"],
+            "unit": "queries/s", "n_gpus": 1, "higher_is_better": True,
+            "config": {"workload": "served-16-graphs-poisson-200qps", "graphs": len(specs),
+                       "queries": len(queries), "workers": args.workers,
+                       "hbm_budget_gb": args.budget_gb, "load_seconds": t_load},
+            "served": {"queries_per_s": st["queries_per_second"], "p50_latency_seconds": st["p50_latency_seconds"],
+                       "p99_latency_seconds": st["p99_latency_seconds"], "mean_latency_seconds": st["mean_latency_seconds"],
+                       "span_seconds": st["span_seconds"], "rr_sets_generated": st["rr_sets_generated"],
+                       "evictions": st["evictions"], "max_running": st["max_running"], "failed": st["failed"],
+                       "device_gb": st["device_bytes"] / 2**30},
+            "plain_form": {"queries": npl, "busy_seconds": t_plain, "queries_per_s": npl / t_plain,
+                           "p50_latency_seconds": pct(0.5), "p99_latency_seconds": pct(0.99)},
+            "identical_seeds": same}
+    print(json.dumps(line), flush=True)
+    for g in loaded:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,11 +657,23 @@ def main():
                     help="skip the extra measurement of BRR with the Eq. upper_2 bound")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling aid: one RR-kernel launch growing a fresh pool by this theta")
+    ap.add_argument("--batched", action="store_true",
+                    help="the 64-graph batched configuration (its own JSON line) instead of the bench")
+    ap.add_argument("--served", action="store_true",
+                    help="the 16-graph served configuration (its own JSON line) instead of the bench")
+    ap.add_argument("--workers", type=int, default=8, help="server workers (--batched, --served)")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="server HBM budget, GiB (0: none)")
+    ap.add_argument("--queries", type=int, default=200, help="queries of the stream (--served)")
+    ap.add_argument("--plain-queries", type=int, default=24, help="of them run in the plain form (--served)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.profile_batch:
         profile_batch(args)
+    elif args.batched and args.impl == "ours":
+        bench_batched(args)
+    elif args.served and args.impl == "ours":
+        bench_served(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

@@ -381,6 +381,8 @@ hyperim_status hyperim_coverage_noalloc(int32_t n, const int64_t* rr_off, const 
  *   pair (tags 0 and 1), grown by whichever query needs more sets first; every query reads the
  *   prefix its own theta names, so its seeds, theta and estimates equal those of the same query
  *   run alone (hyperim_select_seeds on fresh pools).
+ *   A worker keeps one share at a time (the RR kernel's scratch of a share holds a queue of n
+ *   entries per resident block), replacing it when its next query is on another graph.
  *   Admission by HBM budget: before a query starts, if the device bytes held by the server's
  *   graphs exceed hbm_budget_bytes (0 = no limit), the pools of graphs with no running query are
  *   released (least recently used first; they are regrown on demand, with the same sets); if the

@@ -56,7 +56,7 @@ struct hyperim_server {
     size_t budget = 0;
     int device = 0;
     std::vector<cudaStream_t> streams;
-    std::vector<std::map<int32_t, hyperim_graph*>> shares;  // [worker]: graph id -> its share
+    std::vector<std::map<int32_t, hyperim_graph*>> shares;  // [worker]: graph id -> its share (one at a time)
     std::deque<ServerGraph> graphs;                         // stable addresses
     std::mutex mu;
     std::condition_variable cv_job, cv_done, cv_slot;
@@ -143,13 +143,18 @@ void hyperim_server::worker_main(int w) {
             if (st == HYPERIM_OK && !sg->r2)
                 st = hyperim_sample_rr(sg->g, 1, 0, HYPERIM_ROOTS_STRATIFIED, HYPERIM_STRAT_PAPER, &sg->r2);
         }
+        // the worker's share of the graph; a worker keeps one share at a time, since the RR
+        // kernel's scratch of a share grows with the graph (a queue of n entries per resident block)
         hyperim_graph* h = nullptr;
         if (st == HYPERIM_OK) {
-            auto it = shares[(size_t)w].find(job.q.graph_id);
-            if (it != shares[(size_t)w].end()) {
+            auto& mine = shares[(size_t)w];
+            auto it = mine.find(job.q.graph_id);
+            if (it != mine.end()) {
                 h = it->second;
-            } else if ((st = hyperim_graph_share(sg->g, streams[(size_t)w], &h)) == HYPERIM_OK) {
-                shares[(size_t)w][job.q.graph_id] = h;
+            } else {
+                for (auto& kv : mine) hyperim_graph_free(kv.second);
+                mine.clear();
+                if ((st = hyperim_graph_share(sg->g, streams[(size_t)w], &h)) == HYPERIM_OK) mine[job.q.graph_id] = h;
             }
         }
         if (st == HYPERIM_OK) {
