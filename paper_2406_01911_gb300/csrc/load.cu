@@ -23,6 +23,8 @@ constexpr int kBucketsMax = 4096;
 constexpr int kProfWarpT = 1024;  // vertices with at most this many positions: warp profile
 constexpr int kPWWarps = 4;
 constexpr int kPWThreads = kPWWarps * 32;
+constexpr int kProfMidT = 2048;  // vertices with at most this many positions: warp profile, listed
+constexpr int kPMWarps = 2;
 
 __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
@@ -190,26 +192,30 @@ __device__ void emit_layers(const uint32_t* hist, int dh, int32_t mu, int32_t e0
     }
 }
 
-// Layer profile, small vertices: one warp per vertex whose hyperedges hold at most kProfWarpT
-// positions (mu's own included), and every vertex with d_H <= 1. The members are gathered once
-// into a raw copy and counted into buckets of their top id bits, scattered into id order and
-// sorted per bucket (the RR kernel's warp sort), then the runs give the multiplicity histogram.
-__global__ void __launch_bounds__(kPWThreads)
-k_profile_warp(int32_t n, const int32_t* __restrict__ v_off, const int2* __restrict__ v_span,
-               const int32_t* __restrict__ he_mem, const int32_t* __restrict__ tsum, int id_bits,
-               uint2* __restrict__ pairs, uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
+// Layer profile, small vertices: one warp per vertex whose hyperedges hold at most Cap
+// positions (mu's own included), and every vertex with d_H <= 1 (list == nullptr: all vertices;
+// else the listed ones, all with d_H >= 2 and more than the smaller cap's positions). The
+// members are gathered once into a raw copy and counted into buckets of their top id bits,
+// scattered into id order and sorted per bucket (the RR kernel's warp sort), then the runs give
+// the multiplicity histogram.
+template <int Cap, int W>
+__global__ void __launch_bounds__(W * 32)
+k_profile_warp(int32_t n, const int32_t* __restrict__ list, const int32_t* __restrict__ v_off,
+               const int2* __restrict__ v_span, const int32_t* __restrict__ he_mem,
+               const int32_t* __restrict__ tsum, int id_bits, uint2* __restrict__ pairs,
+               uint32_t* __restrict__ nlayers, uint32_t* __restrict__ deg,
                unsigned long long* __restrict__ maxima) {
-    __shared__ uint32_t raw_s[kPWWarps][kProfWarpT + 4];
-    __shared__ uint32_t buf_s[kPWWarps][kProfWarpT];
-    __shared__ int bkt_s[kPWWarps][256];
-    __shared__ int pre_s[kPWWarps][2 * 32 + 1];
+    __shared__ uint32_t raw_s[W][Cap + 4];
+    __shared__ uint32_t buf_s[W][Cap];
+    __shared__ int bkt_s[W][256];
+    __shared__ int pre_s[W][2 * 32 + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* raw = raw_s[wid];
     uint32_t* buf = buf_s[wid];
     int* bkt = bkt_s[wid];
-    const int64_t nw = (int64_t)gridDim.x * kPWWarps;
-    for (int64_t v = (int64_t)blockIdx.x * kPWWarps + wid; v < n; v += nw) {
-        const int32_t mu = (int32_t)v;
+    const int64_t nw = (int64_t)gridDim.x * W;
+    for (int64_t v = (int64_t)blockIdx.x * W + wid; v < n; v += nw) {
+        const int32_t mu = list ? list[v] : (int32_t)v;
         const int32_t e0 = v_off[mu], dh = v_off[mu + 1] - e0;
         if (dh == 0) {
             if (lane == 0) { nlayers[mu] = 0; deg[mu] = 0; }
@@ -230,7 +236,7 @@ k_profile_warp(int32_t n, const int32_t* __restrict__ v_off, const int2* __restr
             continue;
         }
         const int ts = tsum[mu];
-        if (ts > kProfWarpT) continue;  // the block kernel's vertex
+        if (ts > Cap) continue;  // a vertex of a larger kernel
         const int T = ts - dh;
         const int nbits = bucket_bits(T, 8);
         const int nb = 1 << nbits;
@@ -258,12 +264,13 @@ k_profile_warp(int32_t n, const int32_t* __restrict__ v_off, const int2* __restr
     }
 }
 
-// Vertices for the block profile kernel: d_H >= 2 and more than kProfWarpT positions.
+// Vertices with d_H >= 2 and lo < positions <= hi (the mid-size warp kernel's, then the block
+// kernel's with hi = INT_MAX).
 __global__ void k_big_flags(int32_t n, const int32_t* __restrict__ v_off, const int32_t* __restrict__ tsum,
-                            uint32_t* __restrict__ flag) {
+                            int32_t lo, int32_t hi, uint32_t* __restrict__ flag) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        flag[v] = (v_off[v + 1] - v_off[v] >= 2 && tsum[v] > kProfWarpT) ? 1u : 0u;
+        flag[v] = (v_off[v + 1] - v_off[v] >= 2 && tsum[v] > lo && tsum[v] <= hi) ? 1u : 0u;
 }
 
 __global__ void k_big_list(int32_t n, const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos,
@@ -623,8 +630,8 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = dev_alloc(g, (void**)&g->v_span, sizeof(int2) * nnz_a))) return st;
     if (nnz > 0)
         { k_build_spans<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->v_span); count_launch(); }
-    { k_profile_warp<<<grid_for((int64_t)n * 32, kPWThreads, sm), kPWThreads, 0, s>>>(
-        n, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg, d_max); count_launch(); }
+    { k_profile_warp<kProfWarpT, kPWWarps><<<grid_for((int64_t)n * 32, kPWThreads, sm), kPWThreads, 0, s>>>(
+        n, nullptr, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg, d_max); count_launch(); }
     const size_t prof_smem = sizeof(uint32_t) * (kProfBuf + kProfHist) +
                              sizeof(int) * (2 * kBucketsMax + 2 * kProfThreads + 1 + 32);
     HYP_CUDA(cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -648,7 +655,24 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     int32_t* d_blist = nullptr;
     if ((st = dev_alloc(g, (void**)&d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)))) return st;
     if ((st = dev_alloc(g, (void**)&d_bpos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
-    if (n > 0) { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, d_bflag); count_launch(); }
+    // mid-size vertices (kProfWarpT < positions <= kProfMidT): one warp each, listed
+    if (n > 0 && g->max_tsum > kProfWarpT) {
+        { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, kProfWarpT, kProfMidT, d_bflag); count_launch(); }
+        if ((st = exclusive_scan_u32_to_i64(g, d_bflag, d_bpos, n))) return st;
+        int64_t nmid = 0;
+        HYP_CUDA(cudaMemcpyAsync(&nmid, d_bpos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HYP_CUDA(cudaStreamSynchronize(s));
+        if (nmid > 0) {
+            int32_t* d_mlist = nullptr;
+            if ((st = dev_alloc(g, (void**)&d_mlist, sizeof(int32_t) * (size_t)nmid))) return st;
+            { k_big_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_bflag, d_bpos, d_mlist); count_launch(); }
+            { k_profile_warp<kProfMidT, kPMWarps><<<grid_for(nmid * 32, kPMWarps * 32, sm), kPMWarps * 32, 0, s>>>(
+                (int32_t)nmid, d_mlist, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg,
+                d_max); count_launch(); }
+            dev_free(g, d_mlist, sizeof(int32_t) * (size_t)nmid);
+        }
+    }
+    if (n > 0) { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, kProfMidT, 0x7FFFFFFF, d_bflag); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_bflag, d_bpos, n))) return st;
     int64_t nbig = 0;
     HYP_CUDA(cudaMemcpyAsync(&nbig, d_bpos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
