@@ -120,9 +120,9 @@ hyperim_status hyperim_load(const hyperim_load_args* args, hyperim_graph_t* out)
  * ------------------------------------------------------------------------------------------ */
 hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim_graph_t* out);
 
-/* hyperim_graph_free -- releases a handle. The loaded graph's device data stays until it and all
- * of its shares are freed. Pools must be freed before the loaded graph (pools of a graph may be
- * freed while shares remain). Synchronises the handle's stream. NULL is ignored. */
+/* hyperim_graph_free -- releases a handle. The loaded graph's device data stays until it, all of
+ * its shares and all of its pools are freed (in any order). Synchronises the handle's stream.
+ * NULL is ignored. Creating a share or a pool on a graph already freed: ESTATE. */
 void hyperim_graph_free(hyperim_graph_t g);
 
 /* ------------------------------------------------------------------------------------------

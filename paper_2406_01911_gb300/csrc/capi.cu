@@ -269,6 +269,20 @@ void free_handle(hyperim_graph* g, bool data) {
     }
     cudaStreamSynchronize(g->stream);
 }
+
+// drops one reference (a share or a pool) on a loaded graph; the last one after the graph's own
+// hyperim_graph_free releases it
+void release_root(hyperim_graph* r) {
+    bool last = false;
+    {
+        std::lock_guard<std::mutex> lk(graph_mutex());
+        last = --r->shares == 0 && r->freed;
+    }
+    if (last) {
+        free_handle(r, true);
+        delete r;
+    }
+}
 }  // namespace
 
 void hyperim_graph_free(hyperim_graph_t g) {
@@ -277,15 +291,7 @@ void hyperim_graph_free(hyperim_graph_t g) {
         hyperim_graph* r = g->owner;
         free_handle(g, false);
         delete g;
-        bool last = false;
-        {
-            std::lock_guard<std::mutex> lk(graph_mutex());
-            last = --r->shares == 0 && r->freed;
-        }
-        if (last) {
-            free_handle(r, true);
-            delete r;
-        }
+        release_root(r);
         return;
     }
     bool keep = false;
@@ -486,6 +492,15 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
     hyperim_pool* p = new (std::nothrow) hyperim_pool();
     if (!p) return set_error(HYPERIM_ENOMEM, "host allocation failed");
     p->g = graph_root(g);
+    {
+        // a pool keeps the loaded graph alive like a share does
+        std::lock_guard<std::mutex> lk(graph_mutex());
+        if (p->g->freed) {
+            delete p;
+            return set_error(HYPERIM_ESTATE, "graph already freed");
+        }
+        ++p->g->shares;
+    }
     p->tag = tag;
     p->root_mode = root_mode;
     p->strategy = strategy;
@@ -554,6 +569,7 @@ void hyperim_pool_free(hyperim_pool_t p) {
     dev_free(g, p->rr_j, sizeof(uint32_t) * p->cap_j);
     cudaStreamSynchronize(g->stream);
     delete p;
+    release_root(g);
 }
 
 hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {

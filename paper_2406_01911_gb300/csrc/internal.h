@@ -138,7 +138,7 @@ struct hyperim_graph {
     // handles made by hyperim_graph_share point at the loaded graph, whose device data they read;
     // it is released once it has been freed and no share is left
     hyperim_graph* owner = nullptr;
-    int shares = 0;              // on the loaded graph, under hyperim::graph_mutex()
+    int shares = 0;              // live shares and pools of the loaded graph, under hyperim::graph_mutex()
     bool freed = false;
 };
 

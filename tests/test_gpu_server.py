@@ -147,3 +147,16 @@ def test_share_grows_the_same_pools(H, oracle):
     assert len(seeds_h2) == 5
     r.close()
     h.close()
+
+
+def test_pool_outlives_its_graph_handle(H, oracle):
+    # a pool keeps the loaded graph's data alive: freed graph handle first, pool still readable
+    spec, off, mem = _graphs(1)[0]
+    g = H.Graph(spec.n, off, mem, "wc", 0, seed=SEED)
+    p = g.pool(tag=0, roots="stratified").sample(200)
+    g.close()
+    op = oracle.Pool(oracle.Graph(spec.n, off, mem, "wc", 0), seed=SEED, tag=0, roots="stratified")
+    op.grow_theta(200)
+    from tests import gpu_cases as gc
+    gc.assert_same_pool(p, op)
+    p.close()
