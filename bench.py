@@ -141,7 +141,10 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", sc
     else:
         seeds, res = g.select_seeds(r1, r2, q.k, mode="brr", eps=q.eps, ell=q.ell, upper=upper)
     v1, v2 = r1.view(), r2.view()
-    out = {"rr_sets": v1["count"] + v2["count"], "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
+    # RR sets the query read (its last round's prefix of R1 and R2); sets generated ahead of a
+    # round and never read would not count (none on the benchmark workloads)
+    out = {"rr_sets": int(res["pool_r1"] + res["pool_r2"]), "rr_generated": v1["count"] + v2["count"],
+           "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
            "rr_launches": v1["rr_launches"] + v2["rr_launches"],
            "bytes": rr_algorithmic_bytes(v1) + rr_algorithmic_bytes(v2),
            "edges": sum(v["mat_he"] + v["gathered"] for v in (v1, v2)),
@@ -269,6 +272,7 @@ def bench_gpu(args):
                    "k": w.query.k, "eps": w.query.eps, "ell": w.query.ell, "roots": w.query.roots,
                    "theta": w.query.theta or "adaptive (HyperIM_BRR)",
                    "rr_sets_per_step": rr_local / args.steps,
+                   "rr_sets_generated_per_step": sum(x["rr_generated"] for x in stats) / args.steps,
                    "brr_rounds": stats[-1]["rounds"], "theta_final": stats[-1]["theta"],
                    "parallelism": f"replicas x{world} (independent queries)",
                    "l2": "flushed between steps (256 MiB write), inputs resident in HBM"},

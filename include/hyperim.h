@@ -116,13 +116,13 @@ hyperim_status hyperim_load(const hyperim_load_args* args, hyperim_graph_t* out)
  *   calls see whole growth steps. The result of a call does not depend on other calls running
  *   beside it (RR sets are keyed by (stratum, index); BRR rounds read the prefix of a pool that
  *   their theta names). g may itself be a share; every share is freed with hyperim_graph_free.
- *   EINVAL: g or out NULL. ESTATE: g already freed. ENOMEM: budget or allocation.
+ *   EINVAL: g or out NULL. ENOMEM: budget or allocation.
  * ------------------------------------------------------------------------------------------ */
 hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim_graph_t* out);
 
 /* hyperim_graph_free -- releases a handle. The loaded graph's device data stays until it, all of
  * its shares and all of its pools are freed (in any order). Synchronises the handle's stream.
- * NULL is ignored. Creating a share or a pool on a graph already freed: ESTATE. */
+ * NULL is ignored. A freed handle must not be used again (its shares and pools may). */
 void hyperim_graph_free(hyperim_graph_t g);
 
 /* ------------------------------------------------------------------------------------------

@@ -313,10 +313,6 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     if (!h) return set_error(HYPERIM_ENOMEM, "host allocation failed");
     {
         std::lock_guard<std::mutex> lk(graph_mutex());
-        if (r->freed) {
-            delete h;
-            return set_error(HYPERIM_ESTATE, "graph already freed");
-        }
         ++r->shares;
     }
     h->owner = r;
@@ -493,12 +489,8 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
     if (!p) return set_error(HYPERIM_ENOMEM, "host allocation failed");
     p->g = graph_root(g);
     {
-        // a pool keeps the loaded graph alive like a share does
+        // a pool keeps the loaded graph alive like a share does (g is a live handle of it)
         std::lock_guard<std::mutex> lk(graph_mutex());
-        if (p->g->freed) {
-            delete p;
-            return set_error(HYPERIM_ESTATE, "graph already freed");
-        }
         ++p->g->shares;
     }
     p->tag = tag;
@@ -659,6 +651,14 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     hyperim_theta_plan plan;
     if ((st = plan_theta(g->n, k, opts->eps, opts->ell, &plan))) return st;
     const double target = 1.0 - std::exp(-1.0) - opts->eps;
+    // Early rounds need few sets, and a launch of few sets lasts as long as its slowest set: the
+    // pools are grown to at least theta_early per pool (four sets per resident block of the RR
+    // kernel for R1 and R2 together) so that those rounds share one launch. Rounds read only
+    // their own prefix, so the result is the same; sets beyond the last round's theta are
+    // generated but unused when BRR stops before theta_early.
+    uint64_t theta_early = 4 * (uint64_t)std::max(g->sm_count, 1);
+    if (plan.i_max < 40) theta_early = std::min<uint64_t>(theta_early, plan.theta0 << plan.i_max);
+    if (opts->theta_cap) theta_early = std::min<uint64_t>(theta_early, opts->theta_cap);
     for (int32_t i = 0;; ++i) {
         if (i > 62) return set_error(HYPERIM_EOVERFLOW, "theta doubling overflow");
         const uint64_t theta = plan.theta0 << i;
@@ -670,7 +670,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         allocate_strata(g, r1->root_mode, theta, v1);
         allocate_strata(g, r2->root_mode, theta, v2);
         auto t0 = clk::now();
-        if ((st = pool_grow_pair(g, r1, r2, theta))) return st;
+        if ((st = pool_grow_pair(g, r1, r2, std::max(theta, theta_early)))) return st;
         auto t1 = clk::now();
         {
             std::shared_lock<std::shared_mutex> lk(r1->mu);
