@@ -26,7 +26,7 @@ _lib = None
 class Stats(C.Structure):
     _fields_ = [(name, C.c_uint64) for name in (
         "rr_sets", "pops", "layers_seen", "draws", "mats", "mat_he", "mat_members", "selected",
-        "members_out")]
+        "members_out", "bytes_rr")]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -108,6 +108,11 @@ def lib():
             "or_brr_upper": (C.c_int, [vp, C.c_uint64, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                        C.c_int, C.c_int, C.c_int, i32p, C.POINTER(BrrResult),
                                        C.POINTER(Stats)]),
+            "or_graph_worker": (C.c_int, [vp, C.POINTER(vp)]),
+            "or_pool_grow_mt": (C.c_int, [vp, u64p, C.POINTER(vp), C.c_int]),
+            "or_brr_upper_mt": (C.c_int, [vp, C.c_uint64, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                          C.c_int, C.c_int, C.c_int, i32p, C.POINTER(BrrResult),
+                                          C.POINTER(Stats), C.POINTER(vp), C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -260,12 +265,15 @@ class Pool:
             _lib.or_pool_free(h)
             self._h = None
 
-    def grow(self, n_s):
+    def grow(self, n_s, workers: Optional["Workers"] = None):
         ns = np.ascontiguousarray(n_s, dtype=np.uint64)
-        _check(lib().or_pool_grow(self._h, _p(ns, C.c_uint64)))
+        if workers is not None and len(workers.views) > 1:
+            _check(lib().or_pool_grow_mt(self._h, _p(ns, C.c_uint64), workers.array, len(workers.views)))
+        else:
+            _check(lib().or_pool_grow(self._h, _p(ns, C.c_uint64)))
 
-    def grow_theta(self, theta):
-        self.grow(self.graph.allocate(self.roots, theta))
+    def grow_theta(self, theta, workers: Optional["Workers"] = None):
+        self.grow(self.graph.allocate(self.roots, theta), workers)
 
     def count(self): return lib().or_pool_count(self._h)
     def total(self): return lib().or_pool_total(self._h)
@@ -341,12 +349,60 @@ def prefix_upper_sigma(u, roots, n, N):
     return lib().or_prefix_upper_sigma(u & ((1 << 64) - 1), u >> 64, ROOTS[roots], n, N)
 
 
-def brr(graph: Graph, seed, k, eps, ell=1.0, cap=0, roots="stratified", strategy="paper", upper="closed"):
+class Workers:
+    """Worker views of an oracle graph (one per thread) for the multi-threaded pool growth."""
+
+    def __init__(self, graph: Graph, threads: int):
+        self.graph = graph
+        self.views = []
+        for _ in range(max(int(threads), 1)):
+            h = C.c_void_p()
+            _check(lib().or_graph_worker(graph.handle, C.byref(h)))
+            self.views.append(h)
+        self.array = (C.c_void_p * len(self.views))(*[h.value for h in self.views])
+
+    def rr_set(self, t, seed, tag, roots, stratum, j, strategy="paper"):
+        """Graph.rr_set on worker view t (call it from one thread per view)."""
+        cap = self.graph.n
+        buf = np.zeros(cap, dtype=np.int32)
+        st = Stats()
+        c = lib().or_rr_set(self.views[t], seed, tag, ROOTS[roots], stratum, j, STRATEGIES[strategy],
+                            _p(buf, C.c_int32), cap, C.byref(st))
+        if c < 0:
+            raise OracleError(f"rr_set status {c}")
+        return buf[:c].copy()
+
+    def close(self):
+        for h in self.views:
+            lib().or_graph_free(h)
+        self.views = []
+
+    def __del__(self):
+        try:
+            if _lib is not None:
+                self.close()
+        except Exception:
+            pass
+
+
+def brr(graph: Graph, seed, k, eps, ell=1.0, cap=0, roots="stratified", strategy="paper", upper="closed",
+        threads=1):
+    """HyperIM_BRR (Alg. 4) by the oracle; threads > 1 grows the pools with that many threads
+    (same pools, same result)."""
     seeds = np.zeros(max(k, 1), dtype=np.int32)
     res = BrrResult()
     st = Stats()
-    _check(lib().or_brr_upper(graph.handle, seed, k, eps, ell, cap, ROOTS[roots], STRATEGIES[strategy],
-                              UPPER[upper], _p(seeds, C.c_int32), C.byref(res), C.byref(st)))
+    if threads > 1:
+        W = Workers(graph, threads)
+        try:
+            _check(lib().or_brr_upper_mt(graph.handle, seed, k, eps, ell, cap, ROOTS[roots],
+                                         STRATEGIES[strategy], UPPER[upper], _p(seeds, C.c_int32),
+                                         C.byref(res), C.byref(st), W.array, len(W.views)))
+        finally:
+            W.close()
+    else:
+        _check(lib().or_brr_upper(graph.handle, seed, k, eps, ell, cap, ROOTS[roots], STRATEGIES[strategy],
+                                  UPPER[upper], _p(seeds, C.c_int32), C.byref(res), C.byref(st)))
     out = {f: getattr(res, f) for f, _ in BrrResult._fields_
            if f not in ("alpha_round", "lambda_r1", "lambda_r2")}
     out["alpha_round"] = list(res.alpha_round)[:res.rounds]

@@ -21,7 +21,7 @@ def build(force: bool = False) -> str:
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter", SRC, "-o", tmp, "-lm"]
+           "-shared", "-pthread", "-Wall", "-Wextra", "-Wno-unused-parameter", SRC, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

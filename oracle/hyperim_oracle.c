@@ -25,6 +25,7 @@
 #include "hyperim_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -204,6 +205,7 @@ struct or_graph {
     int32_t* nb;       /* distinct neighbours */
     uint64_t* keys;
     int64_t nb_cap;
+    int worker;        /* 1: a worker view (or_graph_worker) that owns only its scratch */
 };
 
 static int cmp_i32(const void* a, const void* b) {
@@ -218,6 +220,26 @@ static int cmp_u64(const void* a, const void* b) {
 /* A(mu) (Sec. 3.1.1): the vertices sharing a hyperedge with mu, with w(mu,nu) the number of
  * shared hyperedges. Returns the distinct neighbours sorted by (w descending, id ascending) in
  * g->nb and their weights via g->cnt (caller must call nbhd_release). */
+/* bytes of the 32-byte sectors that the byte range [a, a + len) overlaps */
+static uint64_t sector_bytes(uint64_t a, uint64_t len) {
+    if (len == 0) return 0;
+    return 32u * ((a + len - 1) / 32u - a / 32u + 1u);
+}
+
+/* the cost-model bytes of one pop of mu (see or_stats.bytes_rr): its profile entries, and when
+ * it materialises A(mu), v_he(mu) and every hyperedge of mu (two offsets plus its members) */
+static uint64_t pop_bytes(const or_graph* g, int32_t mu, int materialises) {
+    uint64_t b = sector_bytes(12u * (uint64_t)g->prof_off[mu],
+                              12u * (uint64_t)(g->prof_off[mu + 1] - g->prof_off[mu]));
+    if (!materialises) return b;
+    b += sector_bytes(4u * (uint64_t)g->v_off[mu], 4u * (uint64_t)(g->v_off[mu + 1] - g->v_off[mu]));
+    for (int64_t x = g->v_off[mu]; x < g->v_off[mu + 1]; ++x) {
+        const int32_t he = g->v_he[x];
+        b += 8u + sector_bytes(4u * (uint64_t)g->he_off[he], 4u * (uint64_t)(g->he_off[he + 1] - g->he_off[he]));
+    }
+    return b;
+}
+
 static int64_t nbhd_build(or_graph* g, int32_t mu, uint64_t* mat_members) {
     int64_t k = 0;
     uint64_t reads = 0;
@@ -402,11 +424,36 @@ int or_graph_build(int32_t n, int32_t m, const int32_t* he_off, const int32_t* h
 
 void or_graph_free(or_graph* g) {
     if (!g) return;
+    if (g->worker) {
+        free(g->cnt); free(g->seen); free(g->nb); free(g->keys);
+        free(g);
+        return;
+    }
     free(g->he_off); free(g->he_mem); free(g->v_off); free(g->v_he); free(g->deg);
     free(g->nlayers); free(g->prof_off); free(g->lay_w); free(g->lay_n); free(g->lay_thr);
     free(g->stratum); free(g->all_v); free(g->cnt); free(g->seen); free(g->nb); free(g->keys);
     for (int s = 0; s < OR_NSTRATA; ++s) free(g->vs[s]);
     free(g);
+}
+
+/* A second view of g for another thread: the same (read-only) graph arrays, its own scratch.
+ * Freed with or_graph_free before g. */
+int or_graph_worker(const or_graph* g, or_graph** out) {
+    or_graph* w = (or_graph*)malloc(sizeof(or_graph));
+    if (!w) return OR_ENOMEM;
+    memcpy(w, g, sizeof(or_graph));
+    w->worker = 1;
+    w->cnt = (int32_t*)calloc((size_t)g->n, sizeof(int32_t));
+    w->seen = (uint8_t*)calloc((size_t)g->n, 1);
+    w->nb_cap = g->n;
+    w->nb = (int32_t*)malloc(sizeof(int32_t) * (size_t)g->n);
+    w->keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)g->n);
+    if (!w->cnt || !w->seen || !w->nb || !w->keys) {
+        or_graph_free(w);
+        return OR_ENOMEM;
+    }
+    *out = w;
+    return OR_OK;
 }
 
 int32_t or_graph_n(const or_graph* g) { return g->n; }
@@ -597,6 +644,7 @@ static int rr_pop(or_graph* g, uint64_t seed, uint32_t j, uint32_t c1base, int s
         st->mat_he += (uint64_t)(g->v_off[mu + 1] - g->v_off[mu]);
         st->mat_members += reads;
     }
+    st->bytes_rr += pop_bytes(g, mu, any);
 done:
     nbhd_release(g, k);
     return rc;
@@ -620,6 +668,7 @@ static int rr_pop_lt(or_graph* g, uint64_t seed, uint32_t j, uint32_t c1base, in
     st->pops++;
     st->layers_seen += (uint64_t)l;
     int rc = OR_OK;
+    int kept = 0;
     unsigned __int128 M = 0;
     for (int64_t px = g->prof_off[mu]; px < g->prof_off[mu + 1]; ++px)
         M += (unsigned __int128)g->lay_n[px] * (unsigned __int128)g->lay_thr[px];
@@ -643,6 +692,7 @@ static int rr_pop_lt(or_graph* g, uint64_t seed, uint32_t j, uint32_t c1base, in
                 const uint64_t a = (uint64_t)((y - C) / t_i);
                 const int32_t nu = g->nb[start + (int64_t)a];
                 st->selected += 1;
+                kept = 1;
                 st->mats++;
                 st->mat_he += (uint64_t)(g->v_off[mu + 1] - g->v_off[mu]);
                 st->mat_members += reads;
@@ -654,6 +704,7 @@ static int rr_pop_lt(or_graph* g, uint64_t seed, uint32_t j, uint32_t c1base, in
         }
     }
 done:
+    st->bytes_rr += pop_bytes(g, mu, kept);
     nbhd_release(g, k);
     return rc;
 }
@@ -677,6 +728,7 @@ static int rr_generate(or_graph* g, uint64_t seed, uint32_t tag, int root_mode, 
     qsort(R->v, (size_t)R->len, sizeof(int32_t), cmp_i32);
     st->rr_sets++;
     st->members_out += (uint64_t)R->len;
+    st->bytes_rr += 4u * (uint64_t)R->len + 8u;
     return OR_OK;
 }
 
@@ -817,6 +869,96 @@ int or_pool_grow(or_pool* p, const uint64_t n_s[OR_NSTRATA]) {
     }
     free(R.v);
     return OR_OK;
+}
+
+/* The same growth as or_pool_grow, driven by `nworkers` threads over disjoint (s, j): thread t
+ * takes the new sets whose rank in the stratum-major order of the growth is t modulo nworkers,
+ * each with its own worker view of the pool's graph (or_graph_worker). Every set is the single-
+ * threaded rr_generate of (seed, tag, s, j), so the pool is identical to or_pool_grow's. */
+typedef struct {
+    or_pool* p;
+    or_graph* g;
+    const uint64_t* first;  /* per stratum: first new j */
+    const uint64_t* last;   /* per stratum: end of the new j */
+    int t, nworkers;
+    int rc;
+    or_stats stats;
+} grow_job;
+
+static void* grow_worker(void* arg) {
+    grow_job* J = (grow_job*)arg;
+    ivec R = {0, 0, 0};
+    uint64_t rank = 0;
+    for (int s = 0; s < OR_NSTRATA && J->rc == OR_OK; ++s)
+        for (uint64_t j = J->first[s]; j < J->last[s] && J->rc == OR_OK; ++j, ++rank) {
+            if ((int)(rank % (uint64_t)J->nworkers) != J->t) continue;
+            or_pool* p = J->p;
+            int rc = rr_generate(J->g, p->seed, p->tag, p->root_mode, (uint32_t)s, (uint32_t)j, p->strategy,
+                                 &R, &J->stats);
+            if (rc != OR_OK) { J->rc = rc; break; }
+            int32_t* set = (int32_t*)malloc(sizeof(int32_t) * (size_t)(R.len > 0 ? R.len : 1));
+            if (!set) { J->rc = OR_ENOMEM; break; }
+            memcpy(set, R.v, sizeof(int32_t) * (size_t)R.len);
+            p->sets[s][j] = set;
+            p->len[s][j] = R.len;
+        }
+    free(R.v);
+    return NULL;
+}
+
+static void add_stats(or_stats* a, const or_stats* b) {
+    a->rr_sets += b->rr_sets; a->pops += b->pops; a->layers_seen += b->layers_seen;
+    a->draws += b->draws; a->mats += b->mats; a->mat_he += b->mat_he;
+    a->mat_members += b->mat_members; a->selected += b->selected;
+    a->members_out += b->members_out; a->bytes_rr += b->bytes_rr;
+}
+
+int or_pool_grow_mt(or_pool* p, const uint64_t n_s[OR_NSTRATA], or_graph* const* workers, int nworkers) {
+    if (nworkers <= 1 || !workers) return or_pool_grow(p, n_s);
+    uint64_t first[OR_NSTRATA], last[OR_NSTRATA];
+    for (int s = 0; s < OR_NSTRATA; ++s) {
+        first[s] = p->n_s[s];
+        last[s] = n_s[s] > p->n_s[s] ? n_s[s] : p->n_s[s];
+        if (last[s] == first[s]) continue;
+        if (last[s] > 0xFFFFFFFFull) return OR_EOVERFLOW;
+        int32_t sz;
+        stratum_list(p->g, p->root_mode, (uint32_t)s, &sz);
+        if (sz <= 0) return OR_EINVAL;
+        if (last[s] > p->cap_s[s]) {
+            int32_t** ns = (int32_t**)realloc(p->sets[s], sizeof(int32_t*) * last[s]);
+            if (!ns) return OR_ENOMEM;
+            p->sets[s] = ns;
+            int64_t* nl = (int64_t*)realloc(p->len[s], sizeof(int64_t) * last[s]);
+            if (!nl) return OR_ENOMEM;
+            p->len[s] = nl;
+            p->cap_s[s] = last[s];
+        }
+        for (uint64_t j = first[s]; j < last[s]; ++j) p->sets[s][j] = NULL;
+    }
+    grow_job* jobs = (grow_job*)calloc((size_t)nworkers, sizeof(grow_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)nworkers, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return OR_ENOMEM; }
+    int started = 0, rc = OR_OK;
+    for (int t = 0; t < nworkers; ++t) {
+        jobs[t] = (grow_job){p, workers[t], first, last, t, nworkers, OR_OK, {0}};
+        if (pthread_create(&th[t], NULL, grow_worker, &jobs[t]) != 0) { rc = OR_ENOMEM; break; }
+        started++;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    for (int t = 0; t < started; ++t) {
+        if (jobs[t].rc != OR_OK && rc == OR_OK) rc = jobs[t].rc;
+        add_stats(&p->stats, &jobs[t].stats);
+    }
+    if (started < nworkers && rc == OR_OK) rc = OR_ENOMEM;
+    if (rc != OR_OK) {  /* drop the partial growth */
+        for (int s = 0; s < OR_NSTRATA; ++s)
+            for (uint64_t j = first[s]; j < last[s]; ++j) { free(p->sets[s][j]); p->sets[s][j] = NULL; }
+    } else {
+        for (int s = 0; s < OR_NSTRATA; ++s) p->n_s[s] = last[s];
+    }
+    free(jobs);
+    free(th);
+    return rc;
 }
 
 int64_t or_pool_count(const or_pool* p) {
@@ -1050,6 +1192,12 @@ int or_brr(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, 
 int or_brr_upper(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
                  int root_mode, int strategy, int upper_mode, int32_t* seeds, or_brr_result* res,
                  or_stats* st) {
+    return or_brr_upper_mt(g, seed, k, eps, ell, cap, root_mode, strategy, upper_mode, seeds, res, st, NULL, 0);
+}
+
+int or_brr_upper_mt(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
+                    int root_mode, int strategy, int upper_mode, int32_t* seeds, or_brr_result* res,
+                    or_stats* st, or_graph* const* workers, int nworkers) {
     or_plan plan;
     int rc = or_plan_theta(g->n, k, eps, ell, &plan);
     if (rc != OR_OK) return rc;
@@ -1063,8 +1211,8 @@ int or_brr_upper(const or_graph* g, uint64_t seed, int32_t k, double eps, double
         if (cap && theta > cap) { rc = OR_EOVERFLOW; break; }
         uint64_t ns[OR_NSTRATA];
         or_allocate(g, root_mode, theta, ns);
-        if ((rc = or_pool_grow(r1, ns))) break;
-        if ((rc = or_pool_grow(r2, ns))) break;
+        if ((rc = or_pool_grow_mt(r1, ns, workers, nworkers))) break;
+        if ((rc = or_pool_grow_mt(r2, ns, workers, nworkers))) break;
         uint64_t N1 = (uint64_t)or_pool_count(r1), N2 = (uint64_t)or_pool_count(r2);
         uint64_t pu[2] = {0, 0};
         if ((rc = or_greedy_upper(r1, k, seeds, res->lambda_r1, NULL, upper_mode ? pu : NULL))) break;
@@ -1089,11 +1237,9 @@ int or_brr_upper(const or_graph* g, uint64_t seed, int32_t k, double eps, double
         or_stats a, b;
         or_pool_stats(r1, &a);
         or_pool_stats(r2, &b);
-        st->rr_sets = a.rr_sets + b.rr_sets; st->pops = a.pops + b.pops;
-        st->layers_seen = a.layers_seen + b.layers_seen; st->draws = a.draws + b.draws;
-        st->mats = a.mats + b.mats; st->mat_he = a.mat_he + b.mat_he;
-        st->mat_members = a.mat_members + b.mat_members; st->selected = a.selected + b.selected;
-        st->members_out = a.members_out + b.members_out;
+        memset(st, 0, sizeof(*st));
+        add_stats(st, &a);
+        add_stats(st, &b);
     }
     or_pool_free(r1);
     or_pool_free(r2);

@@ -42,6 +42,14 @@ typedef struct {
     uint64_t mat_members;   /* sum over materialising pops of sum_{he in mu} |he| */
     uint64_t selected;      /* activations drawn (sum of h) */
     uint64_t members_out;   /* sum of |R| */
+    /* Algorithmic bytes of RR generation (the cost model behind Thms 2-3: what a pop must read),
+     * at 32-byte-sector granularity, over one layout of the method's data: the layer profile as
+     * 12-byte entries of one array in vertex order, v_he and the normalised hyperedge members as
+     * 4-byte ids at their CSR offsets. Per pop the sectors of mu's profile entries; per
+     * materialising pop also those of v_he(mu) and, for every hyperedge he containing mu, its two
+     * offsets (8 bytes) and the sectors of its member ids; per RR set its output ids (4 |R|), its
+     * root draw and its offset (8). */
+    uint64_t bytes_rr;
 } or_stats;
 
 /* ---- primitives ---- */
@@ -72,6 +80,10 @@ int or_graph_layer(const or_graph* g, int32_t v, int32_t i, uint32_t* w, uint32_
 /* members of layer i of A(v), ascending ids; returns count or <0 on error. */
 int64_t or_graph_layer_members(const or_graph* g, int32_t v, int32_t i, int32_t* out, int64_t cap);
 
+/* A worker view of g for another thread: the same read-only graph, its own scratch (an oracle
+ * graph is not safe for concurrent calls). Free it with or_graph_free before g. */
+int or_graph_worker(const or_graph* g, or_graph** out);
+
 /* ---- roots, allocation, RR sets ---- */
 int or_allocate(const or_graph* g, int root_mode, uint64_t theta, uint64_t n_s[OR_NSTRATA]);
 int32_t or_root(const or_graph* g, uint64_t seed, uint32_t tag, int root_mode, uint32_t stratum,
@@ -84,6 +96,9 @@ int or_pool_create(const or_graph* g, uint64_t seed, uint32_t tag, int root_mode
                    or_pool** out);
 void or_pool_free(or_pool* p);
 int or_pool_grow(or_pool* p, const uint64_t n_s[OR_NSTRATA]);
+/* The same growth driven by nworkers threads over disjoint (s, j), each with its own worker view
+ * (workers[t], views of the pool's graph); the resulting pool is identical to or_pool_grow's. */
+int or_pool_grow_mt(or_pool* p, const uint64_t n_s[OR_NSTRATA], or_graph* const* workers, int nworkers);
 int64_t or_pool_count(const or_pool* p);
 int64_t or_pool_total(const or_pool* p);
 void or_pool_counts(const or_pool* p, uint64_t n_s[OR_NSTRATA]);
@@ -129,6 +144,10 @@ int or_brr(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, 
  * not among them, as an unsigned 128-bit integer {low, high} in the greedy's weights. */
 int or_greedy_upper(const or_pool* p, int32_t k, int32_t* seeds, uint64_t lambda_s[OR_NSTRATA],
                     uint64_t* gains, uint64_t prefix_upper[2]);
+/* or_brr_upper with the pools grown by or_pool_grow_mt over `workers` (NULL / 0: one thread) */
+int or_brr_upper_mt(const or_graph* g, uint64_t seed, int32_t k, double eps, double ell, uint64_t cap,
+                    int root_mode, int strategy, int upper_mode, int32_t* seeds, or_brr_result* res,
+                    or_stats* st, or_graph* const* workers, int nworkers);
 /* that bound in the units of sigma (stratified: x 2^-32; plain: x n / N) */
 double or_prefix_upper_sigma(uint64_t lo, uint64_t hi, int root_mode, int64_t n, uint64_t N);
 /* BRR with the upper bound of Eq. upper_6 (upper_mode 0, the closed form Alg. 4 uses) or of

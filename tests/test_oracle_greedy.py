@@ -248,3 +248,66 @@ def test_brr_with_prefix_upper(oracle, roots):
     s2, _, _, U = p1.greedy_upper(k)
     assert s2.tolist() == seeds.tolist()
     assert pref["upper"] == oracle.prefix_upper_sigma(U, roots, n, pref["pool_r1"])
+
+
+# ------------------------------------------------------------------------------------------------
+# Eq. equation-max at high precision and the benchmark workloads' anchors; Eq. upper_6 for k > 1
+# ------------------------------------------------------------------------------------------------
+def theta_max_mp(n, k, eps, ell):
+    """Eq. equation-max, 2n (sqrt(ln(2/delta)) + sqrt(ln C(n,k) + ln(6/delta))) / (eps^2 k) with
+    delta = n^-ell, at 50 significant digits; ln C(n,k) from the log-gamma function."""
+    mp = pytest.importorskip("mpmath")
+    with mp.workdps(50):
+        n_, k_, e_, l_ = mp.mpf(n), mp.mpf(k), mp.mpf(eps), mp.mpf(ell)
+        delta = n_ ** (-l_)
+        lnc = mp.loggamma(n_ + 1) - mp.loggamma(k_ + 1) - mp.loggamma(n_ - k_ + 1)
+        t = 2 * n_ * (mp.sqrt(mp.log(2 / delta)) + mp.sqrt(lnc + mp.log(6 / delta))) / (e_ ** 2 * k_)
+        return float(t)
+
+
+@pytest.mark.parametrize("n,k,eps,ell", [(100_000, 50, 0.1, 1.0), (2_000_000, 100, 0.1, 1.0),
+                                         (1000, 10, 0.05, 1.0), (5000, 3, 0.3, 2.0),
+                                         (160_217, 100, 0.1, 1.0), (4_000_000, 200, 0.2, 1.5)])
+def test_theta_max_matches_high_precision(oracle, n, k, eps, ell):
+    p = oracle.plan_theta(n, k, eps, ell)
+    ref = theta_max_mp(n, k, eps, ell)
+    assert abs(p["theta_max"] - ref) <= 1e-12 * ref
+    assert p["theta_max_ceil"] == math.ceil(ref)
+
+
+@pytest.mark.parametrize("n,k,floor_theta_max,theta0,i_max", [
+    (100_000, 50, 9_792_352, 49, 18),        # the 100k-vertex workload (p = 0.01, k = 50)
+    (2_000_000, 100, 148_467_123, 75, 21),   # the 2M-vertex workload (weighted cascade, k = 100)
+])
+def test_theta_anchors_of_the_benchmark_workloads(oracle, n, k, floor_theta_max, theta0, i_max):
+    # eps = 0.1, ell = 1 (delta = 1/n, as in Sec. 6): theta_max's integer part, theta_0 and the
+    # number of doublings; a dropped factor 2, eps in place of eps^2 or ln(2/delta) in place of
+    # ln(6/delta) each moves theta_max by far more than one unit
+    p = oracle.plan_theta(n, k, 0.1, 1.0)
+    assert math.floor(p["theta_max"]) == floor_theta_max
+    assert p["theta0"] == theta0 and p["i_max"] == i_max
+
+
+def test_upper6_closed_values(oracle):
+    # (1 - 1/k)^k is 1/4 at k = 2 and 8/27 at k = 3: the bound is 4/3 and 27/19 of the estimate
+    # Lambda n / theta; as k grows (1 - 1/k)^k -> 1/e and the bound -> e/(e - 1) of the estimate
+    est = 57.0 * 1000 / 500
+    assert oracle.upper_bound(57.0, 2, 1000, 500) == pytest.approx(est * 4 / 3, rel=1e-15)
+    assert oracle.upper_bound(57.0, 3, 1000, 500) == pytest.approx(est * 27 / 19, rel=1e-15)
+    assert oracle.upper_bound(57.0, 10 ** 6, 1000, 500) == pytest.approx(est * math.e / (math.e - 1), rel=1e-6)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("k", [2, 3])
+def test_upper6_bounds_the_optimum(oracle, seed, k):
+    # greedy covers at least 1 - (1 - 1/k)^k of the best k-set (Lemma 5 / Eq. upper_6), so the
+    # closed form applied to the greedy's coverage is never below the optimum found by search
+    rng = np.random.default_rng(100 + seed)
+    n = 14
+    hes = [[int(x) for x in rng.integers(0, n, size=int(rng.integers(2, 5)))] for _ in range(10)]
+    g, pool, sets, a = make_pool(oracle, n, hes, "uniform_pair", 1288490188, 60, "plain", seed)
+    seeds, lam, _ = pool.greedy(k)
+    opt = bf.best_cover(sets, n, k)
+    N = len(sets)
+    assert oracle.upper_bound(float(lam[0]), k, N, N) >= opt - 1e-9
+    assert int(lam[0]) <= opt
