@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 from workloads import make_hypergraph, workload  # noqa: E402
 
-DEFAULT_WORKLOAD = "zipf-100k-50k-p001"
+DEFAULT_WORKLOAD = "zipf-2m-1m-wc"
 METRIC = "RR sets/sec + seed-selection seconds at fixed eps vs plain GPU form; % HBM roofline"
 UNIT = "RR sets/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -46,13 +46,22 @@ def peaks():
 
 
 def rr_algorithmic_bytes(v):
-    """Bytes the RR generator must move, from its work counters and the device layout: per pop
-    the per-vertex record (8) and one 32-byte entry per layer of A(mu); per materialising pop the
-    hyperedge spans (8 + 4 per hyperedge) and the record and sum of sizes (12); the member ids
-    the materialisations need (4 each: all of mu's hyperedges in one pass, or only the id slices
-    of the chunks that hold picks when mu has a chunk index) and the words read to locate those
-    slices (4 each: extra span reads, binary-search probes, chunk-index entries); per member of R
-    its queue write, queue read and output write (12); per RR set its root (4)."""
+    """Algorithmic bytes of RR generation (the cost model of Thms 2-3, at 32-byte-sector
+    granularity; the oracle counts the same figure independently): per pop the sectors of mu's
+    layer profile (12-byte entries), per materialising pop also the sectors of v_he(mu) and, for
+    every hyperedge of mu, its two offsets (8) and the sectors of its member ids -- what
+    materialising A(mu) from the incidence lists reads, whatever this design reads instead --
+    plus 4 bytes per output id and 8 per RR set (root draw, offset)."""
+    return 32 * v["sectors"] + 8 * v["mat_he"] + 4 * v["total"] + 8 * v["count"]
+
+
+def rr_design_bytes(v):
+    """The bytes this design's RR kernel reads and writes by its own counters: per pop the vertex
+    record (8) and one 32-byte entry per layer of A(mu); per materialising pop the hyperedge spans
+    (8 + 4 per hyperedge) and the record and sum of sizes (12); the member ids gathered (4 each:
+    all of mu's hyperedges in one pass, or only the id slices of the chunks that hold picks when mu
+    has a chunk index) and the words read to locate those slices (4 each); per member of R its
+    queue write, queue read and output write (12); per RR set its root (4)."""
     return (8 * v["pops"] + 32 * v["layers_seen"] + 12 * v["mats"] + 12 * v["mat_he"]
             + 4 * v["gathered"] + 4 * v["search_words"] + 12 * v["total"] + 4 * v["count"])
 
@@ -147,6 +156,7 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", sc
            "rr_kernel_seconds": v1["rr_kernel_seconds"] + v2["rr_kernel_seconds"],
            "rr_launches": v1["rr_launches"] + v2["rr_launches"],
            "bytes": rr_algorithmic_bytes(v1) + rr_algorithmic_bytes(v2),
+           "design_bytes": rr_design_bytes(v1) + rr_design_bytes(v2),
            "edges": sum(v["mat_he"] + v["gathered"] for v in (v1, v2)),
            "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
            "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
@@ -250,6 +260,7 @@ def bench_gpu(args):
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     kbytes = sum(s["bytes"] for s in stats)
+    dbytes = sum(s["design_bytes"] for s in stats)
     ksec = sum(s["rr_kernel_seconds"] for s in stats)
     klaunch = sum(s["rr_launches"] for s in stats)
     achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
@@ -290,9 +301,16 @@ def bench_gpu(args):
                      "peak": hbm, "peak_source": peak_note, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kbytes / max(klaunch, 1),
-                     "launches": klaunch, "kernel_seconds": ksec},
+                     "launches": klaunch, "kernel_seconds": ksec,
+                     "sm_mhz_x_seconds": None,
+                     "design_bytes_per_launch": dbytes / max(klaunch, 1),
+                     "design_gbs": dbytes / ksec / 1e9 if ksec > 0 else 0.0,
+                     "design_frac": (dbytes / ksec / 1e9) / hbm if ksec > 0 else 0.0},
         "clocks": clk.summary(),
     }
+    mhz = line["clocks"]["sm_mhz"]
+    # the RR kernel's time in SM clock cycles at the median clock sampled under load
+    line["roofline"]["sm_mhz_x_seconds"] = mhz * ksec if mhz else None
     if args.forward_sims > 0:
         line["forward_mc"] = forward_check(H, torch, w, d_off, d_mem, stats[-1], args.forward_sims)
     if not args.no_plain_form:
@@ -397,12 +415,17 @@ def profile_batch(args):
     torch.cuda.synchronize()
 
 
-def oracle_rate(w, off, mem, seconds, seed, tag=0):
+def oracle_graph(w, off, mem):
+    """The CPU oracle's graph of the workload (built once; its build is never timed)."""
+    import oracle as O
+    return O.Graph(w.graph.n, off, mem, w.query.model, w.query.uniform_threshold)
+
+
+def oracle_rate(w, og, seconds, seed, tag=0):
     """RR sets per second of the CPU oracle on the same graph: grows a pool of the workload's root
     mode set by set until `seconds` have passed (graph build excluded)."""
     import oracle as O
     q = w.query
-    og = O.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold)
     pool = O.Pool(og, seed=seed, tag=tag, roots=q.roots, strategy=q.strategy)
     t0 = time.perf_counter()
     theta = 1
@@ -415,22 +438,22 @@ def oracle_rate(w, off, mem, seconds, seed, tag=0):
     return pool.count(), el
 
 
-def oracle_rate_threads(w, off, mem, seconds, seed, threads, tag=0):
-    """The oracle driven by `threads` host threads over disjoint RR ids of one pool (each thread
-    with its own oracle graph; the ctypes calls release the GIL). The (stratum, j) ids of a
-    stratified allocation are interleaved in proportion to the strata, so any prefix of the work
-    list has the pool's mix. Returns (sets done, wall seconds)."""
+def oracle_rate_threads(w, og, seconds, seed, threads, tag=0):
+    """The oracle driven by `threads` host threads over disjoint RR ids of one pool (one oracle
+    graph, one worker view of it per thread; the ctypes calls release the GIL). The (stratum, j)
+    ids of a stratified allocation are interleaved in proportion to the strata, so any prefix of
+    the work list has the pool's mix. Returns (sets done, wall seconds)."""
     import threading
     import oracle
     q = w.query
-    graphs = [oracle.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold) for _ in range(threads)]
-    n_s = graphs[0].allocate(q.roots, 1 << 16)
+    workers = oracle.Workers(og, threads)
+    n_s = og.allocate(q.roots, 1 << 16)
     work = sorted(((j + 0.5) / int(c), s, j) for s, c in enumerate(n_s) if c for j in range(int(c)))
     lock = threading.Lock()
     state = {"next": 0, "done": 0}
     t0 = time.perf_counter()
 
-    def run(g):
+    def run(t):
         while time.perf_counter() - t0 < seconds:
             with lock:
                 i = state["next"]
@@ -438,16 +461,18 @@ def oracle_rate_threads(w, off, mem, seconds, seed, threads, tag=0):
             if i >= len(work):
                 return
             _, s, j = work[i]
-            g.rr_set(seed, tag, q.roots, s, j, strategy=q.strategy)
+            workers.rr_set(t, seed, tag, q.roots, s, j, strategy=q.strategy)
             with lock:
                 state["done"] += 1
 
-    ts = [threading.Thread(target=run, args=(g,)) for g in graphs]
+    ts = [threading.Thread(target=run, args=(t,)) for t in range(threads)]
     for t in ts:
         t.start()
     for t in ts:
         t.join()
-    return state["done"], time.perf_counter() - t0
+    el = time.perf_counter() - t0
+    workers.close()
+    return state["done"], el
 
 
 def host_cores():
@@ -460,12 +485,13 @@ def host_cores():
 def cpu_baseline(w, off, mem, seconds):
     """The oracle on the host: every core (the baseline) and one core (beside it)."""
     cores = host_cores()
-    count, el = oracle_rate_threads(w, off, mem, seconds, w.query.seed, cores)
-    c1, e1 = oracle_rate(w, off, mem, seconds, w.query.seed)
+    og = oracle_graph(w, off, mem)
+    count, el = oracle_rate_threads(w, og, seconds, w.query.seed, cores)
+    c1, e1 = oracle_rate(w, og, seconds, w.query.seed)
     return {"value": count / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{count} RR sets of one pool (tag 0, {w.query.roots} roots, ids interleaved "
                       f"across strata) on the same graph, {el:.1f} s of oracle work on {cores} "
-                      "threads, one oracle graph per thread; graph build excluded",
+                      "threads, one worker view of the oracle graph per thread; graph build excluded",
             "single_core": {"value": c1 / e1, "cores": 1,
                             "sample": f"first {c1} RR sets of pool tag 0, {e1:.1f} s on one thread"}}
 
@@ -479,11 +505,12 @@ def bench_reference(args):
     off, mem = make_hypergraph(w.graph)
     per_step = args.reference_seconds
     cores = host_cores()
+    og = oracle_graph(w, off, mem)
     for i in range(args.warmup):
-        oracle_rate_threads(w, off, mem, min(per_step / 4, 2.0), w.query.seed + 7 + i, cores, tag=3)
+        oracle_rate_threads(w, og, min(per_step / 4, 2.0), w.query.seed + 7 + i, cores, tag=3)
     counts, times = [], []
     for i in range(args.steps):
-        c, el = oracle_rate_threads(w, off, mem, per_step, w.query.seed + 100 + i, cores)
+        c, el = oracle_rate_threads(w, og, per_step, w.query.seed + 100 + i, cores)
         counts.append(c)
         times.append(el)
     value = sum(counts) / sum(times)
@@ -498,7 +525,7 @@ def bench_reference(args):
                          "sample": f"{args.steps} steps of ~{per_step:.0f} s each: "
                                    f"RR sets of one pool per step ({w.query.roots} roots, a new "
                                    f"seed each step) on the same graph, {cores} threads with one "
-                                   "oracle graph each, graph build excluded"},
+                                   "worker view of the oracle graph each, graph build excluded"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -653,7 +680,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--forward-sims", type=int, default=256,
                     help="forward Monte-Carlo simulations of the last query's seeds (0: skip)")
-    ap.add_argument("--reference-seconds", type=float, default=10.0)
+    ap.add_argument("--reference-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain-form", action="store_true",
                     help="skip the plain-schedule comparison query (outside the timed region)")

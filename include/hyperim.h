@@ -87,8 +87,19 @@ typedef struct hyperim_pool* hyperim_pool_t;
  *   pointers when ptrs_on_device != 0 (read during the call only). Members of a hyperedge may
  *   come in any order and may repeat.
  *   EINVAL: n < 1, n >= 2^31 - 1, m < 0, he_off not monotone from 0, a member outside [0, n),
- *   model out of range, uniform_threshold > 2^32. ENOMEM: allocation failed or the device
- *   footprint would exceed hbm_budget_bytes (0 = no budget). On success *out owns the graph.
+ *   model out of range, uniform_threshold > 2^32, only one of dev_alloc / dev_free given.
+ *   ENOMEM: allocation failed or the device footprint would exceed hbm_budget_bytes (0 = no
+ *   budget). On success *out owns the graph.
+ *   Device memory: with dev_alloc and dev_free both NULL every device buffer of the graph, its
+ *   shares and its pools comes from cudaMallocAsync / cudaFreeAsync on the handle's stream. A
+ *   caller that owns the GPU's memory (PyTorch's caching allocator, a server that hands memory
+ *   out by budget) passes both: dev_alloc(bytes, stream, alloc_ctx) returns a device pointer
+ *   aligned to at least 256 bytes, or NULL (the call then fails with ENOMEM); dev_free(ptr,
+ *   stream, alloc_ctx) releases one, ordered after the work queued on `stream` before it (the
+ *   way cudaFreeAsync is). `stream` is the cudaStream_t of the handle making the call (a share
+ *   passes its own). The hooks may be called from any thread that calls into the library
+ *   (query server workers included) and must outlive the graph, its shares and its pools. The
+ *   HBM budget still counts every byte requested through them.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int32_t n;                   /* |V| */
@@ -101,6 +112,9 @@ typedef struct {
     uint64_t seed;               /* Philox key (seed_lo, seed_hi) */
     void* cuda_stream;           /* cudaStream_t, may be NULL */
     size_t hbm_budget_bytes;     /* 0 = unlimited */
+    void* (*dev_alloc)(size_t bytes, void* cuda_stream, void* alloc_ctx);  /* NULL: cudaMallocAsync */
+    void (*dev_free)(void* ptr, void* cuda_stream, void* alloc_ctx);       /* NULL: cudaFreeAsync */
+    void* alloc_ctx;             /* passed to both hooks */
 } hyperim_load_args;
 
 hyperim_status hyperim_load(const hyperim_load_args* args, hyperim_graph_t* out);
@@ -188,6 +202,18 @@ typedef enum { HYPERIM_SCHED_PERSISTENT = 0, HYPERIM_SCHED_PLAIN = 1 } hyperim_s
 hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_graph_set_wait_limit -- bound of the device-side waits of this handle's kernels (a
+ *   warp of the RR or forward kernel waiting for its block's work queue: a claimable vertex, or
+ *   the id of a claimed slot still being stored). A wait that runs `iterations` rounds without
+ *   progress gives up: the kernel records it, every block leaves its current set and the
+ *   launch ends; the call returns HYPERIM_ETIMEDOUT and its results are discarded (the handle
+ *   stays usable, pools keep the sets of earlier growth steps). 0 restores the default of 2^24
+ *   rounds (about a second of sleeping per wait). Not part of the paper: a failure detector of
+ *   this library. Shares made afterwards inherit the value. EINVAL: g NULL. No device work.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_graph_set_wait_limit(hyperim_graph_t g, uint32_t iterations);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_plan_theta -- RR budget of Sec. 4.3 (host arithmetic, IEEE double).
  *   delta = n^-ell (Sec. 6: delta = 1/|V| for ell = 1); ln C(n,k) = sum_{i<=k'} ln((n-k'+i)/i)
  *   with k' = min(k, n-k);
@@ -215,6 +241,8 @@ hyperim_status hyperim_plan_theta(hyperim_graph_t g, int32_t k, double eps, doub
  *   the pool are kept and only j in [old n_s, new n_s) are generated. pool_tag < 256. Device
  *   CSR output; the call synchronises the stream once to size the CSR.
  *   EOVERFLOW: some n_s >= 2^32, or one layer draw needs more than 2^18 Philox words.
+ *   ETIMEDOUT: a bounded device wait gave up (hyperim_graph_set_wait_limit); the pool keeps the
+ *   sets it held before the call.
  * ------------------------------------------------------------------------------------------ */
 hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta,
                                  int32_t root_mode, int32_t strategy, hyperim_pool_t* inout);
@@ -249,6 +277,15 @@ typedef struct {
                                  growing R1 and R2 of a BRR round together counts once, on R1) */
     double rr_kernel_seconds; /* this pool's share (by RR sets) of those launches' duration,
                                  CUDA events on the graph's stream */
+    /* 32-byte sectors of the method's own data that generation touches, whatever this library
+       actually reads: per pop the sectors spanned by mu's profile (l_mu entries of 12 bytes at
+       entry offset prof_off[mu] of one array over all vertices); per materialising pop also
+       those spanned by v_he(mu) (4-byte ids at v_off[mu]) and by mem(he) (4-byte ids at
+       he_off[he]) of every he containing mu, offsets of the normalised incidence store. With
+       the pool's other counters it gives the algorithmic bytes of RR generation,
+       B = 32 sectors + 8 mat_he + 4 total + 8 count (the two offsets read per hyperedge, the
+       output ids, the root draw and the set's offset). */
+    uint64_t sectors;
 } hyperim_pool_view_t;
 
 hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out);
@@ -353,14 +390,18 @@ hyperim_status hyperim_forward_spread(hyperim_graph_t g, const int32_t* seeds_ho
  *   where an allocation may wait on the device or fail under memory pressure.
  *   Inputs (device pointers, caller-owned): rr_off[count + 1] (int64), rr_mem[rr_off[count]]
  *   (int32 vertex ids), rr_stratum[count] (0..15) -- e.g. the CSR of hyperim_pool_view -- and
- *   seeds[k] (ids outside [0, n) are ignored). Output (device, caller-owned): lambda_s[16] gets
+ *   seeds[k] (ids outside [0, n) are ignored). Inputs taken from hyperim_pool_view must stay
+ *   valid until this call's work on cuda_stream has finished: no thread may grow or free that
+ *   pool in the meantime (growth moves the pool's arrays and frees the old ones). Output (device, caller-owned): lambda_s[16] gets
  *   the number of RR sets of each stratum that contain a seed; the call zeroes it first.
  *   Scratch: one flag byte per vertex in a fixed array of HYPERIM_NOALLOC_MAX_N bytes built into
  *   the library; every GPU that loads the library holds those bytes until the process exits.
  *   EINVAL: n < 1 or n > HYPERIM_NOALLOC_MAX_N (the scratch is too small), count < 0, k < 0,
  *   null pointers. Never calls cudaMalloc, cudaFree or any other allocating routine.
  *   The first call on a device looks up the scratch array's device address and caches it (a
- *   set-up step): make that first call before any stream capture. The work is queued on
+ *   set-up step): make that first call before any stream capture. The cached address belongs
+ *   to the device's current context: after cudaDeviceReset the library must be reloaded (the
+ *   process restarted) before this entry point is used on that device again. The work is queued on
  *   cuda_stream (NULL = legacy default stream) and the call returns without waiting. Every call
  *   uses the same scratch array, which keeps the last call's flags until the next call clears
  *   it: calls whose work overlaps on the GPU (other streams, other threads) race and return wrong

@@ -39,11 +39,17 @@ class HyperIMError(RuntimeError):
         self.status = status
 
 
+# the caller's device allocator (hyperim_load_args.dev_alloc / dev_free)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class LoadArgs(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("he_off", C.c_void_p), ("he_mem", C.c_void_p),
                 ("ptrs_on_device", C.c_int32), ("model", C.c_int32),
                 ("uniform_threshold", C.c_uint64), ("seed", C.c_uint64),
-                ("cuda_stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t)]
+                ("cuda_stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class GraphStats(C.Structure):
@@ -67,7 +73,8 @@ class PoolView(C.Structure):
                 ("draws", C.c_uint64), ("mats", C.c_uint64), ("mat_he", C.c_uint64),
                 ("mat_members", C.c_uint64), ("selected", C.c_uint64),
                 ("gathered", C.c_uint64), ("search_words", C.c_uint64),
-                ("rr_launches", C.c_uint64), ("rr_kernel_seconds", C.c_double)]
+                ("rr_launches", C.c_uint64), ("rr_kernel_seconds", C.c_double),
+                ("sectors", C.c_uint64)]
 
 
 class SelectOpts(C.Structure):
@@ -117,6 +124,7 @@ _SIGNATURES = {
     "hyperim_graph_stats": (C.c_int, [_vp, C.POINTER(GraphStats)]),
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hyperim_graph_set_schedule": (C.c_int, [_vp, C.c_int32]),
+    "hyperim_graph_set_wait_limit": (C.c_int, [_vp, C.c_uint32]),
     "hyperim_graph_share": (C.c_int, [_vp, _vp, C.POINTER(_vp)]),
     "hyperim_server_create": (C.c_int, [C.POINTER(ServerArgs), C.POINTER(_vp)]),
     "hyperim_server_add_graph": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
@@ -185,9 +193,47 @@ def current_stream():
 # ------------------------------------------------------------------------------------------------
 # C-named entry points (thin wrappers)
 # ------------------------------------------------------------------------------------------------
+class DeviceAllocator:
+    """A device allocator handed to hyperim_load: ``alloc(nbytes, stream) -> int`` (a device
+    pointer, 0 on failure) and ``free(ptr, stream)``, called by the library for every device
+    buffer of the graph, its shares and its pools (stream: the cudaStream_t of the calling
+    handle, as an int). The C callbacks are kept alive for the life of the process, since pools
+    and shares may outlive the Graph object."""
+
+    _alive = []
+
+    def __init__(self, alloc, free):
+        self.allocs = 0
+        self.frees = 0
+
+        def _a(nbytes, stream, ctx):
+            self.allocs += 1
+            try:
+                return int(alloc(int(nbytes), int(stream or 0))) or None
+            except Exception:
+                return None
+
+        def _f(ptr, stream, ctx):
+            self.frees += 1
+            free(int(ptr), int(stream or 0))
+
+        self.c_alloc = ALLOC_FN(_a)
+        self.c_free = FREE_FN(_f)
+        DeviceAllocator._alive.append(self)
+
+
+def torch_caching_allocator(device=None):
+    """A DeviceAllocator backed by PyTorch's CUDA caching allocator."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    return DeviceAllocator(lambda nbytes, stream: torch.cuda.caching_allocator_alloc(nbytes, dev, stream),
+                           lambda ptr, stream: torch.cuda.caching_allocator_delete(ptr))
+
+
 def hyperim_load(n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, seed=1,
-                 stream=None, hbm_budget_bytes=0):
-    """Returns a graph handle. he_off/he_mem: int32 numpy arrays (host) or CUDA tensors."""
+                 stream=None, hbm_budget_bytes=0, allocator: Optional[DeviceAllocator] = None):
+    """Returns a graph handle. he_off/he_mem: int32 numpy arrays (host) or CUDA tensors.
+    allocator: None (the library's stream-ordered cudaMallocAsync) or a DeviceAllocator."""
     keep = []
     on_dev = 0
     if hasattr(he_off, "is_cuda") and he_off.is_cuda:
@@ -203,7 +249,9 @@ def hyperim_load(n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, s
         p_off, p_mem = he_off.ctypes.data, (he_mem.ctypes.data if he_mem.size else None)
     args = LoadArgs(int(n), len(he_off) - 1, p_off, p_mem, on_dev, MODELS[model],
                     int(uniform_threshold), int(seed),
-                    stream if stream is not None else current_stream(), int(hbm_budget_bytes))
+                    stream if stream is not None else current_stream(), int(hbm_budget_bytes),
+                    allocator.c_alloc if allocator is not None else ALLOC_FN(),
+                    allocator.c_free if allocator is not None else FREE_FN(), None)
     h = C.c_void_p()
     _check(lib().hyperim_load(C.byref(args), C.byref(h)))
     return h
@@ -267,11 +315,11 @@ class Graph:
     """A hypergraph loaded on the device (incidence store + layer profile)."""
 
     def __init__(self, n, he_off, he_mem, model="uniform_pair", uniform_threshold=0, seed=1,
-                 stream=None, hbm_budget_bytes=0):
+                 stream=None, hbm_budget_bytes=0, allocator=None):
         self.n = int(n)
         self.model = model
         self._h = hyperim_load(n, he_off, he_mem, model, uniform_threshold, seed, stream,
-                               hbm_budget_bytes)
+                               hbm_budget_bytes, allocator)
 
     @property
     def handle(self):
@@ -331,6 +379,11 @@ class Graph:
         g = Graph.__new__(Graph)
         g.n, g.model, g._h, g.parent = self.n, self.model, h, self
         return g
+
+    def set_wait_limit(self, iterations):
+        """Bound of the device-side waits of this handle's kernels (0: the default, 2^24 rounds);
+        a wait that runs out makes the call raise HYPERIM_ETIMEDOUT."""
+        _check(lib().hyperim_graph_set_wait_limit(self._h, int(iterations)))
 
     def set_schedule(self, schedule):
         """RR generation schedule: "persistent" (default) or "plain" (one launch per batch of one

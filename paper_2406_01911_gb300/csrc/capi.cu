@@ -39,6 +39,14 @@ hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes) {
         return set_error(HYPERIM_ENOMEM, "device memory budget exceeded (" + std::to_string(before + bytes) +
                                              " > " + std::to_string(r->budget) + " bytes)");
     }
+    if (g->alloc_fn) {
+        *p = g->alloc_fn(bytes, (void*)g->stream, g->alloc_ctx);
+        if (!*p) {
+            r->device_bytes.fetch_sub(bytes);
+            return set_error(HYPERIM_ENOMEM, "the caller's dev_alloc(" + std::to_string(bytes) + ") returned NULL");
+        }
+        return HYPERIM_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, g->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -50,10 +58,16 @@ hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes) {
     return HYPERIM_OK;
 }
 
+// releases a device buffer through the allocator the graph was loaded with
+static void release(hyperim_graph* g, void* p) {
+    if (g->free_fn) g->free_fn(p, (void*)g->stream, g->alloc_ctx);
+    else cudaFreeAsync(p, g->stream);
+}
+
 void dev_free(hyperim_graph* g, void* p, size_t bytes) {
     if (!p) return;
     if (bytes == 0) bytes = 16;
-    cudaFreeAsync(p, g->stream);
+    release(g, p);
     graph_root(g)->device_bytes.fetch_sub(bytes);
 }
 
@@ -86,8 +100,8 @@ hyperim_status check_device_status(hyperim_graph* g, const char* where) {
         return set_error(HYPERIM_EOVERFLOW, msg + "scratch capacity exceeded at vertex " +
                                                 std::to_string(h.detail));
     case kErrSpin:
-        return set_error(HYPERIM_ECUDA, msg + "a work-queue wait ran out in RR set job " +
-                                            std::to_string(h.detail));
+        return set_error(HYPERIM_ETIMEDOUT, msg + "a bounded work-queue wait gave up in job " +
+                                                std::to_string(h.detail));
     default:
         return set_error(HYPERIM_ECUDA, msg + "device error " + std::to_string(h.code));
     }
@@ -195,6 +209,8 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
     if (!a->he_off) return set_error(HYPERIM_EINVAL, "he_off is null");
     if (a->model < 0 || a->model > 2) return set_error(HYPERIM_EINVAL, "unknown probability model");
     if (a->uniform_threshold > HYPERIM_P_ONE) return set_error(HYPERIM_EINVAL, "uniform_threshold > 2^32");
+    if ((a->dev_alloc == nullptr) != (a->dev_free == nullptr))
+        return set_error(HYPERIM_EINVAL, "dev_alloc and dev_free must be given together");
     hyperim_graph* g = new (std::nothrow) hyperim_graph();
     if (!g) return set_error(HYPERIM_ENOMEM, "host allocation failed");
     g->n = a->n;
@@ -204,6 +220,9 @@ hyperim_status hyperim_load(const hyperim_load_args* a, hyperim_graph_t* out) {
     g->seed = a->seed;
     g->stream = (cudaStream_t)a->cuda_stream;
     g->budget = a->hbm_budget_bytes;
+    g->alloc_fn = a->dev_alloc;
+    g->free_fn = a->dev_free;
+    g->alloc_ctx = a->alloc_ctx;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -263,9 +282,10 @@ void free_handle(hyperim_graph* g, bool data) {
     dev_free(g, S.arena, sizeof(int32_t) * S.arena_cap);
     if (data) {
         void* ptrs[] = {g->he_off, g->he_mem, g->v_off, g->v_he, g->tsum, g->v_span, g->vinfo, g->prof_off,
-                        g->prof, g->cdf_tab, g->deg, g->stratum, g->vs_off, g->vs_list, g->idx, g->idx_tab};
+                        g->prof, g->cdf_tab, g->deg, g->stratum, g->vs_off, g->vs_list, g->idx, g->idx_tab,
+                        g->mat_sect, g->he_dir, g->v_dir};
         for (void* p : ptrs)
-            if (p) cudaFreeAsync(p, g->stream);
+            if (p) release(g, p);
     }
     cudaStreamSynchronize(g->stream);
 }
@@ -353,6 +373,14 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->theta_lstar = r->theta_lstar;
     h->sm_count = r->sm_count;
     h->schedule = r->schedule;
+    h->wait_limit = r->wait_limit;
+    h->alloc_fn = r->alloc_fn;
+    h->free_fn = r->free_fn;
+    h->alloc_ctx = r->alloc_ctx;
+    h->mat_sect = r->mat_sect;
+    h->he_dir = r->he_dir;
+    h->v_dir = r->v_dir;
+    h->dir_entries = r->dir_entries;
     hyperim_status st = dev_alloc(h, (void**)&h->d_status, sizeof(DevStatus));
     if (st == HYPERIM_OK) st = dev_alloc(h, (void**)&h->d_counters, 2 * sizeof(RRCounters));
     if (st == HYPERIM_OK) {
@@ -441,6 +469,12 @@ hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule) {
     if (schedule != HYPERIM_SCHED_PERSISTENT && schedule != HYPERIM_SCHED_PLAIN)
         return set_error(HYPERIM_EINVAL, "unknown schedule");
     g->schedule = schedule;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_graph_set_wait_limit(hyperim_graph_t g, uint32_t iterations) {
+    if (!g) return set_error(HYPERIM_EINVAL, "null graph");
+    g->wait_limit = iterations;
     return HYPERIM_OK;
 }
 
@@ -588,6 +622,7 @@ hyperim_status hyperim_pool_view(hyperim_pool_t p, hyperim_pool_view_t* out) {
     out->search_words = p->counters.search_words;
     out->rr_launches = p->rr_launches;
     out->rr_kernel_seconds = p->rr_kernel_seconds;
+    out->sectors = p->counters.sectors;
     return HYPERIM_OK;
 }
 

@@ -347,6 +347,7 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
     for (int i = 0; i < HYPERIM_NSTRATA; ++i)
         W.w[i] = stratum_weight(g, p->root_mode, view_ns[i], i);
     hyperim_status st;
+    CallBuffers tmp(g);
     uint32_t *cnt = nullptr, *inv = nullptr, *covered = nullptr, *bid = nullptr, *ticket = nullptr;
     int64_t* inv_off = nullptr;
     unsigned long long *score = nullptr, *lam = nullptr, *bscore = nullptr;
@@ -356,25 +357,25 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
     const size_t bytes_cnt = sizeof(uint32_t) * ((size_t)n + 1);
     const size_t bytes_inv = sizeof(uint32_t) * (size_t)std::max<int64_t>(T, 1);
     const size_t bytes_cov = sizeof(uint32_t) * (size_t)std::max<int64_t>(N, 1);
-    if ((st = dev_alloc(g, (void**)&cnt, bytes_cnt))) return st;
-    if ((st = dev_alloc(g, (void**)&inv_off, sizeof(int64_t) * ((size_t)n + 1)))) return st;
-    if ((st = dev_alloc(g, (void**)&inv, bytes_inv))) return st;
-    if ((st = dev_alloc(g, (void**)&score, sizeof(unsigned long long) * (size_t)n))) return st;
-    if ((st = dev_alloc(g, (void**)&picked, (size_t)n))) return st;
-    if ((st = dev_alloc(g, (void**)&covered, bytes_cov))) return st;
-    if ((st = dev_alloc(g, (void**)&lam, sizeof(unsigned long long) * HYPERIM_NSTRATA))) return st;
-    if ((st = dev_alloc(g, (void**)&bscore, sizeof(unsigned long long) * ablocks))) return st;
-    if ((st = dev_alloc(g, (void**)&bid, sizeof(uint32_t) * ablocks))) return st;
-    if ((st = dev_alloc(g, (void**)&ticket, sizeof(uint32_t) * 2))) return st;
-    if ((st = dev_alloc(g, (void**)&best, sizeof(int32_t) * 2))) return st;
-    if ((st = dev_alloc(g, (void**)&seeds_d, sizeof(int32_t) * (size_t)k))) return st;
+    if ((st = tmp.alloc(&cnt, bytes_cnt))) return st;
+    if ((st = tmp.alloc(&inv_off, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&inv, bytes_inv))) return st;
+    if ((st = tmp.alloc(&score, sizeof(unsigned long long) * (size_t)n))) return st;
+    if ((st = tmp.alloc(&picked, (size_t)n))) return st;
+    if ((st = tmp.alloc(&covered, bytes_cov))) return st;
+    if ((st = tmp.alloc(&lam, sizeof(unsigned long long) * HYPERIM_NSTRATA))) return st;
+    if ((st = tmp.alloc(&bscore, sizeof(unsigned long long) * ablocks))) return st;
+    if ((st = tmp.alloc(&bid, sizeof(uint32_t) * ablocks))) return st;
+    if ((st = tmp.alloc(&ticket, sizeof(uint32_t) * 2))) return st;
+    if ((st = tmp.alloc(&best, sizeof(int32_t) * 2))) return st;
+    if ((st = tmp.alloc(&seeds_d, sizeof(int32_t) * (size_t)k))) return st;
     TopK* tk = nullptr;
     unsigned int* hist = nullptr;
     unsigned long long* part = nullptr;
     const int tblocks = ablocks;
-    if ((st = dev_alloc(g, (void**)&tk, sizeof(TopK)))) return st;
-    if ((st = dev_alloc(g, (void**)&hist, sizeof(unsigned int) * 256))) return st;
-    if ((st = dev_alloc(g, (void**)&part, sizeof(unsigned long long) * 2 * (size_t)tblocks))) return st;
+    if ((st = tmp.alloc(&tk, sizeof(TopK)))) return st;
+    if ((st = tmp.alloc(&hist, sizeof(unsigned int) * 256))) return st;
+    if ((st = tmp.alloc(&part, sizeof(unsigned long long) * 2 * (size_t)tblocks))) return st;
     {
         TopK t0{};
         t0.kleft = (unsigned int)k;
@@ -428,21 +429,6 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
         prefix_upper[0] = th.best_lo;
         prefix_upper[1] = th.best_hi;
     }
-    dev_free(g, tk, sizeof(TopK));
-    dev_free(g, hist, sizeof(unsigned int) * 256);
-    dev_free(g, part, sizeof(unsigned long long) * 2 * (size_t)tblocks);
-    dev_free(g, cnt, bytes_cnt);
-    dev_free(g, inv_off, sizeof(int64_t) * ((size_t)n + 1));
-    dev_free(g, inv, bytes_inv);
-    dev_free(g, score, sizeof(unsigned long long) * (size_t)n);
-    dev_free(g, picked, (size_t)n);
-    dev_free(g, covered, bytes_cov);
-    dev_free(g, lam, sizeof(unsigned long long) * HYPERIM_NSTRATA);
-    dev_free(g, bscore, sizeof(unsigned long long) * ablocks);
-    dev_free(g, bid, sizeof(uint32_t) * ablocks);
-    dev_free(g, ticket, sizeof(uint32_t) * 2);
-    dev_free(g, best, sizeof(int32_t) * 2);
-    dev_free(g, seeds_d, sizeof(int32_t) * (size_t)k);
     return check_device_status(g, "greedy");
 }
 
@@ -453,13 +439,14 @@ hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_
     uint64_t view_ns[HYPERIM_NSTRATA];
     const Limits L = make_limits(p, lim, view_ns);
     hyperim_status st;
+    CallBuffers tmp(g);
     uint8_t* in_s = nullptr;
     unsigned long long* lam = nullptr;
     int32_t* sd = nullptr;
     const size_t kk = (size_t)std::max(k, 1);
-    if ((st = dev_alloc(g, (void**)&in_s, (size_t)g->n))) return st;
-    if ((st = dev_alloc(g, (void**)&lam, sizeof(unsigned long long) * HYPERIM_NSTRATA))) return st;
-    if ((st = dev_alloc(g, (void**)&sd, sizeof(int32_t) * kk))) return st;
+    if ((st = tmp.alloc(&in_s, (size_t)g->n))) return st;
+    if ((st = tmp.alloc(&lam, sizeof(unsigned long long) * HYPERIM_NSTRATA))) return st;
+    if ((st = tmp.alloc(&sd, sizeof(int32_t) * kk))) return st;
     HYP_CUDA(cudaMemsetAsync(in_s, 0, (size_t)g->n, s));
     HYP_CUDA(cudaMemsetAsync(lam, 0, sizeof(unsigned long long) * HYPERIM_NSTRATA, s));
     if (k > 0) {
@@ -475,9 +462,6 @@ hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_
     HYP_CUDA(cudaMemcpyAsync(hl, lam, sizeof(hl), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < HYPERIM_NSTRATA; ++i) lambda_s[i] = hl[i];
-    dev_free(g, in_s, (size_t)g->n);
-    dev_free(g, lam, sizeof(unsigned long long) * HYPERIM_NSTRATA);
-    dev_free(g, sd, sizeof(int32_t) * kk);
     return check_device_status(g, "coverage");
 }
 

@@ -298,6 +298,7 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
     const int32_t n = g->n;
     const int sm = g->sm_count;
     hyperim_status st;
+    CallBuffers tmp(g);
     if ((st = dev_alloc(g, (void**)&g->idx, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1)))) return st;
     HYP_CUDA(cudaMemsetAsync(g->idx, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s));
     g->idx_entries = 0;
@@ -306,26 +307,22 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
 
     uint32_t* d_flag = nullptr;
     int64_t* d_pos = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_flag, sizeof(uint32_t) * (size_t)n))) return st;
-    if ((st = dev_alloc(g, (void**)&d_pos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_flag, sizeof(uint32_t) * (size_t)n))) return st;
+    if ((st = tmp.alloc(&d_pos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
     { k_idx_candidates<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->vinfo, g->tsum, d_flag); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_flag, d_pos, n))) return st;
     int64_t ncand = 0;
     HYP_CUDA(cudaMemcpyAsync(&ncand, d_pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
-    if (ncand == 0) {
-        dev_free(g, d_flag, sizeof(uint32_t) * (size_t)n);
-        dev_free(g, d_pos, sizeof(int64_t) * ((size_t)n + 1));
-        return HYPERIM_OK;
-    }
+    if (ncand == 0) return HYPERIM_OK;
     int32_t* d_list = nullptr;
     uint8_t* d_bits = nullptr;
     uint32_t* d_entries = nullptr;
     int64_t* d_off = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_list, sizeof(int32_t) * (size_t)ncand))) return st;
-    if ((st = dev_alloc(g, (void**)&d_bits, (size_t)ncand))) return st;
-    if ((st = dev_alloc(g, (void**)&d_entries, sizeof(uint32_t) * (size_t)ncand))) return st;
-    if ((st = dev_alloc(g, (void**)&d_off, sizeof(int64_t) * ((size_t)ncand + 1)))) return st;
+    if ((st = tmp.alloc(&d_list, sizeof(int32_t) * (size_t)ncand))) return st;
+    if ((st = tmp.alloc(&d_bits, (size_t)ncand))) return st;
+    if ((st = tmp.alloc(&d_entries, sizeof(uint32_t) * (size_t)ncand))) return st;
+    if ((st = tmp.alloc(&d_off, sizeof(int64_t) * ((size_t)ncand + 1)))) return st;
     { k_idx_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_flag, d_pos, d_list); count_launch(); }
     const int nl = (int)ncand;
     const int pblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * 4);
@@ -351,15 +348,13 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)1 << 30)) fblocks -= sm;
         uint32_t* d_scratch = nullptr;
         int* d_next = nullptr;
-        if ((st = dev_alloc(g, (void**)&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
-        if ((st = dev_alloc(g, (void**)&d_next, sizeof(int)))) return st;
+        if ((st = tmp.alloc(&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
+        if ((st = tmp.alloc(&d_next, sizeof(int)))) return st;
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
         { k_idx_fill<<<fblocks, kFillThreads, kFillSmem, s>>>(d_list, nl, d_bits, d_entries, d_off, g->vinfo, g->v_span,
                                                   g->he_mem, g->tsum, g->prof, g->id_bits, g->idx_tab, d_scratch,
                                                   cap, d_next, g->d_status); count_launch(); }
         if ((st = check_device_status(g, "chunk index"))) return st;
-        dev_free(g, d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks);
-        dev_free(g, d_next, sizeof(int));
         // indexed vertices
         std::vector<uint32_t> e((size_t)ncand);
         HYP_CUDA(cudaMemcpyAsync(e.data(), d_entries, sizeof(uint32_t) * (size_t)ncand, cudaMemcpyDeviceToHost, s));
@@ -368,12 +363,6 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         for (uint32_t x : e) cnt += x ? 1 : 0;
         g->idx_vertices = cnt;
     }
-    dev_free(g, d_flag, sizeof(uint32_t) * (size_t)n);
-    dev_free(g, d_pos, sizeof(int64_t) * ((size_t)n + 1));
-    dev_free(g, d_list, sizeof(int32_t) * (size_t)ncand);
-    dev_free(g, d_bits, (size_t)ncand);
-    dev_free(g, d_entries, sizeof(uint32_t) * (size_t)ncand);
-    dev_free(g, d_off, sizeof(int64_t) * ((size_t)ncand + 1));
     HYP_CUDA(cudaGetLastError());
     return HYPERIM_OK;
 }

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <shared_mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hyperim.h"
@@ -35,6 +36,7 @@ struct DevStatus {
 struct RRCounters {
     unsigned long long pops, layers_seen, draws, mats, mat_he, mat_members, selected;
     unsigned long long gathered, search_words;
+    unsigned long long sectors;  // 32-byte sectors of the method's own data (pool view: sectors)
 };
 
 // Chunk index of large neighbourhoods. The ids are split into C = 2^c chunks by their top c of
@@ -62,6 +64,16 @@ constexpr int kIdxMaxBits = 12;
 constexpr int kIdxMaxL = 1024;
 // idx word of a vertex: 0 = no index, else (c << 56) | offset of its table
 constexpr int kIdxBitsShift = 56;
+
+// Id directory of a hyperedge (a lookup structure over its sorted member list): for a hyperedge
+// of L members, kDirMinLen < L <= kDirMaxLen, with b = ceil(log2 L) bits (1 <= b <= min(id bits,
+// kDirMaxBits)), D[r] (r = 0..2^b) is the number of members whose top b id bits are < r. The
+// members whose top c id bits equal k (one chunk of the chunk index) are then positions
+// [D[k 2^(b-c)], D[(k+1) 2^(b-c)]) when c <= b, or a sub-range of [D[r], D[r + 1]), r = k >>
+// (c - b), when c > b (about one member on average). Entries are uint16 (L < 2^16).
+constexpr int kDirMinLen = 16;
+constexpr int kDirMaxLen = 65535;
+constexpr int kDirMaxBits = 12;
 
 // Profile entry of layer i of A(mu): 32 bytes, two uint4.
 //   [0] = {w_i | (p == 1 ? 1u << 31 : 0), n_i, floor(p 2^32) for 0 <= p < 1, T_0}
@@ -135,6 +147,15 @@ struct hyperim_graph {
     hyperim::Scratch scratch;
     int sm_count = 0;
     int32_t schedule = 0;        // hyperim_schedule of RR generation
+    uint32_t wait_limit = 0;     // iterations of a bounded device wait (0: the default)
+    // caller's device allocator (hyperim_load_args); null: stream-ordered cudaMallocAsync
+    void* (*alloc_fn)(size_t, void*, void*) = nullptr;
+    void (*free_fn)(void*, void*, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+    uint32_t* mat_sect = nullptr; // n: sectors of v_he(v) plus those of every mem(he), he in v
+    uint16_t* he_dir = nullptr;  // id directories of the hyperedges that have one
+    uint2* v_dir = nullptr;      // nnz, in v_he order: {directory offset, b} (b = 0: none)
+    int64_t dir_entries = 0;
     // handles made by hyperim_graph_share point at the loaded graph, whose device data they read;
     // it is released once it has been freed and no share is left
     hyperim_graph* owner = nullptr;
@@ -181,9 +202,32 @@ hyperim_status cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::hyperim::cuda_fail(e_, #call);  \
     } while (0)
 
-// device memory (capi.cu): stream-ordered allocation accounted against the graph's budget
+// device memory (capi.cu): stream-ordered allocation accounted against the graph's budget,
+// through the caller's allocator when the graph was loaded with one
 hyperim_status dev_alloc(hyperim_graph* g, void** p, size_t bytes);
 void dev_free(hyperim_graph* g, void* p, size_t bytes);
+
+// Device buffers of one call: every allocation made through it is released (stream-ordered)
+// when it goes out of scope, on every return path of the call.
+class CallBuffers {
+  public:
+    explicit CallBuffers(hyperim_graph* g) : g_(g) {}
+    CallBuffers(const CallBuffers&) = delete;
+    CallBuffers& operator=(const CallBuffers&) = delete;
+    ~CallBuffers() {
+        for (auto it = bufs_.rbegin(); it != bufs_.rend(); ++it) dev_free(g_, it->first, it->second);
+    }
+    template <typename T>
+    hyperim_status alloc(T** p, size_t bytes) {
+        hyperim_status st = dev_alloc(g_, reinterpret_cast<void**>(p), bytes);
+        if (st == HYPERIM_OK) bufs_.emplace_back(static_cast<void*>(*p), bytes);
+        return st;
+    }
+
+  private:
+    hyperim_graph* g_;
+    std::vector<std::pair<void*, size_t>> bufs_;
+};
 hyperim_status check_device_status(hyperim_graph* g, const char* where);
 
 // load.cu

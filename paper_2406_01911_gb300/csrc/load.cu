@@ -522,6 +522,75 @@ __global__ void k_build_spans(const int32_t* __restrict__ v_he, int64_t nnz,
     }
 }
 
+// 32-byte sectors of the method's data that a materialising pop of v touches (the work counter
+// behind the pool view's `sectors`): the ids of v_he(v) and of mem(he) for every hyperedge he
+// containing v, 4-byte ids at their offsets in the normalised incidence store. One warp per vertex.
+__device__ __forceinline__ uint32_t span_sectors(uint64_t a, uint64_t len) {
+    return len == 0 ? 0u : (uint32_t)(((a + len - 1) >> 5) - (a >> 5) + 1);
+}
+
+__global__ void k_mat_sect(int32_t n, const int32_t* __restrict__ v_off, const int2* __restrict__ v_span,
+                           uint32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t b = v_off[v], e = v_off[v + 1];
+        uint32_t acc = 0;
+        for (int32_t x = b + lane; x < e; x += 32) {
+            const int2 sp = v_span[x];
+            acc += span_sectors(4ull * (uint64_t)sp.x, 4ull * (uint64_t)sp.y);
+        }
+        acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+        if (lane == 0) out[v] = acc + span_sectors(4ull * (uint64_t)b, 4ull * (uint64_t)(e - b));
+    }
+}
+
+// directory bits of a hyperedge of L members (0: no directory)
+__device__ __forceinline__ uint32_t dir_bits(int32_t L, int id_bits) {
+    if (L <= kDirMinLen || L > kDirMaxLen) return 0;
+    uint32_t b = 1;
+    while ((1 << b) < L) ++b;
+    const uint32_t cap = (uint32_t)min(id_bits, kDirMaxBits);
+    return b < cap ? b : cap;
+}
+
+__global__ void k_dir_size(const int32_t* __restrict__ he_off, int32_t m, int id_bits, uint32_t* __restrict__ size) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = dir_bits(he_off[e + 1] - he_off[e], id_bits);
+        size[e] = b ? (1u << b) + 1u : 0u;
+    }
+}
+
+// one warp per hyperedge: member x (top b bits t_x) sets D[r] = x for t_{x-1} < r <= t_x; the
+// entries above the last member's bits hold L
+__global__ void k_dir_fill(const int32_t* __restrict__ he_off, const int32_t* __restrict__ he_mem, int32_t m,
+                           int id_bits, const int64_t* __restrict__ dir_off, uint16_t* __restrict__ dir) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m;
+         e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t b0 = he_off[e], L = he_off[e + 1] - b0;
+        const uint32_t b = dir_bits(L, id_bits);
+        if (!b) continue;
+        const int sh = id_bits - (int)b;
+        uint16_t* D = dir + dir_off[e];
+        for (int32_t x = lane; x <= L; x += 32) {
+            const int64_t t = x < L ? (int64_t)((uint32_t)he_mem[b0 + x] >> sh) : (int64_t)(1u << b);
+            const int64_t tp = x > 0 ? (int64_t)((uint32_t)he_mem[b0 + x - 1] >> sh) : -1;
+            for (int64_t r = tp + 1; r <= t; ++r) D[r] = (uint16_t)x;
+        }
+    }
+}
+
+// per incidence (v_he order): {offset of its hyperedge's directory, bits} or {0, 0}
+__global__ void k_dir_incidence(const int32_t* __restrict__ v_he, int64_t nnz, const int32_t* __restrict__ he_off,
+                                int id_bits, const int64_t* __restrict__ dir_off, uint2* __restrict__ v_dir) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = v_he[x];
+        const uint32_t b = dir_bits(he_off[e + 1] - he_off[e], id_bits);
+        v_dir[x] = b ? make_uint2((uint32_t)dir_off[e], b) : make_uint2(0u, 0u);
+    }
+}
+
 __global__ void k_build_vinfo(int32_t n, const int32_t* __restrict__ prof_off,
                               const int32_t* __restrict__ v_off, int4* __restrict__ vinfo) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -544,12 +613,13 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     const int32_t n = g->n, m = g->m;
     const int sm = g->sm_count;
     hyperim_status st;
+    CallBuffers tmp(g);
     // --- upload
     int32_t *d_off_in = nullptr, *d_mem_in = nullptr, *d_tmp = nullptr;
     const size_t nnz_alloc = (size_t)(nnz_in > 0 ? nnz_in : 1);
-    if ((st = dev_alloc(g, (void**)&d_off_in, sizeof(int32_t) * ((size_t)m + 1)))) return st;
-    if ((st = dev_alloc(g, (void**)&d_mem_in, sizeof(int32_t) * nnz_alloc))) return st;
-    if ((st = dev_alloc(g, (void**)&d_tmp, sizeof(int32_t) * nnz_alloc))) return st;
+    if ((st = tmp.alloc(&d_off_in, sizeof(int32_t) * ((size_t)m + 1)))) return st;
+    if ((st = tmp.alloc(&d_mem_in, sizeof(int32_t) * nnz_alloc))) return st;
+    if ((st = tmp.alloc(&d_tmp, sizeof(int32_t) * nnz_alloc))) return st;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     HYP_CUDA(cudaMemcpyAsync(d_off_in, he_off_in, sizeof(int32_t) * ((size_t)m + 1), kind, s));
     if (nnz_in > 0)
@@ -560,10 +630,10 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     // --- normalise hyperedges
     uint32_t* d_newsize = nullptr;
     int64_t* d_off_new = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_newsize, sizeof(uint32_t) * ((size_t)m + 1)))) return st;
-    if ((st = dev_alloc(g, (void**)&d_off_new, sizeof(int64_t) * ((size_t)m + 1)))) return st;
+    if ((st = tmp.alloc(&d_newsize, sizeof(uint32_t) * ((size_t)m + 1)))) return st;
+    if ((st = tmp.alloc(&d_off_new, sizeof(int64_t) * ((size_t)m + 1)))) return st;
     uint8_t* d_first = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_first, nnz_alloc))) return st;
+    if ((st = tmp.alloc(&d_first, nnz_alloc))) return st;
     if (m > 0)
         { k_normalise<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(d_off_in, d_mem_in, m, n,
                                                                        d_tmp, d_first, d_newsize,
@@ -586,8 +656,8 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     // --- vertex -> hyperedge lists
     uint32_t* d_cnt = nullptr;
     int64_t* d_voff64 = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_cnt, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
-    if ((st = dev_alloc(g, (void**)&d_voff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_cnt, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_voff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->v_off, sizeof(int32_t) * ((size_t)n + 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->v_he, sizeof(int32_t) * nnz_a))) return st;
     if ((st = dev_alloc(g, (void**)&g->tsum, sizeof(int32_t) * (size_t)n))) return st;
@@ -604,7 +674,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
 
     // --- maxima of d_H and T
     unsigned long long* d_max = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_max, sizeof(unsigned long long) * 8))) return st;
+    if ((st = tmp.alloc(&d_max, sizeof(unsigned long long) * 8))) return st;
     HYP_CUDA(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long) * 8, s));
     int32_t* d_dh = (int32_t*)d_cnt;  // reuse
     { k_vhe_len<<<grid_for(n, 256, sm), 256, 0, s>>>(d_voff64, n, d_dh); count_launch(); }
@@ -620,11 +690,11 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     uint2* d_pairs = nullptr;
     uint32_t *d_nl = nullptr, *d_deg = nullptr;
     int* d_next = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_pairs, sizeof(uint2) * nnz_a))) return st;
-    if ((st = dev_alloc(g, (void**)&d_nl, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_pairs, sizeof(uint2) * nnz_a))) return st;
+    if ((st = tmp.alloc(&d_nl, sizeof(uint32_t) * ((size_t)n + 1)))) return st;
     if ((st = dev_alloc(g, (void**)&g->deg, sizeof(int32_t) * (size_t)n))) return st;
     d_deg = (uint32_t*)g->deg;
-    if ((st = dev_alloc(g, (void**)&d_next, sizeof(int)))) return st;
+    if ((st = tmp.alloc(&d_next, sizeof(int)))) return st;
     HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
     // per-incidence spans first: both profile kernels gather through them
     if ((st = dev_alloc(g, (void**)&g->v_span, sizeof(int2) * nnz_a))) return st;
@@ -644,17 +714,17 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     ProfScratch PS;
     PS.big_cap = g->max_tsum > kProfBuf ? g->max_tsum : 1;
     PS.hist_cap = g->max_dh >= kProfHist ? (int64_t)g->max_dh + 1 : 1;
-    if ((st = dev_alloc(g, (void**)&PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks)))
+    if ((st = tmp.alloc(&PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks)))
         return st;
-    if ((st = dev_alloc(g, (void**)&PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks)))
+    if ((st = tmp.alloc(&PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks)))
         return st;
     Incidence I{g->he_off, g->he_mem, g->v_off, g->v_he};
     // the large vertices, listed
     uint32_t* d_bflag = nullptr;
     int64_t* d_bpos = nullptr;
     int32_t* d_blist = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)))) return st;
-    if ((st = dev_alloc(g, (void**)&d_bpos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)))) return st;
+    if ((st = tmp.alloc(&d_bpos, sizeof(int64_t) * ((size_t)n + 1)))) return st;
     // mid-size vertices (kProfWarpT < positions <= kProfMidT): one warp each, listed
     if (n > 0 && g->max_tsum > kProfWarpT) {
         { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, kProfWarpT, kProfMidT, d_bflag); count_launch(); }
@@ -664,12 +734,11 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
         HYP_CUDA(cudaStreamSynchronize(s));
         if (nmid > 0) {
             int32_t* d_mlist = nullptr;
-            if ((st = dev_alloc(g, (void**)&d_mlist, sizeof(int32_t) * (size_t)nmid))) return st;
+            if ((st = tmp.alloc(&d_mlist, sizeof(int32_t) * (size_t)nmid))) return st;
             { k_big_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_bflag, d_bpos, d_mlist); count_launch(); }
             { k_profile_warp<kProfMidT, kPMWarps><<<grid_for(nmid * 32, kPMWarps * 32, sm), kPMWarps * 32, 0, s>>>(
                 (int32_t)nmid, d_mlist, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg,
                 d_max); count_launch(); }
-            dev_free(g, d_mlist, sizeof(int32_t) * (size_t)nmid);
         }
     }
     if (n > 0) { k_big_flags<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, g->tsum, kProfMidT, 0x7FFFFFFF, d_bflag); count_launch(); }
@@ -677,7 +746,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     int64_t nbig = 0;
     HYP_CUDA(cudaMemcpyAsync(&nbig, d_bpos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
-    if ((st = dev_alloc(g, (void**)&d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1)))) return st;
+    if ((st = tmp.alloc(&d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1)))) return st;
     if (nbig > 0) {
         { k_big_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_bflag, d_bpos, d_blist); count_launch(); }
         { k_profile<<<(int)std::min<int64_t>(pblocks, nbig), kProfThreads, prof_smem, s>>>(
@@ -685,11 +754,6 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
             g->d_status, d_max); count_launch(); }
     }
     if ((st = check_device_status(g, "layer profile"))) return st;
-    dev_free(g, d_bflag, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-    dev_free(g, d_bpos, sizeof(int64_t) * ((size_t)n + 1));
-    dev_free(g, d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1));
-    dev_free(g, PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks);
-    dev_free(g, PS.hist, sizeof(uint32_t) * (size_t)PS.hist_cap * pblocks);
     HYP_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
     g->max_layers = (int32_t)hmax[0];
@@ -698,7 +762,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
 
     // --- profile offsets + pass 2
     int64_t* d_poff64 = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_poff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
+    if ((st = tmp.alloc(&d_poff64, sizeof(int64_t) * ((size_t)n + 1)))) return st;
     if ((st = exclusive_scan_u32_to_i64(g, d_nl, d_poff64, n))) return st;
     int64_t L = 0;
     HYP_CUDA(cudaMemcpyAsync(&L, d_poff64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -711,14 +775,14 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     std::vector<double> ln_l1((size_t)g->max_layers + 2);
     for (size_t l = 0; l < ln_l1.size(); ++l) ln_l1[l] = std::log((double)l + 1.0);
     double* d_ln = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_ln, sizeof(double) * ln_l1.size()))) return st;
+    if ((st = tmp.alloc(&d_ln, sizeof(double) * ln_l1.size()))) return st;
     HYP_CUDA(cudaMemcpyAsync(d_ln, ln_l1.data(), sizeof(double) * ln_l1.size(),
                              cudaMemcpyHostToDevice, s));
     uint32_t* d_tlen = nullptr;
     int64_t* d_toff = nullptr;
     const size_t Lalloc = (size_t)(L > 0 ? L : 1);
-    if ((st = dev_alloc(g, (void**)&d_tlen, sizeof(uint32_t) * Lalloc))) return st;
-    if ((st = dev_alloc(g, (void**)&d_toff, sizeof(int64_t) * (Lalloc + 1)))) return st;
+    if ((st = tmp.alloc(&d_tlen, sizeof(uint32_t) * Lalloc))) return st;
+    if ((st = tmp.alloc(&d_toff, sizeof(int64_t) * (Lalloc + 1)))) return st;
     { k_profile_write<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->v_off, d_pairs, d_poff64, d_deg,
                                                          g->model, g->uniform_thr, d_ln, g->prof,
                                                          d_tlen, g->prof_off, g->stratum); count_launch(); }
@@ -732,13 +796,11 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
         return st;
     if (L > 0)
         { k_table_fill<<<grid_for(L, 256, sm), 256, 0, s>>>(L, d_toff, g->prof, g->cdf_tab); count_launch(); }
-    dev_free(g, d_tlen, sizeof(uint32_t) * Lalloc);
-    dev_free(g, d_toff, sizeof(int64_t) * (Lalloc + 1));
 
     // --- theta(l*) from the histogram of l (Thm 2)
     const int hcap = g->max_layers + 1;
     unsigned long long* d_lh = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1)))) return st;
+    if ((st = tmp.alloc(&d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1)))) return st;
     HYP_CUDA(cudaMemsetAsync(d_lh, 0, sizeof(unsigned long long) * ((size_t)hcap + 1), s));
     { k_hist_layers<<<grid_for(n, 256, sm), 256, 0, s>>>(d_poff64, n, d_lh, hcap); count_launch(); }
     std::vector<unsigned long long> lh((size_t)hcap + 1);
@@ -756,6 +818,34 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     // --- per-vertex records for the RR kernel
     if ((st = dev_alloc(g, (void**)&g->vinfo, sizeof(int4) * (size_t)n))) return st;
     { k_build_vinfo<<<grid_for(n, 256, sm), 256, 0, s>>>(n, g->prof_off, g->v_off, g->vinfo); count_launch(); }
+    if ((st = dev_alloc(g, (void**)&g->mat_sect, sizeof(uint32_t) * (size_t)n))) return st;
+    { k_mat_sect<<<grid_for((int64_t)n * 32, 256, sm), 256, 0, s>>>(n, g->v_off, g->v_span, g->mat_sect); count_launch(); }
+
+    // --- id directories of the larger hyperedges (read by the chunk path of the RR kernel)
+    {
+        uint32_t* d_dsize = nullptr;
+        int64_t* d_doff = nullptr;
+        if ((st = tmp.alloc(&d_dsize, sizeof(uint32_t) * ((size_t)m + 1)))) return st;
+        if ((st = tmp.alloc(&d_doff, sizeof(int64_t) * ((size_t)m + 1)))) return st;
+        if (m > 0) { k_dir_size<<<grid_for(m, 256, sm), 256, 0, s>>>(g->he_off, m, g->id_bits, d_dsize); count_launch(); }
+        if ((st = exclusive_scan_u32_to_i64(g, d_dsize, d_doff, m))) return st;
+        int64_t dtotal = 0;
+        HYP_CUDA(cudaMemcpyAsync(&dtotal, d_doff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HYP_CUDA(cudaStreamSynchronize(s));
+        if (dtotal >= (int64_t)0xFFFFFFFFll) dtotal = 0;  // offsets must fit 32 bits: no directories
+        g->dir_entries = dtotal;
+        if ((st = dev_alloc(g, (void**)&g->v_dir, sizeof(uint2) * nnz_a))) return st;
+        if (dtotal > 0) {
+            if ((st = dev_alloc(g, (void**)&g->he_dir, sizeof(uint16_t) * (size_t)dtotal))) return st;
+            { k_dir_fill<<<grid_for((int64_t)m * 32, 256, sm), 256, 0, s>>>(g->he_off, g->he_mem, m, g->id_bits, d_doff,
+                                                                         g->he_dir); count_launch(); }
+            if (nnz > 0)
+                { k_dir_incidence<<<grid_for(nnz, 256, sm), 256, 0, s>>>(g->v_he, nnz, g->he_off, g->id_bits, d_doff,
+                                                                       g->v_dir); count_launch(); }
+        } else {
+            HYP_CUDA(cudaMemsetAsync(g->v_dir, 0, sizeof(uint2) * nnz_a, s));
+        }
+    }
     if ((st = build_chunk_index(g))) return st;
 
     // --- strata lists V_s (ascending ids)
@@ -775,22 +865,6 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     }
     HYP_CUDA(cudaGetLastError());
     if ((st = check_device_status(g, "profile write"))) return st;
-    // temporaries
-    dev_free(g, d_off_in, sizeof(int32_t) * ((size_t)m + 1));
-    dev_free(g, d_mem_in, sizeof(int32_t) * nnz_alloc);
-    dev_free(g, d_tmp, sizeof(int32_t) * nnz_alloc);
-    dev_free(g, d_newsize, sizeof(uint32_t) * ((size_t)m + 1));
-    dev_free(g, d_first, nnz_alloc);
-    dev_free(g, d_off_new, sizeof(int64_t) * ((size_t)m + 1));
-    dev_free(g, d_cnt, sizeof(uint32_t) * ((size_t)n + 1));
-    dev_free(g, d_voff64, sizeof(int64_t) * ((size_t)n + 1));
-    dev_free(g, d_max, sizeof(unsigned long long) * 8);
-    dev_free(g, d_pairs, sizeof(uint2) * nnz_a);
-    dev_free(g, d_nl, sizeof(uint32_t) * ((size_t)n + 1));
-    dev_free(g, d_next, sizeof(int));
-    dev_free(g, d_poff64, sizeof(int64_t) * ((size_t)n + 1));
-    dev_free(g, d_ln, sizeof(double) * ln_l1.size());
-    dev_free(g, d_lh, sizeof(unsigned long long) * ((size_t)hcap + 1));
     HYP_CUDA(cudaStreamSynchronize(s));
     return check_device_status(g, "load");
 }

@@ -37,7 +37,7 @@ constexpr int kWBuckets = 1 << kWBucketBits;  // warp-path buckets
 constexpr int kChunks = 1024;        // first-level id chunks of the largest neighbourhoods
 constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
 constexpr int kMaxPools = 2;           // pools grown by one launch (R1 and R2 of a BRR round)
-constexpr int kNStat = 9;              // work counters (stat slots below)
+constexpr int kNStat = 10;             // work counters (stat slots below)
 
 struct RRJobMap {
     int64_t job_base[HYPERIM_NSTRATA + 1];
@@ -56,6 +56,9 @@ struct RRParams {
     const int32_t* vs_list;
     const uint64_t* idx;      // per vertex: 0 or (chunk bits << 56) | offset into idx_tab
     const uint32_t* idx_tab;
+    const uint32_t* mat_sect; // per vertex: sectors of v_he(v) and of mem(he) for he in v
+    const uint16_t* he_dir;   // id directories of the larger hyperedges
+    const uint2* v_dir;       // per incidence: {directory offset, bits} (bits 0: none)
     int32_t n;
     int id_bits;
     uint64_t seed;
@@ -84,6 +87,7 @@ struct RRParams {
     int64_t plain_base;
     DevStatus* st;
     RRCounters* counters;                    // kMaxPools entries
+    int spin_limit;                          // rounds of a bounded wait before it gives up
 };
 
 struct Need {                    // a layer with h > 0 at the current pop
@@ -128,7 +132,12 @@ struct Shared {
 enum { C_JOB = 0, C_HEAD, C_TAIL, C_DONE, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_STOP, C_BITS, C_OK,
        C_FAIL };
 // stat slots
-enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL, S_GATH, S_SRCH };
+enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL, S_GATH, S_SRCH, S_SECT };
+
+// 32-byte sectors spanned by the byte range [a, a + len) (0 when empty)
+__device__ __forceinline__ unsigned long long sectors_of(uint64_t a, uint64_t len) {
+    return len == 0 ? 0ull : (unsigned long long)(((a + len - 1) >> 5) - (a >> 5) + 1);
+}
 
 __device__ __forceinline__ void dev_fail(DevStatus* st, int32_t code, int32_t detail) {
     if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
@@ -300,10 +309,9 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
 // itself done, so the head and tail read afterwards include them, and a warp leaves only when
 // the queue is quiescent (a warp that left early would idle at the barrier for the rest of the
 // set). The wait is bounded (kErrSpin).
-constexpr int kSpinLimit = 1 << 24;
 __device__ int claim_slot(const RRParams& P, Shared& S, int64_t job) {
     volatile int* ctrl = S.ctrl;
-    for (int it = 0; it < kSpinLimit; ++it) {
+    for (int it = 0; it < P.spin_limit; ++it) {
         const int d = ctrl[C_DONE];
         __threadfence_block();
         const int h = ctrl[C_HEAD], t = ctrl[C_TAIL], nd = ctrl[C_NDEF];
@@ -321,7 +329,7 @@ __device__ int claim_slot(const RRParams& P, Shared& S, int64_t job) {
 // The id in a claimed slot (its pusher may still be storing it); -1 if the bounded wait ran out.
 __device__ int32_t slot_value(const RRParams& P, const int32_t* list, int idx, int64_t job) {
     const volatile int32_t* v = list + idx;
-    for (int it = 0; it < kSpinLimit; ++it) {
+    for (int it = 0; it < P.spin_limit; ++it) {
         const int32_t x = *v;
         if (x >= 0) return x;
         __nanosleep(32);
@@ -369,11 +377,14 @@ __device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0
 }
 
 // The members != mu of mu's hyperedges whose ids lie in [lo, hi), sorted, in buf[0, count);
-// returns count, or -1 if they exceed kWHalf. Members of a hyperedge are sorted, so the range is
-// one slice found by two binary searches; when mu is in the range its own slot in every slice is
-// skipped (a hole at mu's offset). The slices are gathered with independent loads into the raw
-// half of buf and counted into buckets of the id offset within the range, then scattered and
-// sorted as in small_nbhd. probes counts the words read by the searches.
+// returns count, or -1 if they exceed kWHalf. lo is a multiple of 2^sh (the range is chunk
+// k = lo >> sh of the ids' top c = id_bits - sh bits). Members of a hyperedge are sorted, so the
+// range is one slice of it: read off its id directory when it has one (two entries when c <= b,
+// else one directory range of about one member, scanned), else found by two interleaved binary
+// searches. When mu lies in the range its own slot in every slice is skipped (a hole at mu's
+// offset, found the same way). The slices are gathered with independent loads into the raw half
+// of buf and counted into buckets of the id offset within the range, then scattered and sorted as
+// in small_nbhd. probes counts the words read to locate the slices.
 __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_begin, int32_t dh,
                           uint32_t lo, int sh, uint32_t* buf, uint32_t& probes) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -387,6 +398,8 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
     const uint32_t key_mask = (uint32_t)nb - 1;
     const uint32_t hi = lo + (1u << sh);
     const bool mu_in = (uint32_t)mu >= lo && (uint32_t)mu < hi;
+    const int c = P.id_bits - sh;
+    const uint32_t k = lo >> sh;
     for (int b = lane; b < nb; b += 32) bkt[b] = 0;
     int base = 0;
     for (int c0 = 0; c0 < dh; c0 += 32) {
@@ -394,17 +407,51 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
         int st = 0, len = 0, hl = 0x7FFFFFFF;
         if (lane < cnt) {
             const int2 sp = P.v_span[v_begin + c0 + lane];
+            const uint2 dd = P.v_dir[v_begin + c0 + lane];
             const int32_t* e = P.he_mem + sp.x;
-            // three independent lower bounds (lo, hi, mu) advanced together: their loads overlap
-            int l1 = 0, h1 = sp.y, l2 = 0, h2 = sp.y, l3 = 0, h3 = mu_in ? sp.y : 0;
-            while (l1 < h1 || l2 < h2 || l3 < h3) {
-                const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1, m3 = (l3 + h3) >> 1;
-                const uint32_t v1 = l1 < h1 ? (uint32_t)e[m1] : 0u;
-                const uint32_t v2 = l2 < h2 ? (uint32_t)e[m2] : 0u;
-                const uint32_t v3 = l3 < h3 ? (uint32_t)e[m3] : 0u;
-                if (l1 < h1) { ++probes; if (v1 < lo) l1 = m1 + 1; else h1 = m1; }
-                if (l2 < h2) { ++probes; if (v2 < hi) l2 = m2 + 1; else h2 = m2; }
-                if (l3 < h3) { ++probes; if (v3 < (uint32_t)mu) l3 = m3 + 1; else h3 = m3; }
+            int l1 = 0, l2 = 0, l3 = 0;
+            if (dd.y != 0) {
+                const uint16_t* D = P.he_dir + dd.x;
+                const int b = (int)dd.y;
+                if (c <= b) {
+                    l1 = D[k << (b - c)];
+                    l2 = D[(k + 1) << (b - c)];
+                    probes += 2;
+                } else {
+                    const uint32_t r = k >> (c - b);
+                    const int a0 = D[r], a1 = D[r + 1];
+                    probes += 2;
+                    l1 = a0;
+                    l2 = a0;
+                    for (int x = a0; x < a1; ++x) {
+                        const uint32_t v = (uint32_t)e[x];
+                        ++probes;
+                        l1 += v < lo ? 1 : 0;
+                        l2 += v < hi ? 1 : 0;
+                    }
+                }
+                if (mu_in) {  // mu's slot: its directory range, scanned
+                    const uint32_t rm = (uint32_t)mu >> (P.id_bits - b);
+                    l3 = D[rm];
+                    const int a1 = D[rm + 1];
+                    probes += 2;
+                    while (l3 < a1 && (uint32_t)e[l3] < (uint32_t)mu) {
+                        ++l3;
+                        ++probes;
+                    }
+                }
+            } else {
+                // three lower bounds (lo, hi, mu) advanced together: their loads overlap
+                int h1 = sp.y, h2 = sp.y, h3 = mu_in ? sp.y : 0;
+                while (l1 < h1 || l2 < h2 || l3 < h3) {
+                    const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1, m3 = (l3 + h3) >> 1;
+                    const uint32_t v1 = l1 < h1 ? (uint32_t)e[m1] : 0u;
+                    const uint32_t v2 = l2 < h2 ? (uint32_t)e[m2] : 0u;
+                    const uint32_t v3 = l3 < h3 ? (uint32_t)e[m3] : 0u;
+                    if (l1 < h1) { ++probes; if (v1 < lo) l1 = m1 + 1; else h1 = m1; }
+                    if (l2 < h2) { ++probes; if (v2 < hi) l2 = m2 + 1; else h2 = m2; }
+                    if (l3 < h3) { ++probes; if (v3 < (uint32_t)mu) l3 = m3 + 1; else h3 = m3; }
+                }
             }
             st = sp.x + l1;
             len = l2 - l1;
@@ -572,6 +619,7 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         wst[S_POPS] += 1;
         wst[S_LAYERS] += (unsigned long long)l;
         wst[S_DRAWS] += ndraw;
+        wst[S_SECT] += sectors_of(12ull * (uint64_t)pb, 12ull * (uint64_t)l);
     }
     if (nneed == 0) return false;
     hsum = __reduce_add_sync(0xFFFFFFFFu, hsum);
@@ -582,6 +630,7 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         wst[S_MAT_HE] += (unsigned long long)dh;
         wst[S_MAT_MEM] += (unsigned long long)tsum;
         wst[S_GATH] += (unsigned long long)tsum;  // one pass over the members (the chunk path corrects it)
+        wst[S_SECT] += P.mat_sect[mu];
     }
     if (nneed > kLQ) return true;
     // picks for every needed layer (none when h = n)
@@ -1323,6 +1372,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
         atomicAdd(&c->selected, st[S_SEL]);
         atomicAdd(&c->gathered, st[S_GATH]);
         atomicAdd(&c->search_words, st[S_SRCH]);
+        atomicAdd(&c->sectors, st[S_SECT]);
     }
 }
 
@@ -1383,6 +1433,12 @@ hyperim_status allow_rr_smem() {
     });
     HYP_CUDA(err);
     return HYPERIM_OK;
+}
+
+// rounds of a bounded device wait (hyperim_graph_set_wait_limit; default 2^24)
+int wait_rounds(const hyperim_graph* g) {
+    const uint32_t w = g->wait_limit ? g->wait_limit : (1u << 24);
+    return (int)std::min<uint32_t>(w, 0x7FFFFFFFu);
 }
 
 hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
@@ -1474,9 +1530,10 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     int32_t* d_size = nullptr;
     int* d_next = nullptr;
     unsigned long long* d_used = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_pos, sizeof(int64_t) * (size_t)njobs))) return st;
-    if ((st = dev_alloc(g, (void**)&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
-    if ((st = dev_alloc(g, (void**)&d_next, sizeof(int) + sizeof(unsigned long long) * 2))) return st;
+    CallBuffers tmp(g);
+    if ((st = tmp.alloc(&d_pos, sizeof(int64_t) * (size_t)njobs))) return st;
+    if ((st = tmp.alloc(&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
+    if ((st = tmp.alloc(&d_next, sizeof(int) + sizeof(unsigned long long) * 2))) return st;
     d_used = reinterpret_cast<unsigned long long*>(d_next + 2);
     RRParams P;
     P.vinfo = g->vinfo;
@@ -1490,6 +1547,9 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.vs_list = g->vs_list;
     P.idx = g->idx;
     P.idx_tab = g->idx_tab;
+    P.mat_sect = g->mat_sect;
+    P.he_dir = g->he_dir;
+    P.v_dir = g->v_dir;
     P.n = g->n;
     P.id_bits = g->id_bits;
     P.seed = g->seed;
@@ -1518,8 +1578,17 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.arena_used = d_used;
     P.st = g->d_status;
     P.counters = g->d_counters;
+    P.spin_limit = wait_rounds(g);
     unsigned long long used = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    struct Events {
+        cudaEvent_t* a;
+        cudaEvent_t* b;
+        ~Events() {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } events{&ev0, &ev1};
     HYP_CUDA(cudaEventCreate(&ev0));
     HYP_CUDA(cudaEventCreate(&ev1));
     double seconds = 0.0;
@@ -1564,14 +1633,12 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         if (used <= g->scratch.arena_cap) break;
         want = used + used / 8 + 4096;
     }
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (used > g->scratch.arena_cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
     RRCounters c[kMaxPools];
     HYP_CUDA(cudaMemcpyAsync(c, g->d_counters, sizeof(RRCounters) * kMaxPools, cudaMemcpyDeviceToHost, s));
     // compaction, pool by pool: CSR offsets by an exclusive scan of the sizes
     int64_t* d_boff = nullptr;
-    if ((st = dev_alloc(g, (void**)&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
+    if ((st = tmp.alloc(&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
     for (int q = 0; q < npools; ++q) {
         hyperim_pool* p = pools[q];
         const int64_t b0 = pool_start[q], nq = pool_start[q + 1] - b0;
@@ -1606,15 +1673,12 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         p->counters.selected += c[q].selected;
         p->counters.gathered += c[q].gathered;
         p->counters.search_words += c[q].search_words;
+        p->counters.sectors += c[q].sectors;
         // the launch's time and count are shared by the pools it grew, in proportion to their jobs
         const double share = (double)nq / (double)njobs;
         p->rr_kernel_seconds += seconds * share;
         if (q == 0) p->rr_launches += (uint64_t)launches;
     }
-    dev_free(g, d_boff, sizeof(int64_t) * ((size_t)njobs + 1));
-    dev_free(g, d_pos, sizeof(int64_t) * (size_t)njobs);
-    dev_free(g, d_size, sizeof(int32_t) * (size_t)njobs);
-    dev_free(g, d_next, sizeof(int) + sizeof(unsigned long long) * 2);
     return check_device_status(g, "RR compaction");
 }
 
@@ -1649,9 +1713,10 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     uint32_t* d_counts = nullptr;
     unsigned long long* d_next = nullptr;
     const size_t kk = (size_t)(k > 0 ? k : 1);
-    if ((st = dev_alloc(g, (void**)&d_seeds, sizeof(int32_t) * kk))) return st;
-    if ((st = dev_alloc(g, (void**)&d_counts, sizeof(uint32_t) * (size_t)nsims))) return st;
-    if ((st = dev_alloc(g, (void**)&d_next, sizeof(unsigned long long)))) return st;
+    CallBuffers tmp(g);
+    if ((st = tmp.alloc(&d_seeds, sizeof(int32_t) * kk))) return st;
+    if ((st = tmp.alloc(&d_counts, sizeof(uint32_t) * (size_t)nsims))) return st;
+    if ((st = tmp.alloc(&d_next, sizeof(unsigned long long)))) return st;
     if (k > 0) HYP_CUDA(cudaMemcpyAsync(d_seeds, seeds_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
     HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
     FwdParams F;
@@ -1663,6 +1728,8 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     P.prof_off = g->prof_off;
     P.prof = g->prof;
     P.tsum = g->tsum;
+    P.he_dir = g->he_dir;
+    P.v_dir = g->v_dir;
     P.n = g->n;
     P.id_bits = g->id_bits;
     P.list = g->scratch.list;
@@ -1672,6 +1739,7 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     P.vis_words = vis_smem ? (int64_t)(((size_t)g->n + 31) / 32) : (int64_t)g->scratch.bitmap_words;
     P.next_job = reinterpret_cast<int*>(d_next);
     P.st = g->d_status;
+    P.spin_limit = wait_rounds(g);
     F.seeds = d_seeds;
     F.k = k;
     F.nsims = nsims;
@@ -1686,9 +1754,6 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     }
     HYP_CUDA(cudaMemcpyAsync(counts_host, d_counts, sizeof(uint32_t) * (size_t)nsims, cudaMemcpyDeviceToHost, s));
     HYP_CUDA(cudaStreamSynchronize(s));
-    dev_free(g, d_seeds, sizeof(int32_t) * kk);
-    dev_free(g, d_counts, sizeof(uint32_t) * (size_t)nsims);
-    dev_free(g, d_next, sizeof(unsigned long long));
     return HYPERIM_OK;
 }
 

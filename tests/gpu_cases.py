@@ -124,8 +124,16 @@ def assert_same_pool(gpu_pool, oracle_pool):
     assert np.array_equal(gpu_pool.view()["n_s"], oracle_pool.counts())
 
 
+def algorithmic_bytes(view):
+    """Cost-model bytes of RR generation from a GPU pool's counters (see hyperim_pool_view_t):
+    32 per sector touched, 8 per hyperedge of a materialising pop, 4 per output id, 8 per set."""
+    return 32 * view["sectors"] + 8 * view["mat_he"] + 4 * view["total"] + 8 * view["count"]
+
+
 def assert_same_counters(gpu_pool, oracle_pool):
     c = gpu_pool.counters()
     o = oracle_pool.stats()
     for k in ("pops", "layers_seen", "draws", "mats", "mat_he", "mat_members", "selected"):
         assert c[k] == o[k], (k, c[k], o[k])
+    b = algorithmic_bytes(gpu_pool.view())
+    assert b == o["bytes_rr"], ("algorithmic bytes", b, o["bytes_rr"])
