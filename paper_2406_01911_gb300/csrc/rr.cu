@@ -38,6 +38,10 @@ constexpr int kChunks = 1024;        // first-level id chunks of the largest nei
 constexpr int kVisSmemBits = 1 << 19;  // visited bitmap on chip when n <= this
 constexpr int kMaxPools = 2;           // pools grown by one launch (R1 and R2 of a BRR round)
 constexpr int kNStat = 10;             // work counters (stat slots below)
+// warp phase: a warp builds a whole RR set alone while it stays within kWQ members
+constexpr int kWQ = 128;               // per-warp queue (members of the warp's set)
+constexpr int kWHashBits = 9;
+constexpr int kWHash = 1 << kWHashBits;  // per-warp open-addressing member set
 
 struct RRJobMap {
     int64_t job_base[HYPERIM_NSTRATA + 1];
@@ -83,6 +87,9 @@ struct RRParams {
     int64_t* out_pos;
     int32_t* out_size;
     int* next_job;
+    int* esc_count;           // jobs the warp phase handed to the block phase
+    int32_t* esc_list;        // those jobs
+    int block_phase;          // 1: this launch runs the jobs of esc_list (else all jobs)
     int plain;                // 1: this launch runs jobs [plain_base, plain_base + gridDim.x), one per block
     int64_t plain_base;
     DevStatus* st;
@@ -301,6 +308,37 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
     }
 }
 
+// Where a pop's activations go: the block's RR set (visited bitmap and shared work queue), or
+// the RR set a warp builds alone (an open-addressing member set and a queue in shared memory).
+struct BlockSink {
+    const RRParams* P;
+    Shared* S;
+    uint32_t* vis;
+    int32_t* list;
+    __device__ __forceinline__ void push(uint32_t nu) const { hyperim::push(*P, *S, vis, list, nu); }
+};
+
+struct WarpSink {
+    int32_t* hash;   // kWHash slots, -1 empty
+    int32_t* queue;  // kWQ slots
+    int* tail;       // members so far (may pass kWQ: the set then leaves the warp phase)
+    __device__ __forceinline__ void push(uint32_t nu) const {
+        if (*(volatile int*)tail > kWQ) return;  // already too large: the set is redone by a block
+        uint32_t h = (nu * 0x9E3779B1u) >> (32 - kWHashBits);
+        for (int probe = 0; probe < kWHash; ++probe) {
+            const int32_t old = atomicCAS(&hash[h], -1, (int32_t)nu);
+            if (old == -1) {
+                const int pos = atomicAdd(tail, 1);
+                if (pos < kWQ) queue[pos] = (int32_t)nu;
+                return;
+            }
+            if (old == (int32_t)nu) return;
+            h = (h + 1) & (kWHash - 1);
+        }
+        atomicMax(tail, kWQ + 1);  // no free slot (cannot happen below kWQ + 32 members)
+    }
+};
+
 // Work queue of one RR set (lane 0 of a warp). Slots [0, tail) are reserved, [0, head) claimed,
 // done pops are finished (their pushes are in), ndef claimed pops wait for the block path.
 // Returns a claimed slot, or -1 when this warp should go to the block barrier: no pop is in
@@ -345,7 +383,8 @@ __device__ int32_t slot_value(const RRParams& P, const int32_t* list, int idx, i
 // members: a raw copy goes to buf[kWHalf, kWHalf + tsum) and the members are counted into
 // buckets of their top id bits; the raw copy is then scattered into buf[0, T) in bucket order and
 // each bucket is sorted (members sorted by id).
-__device__ void small_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_begin, int32_t dh, int tsum,
+template <class SM>
+__device__ void small_nbhd(const RRParams& P, SM& S, int32_t mu, int32_t v_begin, int32_t dh, int tsum,
                            int T, uint32_t* buf) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* bkt = S.u.w.wbkt[wid];
@@ -385,7 +424,8 @@ __device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0
 // offset, found the same way). The slices are gathered with independent loads into the raw half
 // of buf and counted into buckets of the id offset within the range, then scattered and sorted as
 // in small_nbhd. probes counts the words read to locate the slices.
-__device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_begin, int32_t dh,
+template <class SM>
+__device__ int chunk_nbhd(const RRParams& P, SM& S, int32_t mu, int32_t v_begin, int32_t dh,
                           uint32_t lo, int sh, uint32_t* buf, uint32_t& probes) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* pre = S.wpre[wid];
@@ -522,8 +562,9 @@ __device__ int chunk_nbhd(const RRParams& P, Shared& S, int32_t mu, int32_t v_be
 // runs of that layer before it; members whose rank is a pick, or all of them when h = n, enter R.
 // The running rank of layer q lives in lane q's register; each 32 positions take one ballot per
 // needed layer. Stops once every layer with picks has ranked past its last pick.
-__device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, const uint32_t* buf,
-                          int got, uint32_t nneed) {
+template <class SM, class Sink>
+__device__ void warp_walk(const RRParams& P, SM& S, const Sink& sink, const uint32_t* buf, int got,
+                          uint32_t nneed) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const Need* need = S.wneed[wid];
     const uint32_t* picks = S.u.w.wpick[wid];
@@ -559,7 +600,7 @@ __device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
             if (f) {
                 const Need nd = need[q];
                 const uint32_t rank = before + __popc(bal & lanemask_lt());
-                if (nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank)) push(P, S, vis, list, x);
+                if (nd.h >= nd.n || in_sorted(picks + poff[q], nd.h, rank)) sink.push(x);
             }
             if ((uint32_t)lane == q) mycnt = before + __popc(bal);
         }
@@ -570,8 +611,8 @@ __device__ void warp_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* 
 }
 
 // Returns true when the pop must be handed to the block path.
-__device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
-                         uint32_t ybase, int32_t mu) {
+template <class SM, class Sink>
+__device__ bool pop_warp(const RRParams& P, SM& S, const Sink& sink, uint32_t j, uint32_t ybase, int32_t mu) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 vi = P.vinfo[mu];
     const int32_t pb = vi.x, l = vi.y, v_begin = vi.z, dh = vi.w;
@@ -684,11 +725,11 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
         const Need nd = need[0];
         if (nd.h >= nd.n) {
             for (int x = lane; x < len - 1; x += 32)
-                push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+                sink.push((uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
         } else {
             for (uint32_t r = lane; r < nd.h; r += 32) {
                 const uint32_t x = picks[r];
-                push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+                sink.push((uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
             }
         }
         __syncwarp();
@@ -729,7 +770,7 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
                 return false;
             }
             gath += (unsigned long long)got;
-            warp_walk(P, S, vis, list, buf, got, nneed);
+            warp_walk(P, S, sink, buf, got, nneed);
             ++chunks;
             if (cur == k) {
                 const uint32_t endk = (int)k + 1 < C ? row[k + 1] : nd.n;  // members of L_q before chunk k + 1
@@ -766,7 +807,7 @@ __device__ bool pop_warp(const RRParams& P, Shared& S, uint32_t* vis, int32_t* l
     }
     for (uint32_t q = lane; q < nneed; q += 32) cnt[q] = 0;
     __syncwarp();
-    warp_walk(P, S, vis, list, buf, got, nneed);
+    warp_walk(P, S, sink, buf, got, nneed);
     return false;
 }
 
@@ -1192,8 +1233,142 @@ __global__ void __launch_bounds__(kThreads, 2) k_forward(FwdParams F) {
 }
 
 // ------------------------------------------------------------------------------------------
-// the kernel
+// the kernels
 // ------------------------------------------------------------------------------------------
+// A job (an RR set of one of the launch's pools): its pool, stratum, index j in the stratum and
+// the y word of its Philox counters.
+struct Job {
+    int pi, s;
+    uint32_t j, ybase;
+};
+
+__device__ __forceinline__ Job decode_job(const RRParams& P, int64_t job) {
+    Job J;
+    J.pi = 0;
+    while (J.pi + 1 < P.npools && job >= P.pool_start[J.pi + 1]) ++J.pi;
+    const RRJobMap& jm = P.jm[J.pi];
+    const int64_t local = job - P.pool_start[J.pi];
+    J.s = 0;
+    while (J.s < HYPERIM_NSTRATA - 1 && local >= jm.job_base[J.s + 1]) ++J.s;
+    J.j = jm.j_base[J.s] + (uint32_t)(local - jm.job_base[J.s]);
+    const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)J.s;
+    J.ybase = stream_ybase(P.tags[J.pi], sfield);
+    return J;
+}
+
+// the root of a job: uniform over its stratum (multiply-shift of one word), or over V
+__device__ __forceinline__ int32_t draw_root(const RRParams& P, const Job& J) {
+    WordStream ws;
+    ws.init(P.seed, J.j, J.ybase, 0xFFFFFFFFu, 0u);
+    const uint32_t w0 = ws.word(0);
+    if (P.root_mode == HYPERIM_ROOTS_PLAIN) return (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)P.n) >> 32);
+    const int32_t b = P.vs_off[J.s], size = P.vs_off[J.s + 1] - b;
+    return P.vs_list[b + (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)size) >> 32)];
+}
+
+// Shared memory of the warp phase: the warp-path buffers of every warp, plus each warp's own
+// RR set (member set, queue, size).
+struct WarpShared {
+    unsigned long long stat[kMaxPools][kNStat];  // per pool work counters of this block
+    unsigned long long wstat[kWarps][kNStat];    // per-warp counters of the warp's current set
+    Need wneed[kWarps][kLQ];
+    int wpre[kWarps][3 * 32 + 1];
+    uint32_t wpoff[kWarps][kLQ + 1];
+    int wcnt[kWarps][kBLQ];
+    int wtail[kWarps];
+    int32_t whash[kWarps][kWHash];
+    int32_t wqueue[kWarps][kWQ];
+    union {
+        WarpArea w;
+    } u;
+};
+
+// Warp phase of RR generation: every warp takes jobs from the launch's counter and builds each
+// RR set alone -- pops in queue order, activations into its own member set -- while the set
+// stays within kWQ members and no pop needs the block path. Such sets are written out at once;
+// any other job is listed for the block phase (k_rr with block_phase), which builds it again
+// from its root (the draws are keyed by (RR, vertex, layer), so the set is the same) and the warp's
+// partial counters are dropped. Jobs are taken from the last one down, as in k_rr.
+__global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpShared& S = *reinterpret_cast<WarpShared*>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t njobs = P.pool_start[P.npools];
+    if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kWarps * kWHash; i += kThreads) (&S.whash[0][0])[i] = -1;
+    __syncthreads();
+    int32_t* hash = S.whash[wid];
+    int32_t* queue = S.wqueue[wid];
+    int* tail = &S.wtail[wid];
+    const WarpSink sink{hash, queue, tail};
+    unsigned long long* wst = S.wstat[wid];
+    for (;;) {
+        int64_t ticket = 0;
+        if (lane == 0) ticket = atomicAdd(P.next_job, 1);
+        ticket = __shfl_sync(0xFFFFFFFFu, ticket, 0);
+        if (ticket >= njobs) break;
+        const int64_t job = njobs - 1 - ticket;
+        const Job J = decode_job(P, job);
+        if (lane == 0) {
+            const int32_t root = draw_root(P, J);
+            *tail = 0;
+            sink.push((uint32_t)root);
+        }
+        __syncwarp();
+        bool escalate = false;
+        for (int head = 0;; ++head) {
+            const int t = *(volatile int*)tail;
+            if (t > kWQ) { escalate = true; break; }
+            if (head >= t) break;
+            const int32_t mu = queue[head];
+            if (pop_warp(P, S, sink, J.j, J.ybase, mu)) { escalate = true; break; }
+            __syncwarp();
+            if (*(volatile int32_t*)&P.st->code != 0) break;  // a failure elsewhere: stop early
+        }
+        __syncwarp();
+        const int size = min(*(volatile int*)tail, kWQ);
+        if (escalate) {
+            if (lane == 0) P.esc_list[atomicAdd(P.esc_count, 1)] = (int32_t)job;
+        } else {
+            // output: the members in ascending order
+            uint32_t* buf = S.u.w.wbuf[wid];
+            for (int i = lane; i < size; i += 32) buf[i] = (uint32_t)queue[i];
+            __syncwarp();
+            group_sort<32>(buf, size);
+            unsigned long long pos = 0;
+            if (lane == 0) {
+                pos = atomicAdd(P.arena_used, (unsigned long long)size);
+                P.out_pos[job] = (int64_t)pos;
+                P.out_size[job] = size;
+            }
+            pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+            if (pos + (unsigned long long)size <= P.arena_cap)
+                for (int i = lane; i < size; i += 32) P.arena[pos + i] = (int32_t)buf[i];
+            if (lane < kNStat) atomicAdd(&S.stat[J.pi][lane], wst[lane]);
+        }
+        __syncwarp();
+        if (lane < kNStat) wst[lane] = 0;
+        for (int i = lane; i < kWHash; i += 32) hash[i] = -1;
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < P.npools) {
+        RRCounters* c = P.counters + threadIdx.x;
+        const unsigned long long* st = S.stat[threadIdx.x];
+        atomicAdd(&c->pops, st[S_POPS]);
+        atomicAdd(&c->layers_seen, st[S_LAYERS]);
+        atomicAdd(&c->draws, st[S_DRAWS]);
+        atomicAdd(&c->mats, st[S_MATS]);
+        atomicAdd(&c->mat_he, st[S_MAT_HE]);
+        atomicAdd(&c->mat_members, st[S_MAT_MEM]);
+        atomicAdd(&c->selected, st[S_SEL]);
+        atomicAdd(&c->gathered, st[S_GATH]);
+        atomicAdd(&c->search_words, st[S_SRCH]);
+        atomicAdd(&c->sectors, st[S_SECT]);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
@@ -1203,7 +1378,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
     uint32_t* picks_g = P.picks + (int64_t)blockIdx.x * P.pick_cap;
     uint32_t* big = P.big + (int64_t)blockIdx.x * P.big_cap;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t njobs = P.pool_start[P.npools];
+    const int64_t njobs = P.block_phase ? (int64_t)*(volatile int*)P.esc_count : P.pool_start[P.npools];
     if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
@@ -1218,34 +1393,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
                 S.ctrl[C_JOB] = (int)plain_ticket;
                 plain_ticket = njobs;
             } else {
-                S.ctrl[C_JOB] = atomicAdd(P.next_job, 1);
+                S.ctrl[C_JOB] = atomicAdd(P.next_job + P.block_phase, 1);
             }
         }
         __syncthreads();
         const int64_t ticket = S.ctrl[C_JOB];
         if (ticket >= njobs) break;
-        const int64_t job = njobs - 1 - ticket;
-        int pi = 0;
-        while (pi + 1 < P.npools && job >= P.pool_start[pi + 1]) ++pi;
-        const RRJobMap& jm = P.jm[pi];
-        const int64_t local = job - P.pool_start[pi];
-        int s = 0;
-        while (s < HYPERIM_NSTRATA - 1 && local >= jm.job_base[s + 1]) ++s;
-        const uint32_t j = jm.j_base[s] + (uint32_t)(local - jm.job_base[s]);
-        const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)s;
-        const uint32_t ybase = stream_ybase(P.tags[pi], sfield);
+        // the block phase takes the jobs the warp phase listed, in listed order
+        const int64_t job = P.block_phase ? (int64_t)P.esc_list[ticket] : njobs - 1 - ticket;
+        const Job J = decode_job(P, job);
+        const int pi = J.pi;
+        const uint32_t j = J.j, ybase = J.ybase;
         if (threadIdx.x == 0) {
-            // root: uniform over the stratum (multiply-shift of one word)
-            WordStream ws;
-            ws.init(P.seed, j, ybase, 0xFFFFFFFFu, 0u);
-            const uint32_t w0 = ws.word(0);
-            int32_t root;
-            if (P.root_mode == HYPERIM_ROOTS_PLAIN) {
-                root = (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)P.n) >> 32);
-            } else {
-                const int32_t b = P.vs_off[s], size = P.vs_off[s + 1] - b;
-                root = P.vs_list[b + (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)size) >> 32)];
-            }
+            const int32_t root = draw_root(P, J);
             list[0] = root;
             vis[root >> 5] |= 1u << (root & 31);
             S.ctrl[C_HEAD] = 0;
@@ -1266,7 +1426,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
                 int32_t mu = 0;
                 if (lane == 0) mu = slot_value(P, list, idx, job);
                 mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
-                const bool defer = mu >= 0 && pop_warp(P, S, vis, list, j, ybase, mu);
+                const bool defer = mu >= 0 && pop_warp(P, S, BlockSink{&P, &S, vis, list}, j, ybase, mu);
                 __syncwarp();
                 if (lane == 0) {
                     if (defer) {
@@ -1430,6 +1590,8 @@ hyperim_status allow_rr_smem() {
         const int most = (int)(sizeof(Shared) + kVisSmemBits / 8);
         err = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_rr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WarpShared));
     });
     HYP_CUDA(err);
     return HYPERIM_OK;
@@ -1526,15 +1688,32 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         want_d += (double)(pool_start[q + 1] - pool_start[q]) * hint * 1.25;
     }
     uint64_t want = (uint64_t)want_d;
+    // the warp phase (one RR set per warp) runs first in the persistent schedule; its grid
+    const bool warp_phase = g->schedule != HYPERIM_SCHED_PLAIN;
+    int wblocks = 0;
+    if (warp_phase) {
+        int wper_sm = 0;
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper_sm, k_rr_warp, kThreads, sizeof(WarpShared)));
+        if (wper_sm < 1) return set_error(HYPERIM_ECUDA, "RR warp-phase kernel does not fit on an SM");
+        wblocks = (int)std::min<int64_t>((int64_t)g->sm_count * wper_sm, (njobs + kWarps - 1) / kWarps);
+    }
+    // control words: two job counters (warp phase, block phase), the listed jobs, the arena fill
+    struct Ctrl {
+        int next_job[2];
+        int esc_count;
+        int pad;
+        unsigned long long arena_used;
+    };
     int64_t* d_pos = nullptr;
     int32_t* d_size = nullptr;
-    int* d_next = nullptr;
-    unsigned long long* d_used = nullptr;
+    int32_t* d_esc = nullptr;
+    Ctrl* d_ctrl = nullptr;
     CallBuffers tmp(g);
     if ((st = tmp.alloc(&d_pos, sizeof(int64_t) * (size_t)njobs))) return st;
     if ((st = tmp.alloc(&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
-    if ((st = tmp.alloc(&d_next, sizeof(int) + sizeof(unsigned long long) * 2))) return st;
-    d_used = reinterpret_cast<unsigned long long*>(d_next + 2);
+    if ((st = tmp.alloc(&d_esc, sizeof(int32_t) * (size_t)njobs))) return st;
+    if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
+    unsigned long long* d_used = &d_ctrl->arena_used;
     RRParams P;
     P.vinfo = g->vinfo;
     P.v_span = g->v_span;
@@ -1572,7 +1751,10 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.big_cap = (int64_t)g->scratch.big_cap;
     P.out_pos = d_pos;
     P.out_size = d_size;
-    P.next_job = d_next;
+    P.next_job = d_ctrl->next_job;
+    P.esc_count = &d_ctrl->esc_count;
+    P.esc_list = d_esc;
+    P.block_phase = 0;
     P.plain = g->schedule == HYPERIM_SCHED_PLAIN ? 1 : 0;
     P.plain_base = 0;
     P.arena_used = d_used;
@@ -1603,7 +1785,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         }
         P.arena = g->scratch.arena;
         P.arena_cap = g->scratch.arena_cap;
-        HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int) + sizeof(unsigned long long) * 2, s));
+        HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
         HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
         HYP_CUDA(cudaEventRecord(ev0, s));
         if (P.plain) {
@@ -1616,7 +1798,13 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
                 ++launches;
             }
         } else {
+            // warp phase over every job, then the block phase over the jobs it listed
+            P.block_phase = 0;
+            { k_rr_warp<<<wblocks, kThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
+            HYP_CUDA(cudaGetLastError());
+            P.block_phase = 1;
             { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+            P.block_phase = 0;
             ++launches;
         }
         HYP_CUDA(cudaGetLastError());
