@@ -202,6 +202,26 @@ typedef enum { HYPERIM_SCHED_PERSISTENT = 0, HYPERIM_SCHED_PLAIN = 1 } hyperim_s
 hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_graph_set_tuning / hyperim_graph_get_tuning -- scheduling parameters of RR generation
+ *   on this handle (shares made afterwards inherit them). None changes any RR set, seed or
+ *   estimate: the draws are keyed by (RR, vertex, layer), so only the time differs.
+ *   warp_set_limit: in the persistent schedule every RR set is first built by one warp alone
+ *     (its members in on-chip memory) while it has at most this many members (1..128) and no
+ *     pop needs the block path; larger sets are built again by a whole block. 0: every set by a
+ *     block (no warp phase). Default 128.
+ *   early_sets_per_block: BRR (hyperim_select_seeds) grows R1 and R2 in its first launch to at
+ *     least this many sets per resident block of the RR kernel per pool (the rounds up to that
+ *     theta read their prefixes of it). >= 1; default 4.
+ *   EINVAL: g or t NULL, a value out of range. No device work.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t warp_set_limit;
+    int32_t early_sets_per_block;
+} hyperim_tuning;
+hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning* t);
+hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_graph_set_wait_limit -- bound of the device-side waits of this handle's kernels (a
  *   warp of the RR or forward kernel waiting for its block's work queue: a claimable vertex, or
  *   the id of a claimed slot still being stored). A wait that runs `iterations` rounds without

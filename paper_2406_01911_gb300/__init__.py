@@ -77,6 +77,10 @@ class PoolView(C.Structure):
                 ("sectors", C.c_uint64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32)]
+
+
 class SelectOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("eps", C.c_double), ("ell", C.c_double),
                 ("theta_cap", C.c_uint64), ("root_mode", C.c_int32), ("strategy", C.c_int32),
@@ -125,6 +129,8 @@ _SIGNATURES = {
     "hyperim_graph_profile": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hyperim_graph_set_schedule": (C.c_int, [_vp, C.c_int32]),
     "hyperim_graph_set_wait_limit": (C.c_int, [_vp, C.c_uint32]),
+    "hyperim_graph_set_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
+    "hyperim_graph_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
     "hyperim_graph_share": (C.c_int, [_vp, _vp, C.POINTER(_vp)]),
     "hyperim_server_create": (C.c_int, [C.POINTER(ServerArgs), C.POINTER(_vp)]),
     "hyperim_server_add_graph": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
@@ -379,6 +385,18 @@ class Graph:
         g = Graph.__new__(Graph)
         g.n, g.model, g._h, g.parent = self.n, self.model, h, self
         return g
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().hyperim_graph_get_tuning(self._h, C.byref(t)))
+        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block}
+
+    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None):
+        """RR-generation scheduling (hyperim_graph_set_tuning); the results never change."""
+        cur = self.tuning()
+        t = Tuning(int(cur["warp_set_limit"] if warp_set_limit is None else warp_set_limit),
+                   int(cur["early_sets_per_block"] if early_sets_per_block is None else early_sets_per_block))
+        _check(lib().hyperim_graph_set_tuning(self._h, C.byref(t)))
 
     def set_wait_limit(self, iterations):
         """Bound of the device-side waits of this handle's kernels (0: the default, 2^24 rounds);

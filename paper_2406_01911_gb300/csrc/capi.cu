@@ -374,6 +374,8 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->sm_count = r->sm_count;
     h->schedule = r->schedule;
     h->wait_limit = r->wait_limit;
+    h->warp_set_limit = r->warp_set_limit;
+    h->early_sets_per_block = r->early_sets_per_block;
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -469,6 +471,23 @@ hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule) {
     if (schedule != HYPERIM_SCHED_PERSISTENT && schedule != HYPERIM_SCHED_PLAIN)
         return set_error(HYPERIM_EINVAL, "unknown schedule");
     g->schedule = schedule;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning* t) {
+    if (!g || !t) return set_error(HYPERIM_EINVAL, "null argument");
+    if (t->warp_set_limit < 0 || t->warp_set_limit > 128) return set_error(HYPERIM_EINVAL, "warp_set_limit outside [0, 128]");
+    if (t->early_sets_per_block < 1 || t->early_sets_per_block > 4096)
+        return set_error(HYPERIM_EINVAL, "early_sets_per_block outside [1, 4096]");
+    g->warp_set_limit = t->warp_set_limit;
+    g->early_sets_per_block = t->early_sets_per_block;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out) {
+    if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    out->warp_set_limit = g->warp_set_limit;
+    out->early_sets_per_block = g->early_sets_per_block;
     return HYPERIM_OK;
 }
 
@@ -691,7 +710,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     // kernel for R1 and R2 together) so that those rounds share one launch. Rounds read only
     // their own prefix, so the result is the same; sets beyond the last round's theta are
     // generated but unused when BRR stops before theta_early.
-    uint64_t theta_early = 4 * (uint64_t)std::max(g->sm_count, 1);
+    uint64_t theta_early = (uint64_t)std::max(g->early_sets_per_block, 1) * (uint64_t)std::max(g->sm_count, 1);
     if (plan.i_max < 40) theta_early = std::min<uint64_t>(theta_early, plan.theta0 << plan.i_max);
     if (opts->theta_cap) theta_early = std::min<uint64_t>(theta_early, opts->theta_cap);
     for (int32_t i = 0;; ++i) {

@@ -90,6 +90,9 @@ struct RRParams {
     int* esc_count;           // jobs the warp phase handed to the block phase
     int32_t* esc_list;        // those jobs
     int block_phase;          // 1: this launch runs the jobs of esc_list (else all jobs)
+    struct SetCtl* sctl;      // block phase with helping: one set-control record per block
+    int32_t* gdefer;          // block phase with helping: kDCapG deferred pops per block (a ring)
+    int warp_limit;           // warp phase: the largest RR set a warp builds alone (1..kWQ)
     int plain;                // 1: this launch runs jobs [plain_base, plain_base + gridDim.x), one per block
     int64_t plain_base;
     DevStatus* st;
@@ -308,36 +311,108 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
     }
 }
 
-// Where a pop's activations go: the block's RR set (visited bitmap and shared work queue), or
-// the RR set a warp builds alone (an open-addressing member set and a queue in shared memory).
-struct BlockSink {
-    const RRParams* P;
-    Shared* S;
+// Where a pop's activations go: the RR set of a block (its visited bitmap and work queue, the
+// queue's tail counter in shared memory, or in global memory for a set other blocks may help
+// with), or the RR set a warp builds alone (an open-addressing member set and a queue in shared
+// memory).
+struct QueueSink {
     uint32_t* vis;
     int32_t* list;
-    __device__ __forceinline__ void push(uint32_t nu) const { hyperim::push(*P, *S, vis, list, nu); }
+    int* tail;
+    __device__ __forceinline__ void push(uint32_t nu) const {
+        const uint32_t bit = 1u << (nu & 31);
+        const uint32_t old = atomicOr(&vis[nu >> 5], bit);
+        if (!(old & bit)) {
+            const int pos = atomicAdd(tail, 1);
+            *(volatile int32_t*)&list[pos] = (int32_t)nu;
+        }
+    }
 };
 
 struct WarpSink {
     int32_t* hash;   // kWHash slots, -1 empty
     int32_t* queue;  // kWQ slots
-    int* tail;       // members so far (may pass kWQ: the set then leaves the warp phase)
+    int* tail;       // members so far (may pass limit: the set then leaves the warp phase)
+    int limit;       // the largest set a warp builds alone (<= kWQ)
     __device__ __forceinline__ void push(uint32_t nu) const {
-        if (*(volatile int*)tail > kWQ) return;  // already too large: the set is redone by a block
+        if (*(volatile int*)tail > limit) return;  // already too large: the set is redone by a block
         uint32_t h = (nu * 0x9E3779B1u) >> (32 - kWHashBits);
         for (int probe = 0; probe < kWHash; ++probe) {
             const int32_t old = atomicCAS(&hash[h], -1, (int32_t)nu);
             if (old == -1) {
                 const int pos = atomicAdd(tail, 1);
-                if (pos < kWQ) queue[pos] = (int32_t)nu;
+                if (pos < limit) queue[pos] = (int32_t)nu;
                 return;
             }
             if (old == (int32_t)nu) return;
             h = (h + 1) & (kWHash - 1);
         }
-        atomicMax(tail, kWQ + 1);  // no free slot (cannot happen below kWQ + 32 members)
+        atomicMax(tail, limit + 1);  // no free slot (cannot happen below kWQ + 32 members)
     }
 };
+
+// The RR set a block builds in the helped block phase, with its queue counters in global memory so
+// that blocks without a job of their own can take pops of it. claim packs the set's epoch (bumped
+// at every new set of the block) with the number of queue slots claimed, so a claim never lands
+// in a later set. A claimed pop ends done, or deferred to the owner's block path: reserved in the
+// ring (ndef_res), written, then counted (ndef); the owner runs deferred pops once nothing is in
+// flight and counts them in ndef_done and done.
+struct SetCtl {
+    unsigned long long claim;  // (epoch << 32) | slots claimed in this epoch
+    int tail;                  // members pushed
+    int done;                  // pops finished
+    int ndef_res;              // deferred-ring slots reserved
+    int ndef;                  // deferred pops written
+    int ndef_done;             // deferred pops the owner has run
+    int job;                   // the set's job (valid for the epoch in claim)
+    int active;                // 1 while the owner works on a set
+    int pad;
+};
+constexpr int kDCapG = 8192;       // deferred ring per block
+constexpr int kDClaimMax = 4096;   // no claim while this many deferred pops wait (ring margin)
+constexpr int kHelpIdle = 256;     // empty scans after which a helper block stops
+
+// Claim a queue slot of the set behind c in epoch `epoch` (lane 0). The owner waits (bounded)
+// while pops are in flight and returns -1 once nothing is (quiescent: every claimed pop is done
+// or deferred); a helper never waits: -1 when nothing is claimable or the set is gone.
+__device__ int claim_global(const RRParams& P, SetCtl* c, uint32_t epoch, int64_t job, bool owner) {
+    for (int it = 0; it < P.spin_limit; ++it) {
+        const int d = *(volatile int*)&c->done;
+        __threadfence();
+        const unsigned long long cl = *(volatile unsigned long long*)&c->claim;
+        __threadfence();
+        const int t = *(volatile int*)&c->tail;
+        const int nd = *(volatile int*)&c->ndef, ndd = *(volatile int*)&c->ndef_done;
+        if ((uint32_t)(cl >> 32) != epoch) return -1;  // (a helper) the set is finished
+        const int h = (int)(uint32_t)cl;
+        const int pending = nd - ndd;
+        if (h < t && pending < kDClaimMax) {
+            if (atomicCAS(&c->claim, cl, cl + 1) == cl) {
+                __threadfence();
+                return h;
+            }
+            continue;
+        }
+        if (!owner) return -1;
+        if (h - pending == d) return -1;
+        __nanosleep(64);
+    }
+    if (owner) dev_fail(P.st, kErrSpin, (int32_t)job);
+    return -1;
+}
+
+// A claimed pop of the set behind c ends: counted done, or put in the owner's deferred ring
+__device__ __forceinline__ void end_pop_global(SetCtl* c, int32_t* ring, bool defer, int32_t mu) {
+    if (defer) {
+        const int d = atomicAdd(&c->ndef_res, 1);
+        ring[d & (kDCapG - 1)] = mu;
+        __threadfence();
+        atomicAdd(&c->ndef, 1);
+    } else {
+        __threadfence();  // this pop's pushes before its completion
+        atomicAdd(&c->done, 1);
+    }
+}
 
 // Work queue of one RR set (lane 0 of a warp). Slots [0, tail) are reserved, [0, head) claimed,
 // done pops are finished (their pushes are in), ndef claimed pops wait for the block path.
@@ -835,8 +910,9 @@ __device__ __forceinline__ bool block_done(const Shared& S, uint32_t nq, const u
 // that starts there. Pass A counts the runs of each needed layer per warp, the counts are
 // prefix-summed across warps (on top of the running layer ranks), pass B re-walks and pushes
 // the runs whose rank is a pick. Returns (uniformly) whether all picks have been passed.
-__device__ bool block_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
-                           const uint32_t* buf, int count, uint32_t nq, const uint32_t* picks) {
+template <class Sink>
+__device__ bool block_walk(const RRParams& P, Shared& S, const Sink& sink, const uint32_t* buf, int count,
+                           uint32_t nq, const uint32_t* picks) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int L = (count + kWarps - 1) / kWarps;
     const int s0 = min(count, wid * L), s1 = min(count, s0 + L);
@@ -882,7 +958,7 @@ __device__ bool block_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t*
         if (q >= 0) {
             const Need nd = S.bneed[q];
             const uint32_t rank = (uint32_t)(S.wcnt[wid][q] + rin);
-            if (nd.h >= nd.n || in_sorted(picks + S.bpick_off[q], nd.h, rank)) push(P, S, vis, list, x);
+            if (nd.h >= nd.n || in_sorted(picks + S.bpick_off[q], nd.h, rank)) sink.push(x);
         }
         __syncwarp();
         if (q >= 0 && rin == 0) S.wcnt[wid][q] += __popc(mask);
@@ -892,7 +968,8 @@ __device__ bool block_walk(const RRParams& P, Shared& S, uint32_t* vis, int32_t*
     return block_done(S, nq, picks);
 }
 
-__device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list, uint32_t j,
+template <class Sink>
+__device__ __noinline__ void pop_block(const RRParams& P, Shared& S, const Sink& sink, uint32_t j,
                           uint32_t ybase, int32_t mu, uint32_t* picks_g, uint32_t* big) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 vi = P.vinfo[mu];
@@ -984,11 +1061,11 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
                 const Need nd = S.bneed[0];
                 if (nd.h >= nd.n) {
                     for (int x = threadIdx.x; x < len - 1; x += kThreads)
-                        push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
+                        sink.push((uint32_t)P.he_mem[hb + x + (x >= pmu ? 1 : 0)]);
                 } else {
                     for (uint32_t r = threadIdx.x; r < nd.h; r += kThreads) {
                         const uint32_t x = picks_g[r];
-                        push(P, S, vis, list, (uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
+                        sink.push((uint32_t)P.he_mem[hb + x + ((int)x >= pmu ? 1 : 0)]);
                     }
                 }
                 __syncthreads();
@@ -998,7 +1075,7 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
                     const int got = sorted_nbhd<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, T,
                                                           P.id_bits, S.u.b.bbuf, S.u.b.bucket,
                                                           kBucketBits, S.bpre, S.tmp);
-                    block_walk(P, S, vis, list, S.u.b.bbuf, got, nq, picks_g);
+                    block_walk(P, S, sink, S.u.b.bbuf, got, nq, picks_g);
                 } else if ((int64_t)T > P.big_cap) {
                     if (threadIdx.x == 0) dev_fail(P.st, kErrCapacity, mu);
                 } else {
@@ -1057,7 +1134,7 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, uint32_t* v
                             if (cnt > 0) {
                                 sort_chunk<kThreads>(big + begin, cnt, shift, S.u.b.bbuf, S.u.b.bucket,
                                                      kBucketBits, S.tmp);
-                                const bool stop = block_walk(P, S, vis, list, S.u.b.bbuf, cnt, nq, picks_g);
+                                const bool stop = block_walk(P, S, sink, S.u.b.bbuf, cnt, nq, picks_g);
                                 if (stop) break;
                             }
                             begin = end;
@@ -1301,7 +1378,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
     int32_t* hash = S.whash[wid];
     int32_t* queue = S.wqueue[wid];
     int* tail = &S.wtail[wid];
-    const WarpSink sink{hash, queue, tail};
+    const WarpSink sink{hash, queue, tail, P.warp_limit};
     unsigned long long* wst = S.wstat[wid];
     for (;;) {
         int64_t ticket = 0;
@@ -1319,7 +1396,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
         bool escalate = false;
         for (int head = 0;; ++head) {
             const int t = *(volatile int*)tail;
-            if (t > kWQ) { escalate = true; break; }
+            if (t > P.warp_limit) { escalate = true; break; }
             if (head >= t) break;
             const int32_t mu = queue[head];
             if (pop_warp(P, S, sink, J.j, J.ybase, mu)) { escalate = true; break; }
@@ -1327,7 +1404,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
             if (*(volatile int32_t*)&P.st->code != 0) break;  // a failure elsewhere: stop early
         }
         __syncwarp();
-        const int size = min(*(volatile int*)tail, kWQ);
+        const int size = min(*(volatile int*)tail, P.warp_limit);
         if (escalate) {
             if (lane == 0) P.esc_list[atomicAdd(P.esc_count, 1)] = (int32_t)job;
         } else {
@@ -1366,6 +1443,253 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
         atomicAdd(&c->gathered, st[S_GATH]);
         atomicAdd(&c->search_words, st[S_SRCH]);
         atomicAdd(&c->sectors, st[S_SECT]);
+    }
+}
+
+// Output of a finished RR set of `size` members (its queue holds them, its visited bitmap marks
+// them): an arena slot for the job, the members in ascending order (sorted on chip up to kBCap,
+// else read off the bitmap in id order), and the bitmap cleared again. Whole block.
+__device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int32_t* list, int size, int64_t job) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        const unsigned long long pos = atomicAdd(P.arena_used, (unsigned long long)size);
+        P.out_pos[job] = (int64_t)pos;
+        P.out_size[job] = size;
+        S.ctrl[C_ROOT] = pos + (unsigned long long)size <= P.arena_cap ? 1 : 0;
+        S.out_pos = pos;
+    }
+    __syncthreads();
+    const bool fits = S.ctrl[C_ROOT] != 0;
+    const unsigned long long pos = S.out_pos;
+    if (size <= kBCap) {
+        for (int i = threadIdx.x; i < size; i += kThreads) S.u.b.bbuf[i] = (uint32_t)list[i];
+        __syncthreads();
+        group_sort<kThreads>(S.u.b.bbuf, size);
+        if (fits)
+            for (int i = threadIdx.x; i < size; i += kThreads) P.arena[pos + i] = (int32_t)S.u.b.bbuf[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < size; i += kThreads) vis[S.u.b.bbuf[i] >> 5] = 0;
+    } else {
+        // R is large: read it off the visited bitmap in id order
+        const int64_t nwords = ((int64_t)P.n + 31) >> 5;
+        int64_t carry = 0;
+        for (int64_t b0 = 0; b0 < nwords; b0 += kThreads) {
+            const int64_t wi = b0 + threadIdx.x;
+            const uint32_t word = wi < nwords ? vis[wi] : 0u;
+            int total;
+            // exclusive sum of popcounts across the block
+            const int c = __popc(word);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) S.tmp[wid] = incl;
+            __syncthreads();
+            int woff = 0;
+            total = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                woff += w < wid ? S.tmp[w] : 0;
+                total += S.tmp[w];
+            }
+            __syncthreads();
+            int64_t o = carry + woff + incl - c;
+            uint32_t bits = word;
+            while (bits) {
+                const int bpos = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (fits) P.arena[pos + o] = (int32_t)(wi * 32 + bpos);
+                ++o;
+            }
+            carry += total;
+        }
+        __syncthreads();
+        for (int64_t w = threadIdx.x; w < nwords; w += kThreads) vis[w] = 0;
+    }
+}
+
+// Block phase with helping (graphs whose visited bitmaps live in global memory): each block
+// builds the listed jobs it takes, as in k_rr but with its set's queue counters in SetCtl; a
+// block without a job left helps the block whose set has the most claimable slots, popping with
+// its own warps into that set's queue and bitmap (the draws are keyed by (RR, vertex, layer), so
+// who pops a vertex does not matter), until it finds no claimable slot in kHelpIdle scans.
+__global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+    const int b = blockIdx.x;
+    uint32_t* vis = P.gvis + (int64_t)b * P.vis_words;
+    int32_t* list = P.list + (int64_t)b * P.list_cap;
+    uint32_t* picks_g = P.picks + (int64_t)b * P.pick_cap;
+    uint32_t* big = P.big + (int64_t)b * P.big_cap;
+    int32_t* ring = P.gdefer + (int64_t)b * kDCapG;
+    SetCtl* c = P.sctl + b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t njobs = (int64_t)*(volatile int*)P.esc_count;
+    if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
+    for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
+    __syncthreads();
+    uint32_t epoch = 0;
+    // own jobs
+    for (;;) {
+        if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job + 1, 1);
+        __syncthreads();
+        const int64_t ticket = S.ctrl[C_JOB];
+        if (ticket >= njobs) break;
+        const int64_t job = (int64_t)P.esc_list[ticket];
+        const Job J = decode_job(P, job);
+        ++epoch;
+        if (threadIdx.x == 0) {
+            const int32_t root = draw_root(P, J);
+            list[0] = root;
+            vis[root >> 5] |= 1u << (root & 31);
+            c->tail = 1;
+            c->done = 0;
+            c->ndef_res = 0;
+            c->ndef = 0;
+            c->ndef_done = 0;
+            c->job = (int)job;
+            c->active = 1;
+            __threadfence();
+            atomicExch(&c->claim, (unsigned long long)epoch << 32);
+        }
+        __syncthreads();
+        const QueueSink sink{vis, list, &c->tail};
+        for (;;) {
+            for (;;) {
+                int idx = 0;
+                if (lane == 0) idx = claim_global(P, c, epoch, job, true);
+                idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+                if (idx < 0) break;
+                int32_t mu = 0;
+                if (lane == 0) mu = slot_value(P, list, idx, job);
+                mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
+                const bool defer = mu >= 0 && pop_warp(P, S, sink, J.j, J.ybase, mu);
+                __syncwarp();
+                if (lane == 0) end_pop_global(c, ring, defer, mu);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int nd = *(volatile int*)&c->ndef, ndd = *(volatile int*)&c->ndef_done;
+                S.ctrl[C_NDEF] = nd;
+                S.ctrl[C_CURSOR] = ndd;
+                S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0;
+                S.ctrl[C_STOP] = *(volatile int*)&c->done == *(volatile int*)&c->tail;
+            }
+            __syncthreads();
+            if (S.ctrl[C_STOP] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
+            const int nd = S.ctrl[C_NDEF], ndd = S.ctrl[C_CURSOR];
+            for (int d = ndd; d < nd; ++d)
+                pop_block(P, S, sink, J.j, J.ybase, ring[d & (kDCapG - 1)], picks_g, big);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                c->ndef_done = nd;
+                __threadfence();
+                atomicAdd(&c->done, nd - ndd);
+            }
+            __syncthreads();
+        }
+        // counters of this set (its helpers flush their own), then the output
+        if (threadIdx.x < kNStat) {
+            unsigned long long sum = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                sum += S.wstat[w][threadIdx.x];
+                S.wstat[w][threadIdx.x] = 0;
+            }
+            S.stat[J.pi][threadIdx.x] += sum;
+        }
+        const int size = *(volatile int*)&c->tail;
+        __syncthreads();
+        write_set(P, S, vis, list, size, job);
+        for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        c->active = 0;
+        __threadfence();
+    }
+    // help the other blocks' sets
+    for (int idle = 0; idle < kHelpIdle;) {
+        if (wid == 0) {
+            int best = -1, bl = 0, anyact = 0;
+            uint32_t be = 0;
+            for (int o = lane; o < (int)gridDim.x; o += 32) {
+                const SetCtl* oc = P.sctl + o;
+                const unsigned long long cl = *(volatile const unsigned long long*)&oc->claim;
+                const int t = *(volatile const int*)&oc->tail;
+                const int act = *(volatile const int*)&oc->active;
+                anyact |= act;
+                const int backlog = act ? t - (int)(uint32_t)cl : 0;
+                if (backlog > bl) { bl = backlog; best = o; be = (uint32_t)(cl >> 32); }
+            }
+            anyact = __any_sync(0xFFFFFFFFu, anyact != 0);
+            for (int off = 16; off > 0; off >>= 1) {
+                const int obl = __shfl_down_sync(0xFFFFFFFFu, bl, off);
+                const int ob = __shfl_down_sync(0xFFFFFFFFu, best, off);
+                const uint32_t oe = __shfl_down_sync(0xFFFFFFFFu, be, off);
+                if (obl > bl || (obl == bl && obl > 0 && ob < best)) { bl = obl; best = ob; be = oe; }
+            }
+            if (lane == 0) {
+                S.ctrl[C_ROOT] = best;
+                S.ctrl[C_BITS] = (int)be;
+                // stop on a failure, or once no block has a set left to help with
+                S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0 || !anyact;
+            }
+        }
+        __syncthreads();
+        const int tb = S.ctrl[C_ROOT];
+        const uint32_t te = (uint32_t)S.ctrl[C_BITS];
+        if (S.ctrl[C_FAIL]) break;
+        __syncthreads();
+        if (tb < 0) {
+            ++idle;
+            __nanosleep(2000);
+            continue;
+        }
+        idle = 0;
+        SetCtl* tc = P.sctl + tb;
+        int32_t* tlist = P.list + (int64_t)tb * P.list_cap;
+        int32_t* tring = P.gdefer + (int64_t)tb * kDCapG;
+        const QueueSink tsink{P.gvis + (int64_t)tb * P.vis_words, tlist, &tc->tail};
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = claim_global(P, tc, te, -1, false);
+            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+            if (idx < 0) break;
+            int64_t job = 0;
+            int32_t mu = 0;
+            if (lane == 0) {
+                job = *(volatile int*)&tc->job;
+                mu = slot_value(P, tlist, idx, job);
+            }
+            job = __shfl_sync(0xFFFFFFFFu, job, 0);
+            mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
+            const Job J = decode_job(P, job);
+            const bool defer = mu >= 0 && pop_warp(P, S, tsink, J.j, J.ybase, mu);
+            __syncwarp();
+            if (lane == 0) end_pop_global(tc, tring, defer, mu);
+            if (lane < kNStat) {
+                atomicAdd(&S.stat[J.pi][lane], S.wstat[wid][lane]);
+                S.wstat[wid][lane] = 0;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x < P.npools) {
+        RRCounters* cc = P.counters + threadIdx.x;
+        const unsigned long long* st = S.stat[threadIdx.x];
+        atomicAdd(&cc->pops, st[S_POPS]);
+        atomicAdd(&cc->layers_seen, st[S_LAYERS]);
+        atomicAdd(&cc->draws, st[S_DRAWS]);
+        atomicAdd(&cc->mats, st[S_MATS]);
+        atomicAdd(&cc->mat_he, st[S_MAT_HE]);
+        atomicAdd(&cc->mat_members, st[S_MAT_MEM]);
+        atomicAdd(&cc->selected, st[S_SEL]);
+        atomicAdd(&cc->gathered, st[S_GATH]);
+        atomicAdd(&cc->search_words, st[S_SRCH]);
+        atomicAdd(&cc->sectors, st[S_SECT]);
     }
 }
 
@@ -1426,7 +1750,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
                 int32_t mu = 0;
                 if (lane == 0) mu = slot_value(P, list, idx, job);
                 mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
-                const bool defer = mu >= 0 && pop_warp(P, S, BlockSink{&P, &S, vis, list}, j, ybase, mu);
+                const bool defer = mu >= 0 && pop_warp(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, mu);
                 __syncwarp();
                 if (lane == 0) {
                     if (defer) {
@@ -1442,7 +1766,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
             if (S.ctrl[C_DONE] == S.ctrl[C_TAIL] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
             // the block materialises the deferred pops
             const int ndef = S.ctrl[C_NDEF];
-            for (int d = 0; d < ndef; ++d) pop_block(P, S, vis, list, j, ybase, S.deferred[d], picks_g, big);
+            for (int d = 0; d < ndef; ++d)
+                pop_block(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, S.deferred[d], picks_g, big);
             __syncthreads();
             if (threadIdx.x == 0) {
                 S.ctrl[C_DONE] += ndef;
@@ -1461,61 +1786,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
         }
         // output: members in ascending order
         const int size = S.ctrl[C_TAIL];
-        if (threadIdx.x == 0) {
-            const unsigned long long pos = atomicAdd(P.arena_used, (unsigned long long)size);
-            P.out_pos[job] = (int64_t)pos;
-            P.out_size[job] = size;
-            S.ctrl[C_ROOT] = pos + (unsigned long long)size <= P.arena_cap ? 1 : 0;
-            S.out_pos = pos;
-        }
-        __syncthreads();
-        const bool fits = S.ctrl[C_ROOT] != 0;
-        const unsigned long long pos = S.out_pos;
-        if (size <= kBCap) {
-            for (int i = threadIdx.x; i < size; i += kThreads) S.u.b.bbuf[i] = (uint32_t)list[i];
-            __syncthreads();
-            group_sort<kThreads>(S.u.b.bbuf, size);
-            if (fits)
-                for (int i = threadIdx.x; i < size; i += kThreads) P.arena[pos + i] = (int32_t)S.u.b.bbuf[i];
-            __syncthreads();
-            for (int i = threadIdx.x; i < size; i += kThreads) vis[S.u.b.bbuf[i] >> 5] = 0;
-        } else {
-            // R is large: read it off the visited bitmap in id order
-            const int64_t nwords = ((int64_t)P.n + 31) >> 5;
-            int64_t carry = 0;
-            for (int64_t b0 = 0; b0 < nwords; b0 += kThreads) {
-                const int64_t wi = b0 + threadIdx.x;
-                const uint32_t word = wi < nwords ? vis[wi] : 0u;
-                int total;
-                // exclusive sum of popcounts across the block
-                const int c = __popc(word);
-                int incl = c;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                if (lane == 31) S.tmp[wid] = incl;
-                __syncthreads();
-                int woff = 0;
-                total = 0;
-                for (int w = 0; w < kWarps; ++w) {
-                    woff += w < wid ? S.tmp[w] : 0;
-                    total += S.tmp[w];
-                }
-                __syncthreads();
-                int64_t o = carry + woff + incl - c;
-                uint32_t bits = word;
-                while (bits) {
-                    const int bpos = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    if (fits) P.arena[pos + o] = (int32_t)(wi * 32 + bpos);
-                    ++o;
-                }
-                carry += total;
-            }
-            __syncthreads();
-            for (int64_t w = threadIdx.x; w < nwords; w += kThreads) vis[w] = 0;
-        }
+        write_set(P, S, vis, list, size, job);
         for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
         __syncthreads();
     }
@@ -1592,6 +1863,7 @@ hyperim_status allow_rr_smem() {
         if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(k_rr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WarpShared));
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(k_rr_help, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     });
     HYP_CUDA(err);
     return HYPERIM_OK;
@@ -1688,8 +1960,9 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         want_d += (double)(pool_start[q + 1] - pool_start[q]) * hint * 1.25;
     }
     uint64_t want = (uint64_t)want_d;
-    // the warp phase (one RR set per warp) runs first in the persistent schedule; its grid
-    const bool warp_phase = g->schedule != HYPERIM_SCHED_PLAIN;
+    // the warp phase (one RR set per warp) runs first in the persistent schedule, unless the
+    // graph's tuning turned it off; its grid
+    const bool warp_phase = g->schedule != HYPERIM_SCHED_PLAIN && g->warp_set_limit > 0;
     int wblocks = 0;
     if (warp_phase) {
         int wper_sm = 0;
@@ -1713,6 +1986,15 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if ((st = tmp.alloc(&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
     if ((st = tmp.alloc(&d_esc, sizeof(int32_t) * (size_t)njobs))) return st;
     if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
+    // the block phase lets idle blocks help with other blocks' sets when the visited bitmaps are
+    // in global memory (every block can reach them)
+    const bool helped = warp_phase && !vis_smem;
+    SetCtl* d_sctl = nullptr;
+    int32_t* d_ring = nullptr;
+    if (helped) {
+        if ((st = tmp.alloc(&d_sctl, sizeof(SetCtl) * (size_t)blocks))) return st;
+        if ((st = tmp.alloc(&d_ring, sizeof(int32_t) * (size_t)kDCapG * (size_t)blocks))) return st;
+    }
     unsigned long long* d_used = &d_ctrl->arena_used;
     RRParams P;
     P.vinfo = g->vinfo;
@@ -1754,7 +2036,10 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.next_job = d_ctrl->next_job;
     P.esc_count = &d_ctrl->esc_count;
     P.esc_list = d_esc;
+    P.sctl = d_sctl;
+    P.gdefer = d_ring;
     P.block_phase = 0;
+    P.warp_limit = std::min(std::max(g->warp_set_limit, 1), kWQ);
     P.plain = g->schedule == HYPERIM_SCHED_PLAIN ? 1 : 0;
     P.plain_base = 0;
     P.arena_used = d_used;
@@ -1786,6 +2071,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         P.arena = g->scratch.arena;
         P.arena_cap = g->scratch.arena_cap;
         HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
+        if (helped) HYP_CUDA(cudaMemsetAsync(d_sctl, 0, sizeof(SetCtl) * (size_t)blocks, s));
         HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
         HYP_CUDA(cudaEventRecord(ev0, s));
         if (P.plain) {
@@ -1797,14 +2083,22 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
                 HYP_CUDA(cudaGetLastError());
                 ++launches;
             }
-        } else {
+        } else if (warp_phase) {
             // warp phase over every job, then the block phase over the jobs it listed
             P.block_phase = 0;
             { k_rr_warp<<<wblocks, kThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
             HYP_CUDA(cudaGetLastError());
             P.block_phase = 1;
-            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+            if (helped) {
+                k_rr_help<<<blocks, kThreads, smem, s>>>(P);
+            } else {
+                k_rr<<<blocks, kThreads, smem, s>>>(P);
+            }
+            count_launch();
             P.block_phase = 0;
+            ++launches;
+        } else {
+            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
             ++launches;
         }
         HYP_CUDA(cudaGetLastError());
