@@ -78,7 +78,13 @@ class PoolView(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32)]
+    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32), ("helping", C.c_int32)]
+
+
+class AutotuneResult(C.Structure):
+    _fields_ = [("chosen", Tuning), ("from_cache", C.c_int32), ("candidates", C.c_int32),
+                ("warp_set_limit", C.c_int32 * 10), ("helping", C.c_int32 * 10), ("seconds", C.c_double * 10),
+                ("profile_key", C.c_uint64)]
 
 
 class SelectOpts(C.Structure):
@@ -131,6 +137,7 @@ _SIGNATURES = {
     "hyperim_graph_set_wait_limit": (C.c_int, [_vp, C.c_uint32]),
     "hyperim_graph_set_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
     "hyperim_graph_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
+    "hyperim_graph_autotune": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(AutotuneResult)]),
     "hyperim_graph_share": (C.c_int, [_vp, _vp, C.POINTER(_vp)]),
     "hyperim_server_create": (C.c_int, [C.POINTER(ServerArgs), C.POINTER(_vp)]),
     "hyperim_server_add_graph": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
@@ -389,14 +396,26 @@ class Graph:
     def tuning(self):
         t = Tuning()
         _check(lib().hyperim_graph_get_tuning(self._h, C.byref(t)))
-        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block}
+        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block,
+                "helping": t.helping}
 
-    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None):
+    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None, helping=None):
         """RR-generation scheduling (hyperim_graph_set_tuning); the results never change."""
         cur = self.tuning()
-        t = Tuning(int(cur["warp_set_limit"] if warp_set_limit is None else warp_set_limit),
-                   int(cur["early_sets_per_block"] if early_sets_per_block is None else early_sets_per_block))
+        pick = lambda v, k: int(cur[k] if v is None else v)
+        t = Tuning(pick(warp_set_limit, "warp_set_limit"), pick(early_sets_per_block, "early_sets_per_block"),
+                   pick(helping, "helping"))
         _check(lib().hyperim_graph_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, roots="stratified", strategy="paper", sets=0):
+        """hyperim_graph_autotune: measure the RR-scheduling candidates (or reuse the process's
+        choice for an equal degree profile) and apply the fastest; returns what was chosen."""
+        r = AutotuneResult()
+        _check(lib().hyperim_graph_autotune(self._h, ROOTS[roots], STRATEGIES[strategy], int(sets), C.byref(r)))
+        return {"warp_set_limit": r.chosen.warp_set_limit, "helping": r.chosen.helping,
+                "early_sets_per_block": r.chosen.early_sets_per_block, "from_cache": bool(r.from_cache),
+                "candidates": [(r.warp_set_limit[i], r.helping[i], r.seconds[i]) for i in range(r.candidates)],
+                "profile_key": r.profile_key}
 
     def set_wait_limit(self, iterations):
         """Bound of the device-side waits of this handle's kernels (0: the default, 2^24 rounds);

@@ -6,6 +6,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -376,6 +378,7 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->wait_limit = r->wait_limit;
     h->warp_set_limit = r->warp_set_limit;
     h->early_sets_per_block = r->early_sets_per_block;
+    h->helping = r->helping;
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -479,8 +482,10 @@ hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning*
     if (t->warp_set_limit < 0 || t->warp_set_limit > 128) return set_error(HYPERIM_EINVAL, "warp_set_limit outside [0, 128]");
     if (t->early_sets_per_block < 1 || t->early_sets_per_block > 4096)
         return set_error(HYPERIM_EINVAL, "early_sets_per_block outside [1, 4096]");
+    if (t->helping < -1 || t->helping > 8) return set_error(HYPERIM_EINVAL, "helping outside [-1, 8]");
     g->warp_set_limit = t->warp_set_limit;
     g->early_sets_per_block = t->early_sets_per_block;
+    g->helping = t->helping;
     return HYPERIM_OK;
 }
 
@@ -488,6 +493,119 @@ hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out) 
     if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
     out->warp_set_limit = g->warp_set_limit;
     out->early_sets_per_block = g->early_sets_per_block;
+    out->helping = g->helping;
+    return HYPERIM_OK;
+}
+
+static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_mode, int32_t strategy,
+                                  hyperim_pool** out);
+static hyperim_status pool_grow(hyperim_graph* g, hyperim_pool* p, uint64_t theta);
+
+namespace {
+// the autotuner's key: the degree profile of the graph (logarithmic buckets) and the query kind
+uint64_t profile_key(const hyperim_graph* g, int32_t root_mode, int32_t strategy) {
+    auto lg = [](double x) { return x <= 1.0 ? 0ull : (unsigned long long)std::lround(std::log2(x) * 2.0); };
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the fields
+    auto mix = [&h](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xFF;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)g->model);
+    mix(g->uniform_thr);
+    mix((uint64_t)root_mode);
+    mix((uint64_t)strategy);
+    mix(lg((double)g->n));
+    mix(lg((double)g->nnz));
+    mix(lg((double)g->max_tsum));
+    mix(lg((double)g->max_deg));
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) mix(lg(64.0 * (double)g->stratum_size[s] / (double)g->n));
+    return h;
+}
+
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+std::map<uint64_t, hyperim_tuning>& tune_cache() {
+    static std::map<uint64_t, hyperim_tuning> c;
+    return c;
+}
+}  // namespace
+
+hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int32_t strategy, uint64_t sets,
+                                      hyperim_autotune_result* out) {
+    if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    if (root_mode != HYPERIM_ROOTS_PLAIN && root_mode != HYPERIM_ROOTS_STRATIFIED)
+        return set_error(HYPERIM_EINVAL, "unknown root mode");
+    if (strategy < HYPERIM_STRAT_PAPER || strategy > HYPERIM_STRAT_LT) return set_error(HYPERIM_EINVAL, "unknown strategy");
+    std::memset(out, 0, sizeof(*out));
+    const uint64_t key = profile_key(g, root_mode, strategy);
+    out->profile_key = key;
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            hyperim_tuning t = it->second;
+            t.early_sets_per_block = g->early_sets_per_block;
+            g->warp_set_limit = t.warp_set_limit;
+            g->helping = t.helping;
+            out->chosen = t;
+            out->from_cache = 1;
+            return HYPERIM_OK;
+        }
+    }
+    if (sets == 0) sets = 8 * (uint64_t)std::max(g->sm_count, 1);
+    const int32_t keep_w = g->warp_set_limit, keep_h = g->helping, keep_sched = g->schedule;
+    g->schedule = HYPERIM_SCHED_PERSISTENT;
+    // (warp_set_limit, helping): no warp phase; warp phase with teams of 1, 2, 4, 8 blocks
+    const int32_t cand[9][2] = {{0, -1}, {32, -1}, {32, 2}, {32, 4}, {32, 8}, {128, -1}, {128, 2}, {128, 4}, {128, 8}};
+    double best = -1.0;
+    hyperim_tuning choice{keep_w, g->early_sets_per_block, keep_h};
+    hyperim_status st = HYPERIM_OK;
+    int c = 0;
+    {
+        for (int ci = 0; ci < 9 && st == HYPERIM_OK; ++ci) {
+            g->warp_set_limit = cand[ci][0];
+            g->helping = cand[ci][1];
+            double secs = -1.0;
+            for (int rep = 0; rep < 2 && st == HYPERIM_OK; ++rep) {
+                hyperim_pool* p = nullptr;
+                if ((st = pool_create(g, 0xFF, root_mode, strategy, &p))) break;
+                {
+                    std::unique_lock<std::shared_mutex> lk(p->mu);
+                    st = pool_grow(g, p, sets);
+                }
+                const double t = p->rr_kernel_seconds;
+                hyperim_pool_free(p);
+                if (st == HYPERIM_OK && (secs < 0.0 || t < secs)) secs = t;
+            }
+            if (st != HYPERIM_OK) break;
+            out->warp_set_limit[c] = cand[ci][0];
+            out->helping[c] = cand[ci][1];
+            out->seconds[c] = secs;
+            ++c;
+            if (best < 0.0 || secs < best) {
+                best = secs;
+                choice.warp_set_limit = cand[ci][0];
+                choice.helping = cand[ci][1];
+            }
+        }
+    }
+    out->candidates = c;
+    g->schedule = keep_sched;
+    if (st != HYPERIM_OK) {
+        g->warp_set_limit = keep_w;
+        g->helping = keep_h;
+        return st;
+    }
+    g->warp_set_limit = choice.warp_set_limit;
+    g->helping = choice.helping;
+    out->chosen = choice;
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    tune_cache()[key] = choice;
     return HYPERIM_OK;
 }
 

@@ -21,15 +21,18 @@
 namespace hyperim {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;    // a block of the block-per-set kernels: one per SM
 constexpr int kWarps = kThreads / 32;
+constexpr int kPThreads = 256;   // a block of the warp phase (a set per warp): two per SM
+constexpr int kPWarps = kPThreads / 32;
 constexpr int kWCap = 2048;      // per-warp on-chip neighbourhood keys (power of two)
 constexpr int kWHalf = kWCap / 2;  // raw copy + sorted copy of neighbourhoods up to this size
 constexpr int kPCap = 256;       // per-warp picks
 constexpr int kLQ = 32;          // per-warp layers with h > 0 handled on the warp path
+constexpr int kCG = 64;          // hyperedges per group of the chunk path (two per lane)
 constexpr int kBCap = 8192;      // block on-chip keys (power of two)
 constexpr int kBLQ = 64;         // layers with h > 0 per block round
-constexpr int kDCap = 512;       // deferred pops per level round
+constexpr int kDCap = 256;       // deferred pops per level round
 constexpr int kBucketBits = 12;
 constexpr int kBuckets = 1 << kBucketBits;    // block-path buckets
 constexpr int kWBucketBits = 8;
@@ -40,7 +43,7 @@ constexpr int kMaxPools = 2;           // pools grown by one launch (R1 and R2 o
 constexpr int kNStat = 10;             // work counters (stat slots below)
 // warp phase: a warp builds a whole RR set alone while it stays within kWQ members
 constexpr int kWQ = 128;               // per-warp queue (members of the warp's set)
-constexpr int kWHashBits = 9;
+constexpr int kWHashBits = 8;
 constexpr int kWHash = 1 << kWHashBits;  // per-warp open-addressing member set
 
 struct RRJobMap {
@@ -90,6 +93,7 @@ struct RRParams {
     int* esc_count;           // jobs the warp phase handed to the block phase
     int32_t* esc_list;        // those jobs
     int block_phase;          // 1: this launch runs the jobs of esc_list (else all jobs)
+    int team;                 // block phase with helping: blocks per team (the first leads)
     struct SetCtl* sctl;      // block phase with helping: one set-control record per block
     int32_t* gdefer;          // block phase with helping: kDCapG deferred pops per block (a ring)
     int warp_limit;           // warp phase: the largest RR set a warp builds alone (1..kWQ)
@@ -106,15 +110,18 @@ struct Need {                    // a layer with h > 0 at the current pop
 
 // Buffers of phase 1 (warps pop independently) and of phase 2 / output (the whole block works on
 // one deferred pop, or on the finished set) never live at the same time: they share storage.
-struct WarpArea {
-    uint32_t wbuf[kWarps][kWCap];
-    int wbkt[kWarps][kWBuckets];
-    uint32_t wpick[kWarps][kPCap];
+template <int W>
+struct WarpAreaT {
+    uint32_t wbuf[W][kWCap];
+    int wbkt[W][kWBuckets];
+    uint32_t wpick[W][kPCap];
 };
+using WarpArea = WarpAreaT<kWarps>;
 struct BlockArea {
     uint32_t bbuf[kBCap];
     int bucket[kBuckets];
     int chunk_end[kChunks];
+    int bpre[2 * kThreads + 1];
 };
 
 struct Shared {
@@ -126,8 +133,7 @@ struct Shared {
     int32_t deferred[kDCap];
     Need wneed[kWarps][kLQ];
     int wcursor[kWarps];
-    int wpre[kWarps][3 * 32 + 1];   // span prefix, starts, holes (chunk path)
-    int bpre[2 * kThreads + 1];
+    int wpre[kWarps][3 * kCG + 1];  // span prefix, starts, holes of a group of hyperedges (chunk path)
     uint32_t wpoff[kWarps][kLQ + 1];
     int wcnt[kWarps][kBLQ];     // per-warp per-layer counts (ranks)
     int lcnt[kBLQ];             // running rank per needed layer (block path)
@@ -366,11 +372,10 @@ struct SetCtl {
     int ndef_done;             // deferred pops the owner has run
     int job;                   // the set's job (valid for the epoch in claim)
     int active;                // 1 while the owner works on a set
-    int pad;
+    int finished;              // 1 once the owner has no job left
 };
 constexpr int kDCapG = 8192;       // deferred ring per block
 constexpr int kDClaimMax = 4096;   // no claim while this many deferred pops wait (ring margin)
-constexpr int kHelpIdle = 256;     // empty scans after which a helper block stops
 
 // Claim a queue slot of the set behind c in epoch `epoch` (lane 0). The owner waits (bounded)
 // while pops are in flight and returns -1 once nothing is (quiescent: every claimed pop is done
@@ -387,10 +392,7 @@ __device__ int claim_global(const RRParams& P, SetCtl* c, uint32_t epoch, int64_
         const int h = (int)(uint32_t)cl;
         const int pending = nd - ndd;
         if (h < t && pending < kDClaimMax) {
-            if (atomicCAS(&c->claim, cl, cl + 1) == cl) {
-                __threadfence();
-                return h;
-            }
+            if (atomicCAS(&c->claim, cl, cl + 1) == cl) return h;
             continue;
         }
         if (!owner) return -1;
@@ -478,6 +480,51 @@ __device__ void small_nbhd(const RRParams& P, SM& S, int32_t mu, int32_t v_begin
     warp_scatter_sort(raw, tsum, (uint32_t)mu, buf, T, bkt, nb, 0u, shift, key_mask, maxb);
 }
 
+// For every needed layer q < nq (lane q passes its row, k0, pos and whether it searches): the
+// last chunk k in [k0, C) whose prefix row[k] is <= pos (row[k0] <= pos is given). The warp
+// splits into groups of G = 32 / Q lanes (Q = the power of two >= nq), group q searching for layer
+// q G-ary: each round probes G evenly spaced entries of the range at once, so C = 4096 chunks take
+// 3 rounds with one or two needed layers instead of 12 dependent probes. Lane q gets its layer's
+// answer (-1 for a layer that does not search). With more than 16 needed layers every lane
+// searches alone (binary search).
+__device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0, int C, uint32_t pos,
+                                        uint32_t& probes);
+
+__device__ __forceinline__ int warp_chunk_search(const uint32_t* row, int k0, int C, uint32_t pos, bool want,
+                                                 uint32_t nq, uint32_t& probes) {
+    const int lane = threadIdx.x & 31;
+    int Q = 1;
+    while (Q < (int)nq) Q <<= 1;
+    if (Q > 16) return want ? chunk_of(row, k0, C, pos, probes) : -1;
+    const int G = 32 / Q, q = lane / G, gl = lane - q * G;
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(
+        __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(row), q));
+    int lo = __shfl_sync(0xFFFFFFFFu, k0, q);
+    const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, q);
+    const bool act = __shfl_sync(0xFFFFFFFFu, want ? 1 : 0, q) != 0 && q < (int)nq;
+    int hi = act ? C : lo + 1;
+    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    while (__any_sync(0xFFFFFFFFu, hi - lo > 1)) {
+        const int span = hi - lo;
+        const int step = (span + G - 1) / G;
+        const int x = lo + gl * step;
+        bool pred = gl == 0;  // row[lo] <= pos holds
+        if (span > 1 && gl > 0 && x < hi) {
+            ++probes;
+            pred = r[x] <= ps;
+        }
+        const uint32_t gb = (__ballot_sync(0xFFFFFFFFu, pred) >> (q * G)) & gmask;
+        if (span > 1) {
+            const int g = 31 - __clz(gb);
+            const int nlo = lo + g * step;
+            hi = min(nlo + step, hi);
+            lo = nlo;
+        }
+    }
+    const int res = __shfl_sync(0xFFFFFFFFu, lo, lane < Q ? lane * G : 0);
+    return want ? res : -1;
+}
+
 // Last chunk k in [k0, C) whose prefix row[k] is <= pos (row[k0] <= pos is given).
 __device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0, int C, uint32_t pos,
                                         uint32_t& probes) {
@@ -490,22 +537,86 @@ __device__ __forceinline__ int chunk_of(const uint32_t* __restrict__ row, int k0
     return lo;
 }
 
+// The slice of one sorted hyperedge (members e[0, len)) whose ids lie in chunk k = lo >> sh of
+// the ids' top c = id_bits - sh bits: offsets [l1, l2) and, when mu lies in the range, mu's offset
+// l3. Read off the hyperedge's id directory when it has one (two entries when c <= b, else one
+// directory range of about one member, scanned), else found by interleaved binary searches.
+struct Slice {
+    int l1, l2, l3;
+};
+
+__device__ __forceinline__ Slice hyperedge_slice(const RRParams& P, int2 sp, uint2 dd, uint32_t lo, uint32_t hi,
+                                                 int c, uint32_t k, int32_t mu, bool mu_in, uint32_t& probes) {
+    const int32_t* e = P.he_mem + sp.x;
+    Slice r{0, 0, 0};
+    if (dd.y != 0) {
+        const uint16_t* D = P.he_dir + dd.x;
+        const int b = (int)dd.y;
+        const uint32_t rm = (uint32_t)mu >> (P.id_bits - b);
+        int m0 = 0, m1 = 0;
+        if (mu_in) {  // mu's directory range (issued with the slice's entries)
+            m0 = D[rm];
+            m1 = D[rm + 1];
+            probes += 2;
+        }
+        if (c <= b) {
+            r.l1 = D[k << (b - c)];
+            r.l2 = D[(k + 1) << (b - c)];
+            probes += 2;
+        } else {
+            const uint32_t rr = k >> (c - b);
+            const int a0 = D[rr], a1 = D[rr + 1];
+            probes += 2;
+            r.l1 = a0;
+            r.l2 = a0;
+            for (int x = a0; x < a1; ++x) {
+                const uint32_t v = (uint32_t)e[x];
+                ++probes;
+                r.l1 += v < lo ? 1 : 0;
+                r.l2 += v < hi ? 1 : 0;
+            }
+        }
+        if (mu_in) {
+            r.l3 = m0;
+            while (r.l3 < m1 && (uint32_t)e[r.l3] < (uint32_t)mu) {
+                ++r.l3;
+                ++probes;
+            }
+        }
+        return r;
+    }
+    // three lower bounds (lo, hi, mu) advanced together: their loads overlap
+    int l1 = 0, h1 = sp.y, l2 = 0, h2 = sp.y, l3 = 0, h3 = mu_in ? sp.y : 0;
+    while (l1 < h1 || l2 < h2 || l3 < h3) {
+        const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1, m3 = (l3 + h3) >> 1;
+        const uint32_t v1 = l1 < h1 ? (uint32_t)e[m1] : 0u;
+        const uint32_t v2 = l2 < h2 ? (uint32_t)e[m2] : 0u;
+        const uint32_t v3 = l3 < h3 ? (uint32_t)e[m3] : 0u;
+        if (l1 < h1) { ++probes; if (v1 < lo) l1 = m1 + 1; else h1 = m1; }
+        if (l2 < h2) { ++probes; if (v2 < hi) l2 = m2 + 1; else h2 = m2; }
+        if (l3 < h3) { ++probes; if (v3 < (uint32_t)mu) l3 = m3 + 1; else h3 = m3; }
+    }
+    r.l1 = l1;
+    r.l2 = l2;
+    r.l3 = l3;
+    return r;
+}
+
 // The members != mu of mu's hyperedges whose ids lie in [lo, hi), sorted, in buf[0, count);
 // returns count, or -1 if they exceed kWHalf. lo is a multiple of 2^sh (the range is chunk
 // k = lo >> sh of the ids' top c = id_bits - sh bits). Members of a hyperedge are sorted, so the
-// range is one slice of it: read off its id directory when it has one (two entries when c <= b,
-// else one directory range of about one member, scanned), else found by two interleaved binary
-// searches. When mu lies in the range its own slot in every slice is skipped (a hole at mu's
-// offset, found the same way). The slices are gathered with independent loads into the raw half
-// of buf and counted into buckets of the id offset within the range, then scattered and sorted as
-// in small_nbhd. probes counts the words read to locate the slices.
+// range is one slice of each (hyperedge_slice); when mu lies in the range its own slot in every
+// slice is skipped (a hole at mu's offset). The hyperedges are taken kCG at a time, two per lane,
+// so that the lookups of both overlap; the slices are gathered with independent loads into the
+// raw half of buf and counted into buckets of the id offset within the range, then scattered and
+// sorted as in small_nbhd. probes counts the words read to locate the slices.
 template <class SM>
 __device__ int chunk_nbhd(const RRParams& P, SM& S, int32_t mu, int32_t v_begin, int32_t dh,
                           uint32_t lo, int sh, uint32_t* buf, uint32_t& probes) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* pre = S.wpre[wid];
-    int* start = pre + 33;
-    int* hole = pre + 65;
+    int* start = pre + kCG + 1;
+    int* hole = start + kCG;
     uint32_t* raw = buf + kWHalf;
     int* bkt = S.u.w.wbkt[wid];
     constexpr int nb = kWBuckets;
@@ -517,76 +628,55 @@ __device__ int chunk_nbhd(const RRParams& P, SM& S, int32_t mu, int32_t v_begin,
     const uint32_t k = lo >> sh;
     for (int b = lane; b < nb; b += 32) bkt[b] = 0;
     int base = 0;
-    for (int c0 = 0; c0 < dh; c0 += 32) {
-        const int cnt = min(32, dh - c0);
-        int st = 0, len = 0, hl = 0x7FFFFFFF;
-        if (lane < cnt) {
-            const int2 sp = P.v_span[v_begin + c0 + lane];
-            const uint2 dd = P.v_dir[v_begin + c0 + lane];
-            const int32_t* e = P.he_mem + sp.x;
-            int l1 = 0, l2 = 0, l3 = 0;
-            if (dd.y != 0) {
-                const uint16_t* D = P.he_dir + dd.x;
-                const int b = (int)dd.y;
-                if (c <= b) {
-                    l1 = D[k << (b - c)];
-                    l2 = D[(k + 1) << (b - c)];
-                    probes += 2;
-                } else {
-                    const uint32_t r = k >> (c - b);
-                    const int a0 = D[r], a1 = D[r + 1];
-                    probes += 2;
-                    l1 = a0;
-                    l2 = a0;
-                    for (int x = a0; x < a1; ++x) {
-                        const uint32_t v = (uint32_t)e[x];
-                        ++probes;
-                        l1 += v < lo ? 1 : 0;
-                        l2 += v < hi ? 1 : 0;
-                    }
+    for (int c0 = 0; c0 < dh; c0 += kCG) {
+        const int cnt = min(kCG, dh - c0);
+        // lane takes hyperedges c0 + lane and c0 + 32 + lane
+        int st[2] = {0, 0}, len[2] = {0, 0}, hl[2] = {0x7FFFFFFF, 0x7FFFFFFF};
+        int2 sp[2];
+        uint2 dd[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int x = u * 32 + lane;
+            sp[u] = x < cnt ? P.v_span[v_begin + c0 + x] : make_int2(0, 0);
+            dd[u] = x < cnt ? P.v_dir[v_begin + c0 + x] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int x = u * 32 + lane;
+            if (x < cnt) {
+                const Slice r = hyperedge_slice(P, sp[u], dd[u], lo, hi, c, k, mu, mu_in, probes);
+                st[u] = sp[u].x + r.l1;
+                len[u] = r.l2 - r.l1;
+                if (mu_in) {
+                    hl[u] = r.l3 - r.l1;
+                    len[u] -= 1;
                 }
-                if (mu_in) {  // mu's slot: its directory range, scanned
-                    const uint32_t rm = (uint32_t)mu >> (P.id_bits - b);
-                    l3 = D[rm];
-                    const int a1 = D[rm + 1];
-                    probes += 2;
-                    while (l3 < a1 && (uint32_t)e[l3] < (uint32_t)mu) {
-                        ++l3;
-                        ++probes;
-                    }
-                }
-            } else {
-                // three lower bounds (lo, hi, mu) advanced together: their loads overlap
-                int h1 = sp.y, h2 = sp.y, h3 = mu_in ? sp.y : 0;
-                while (l1 < h1 || l2 < h2 || l3 < h3) {
-                    const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1, m3 = (l3 + h3) >> 1;
-                    const uint32_t v1 = l1 < h1 ? (uint32_t)e[m1] : 0u;
-                    const uint32_t v2 = l2 < h2 ? (uint32_t)e[m2] : 0u;
-                    const uint32_t v3 = l3 < h3 ? (uint32_t)e[m3] : 0u;
-                    if (l1 < h1) { ++probes; if (v1 < lo) l1 = m1 + 1; else h1 = m1; }
-                    if (l2 < h2) { ++probes; if (v2 < hi) l2 = m2 + 1; else h2 = m2; }
-                    if (l3 < h3) { ++probes; if (v3 < (uint32_t)mu) l3 = m3 + 1; else h3 = m3; }
-                }
-            }
-            st = sp.x + l1;
-            len = l2 - l1;
-            if (mu_in) {
-                hl = l3 - l1;
-                len -= 1;
             }
         }
-        int inc = len;
+        // inclusive prefix of the lengths over the group (first the lanes' first hyperedges)
+        int inc0 = len[0], inc1 = len[1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-            if (lane >= o) inc += t;
+            const int t0 = __shfl_up_sync(0xFFFFFFFFu, inc0, o);
+            const int t1 = __shfl_up_sync(0xFFFFFFFFu, inc1, o);
+            if (lane >= o) {
+                inc0 += t0;
+                inc1 += t1;
+            }
         }
+        const int tot0 = __shfl_sync(0xFFFFFFFFu, inc0, 31);
+        inc1 += tot0;
         __syncwarp();  // the previous group's readers of pre / start / hole are done
         if (lane == 0) pre[0] = 0;
         if (lane < cnt) {
-            pre[lane + 1] = inc;
-            start[lane] = st;
-            hole[lane] = hl;
+            pre[lane + 1] = inc0;
+            start[lane] = st[0];
+            hole[lane] = hl[0];
+        }
+        if (32 + lane < cnt) {
+            pre[33 + lane] = inc1;
+            start[32 + lane] = st[1];
+            hole[32 + lane] = hl[1];
         }
         __syncwarp();
         const int total = pre[cnt];
@@ -825,11 +915,15 @@ __device__ bool pop_warp(const RRParams& P, SM& S, const Sink& sink, uint32_t j,
         unsigned long long gath = 0;
         Need nd{};
         const uint32_t* row = nullptr;
+        uint32_t first = 0;
         if ((uint32_t)lane < nneed) {
             nd = need[lane];
             row = P.idx_tab + toff + ((uint64_t)(nd.layer - 1) << c);
-            const uint32_t first = nd.h < nd.n ? picks[poff[lane]] : 0u;
-            cur = (uint32_t)chunk_of(row, 0, C, first, probes);
+            first = nd.h < nd.n ? picks[poff[lane]] : 0u;
+        }
+        {
+            const int r0 = warp_chunk_search(row, 0, C, first, (uint32_t)lane < nneed, nneed, probes);
+            if ((uint32_t)lane < nneed) cur = (uint32_t)r0;
         }
         uint32_t k = __reduce_min_sync(0xFFFFFFFFu, cur);
         int chunks = 0;
@@ -847,10 +941,11 @@ __device__ bool pop_warp(const RRParams& P, SM& S, const Sink& sink, uint32_t j,
             gath += (unsigned long long)got;
             warp_walk(P, S, sink, buf, got, nneed);
             ++chunks;
-            if (cur == k) {
+            uint32_t nxt = 0xFFFFFFFFu;
+            const bool moved = cur == k;  // this lane's layer needs a later chunk (or none)
+            if (moved) {
                 const uint32_t endk = (int)k + 1 < C ? row[k + 1] : nd.n;  // members of L_q before chunk k + 1
                 ++probes;
-                uint32_t nxt = 0xFFFFFFFFu;
                 if (nd.h < nd.n) {
                     const uint32_t* pk = picks + poff[lane];
                     while (cursor < nd.h && pk[cursor] < endk) ++cursor;
@@ -858,7 +953,11 @@ __device__ bool pop_warp(const RRParams& P, SM& S, const Sink& sink, uint32_t j,
                 } else if (endk < nd.n) {
                     nxt = endk;
                 }
-                cur = nxt != 0xFFFFFFFFu ? (uint32_t)chunk_of(row, (int)k + 1, C, nxt, probes) : 0xFFFFFFFFu;
+            }
+            {
+                const bool want = moved && nxt != 0xFFFFFFFFu;
+                const int r1 = warp_chunk_search(row, (int)k + 1, C, nxt, want, nneed, probes);
+                if (moved) cur = want ? (uint32_t)r1 : 0xFFFFFFFFu;
             }
             k = __reduce_min_sync(0xFFFFFFFFu, cur);
         }
@@ -1074,7 +1173,7 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, const Sink&
                 if (T <= kBCap) {
                     const int got = sorted_nbhd<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, T,
                                                           P.id_bits, S.u.b.bbuf, S.u.b.bucket,
-                                                          kBucketBits, S.bpre, S.tmp);
+                                                          kBucketBits, S.u.b.bpre, S.tmp);
                     block_walk(P, S, sink, S.u.b.bbuf, got, nq, picks_g);
                 } else if ((int64_t)T > P.big_cap) {
                     if (threadIdx.x == 0) dev_fail(P.st, kErrCapacity, mu);
@@ -1089,7 +1188,7 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, const Sink&
                         const int nb = 1 << b, shift = P.id_bits - b;
                         for (int i = threadIdx.x; i < nb; i += kThreads) S.u.b.chunk_end[i] = 0;
                         __syncthreads();
-                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.bpre,
+                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.u.b.bpre,
                                                   [&](uint32_t x) { atomicAdd(&S.u.b.chunk_end[x >> shift], 1); });
                         int mx = 0;
                         for (int i = threadIdx.x; i < nb; i += kThreads) mx = max(mx, S.u.b.chunk_end[i]);
@@ -1122,7 +1221,7 @@ __device__ __noinline__ void pop_block(const RRParams& P, Shared& S, const Sink&
                             }
                         }
                         __syncthreads();
-                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.bpre,
+                        for_each_member<kThreads>(P.v_span, P.he_mem, mu, v_begin, dh, S.u.b.bpre,
                                                   [&](uint32_t x) { big[atomicAdd(&S.u.b.chunk_end[x >> shift], 1)] = x; });
                         __threadfence_block();
                         __syncthreads();
@@ -1257,7 +1356,7 @@ __device__ void fwd_pop_warp(const FwdParams& F, Shared& S, uint32_t* vis, int32
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_forward(FwdParams F) {
+__global__ void __launch_bounds__(kThreads, 1) k_forward(FwdParams F) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RRParams& P = F.P;
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
@@ -1301,7 +1400,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_forward(FwdParams F) {
         const int size = S.ctrl[C_TAIL];
         if (threadIdx.x == 0) F.counts[r] = (uint32_t)size;
         for (int i = threadIdx.x; i < size; i += kThreads) {
-            const int32_t v = list[i];
+            const int32_t v = __ldcg(list + i);
             if (v >= 0) vis[v >> 5] = 0;
             list[i] = -1;
         }
@@ -1347,16 +1446,16 @@ __device__ __forceinline__ int32_t draw_root(const RRParams& P, const Job& J) {
 // RR set (member set, queue, size).
 struct WarpShared {
     unsigned long long stat[kMaxPools][kNStat];  // per pool work counters of this block
-    unsigned long long wstat[kWarps][kNStat];    // per-warp counters of the warp's current set
-    Need wneed[kWarps][kLQ];
-    int wpre[kWarps][3 * 32 + 1];
-    uint32_t wpoff[kWarps][kLQ + 1];
-    int wcnt[kWarps][kBLQ];
-    int wtail[kWarps];
-    int32_t whash[kWarps][kWHash];
-    int32_t wqueue[kWarps][kWQ];
+    unsigned long long wstat[kPWarps][kNStat];    // per-warp counters of the warp's current set
+    Need wneed[kPWarps][kLQ];
+    int wpre[kPWarps][3 * kCG + 1];
+    uint32_t wpoff[kPWarps][kLQ + 1];
+    int wcnt[kPWarps][kBLQ];
+    int wtail[kPWarps];
+    int32_t whash[kPWarps][kWHash];
+    int32_t wqueue[kPWarps][kWQ];
     union {
-        WarpArea w;
+        WarpAreaT<kPWarps> w;
     } u;
 };
 
@@ -1366,14 +1465,14 @@ struct WarpShared {
 // any other job is listed for the block phase (k_rr with block_phase), which builds it again
 // from its root (the draws are keyed by (RR, vertex, layer), so the set is the same) and the warp's
 // partial counters are dropped. Jobs are taken from the last one down, as in k_rr.
-__global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
+__global__ void __launch_bounds__(kPThreads, 2) k_rr_warp(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpShared& S = *reinterpret_cast<WarpShared*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t njobs = P.pool_start[P.npools];
     if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
-    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
-    for (int i = threadIdx.x; i < kWarps * kWHash; i += kThreads) (&S.whash[0][0])[i] = -1;
+    if (threadIdx.x < kPWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kPWarps * kWHash; i += kPThreads) (&S.whash[0][0])[i] = -1;
     __syncthreads();
     int32_t* hash = S.whash[wid];
     int32_t* queue = S.wqueue[wid];
@@ -1448,7 +1547,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_warp(RRParams P) {
 
 // Output of a finished RR set of `size` members (its queue holds them, its visited bitmap marks
 // them): an arena slot for the job, the members in ascending order (sorted on chip up to kBCap,
-// else read off the bitmap in id order), and the bitmap cleared again. Whole block.
+// else read off the bitmap in id order), and the bitmap cleared again. Whole block. The queue, and
+// the bitmap when it is in global memory, were written by other warps through L2 (volatile stores,
+// atomics): they are read with L2 loads, never from a possibly stale L1 line.
 __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int32_t* list, int size, int64_t job) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
@@ -1462,7 +1563,7 @@ __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int
     const bool fits = S.ctrl[C_ROOT] != 0;
     const unsigned long long pos = S.out_pos;
     if (size <= kBCap) {
-        for (int i = threadIdx.x; i < size; i += kThreads) S.u.b.bbuf[i] = (uint32_t)list[i];
+        for (int i = threadIdx.x; i < size; i += kThreads) S.u.b.bbuf[i] = (uint32_t)__ldcg(list + i);
         __syncthreads();
         group_sort<kThreads>(S.u.b.bbuf, size);
         if (fits)
@@ -1475,7 +1576,7 @@ __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int
         int64_t carry = 0;
         for (int64_t b0 = 0; b0 < nwords; b0 += kThreads) {
             const int64_t wi = b0 + threadIdx.x;
-            const uint32_t word = wi < nwords ? vis[wi] : 0u;
+            const uint32_t word = wi >= nwords ? 0u : P.vis_smem ? vis[wi] : (uint32_t)__ldcg(vis + wi);
             int total;
             // exclusive sum of popcounts across the block
             const int c = __popc(word);
@@ -1508,15 +1609,18 @@ __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int
     }
 }
 
-// Block phase with helping (graphs whose visited bitmaps live in global memory): each block
-// builds the listed jobs it takes, as in k_rr but with its set's queue counters in SetCtl; a
-// block without a job left helps the block whose set has the most claimable slots, popping with
-// its own warps into that set's queue and bitmap (the draws are keyed by (RR, vertex, layer), so
-// who pops a vertex does not matter), until it finds no claimable slot in kHelpIdle scans.
-__global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
+// Block phase with helping (graphs whose visited bitmaps live in global memory): the blocks form
+// teams of P.team consecutive blocks. The first block of a team takes the listed jobs and builds
+// each set as k_rr does, but with the set's queue counters in its SetCtl; the other blocks of the
+// team only pop vertices of their leader's current set -- into its queue and bitmap; the draws
+// are keyed by (RR, vertex, layer), so who pops a vertex does not matter -- and leave once the
+// leader has no job left. A helper never makes its leader wait except for the pops it has claimed
+// (finite work), and waits for its leader's next set only in bounded rounds.
+__global__ void __launch_bounds__(kThreads, 1) k_rr_help(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
     const int b = blockIdx.x;
+    const int leader = b - b % P.team;
     uint32_t* vis = P.gvis + (int64_t)b * P.vis_words;
     int32_t* list = P.list + (int64_t)b * P.list_cap;
     uint32_t* picks_g = P.picks + (int64_t)b * P.pick_cap;
@@ -1530,8 +1634,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
     uint32_t epoch = 0;
-    // own jobs
+    // a leader: the jobs
     for (;;) {
+        if (leader != b) break;
         if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job + 1, 1);
         __syncthreads();
         const int64_t ticket = S.ctrl[C_JOB];
@@ -1580,7 +1685,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
             if (S.ctrl[C_STOP] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
             const int nd = S.ctrl[C_NDEF], ndd = S.ctrl[C_CURSOR];
             for (int d = ndd; d < nd; ++d)
-                pop_block(P, S, sink, J.j, J.ybase, ring[d & (kDCapG - 1)], picks_g, big);
+                pop_block(P, S, sink, J.j, J.ybase, __ldcg(ring + (d & (kDCapG - 1))), picks_g, big);
             __syncthreads();
             if (threadIdx.x == 0) {
                 c->ndef_done = nd;
@@ -1604,65 +1709,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
         for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        c->active = 0;
-        __threadfence();
-    }
-    // help the other blocks' sets
-    for (int idle = 0; idle < kHelpIdle;) {
-        if (wid == 0) {
-            int best = -1, bl = 0, anyact = 0;
-            uint32_t be = 0;
-            for (int o = lane; o < (int)gridDim.x; o += 32) {
-                const SetCtl* oc = P.sctl + o;
-                const unsigned long long cl = *(volatile const unsigned long long*)&oc->claim;
-                const int t = *(volatile const int*)&oc->tail;
-                const int act = *(volatile const int*)&oc->active;
-                anyact |= act;
-                const int backlog = act ? t - (int)(uint32_t)cl : 0;
-                if (backlog > bl) { bl = backlog; best = o; be = (uint32_t)(cl >> 32); }
-            }
-            anyact = __any_sync(0xFFFFFFFFu, anyact != 0);
-            for (int off = 16; off > 0; off >>= 1) {
-                const int obl = __shfl_down_sync(0xFFFFFFFFu, bl, off);
-                const int ob = __shfl_down_sync(0xFFFFFFFFu, best, off);
-                const uint32_t oe = __shfl_down_sync(0xFFFFFFFFu, be, off);
-                if (obl > bl || (obl == bl && obl > 0 && ob < best)) { bl = obl; best = ob; be = oe; }
-            }
-            if (lane == 0) {
-                S.ctrl[C_ROOT] = best;
-                S.ctrl[C_BITS] = (int)be;
-                // stop on a failure, or once no block has a set left to help with
-                S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0 || !anyact;
-            }
+    if (leader == b) {
+        if (threadIdx.x == 0) {
+            c->active = 0;
+            __threadfence();
+            c->finished = 1;
         }
-        __syncthreads();
-        const int tb = S.ctrl[C_ROOT];
-        const uint32_t te = (uint32_t)S.ctrl[C_BITS];
-        if (S.ctrl[C_FAIL]) break;
-        __syncthreads();
-        if (tb < 0) {
-            ++idle;
-            __nanosleep(2000);
-            continue;
-        }
-        idle = 0;
-        SetCtl* tc = P.sctl + tb;
-        int32_t* tlist = P.list + (int64_t)tb * P.list_cap;
-        int32_t* tring = P.gdefer + (int64_t)tb * kDCapG;
-        const QueueSink tsink{P.gvis + (int64_t)tb * P.vis_words, tlist, &tc->tail};
-        for (;;) {
-            int idx = 0;
-            if (lane == 0) idx = claim_global(P, tc, te, -1, false);
-            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-            if (idx < 0) break;
+    } else {
+        // a helper: pop vertices of the leader's current set, warp by warp
+        SetCtl* tc = P.sctl + leader;
+        int32_t* tlist = P.list + (int64_t)leader * P.list_cap;
+        int32_t* tring = P.gdefer + (int64_t)leader * kDCapG;
+        const QueueSink tsink{P.gvis + (int64_t)leader * P.vis_words, tlist, &tc->tail};
+        for (int idle = 0; idle < P.spin_limit;) {
+            int idx = -1, fin = 0;
             int64_t job = 0;
-            int32_t mu = 0;
             if (lane == 0) {
-                job = *(volatile int*)&tc->job;
-                mu = slot_value(P, tlist, idx, job);
+                fin = *(volatile int*)&tc->finished;
+                const unsigned long long cl = *(volatile unsigned long long*)&tc->claim;
+                __threadfence();
+                job = *(volatile int*)&tc->job;  // read before the claim: a claim in epoch cl >> 32 means it is that set's
+                if (!fin && *(volatile int*)&tc->active) idx = claim_global(P, tc, (uint32_t)(cl >> 32), -1, false);
             }
+            fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
+            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+            if (fin || *(volatile int32_t*)&P.st->code != 0) break;
+            if (idx < 0) {
+                ++idle;
+                __nanosleep(256);
+                continue;
+            }
+            idle = 0;
             job = __shfl_sync(0xFFFFFFFFu, job, 0);
+            int32_t mu = 0;
+            if (lane == 0) mu = slot_value(P, tlist, idx, job);
             mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
             const Job J = decode_job(P, job);
             const bool defer = mu >= 0 && pop_warp(P, S, tsink, J.j, J.ybase, mu);
@@ -1674,7 +1754,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
             }
             __syncwarp();
         }
-        __syncthreads();
     }
     __syncthreads();
     if (threadIdx.x < P.npools) {
@@ -1693,7 +1772,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rr_help(RRParams P) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_rr(RRParams P) {
+__global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
     uint32_t* vis = P.vis_smem ? reinterpret_cast<uint32_t*>(smem_raw + sizeof(Shared))
@@ -1854,11 +1933,19 @@ hyperim_status grow_array(hyperim_graph* g, T** arr, size_t used, size_t* cap, s
 // The dynamic shared memory limit of a kernel is one value per function, not per launch: it is
 // raised once to the most any launch can ask for (an on-chip visited bitmap of kVisSmemBits), so
 // that launches from several host threads with different sizes never race on it.
+// the most dynamic shared memory a block of this device may use
+size_t smem_optin() {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)optin;
+}
+
 hyperim_status allow_rr_smem() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        const int most = (int)(sizeof(Shared) + kVisSmemBits / 8);
+        const int most = (int)std::min<size_t>(sizeof(Shared) + kVisSmemBits / 8, smem_optin());
         err = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess)
@@ -1936,16 +2023,19 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     cudaStream_t s = g->stream;
     hyperim_status st;
 
-    // the visited bitmap goes on chip only while two blocks still fit on an SM
+    // the visited bitmap goes on chip while the block still fits on an SM (and the tuning does not
+    // ask for global bitmaps, which let teams of blocks build one set)
     if ((st = allow_rr_smem())) return st;
-    bool vis_smem = (int64_t)g->n <= kVisSmemBits;
+    bool vis_smem = (int64_t)g->n <= kVisSmemBits &&
+                    sizeof(Shared) + sizeof(uint32_t) * (((size_t)g->n + 31) / 32) <= smem_optin() &&
+                    !(g->helping > 1 && g->schedule != HYPERIM_SCHED_PLAIN && g->warp_set_limit > 0);
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
         const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
         smem = sizeof(Shared) + vis_bytes;
         HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr, kThreads, smem));
-        if (per_sm >= 2 || !vis_smem) break;
+        if (per_sm >= 1 || !vis_smem) break;
         vis_smem = false;
     }
     if (per_sm < 1) return set_error(HYPERIM_ECUDA, "RR kernel does not fit on an SM");
@@ -1966,9 +2056,9 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     int wblocks = 0;
     if (warp_phase) {
         int wper_sm = 0;
-        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper_sm, k_rr_warp, kThreads, sizeof(WarpShared)));
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper_sm, k_rr_warp, kPThreads, sizeof(WarpShared)));
         if (wper_sm < 1) return set_error(HYPERIM_ECUDA, "RR warp-phase kernel does not fit on an SM");
-        wblocks = (int)std::min<int64_t>((int64_t)g->sm_count * wper_sm, (njobs + kWarps - 1) / kWarps);
+        wblocks = (int)std::min<int64_t>((int64_t)g->sm_count * wper_sm, (njobs + kPWarps - 1) / kPWarps);
     }
     // control words: two job counters (warp phase, block phase), the listed jobs, the arena fill
     struct Ctrl {
@@ -1988,7 +2078,9 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
     // the block phase lets idle blocks help with other blocks' sets when the visited bitmaps are
     // in global memory (every block can reach them)
-    const bool helped = warp_phase && !vis_smem;
+    // teams of blocks on the block phase's sets: the tuning's size, or 4 by default
+    const int team = g->helping > 1 ? std::min(g->helping, 8) : 4;
+    const bool helped = warp_phase && !vis_smem && g->helping >= 0 && team > 1;
     SetCtl* d_sctl = nullptr;
     int32_t* d_ring = nullptr;
     if (helped) {
@@ -2038,6 +2130,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.esc_list = d_esc;
     P.sctl = d_sctl;
     P.gdefer = d_ring;
+    P.team = team;
     P.block_phase = 0;
     P.warp_limit = std::min(std::max(g->warp_set_limit, 1), kWQ);
     P.plain = g->schedule == HYPERIM_SCHED_PLAIN ? 1 : 0;
@@ -2086,7 +2179,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         } else if (warp_phase) {
             // warp phase over every job, then the block phase over the jobs it listed
             P.block_phase = 0;
-            { k_rr_warp<<<wblocks, kThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
+            { k_rr_warp<<<wblocks, kPThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
             HYP_CUDA(cudaGetLastError());
             P.block_phase = 1;
             if (helped) {
@@ -2177,14 +2270,15 @@ hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32
     cudaStream_t s = g->stream;
     hyperim_status st;
     if ((st = allow_rr_smem())) return st;
-    bool vis_smem = (int64_t)g->n <= kVisSmemBits;
+    bool vis_smem = (int64_t)g->n <= kVisSmemBits &&
+                    sizeof(Shared) + sizeof(uint32_t) * (((size_t)g->n + 31) / 32) <= smem_optin();
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
         const size_t vis_bytes = vis_smem ? sizeof(uint32_t) * (((size_t)g->n + 31) / 32) : 0;
         smem = sizeof(Shared) + vis_bytes;
         HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kThreads, smem));
-        if (per_sm >= 2 || !vis_smem) break;
+        if (per_sm >= 1 || !vis_smem) break;
         vis_smem = false;
     }
     if (per_sm < 1) return set_error(HYPERIM_ECUDA, "forward kernel does not fit on an SM");
