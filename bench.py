@@ -136,10 +136,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", schedule="persistent"):
-    """One whole IM query through the C ABI; returns counters of the work done."""
+def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", schedule="persistent",
+              tune=True):
+    """One whole IM query through the C ABI; returns counters of the work done. With `tune`, the
+    graph takes the autotuner's RR scheduling for its degree profile (measured once per process,
+    on the first query; a cache lookup afterwards)."""
     q = w.query
     g = H.Graph(w.graph.n, off, mem, q.model, q.uniform_threshold, seed=seed)
+    tuning = g.autotune(roots=q.roots, strategy=q.strategy) if tune else g.tuning()
     if schedule != "persistent":
         g.set_schedule(schedule)
     r1 = g.pool(tag=0, roots=q.roots, strategy=q.strategy)
@@ -160,7 +164,8 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", sc
            "edges": sum(v["mat_he"] + v["gathered"] for v in (v1, v2)),
            "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
            "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
-           "sigma_r2": res["sigma_r2"], "seeds": seeds}
+           "sigma_r2": res["sigma_r2"], "seeds": seeds,
+           "tuning": {k: tuning[k] for k in ("warp_set_limit", "helping", "early_sets_per_block")}}
     r1.close()
     r2.close()
     g.close()
@@ -286,6 +291,7 @@ def bench_gpu(args):
                    "rr_sets_generated_per_step": sum(x["rr_generated"] for x in stats) / args.steps,
                    "brr_rounds": stats[-1]["rounds"], "theta_final": stats[-1]["theta"],
                    "parallelism": f"replicas x{world} (independent queries)",
+                   "rr_tuning": stats[-1]["tuning"],
                    "l2": "flushed between steps (256 MiB write), inputs resident in HBM"},
         "seed_selection_seconds": sum(s["select_seconds"] for s in stats) / args.steps,
         # incidence entries the RR generator read (hyperedge ids of materialising pops plus the

@@ -301,6 +301,68 @@ hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t 
 void hyperim_pool_free(hyperim_pool_t p);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_sample_rr_shard -- like hyperim_sample_rr for one shard of a pool split over `world`
+ *   ranks (processes or GPUs): the shard holds the sets (s, j) of the allocation of theta with
+ *   j = rank (mod world), so the shards of ranks 0..world-1 together hold exactly the pool
+ *   hyperim_sample_rr would build (every set is keyed by (seed, tag, s, j)), with no exchange.
+ *   The shard's n_s (pool view) is the whole allocation it covers; its count is its own sets.
+ *   A pool made by this call is a shard for good (ESTATE if grown with another rank or world,
+ *   or by hyperim_sample_rr). EINVAL: world < 1, rank outside [0, world), others as
+ *   hyperim_sample_rr.
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_sample_rr_shard(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
+                                       int32_t strategy, int32_t rank, int32_t world, hyperim_pool_t* inout);
+
+/* ------------------------------------------------------------------------------------------
+ * Greedy max coverage one round at a time (Algorithm 1), for pools split into shards: each
+ *   round every rank hands its shard's weighted marginal scores (Eq. 2) to an all-reduce (sum),
+ *   and each rank picks the argmax of the sum -- the same vertex everywhere: integer weights,
+ *   ties to the lowest id -- and retires the RR sets of its own shard that it covers.
+ *   hyperim_greedy_begin: the state of a pool's prefix view (the sets a pool grown to theta
+ *     holds; theta = 0: every set of the pool): inverted index and initial scores, weights
+ *     floor(|V_s| 2^32 / n_s) from the view's allocation (1 with plain roots). The pool must not
+ *     grow while the state lives (it holds the pool's read lock).
+ *   hyperim_greedy_scores: copies the shard's n current scores (uint64, device) to dev_out
+ *     (caller-owned device memory, n entries), ordered on the graph's stream.
+ *   hyperim_greedy_pick: argmax over the vertices not picked yet of dev_total (device, n uint64:
+ *     the summed scores; NULL: this shard's own), ties to the lowest id; marks it picked,
+ *     retires this shard's uncovered sets that contain it; *picked = the vertex (host).
+ *     Synchronises the stream.
+ *   hyperim_greedy_end: this shard's coverage per stratum of the picks (Lambda_s) and frees the
+ *     state. EINVAL: null arguments.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct hyperim_greedy* hyperim_greedy_t;
+hyperim_status hyperim_greedy_begin(hyperim_graph_t g, hyperim_pool_t pool, uint64_t theta, hyperim_greedy_t* out);
+hyperim_status hyperim_greedy_scores(hyperim_greedy_t s, uint64_t* dev_out);
+hyperim_status hyperim_greedy_pick(hyperim_greedy_t s, const uint64_t* dev_total, int32_t* picked);
+hyperim_status hyperim_greedy_end(hyperim_greedy_t s, uint64_t lambda_s[HYPERIM_NSTRATA]);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_coverage_view -- Lambda_s of a seed set (host ids) on a pool's prefix view of theta
+ *   (0: the whole pool): the RR sets of each stratum with a member in the set (Sec. 2.2); for a
+ *   shard, its own sets. Synchronises the stream. EINVAL: a seed outside [0, n).
+ * ------------------------------------------------------------------------------------------ */
+hyperim_status hyperim_coverage_view(hyperim_graph_t g, hyperim_pool_t pool, uint64_t theta, const int32_t* seeds_host,
+                                     int32_t k, uint64_t lambda_s[HYPERIM_NSTRATA]);
+
+/* ------------------------------------------------------------------------------------------
+ * hyperim_brr_round -- the host arithmetic of one HyperIM_BRR round (Algorithm 4) from the
+ *   coverages summed over every shard: with theta_i = theta0 2^i and n_s = its allocation,
+ *   sigma_r = sum_s |V_s|/n_s Lambda_s (Eq. 1) on R1 and R2, the Eq. upper_6 bound (p_max = 1)
+ *   from R1, the Sec. 4.2 lower bound from R2, alpha = lower / upper, and stop = 1 when alpha >=
+ *   1 - 1/e - eps or round >= i_max -- exactly what hyperim_select_seeds does per round.
+ *   EINVAL: bad k, eps, ell, root mode or a round beyond 62.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t theta;
+    double sigma_r1, sigma_r2, upper, lower, alpha;
+    int32_t stop;
+} hyperim_brr_round_t;
+hyperim_status hyperim_brr_round(hyperim_graph_t g, int32_t k, double eps, double ell, int32_t root_mode, int32_t round,
+                                 const uint64_t lambda_r1[HYPERIM_NSTRATA], const uint64_t lambda_r2[HYPERIM_NSTRATA],
+                                 hyperim_brr_round_t* out);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_pool_view -- read-only device view of a pool (valid until the pool grows or is freed).
  *   RR set r has members rr_mem[rr_off[r] .. rr_off[r+1]) (ascending ids), stratum rr_stratum[r]
  *   and index rr_j[r] within its stratum. Sets are stored in generation order: one stratum-major

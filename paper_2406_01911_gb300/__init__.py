@@ -102,6 +102,11 @@ class SelectResult(C.Structure):
                 ("seconds_sample", C.c_double), ("seconds_select", C.c_double)]
 
 
+class BrrRound(C.Structure):
+    _fields_ = [("theta", C.c_uint64), ("sigma_r1", C.c_double), ("sigma_r2", C.c_double), ("upper", C.c_double),
+                ("lower", C.c_double), ("alpha", C.c_double), ("stop", C.c_int32)]
+
+
 class ServerArgs(C.Structure):
     _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_size_t)]
 
@@ -153,6 +158,15 @@ _SIGNATURES = {
     "hyperim_sample_rr": (C.c_int, [_vp, C.c_uint32, C.c_uint64, C.c_int32, C.c_int32,
                                     C.POINTER(_vp)]),
     "hyperim_pool_free": (None, [_vp]),
+    "hyperim_sample_rr_shard": (C.c_int, [_vp, C.c_uint32, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                          C.POINTER(_vp)]),
+    "hyperim_greedy_begin": (C.c_int, [_vp, _vp, C.c_uint64, C.POINTER(_vp)]),
+    "hyperim_greedy_scores": (C.c_int, [_vp, _vp]),
+    "hyperim_greedy_pick": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
+    "hyperim_greedy_end": (C.c_int, [_vp, _vp]),
+    "hyperim_coverage_view": (C.c_int, [_vp, _vp, C.c_uint64, _vp, C.c_int32, _vp]),
+    "hyperim_brr_round": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32, _vp, _vp,
+                                    C.POINTER(BrrRound)]),
     "hyperim_pool_view": (C.c_int, [_vp, C.POINTER(PoolView)]),
     "hyperim_pool_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "hyperim_select_seeds": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(SelectOpts), _vp,
@@ -503,6 +517,67 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+class ShardPool(Pool):
+    """One shard of an RR pool split over `world` ranks (hyperim_sample_rr_shard): the sets
+    (s, j) with j = rank (mod world) of each growth's allocation."""
+
+    def __init__(self, graph: Graph, tag=0, rank=0, world=1, roots="stratified", strategy="paper"):
+        self.graph = graph
+        self.tag = int(tag)
+        self.roots = roots
+        self.strategy = strategy
+        self.rank, self.world = int(rank), int(world)
+        self._h = C.c_void_p()
+        self.sample(0)
+
+    def sample(self, theta):
+        _check(lib().hyperim_sample_rr_shard(self.graph.handle, self.tag, int(theta), ROOTS[self.roots],
+                                             STRATEGIES[self.strategy], self.rank, self.world, C.byref(self._h)))
+        return self
+
+
+class GreedyRounds:
+    """Greedy max coverage one round at a time on a pool's prefix view (hyperim_greedy_*)."""
+
+    def __init__(self, graph: Graph, pool: Pool, theta=0):
+        self._h = C.c_void_p()
+        _check(lib().hyperim_greedy_begin(graph.handle, pool.handle, int(theta), C.byref(self._h)))
+
+    def scores_into(self, dev_ptr: int):
+        """Copies the n current scores (uint64) to caller-owned device memory."""
+        _check(lib().hyperim_greedy_scores(self._h, C.c_void_p(int(dev_ptr))))
+
+    def pick(self, dev_total=None) -> int:
+        """Argmax of the summed scores at dev_total (device pointer; None: this pool's own), then
+        the retirement of this pool's sets that contain it; returns the vertex."""
+        v = C.c_int32()
+        _check(lib().hyperim_greedy_pick(self._h, C.c_void_p(int(dev_total)) if dev_total else None, C.byref(v)))
+        return v.value
+
+    def end(self):
+        lam = np.zeros(NSTRATA, np.uint64)
+        _check(lib().hyperim_greedy_end(self._h, _ptr(lam)))
+        self._h = None
+        return lam
+
+
+def hyperim_coverage_view(graph: Graph, pool: Pool, theta, seeds):
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+    lam = np.zeros(NSTRATA, np.uint64)
+    _check(lib().hyperim_coverage_view(graph.handle, pool.handle, int(theta), _ptr(s) if s.size else None, len(s),
+                                       _ptr(lam)))
+    return lam
+
+
+def hyperim_brr_round(graph: Graph, k, eps, ell, roots, i, lambda_r1, lambda_r2):
+    a = np.ascontiguousarray(lambda_r1, dtype=np.uint64)
+    b = np.ascontiguousarray(lambda_r2, dtype=np.uint64)
+    r = BrrRound()
+    _check(lib().hyperim_brr_round(graph.handle, int(k), float(eps), float(ell), ROOTS[roots], int(i), _ptr(a), _ptr(b),
+                                   C.byref(r)))
+    return {f: getattr(r, f) for f, _ in BrrRound._fields_}
 
 
 class Server:

@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <shared_mutex>
 #include <string>
 #include <vector>
 
@@ -696,19 +697,24 @@ static hyperim_status pool_grow(hyperim_graph* g, hyperim_pool* p, uint64_t thet
     return sample_rr(g, p, ns);
 }
 
-hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
-                                 int32_t strategy, hyperim_pool_t* inout) {
+static hyperim_status sample_rr_shard(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
+                                      int32_t strategy, int32_t rank, int32_t world, hyperim_pool_t* inout) {
     if (!g || !inout) return set_error(HYPERIM_EINVAL, "null argument");
+    if (world < 1 || rank < 0 || rank >= world) return set_error(HYPERIM_EINVAL, "need 0 <= rank < world");
     hyperim_status st;
     bool created = false;
     if (!*inout) {
         if ((st = pool_create(g, pool_tag, root_mode, strategy, inout))) return st;
+        (*inout)->shard_rank = rank;
+        (*inout)->shard_world = world;
         created = true;
     } else {
         hyperim_pool* p = *inout;
         if (graph_root(p->g) != graph_root(g)) return set_error(HYPERIM_ESTATE, "pool belongs to another graph");
         if (p->tag != pool_tag || p->root_mode != root_mode || p->strategy != strategy)
             return set_error(HYPERIM_ESTATE, "pool was created with other tag/root mode/strategy");
+        if (p->shard_rank != rank || p->shard_world != world)
+            return set_error(HYPERIM_ESTATE, "pool was created as another shard");
     }
     {
         std::unique_lock<std::shared_mutex> lk((*inout)->mu);
@@ -721,6 +727,16 @@ hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t 
         g_last_error = keep;
     }
     return st;
+}
+
+hyperim_status hyperim_sample_rr(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
+                                 int32_t strategy, hyperim_pool_t* inout) {
+    return sample_rr_shard(g, pool_tag, theta, root_mode, strategy, 0, 1, inout);
+}
+
+hyperim_status hyperim_sample_rr_shard(hyperim_graph_t g, uint32_t pool_tag, uint64_t theta, int32_t root_mode,
+                                       int32_t strategy, int32_t rank, int32_t world, hyperim_pool_t* inout) {
+    return sample_rr_shard(g, pool_tag, theta, root_mode, strategy, rank, world, inout);
 }
 
 void hyperim_pool_free(hyperim_pool_t p) {
@@ -881,6 +897,89 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     }
     out->seconds_sample = t_sample;
     out->seconds_select = t_select;
+    return HYPERIM_OK;
+}
+
+}  // extern "C"
+
+struct hyperim_greedy {
+    hyperim::GreedyState* st = nullptr;
+};
+
+extern "C" {
+
+hyperim_status hyperim_greedy_begin(hyperim_graph_t g, hyperim_pool_t pool, uint64_t theta, hyperim_greedy_t* out) {
+    if (!g || !pool || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    *out = nullptr;
+    if (graph_root(pool->g) != graph_root(g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    uint64_t lim[HYPERIM_NSTRATA];
+    if (theta) allocate_strata(g, pool->root_mode, theta, lim);
+    hyperim_greedy* h = new (std::nothrow) hyperim_greedy();
+    if (!h) return set_error(HYPERIM_ENOMEM, "host allocation failed");
+    hyperim_status st = greedy_begin(g, pool, theta ? lim : nullptr, &h->st);
+    if (st != HYPERIM_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return HYPERIM_OK;
+}
+
+hyperim_status hyperim_greedy_scores(hyperim_greedy_t s, uint64_t* dev_out) {
+    if (!s || !dev_out) return set_error(HYPERIM_EINVAL, "null argument");
+    return greedy_scores(s->st, reinterpret_cast<unsigned long long*>(dev_out));
+}
+
+hyperim_status hyperim_greedy_pick(hyperim_greedy_t s, const uint64_t* dev_total, int32_t* picked) {
+    if (!s || !picked) return set_error(HYPERIM_EINVAL, "null argument");
+    return greedy_pick(s->st, reinterpret_cast<const unsigned long long*>(dev_total), picked);
+}
+
+hyperim_status hyperim_greedy_end(hyperim_greedy_t s, uint64_t lambda_s[HYPERIM_NSTRATA]) {
+    if (!s) return set_error(HYPERIM_EINVAL, "null argument");
+    hyperim_status st = greedy_end(s->st, lambda_s);
+    delete s;
+    return st;
+}
+
+hyperim_status hyperim_coverage_view(hyperim_graph_t g, hyperim_pool_t pool, uint64_t theta, const int32_t* seeds_host,
+                                     int32_t k, uint64_t lambda_s[HYPERIM_NSTRATA]) {
+    if (!g || !pool || !lambda_s || (k > 0 && !seeds_host) || k < 0) return set_error(HYPERIM_EINVAL, "null argument");
+    if (graph_root(pool->g) != graph_root(g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
+    for (int32_t i = 0; i < k; ++i)
+        if (seeds_host[i] < 0 || seeds_host[i] >= g->n) return set_error(HYPERIM_EINVAL, "seed outside [0, n)");
+    uint64_t lim[HYPERIM_NSTRATA];
+    if (theta) allocate_strata(g, pool->root_mode, theta, lim);
+    std::shared_lock<std::shared_mutex> lk(pool->mu);
+    return coverage(g, pool, seeds_host, k, lambda_s, theta ? lim : nullptr);
+}
+
+hyperim_status hyperim_brr_round(hyperim_graph_t g, int32_t k, double eps, double ell, int32_t root_mode, int32_t round,
+                                 const uint64_t lambda_r1[HYPERIM_NSTRATA], const uint64_t lambda_r2[HYPERIM_NSTRATA],
+                                 hyperim_brr_round_t* out) {
+    if (!g || !lambda_r1 || !lambda_r2 || !out) return set_error(HYPERIM_EINVAL, "null argument");
+    if (root_mode != HYPERIM_ROOTS_PLAIN && root_mode != HYPERIM_ROOTS_STRATIFIED)
+        return set_error(HYPERIM_EINVAL, "unknown root mode");
+    if (round < 0 || round > 62) return set_error(HYPERIM_EINVAL, "round outside [0, 62]");
+    hyperim_theta_plan plan;
+    hyperim_status st;
+    if ((st = plan_theta(g->n, k, eps, ell, &plan))) return st;
+    const uint64_t theta = plan.theta0 << round;
+    uint64_t ns[HYPERIM_NSTRATA];
+    allocate_strata(g, root_mode, theta, ns);
+    uint64_t N = 0;
+    for (int s = 0; s < HYPERIM_NSTRATA; ++s) N += ns[s];
+    const double s1 = estimate(g, root_mode, ns, lambda_r1);
+    const double s2 = estimate(g, root_mode, ns, lambda_r2);
+    const double lam1 = s1 * (double)N / (double)g->n;
+    const double lam2 = s2 * (double)N / (double)g->n;
+    out->theta = theta;
+    out->sigma_r1 = s1;
+    out->sigma_r2 = s2;
+    out->upper = upper_bound(lam1, k, g->n, N);
+    out->lower = lower_bound(lam2, plan.delta, g->n, N);
+    out->alpha = out->lower / out->upper;
+    out->stop = (out->alpha >= 1.0 - std::exp(-1.0) - eps || round >= plan.i_max) ? 1 : 0;
     return HYPERIM_OK;
 }
 

@@ -8,6 +8,8 @@
 // winner of a round is read on the device by the next launch.
 #include <algorithm>
 #include <cstddef>
+#include <new>
+#include <string>
 
 #include "internal.h"
 
@@ -463,6 +465,144 @@ hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_
     HYP_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < HYPERIM_NSTRATA; ++i) lambda_s[i] = hl[i];
     return check_device_status(g, "coverage");
+}
+
+}  // namespace hyperim
+
+// ---- greedy one round at a time (sharded pools) ---------------------------------------------
+// The state of Algorithm 1 on one pool (a prefix view of it): the inverted index and the
+// weighted marginal scores of its RR sets, which sets are covered, which vertices are picked and
+// Lambda per stratum. greedy_pick takes the argmax over a score vector the caller supplies --
+// the sum, over every shard of a pool, of their scores (integer sums: the order of the shards'
+// additions does not matter) -- then retires the pick's uncovered sets of this shard.
+namespace hyperim {
+
+struct GreedyState {
+    hyperim_graph* g = nullptr;
+    hyperim_pool* p = nullptr;
+    std::shared_lock<std::shared_mutex> lock;  // the pool may not grow while the state lives
+    Weights W{};
+    int ablocks = 0;
+    uint32_t *cnt = nullptr, *inv = nullptr, *covered = nullptr, *bid = nullptr, *ticket = nullptr;
+    int64_t* inv_off = nullptr;
+    unsigned long long *score = nullptr, *lam = nullptr, *bscore = nullptr;
+    uint8_t* picked = nullptr;
+    int32_t *best = nullptr, *seed_d = nullptr;
+    TopK* tk = nullptr;
+    size_t bytes_cnt = 0, bytes_inv = 0, bytes_cov = 0;
+};
+
+namespace {
+void free_state(GreedyState* s) {
+    hyperim_graph* g = s->g;
+    const size_t n = (size_t)g->n;
+    dev_free(g, s->cnt, s->bytes_cnt);
+    dev_free(g, s->inv_off, sizeof(int64_t) * (n + 1));
+    dev_free(g, s->inv, s->bytes_inv);
+    dev_free(g, s->score, sizeof(unsigned long long) * n);
+    dev_free(g, s->picked, n);
+    dev_free(g, s->covered, s->bytes_cov);
+    dev_free(g, s->lam, sizeof(unsigned long long) * HYPERIM_NSTRATA);
+    dev_free(g, s->bscore, sizeof(unsigned long long) * s->ablocks);
+    dev_free(g, s->bid, sizeof(uint32_t) * s->ablocks);
+    dev_free(g, s->ticket, sizeof(uint32_t) * 2);
+    dev_free(g, s->best, sizeof(int32_t) * 2);
+    dev_free(g, s->seed_d, sizeof(int32_t));
+    dev_free(g, s->tk, sizeof(TopK));
+    cudaStreamSynchronize(g->stream);
+    delete s;
+}
+}  // namespace
+
+hyperim_status greedy_begin(hyperim_graph* g, hyperim_pool* p, const uint64_t* lim, GreedyState** out) {
+    *out = nullptr;
+    GreedyState* s = new (std::nothrow) GreedyState();
+    if (!s) return set_error(HYPERIM_ENOMEM, "host allocation failed");
+    s->g = g;
+    s->p = p;
+    s->lock = std::shared_lock<std::shared_mutex>(p->mu);
+    cudaStream_t st_ = g->stream;
+    const int32_t n = g->n;
+    const int64_t N = p->count, T = p->total;
+    const int sm = g->sm_count;
+    if (N >= (int64_t)0xFFFFFFFFll) {
+        delete s;
+        return set_error(HYPERIM_EOVERFLOW, "more than 2^32 - 1 RR sets");
+    }
+    uint64_t view_ns[HYPERIM_NSTRATA];
+    const Limits L = make_limits(p, lim, view_ns);
+    for (int i = 0; i < HYPERIM_NSTRATA; ++i) s->W.w[i] = stratum_weight(g, p->root_mode, view_ns[i], i);
+    s->ablocks = grid_cap(n, kArgThreads, sm, 2);
+    s->bytes_cnt = sizeof(uint32_t) * ((size_t)n + 1);
+    s->bytes_inv = sizeof(uint32_t) * (size_t)std::max<int64_t>(T, 1);
+    s->bytes_cov = sizeof(uint32_t) * (size_t)std::max<int64_t>(N, 1);
+    hyperim_status st;
+    auto fail = [&](hyperim_status e) {
+        free_state(s);
+        return e;
+    };
+    if ((st = dev_alloc(g, (void**)&s->cnt, s->bytes_cnt)) || (st = dev_alloc(g, (void**)&s->inv_off, sizeof(int64_t) * ((size_t)n + 1))) ||
+        (st = dev_alloc(g, (void**)&s->inv, s->bytes_inv)) || (st = dev_alloc(g, (void**)&s->score, sizeof(unsigned long long) * (size_t)n)) ||
+        (st = dev_alloc(g, (void**)&s->picked, (size_t)n)) || (st = dev_alloc(g, (void**)&s->covered, s->bytes_cov)) ||
+        (st = dev_alloc(g, (void**)&s->lam, sizeof(unsigned long long) * HYPERIM_NSTRATA)) ||
+        (st = dev_alloc(g, (void**)&s->bscore, sizeof(unsigned long long) * s->ablocks)) ||
+        (st = dev_alloc(g, (void**)&s->bid, sizeof(uint32_t) * s->ablocks)) || (st = dev_alloc(g, (void**)&s->ticket, sizeof(uint32_t) * 2)) ||
+        (st = dev_alloc(g, (void**)&s->best, sizeof(int32_t) * 2)) || (st = dev_alloc(g, (void**)&s->seed_d, sizeof(int32_t))) ||
+        (st = dev_alloc(g, (void**)&s->tk, sizeof(TopK))))
+        return fail(st);
+    cudaError_t e = cudaMemsetAsync(s->cnt, 0, s->bytes_cnt, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->score, 0, sizeof(unsigned long long) * (size_t)n, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->picked, 0, (size_t)n, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->covered, 0, s->bytes_cov, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->lam, 0, sizeof(unsigned long long) * HYPERIM_NSTRATA, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ticket, 0, sizeof(uint32_t) * 2, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->tk, 0, sizeof(TopK), st_);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "greedy state"));
+    if (T > 0 && !L.on) { k_count_occ<<<grid_cap(T, 256, sm, 32), 256, 0, st_>>>(p->rr_mem, T, s->cnt); count_launch(); }
+    if (T > 0 && L.on)
+        { k_count_occ_view<<<grid_cap(N * 32, 256, sm, 32), 256, 0, st_>>>(p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j, N, L,
+                                                                          s->cnt); count_launch(); }
+    if ((st = exclusive_scan_u32_to_i64(g, s->cnt, s->inv_off, n))) return fail(st);
+    e = cudaMemsetAsync(s->cnt, 0, s->bytes_cnt, st_);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "greedy state"));
+    if (N > 0)
+        { k_scatter_inv<<<grid_cap(N * 32, 256, sm, 32), 256, 0, st_>>>(p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j, N, L,
+                                                                      s->inv_off, s->cnt, s->inv, s->score, s->W); count_launch(); }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(cuda_fail(e, "greedy index"));
+    *out = s;
+    return HYPERIM_OK;
+}
+
+hyperim_status greedy_scores(GreedyState* s, unsigned long long* dev_out) {
+    HYP_CUDA(cudaMemcpyAsync(dev_out, s->score, sizeof(unsigned long long) * (size_t)s->g->n, cudaMemcpyDeviceToDevice,
+                             s->g->stream));
+    return HYPERIM_OK;
+}
+
+hyperim_status greedy_pick(GreedyState* s, const unsigned long long* dev_total, int32_t* picked) {
+    hyperim_graph* g = s->g;
+    hyperim_pool* p = s->p;
+    cudaStream_t st_ = g->stream;
+    { k_argmax<<<s->ablocks, kArgThreads, 0, st_>>>(dev_total ? dev_total : s->score, s->picked, g->n, s->bscore, s->bid,
+                                                    s->ticket, s->best, s->seed_d, 0, s->tk); count_launch(); }
+    { k_retire<<<g->sm_count * 8, 256, 0, st_>>>(s->best, s->inv_off, s->inv, p->rr_off, p->rr_mem, p->rr_stratum,
+                                                 s->covered, s->score, s->lam, s->W); count_launch(); }
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(cudaMemcpyAsync(picked, s->best, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    HYP_CUDA(cudaStreamSynchronize(st_));
+    return check_device_status(g, "greedy pick");
+}
+
+hyperim_status greedy_end(GreedyState* s, uint64_t lambda_s[HYPERIM_NSTRATA]) {
+    unsigned long long hl[HYPERIM_NSTRATA];
+    cudaError_t e = cudaMemcpyAsync(hl, s->lam, sizeof(hl), cudaMemcpyDeviceToHost, s->g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->g->stream);
+    if (e == cudaSuccess && lambda_s)
+        for (int i = 0; i < HYPERIM_NSTRATA; ++i) lambda_s[i] = hl[i];
+    free_state(s);
+    if (e != cudaSuccess) return cuda_fail(e, "greedy end");
+    return HYPERIM_OK;
 }
 
 }  // namespace hyperim

@@ -170,7 +170,8 @@ struct hyperim_pool {
     hyperim_graph* g = nullptr;
     uint32_t tag = 0;
     int32_t root_mode = 0, strategy = 0;
-    uint64_t n_s[HYPERIM_NSTRATA] = {};
+    int32_t shard_rank = 0, shard_world = 1;  // a shard holds the sets (s, j) with j = rank (mod world)
+    uint64_t n_s[HYPERIM_NSTRATA] = {};       // the allocation it covers (every shard: all of it)
     int64_t count = 0, total = 0;
     size_t cap_off = 0, cap_stratum = 0, cap_j = 0, cap_total = 0;  // allocated entries
     int64_t* rr_off = nullptr;      // count + 1
@@ -261,6 +262,14 @@ hyperim_status greedy(hyperim_graph* g, hyperim_pool* p, int32_t k, int32_t* see
                       const uint64_t* lim = nullptr);
 hyperim_status coverage(hyperim_graph* g, hyperim_pool* p, const int32_t* seeds_host, int32_t k,
                         uint64_t lambda_s[HYPERIM_NSTRATA], const uint64_t* lim = nullptr);
+
+// greedy.cu: greedy max coverage one round at a time, with the argmax taken over a score vector
+// the caller supplies (the sum of every shard's scores); see hyperim_greedy_begin
+struct GreedyState;
+hyperim_status greedy_begin(hyperim_graph* g, hyperim_pool* p, const uint64_t* lim, GreedyState** out);
+hyperim_status greedy_scores(GreedyState* st, unsigned long long* dev_out);
+hyperim_status greedy_pick(GreedyState* st, const unsigned long long* dev_total, int32_t* picked);
+hyperim_status greedy_end(GreedyState* st, uint64_t lambda_s[HYPERIM_NSTRATA]);
 
 // host arithmetic (plan.cpp)
 void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,

@@ -49,6 +49,7 @@ constexpr int kWHash = 1 << kWHashBits;  // per-warp open-addressing member set
 struct RRJobMap {
     int64_t job_base[HYPERIM_NSTRATA + 1];
     uint32_t j_base[HYPERIM_NSTRATA];
+    uint32_t j_step;   // the pool's shard stride: job x of stratum s is j = j_base[s] + x j_step
 };
 
 struct RRParams {
@@ -1426,7 +1427,7 @@ __device__ __forceinline__ Job decode_job(const RRParams& P, int64_t job) {
     const int64_t local = job - P.pool_start[J.pi];
     J.s = 0;
     while (J.s < HYPERIM_NSTRATA - 1 && local >= jm.job_base[J.s + 1]) ++J.s;
-    J.j = jm.j_base[J.s] + (uint32_t)(local - jm.job_base[J.s]);
+    J.j = jm.j_base[J.s] + (uint32_t)(local - jm.job_base[J.s]) * jm.j_step;
     const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)J.s;
     J.ybase = stream_ybase(P.tags[J.pi], sfield);
     return J;
@@ -1909,7 +1910,7 @@ __global__ void k_compact_rr(const int32_t* __restrict__ arena, const int64_t* _
             while (s < HYPERIM_NSTRATA - 1 && r >= jm.job_base[s + 1]) ++s;
             rr_off[base_count + r] = dst;
             rr_stratum[base_count + r] = (uint8_t)s;
-            rr_j[base_count + r] = jm.j_base[s] + (uint32_t)(r - jm.job_base[s]);
+            rr_j[base_count + r] = jm.j_base[s] + (uint32_t)(r - jm.job_base[s]) * jm.j_step;
             if (r == njobs - 1) rr_off[base_count + njobs] = base_total + boff[njobs];
         }
     }
@@ -2006,13 +2007,17 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     pool_start[0] = 0;
     for (int q = 0; q < npools; ++q) {
         hyperim_pool* p = pools[q];
+        // a shard (rank r of W) holds the sets j = r (mod W) of each stratum's allocation
+        const uint64_t W = (uint64_t)std::max(p->shard_world, 1), R = (uint64_t)std::max(p->shard_rank, 0);
         jm[q].job_base[0] = 0;
+        jm[q].j_step = (uint32_t)W;
         for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
             const uint64_t old = p->n_s[s];
-            const uint64_t add = new_ns[q][s] > old ? new_ns[q][s] - old : 0;
             if (new_ns[q][s] > 0xFFFFFFFFull)
                 return set_error(HYPERIM_EOVERFLOW, "an RR index within a stratum would reach 2^32");
-            jm[q].j_base[s] = (uint32_t)old;
+            const uint64_t j0 = old + (R + W - old % W) % W;  // first j >= old of this shard
+            const uint64_t add = new_ns[q][s] > j0 ? (new_ns[q][s] - 1 - j0) / W + 1 : 0;
+            jm[q].j_base[s] = (uint32_t)std::min<uint64_t>(j0, 0xFFFFFFFFull);
             jm[q].job_base[s + 1] = jm[q].job_base[s] + (int64_t)add;
         }
         pool_start[q + 1] = pool_start[q] + jm[q].job_base[HYPERIM_NSTRATA];
