@@ -165,7 +165,7 @@ def run_query(H, torch, w, off, mem, seed, host_inputs=False, upper="closed", sc
            "select_seconds": res["seconds_select"], "sample_seconds": res["seconds_sample"],
            "rounds": res["rounds"], "theta": res["theta"] or (q.theta or 0), "sigma": res["sigma_r1"],
            "sigma_r2": res["sigma_r2"], "seeds": seeds,
-           "tuning": {k: tuning[k] for k in ("warp_set_limit", "helping", "early_sets_per_block")}}
+           "tuning": {k: tuning[k] for k in ("warp_set_limit", "early_sets_per_block")}}
     r1.close()
     r2.close()
     g.close()

@@ -217,12 +217,6 @@ hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule);
 typedef struct {
     int32_t warp_set_limit;
     int32_t early_sets_per_block;
-    /* block phase (sets larger than warp_set_limit, persistent schedule, warp phase on): teams
-       of consecutive blocks build one set at a time, the first block taking the jobs and the
-       others popping vertices of its set. 0: teams of 4 when the visited bitmaps live in global
-       memory (n > 2^19), the default; 2..8: teams of that many blocks (bitmaps moved to global
-       memory); -1 or 1: no teams. */
-    int32_t helping;
 } hyperim_tuning;
 hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning* t);
 hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out);
@@ -233,8 +227,7 @@ hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out);
  *   threshold, n and nnz, the shares of the 16 strata, the largest neighbourhood and degree, in
  *   logarithmic buckets) and (root_mode, strategy) form a key; if the process has tuned a graph
  *   of that key before, its choice is applied at once (from_cache = 1). Otherwise every
- *   candidate -- no warp phase, or warp_set_limit in {32, 128} with teams of 1, 2, 4 or 8
- *   blocks (helping -1, 2, 4, 8) -- grows a scratch
+ *   candidate -- warp_set_limit in {0 (no warp phase), 16, 32, 64, 128} -- grows a scratch
  *   pool (tag 255) to `sets` RR sets (0: 8 per SM), the same sets each time since they are keyed
  *   by (stratum, index), and the candidate with the least RR-kernel time (CUDA events, best of
  *   two) is applied to g and cached under the key. early_sets_per_block is left as it is. The
@@ -245,9 +238,8 @@ typedef struct {
     hyperim_tuning chosen;
     int32_t from_cache;
     int32_t candidates;          /* timed now (0 when from_cache) */
-    int32_t warp_set_limit[10];  /* per candidate */
-    int32_t helping[10];
-    double seconds[10];          /* RR-kernel seconds of the candidate's growth */
+    int32_t warp_set_limit[8];   /* per candidate */
+    double seconds[8];           /* RR-kernel seconds of the candidate's growth */
     uint64_t profile_key;
 } hyperim_autotune_result;
 hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int32_t strategy, uint64_t sets,

@@ -78,12 +78,12 @@ class PoolView(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32), ("helping", C.c_int32)]
+    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32)]
 
 
 class AutotuneResult(C.Structure):
     _fields_ = [("chosen", Tuning), ("from_cache", C.c_int32), ("candidates", C.c_int32),
-                ("warp_set_limit", C.c_int32 * 10), ("helping", C.c_int32 * 10), ("seconds", C.c_double * 10),
+                ("warp_set_limit", C.c_int32 * 8), ("seconds", C.c_double * 8),
                 ("profile_key", C.c_uint64)]
 
 
@@ -410,15 +410,13 @@ class Graph:
     def tuning(self):
         t = Tuning()
         _check(lib().hyperim_graph_get_tuning(self._h, C.byref(t)))
-        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block,
-                "helping": t.helping}
+        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block}
 
-    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None, helping=None):
+    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None):
         """RR-generation scheduling (hyperim_graph_set_tuning); the results never change."""
         cur = self.tuning()
         pick = lambda v, k: int(cur[k] if v is None else v)
-        t = Tuning(pick(warp_set_limit, "warp_set_limit"), pick(early_sets_per_block, "early_sets_per_block"),
-                   pick(helping, "helping"))
+        t = Tuning(pick(warp_set_limit, "warp_set_limit"), pick(early_sets_per_block, "early_sets_per_block"))
         _check(lib().hyperim_graph_set_tuning(self._h, C.byref(t)))
 
     def autotune(self, roots="stratified", strategy="paper", sets=0):
@@ -426,9 +424,9 @@ class Graph:
         choice for an equal degree profile) and apply the fastest; returns what was chosen."""
         r = AutotuneResult()
         _check(lib().hyperim_graph_autotune(self._h, ROOTS[roots], STRATEGIES[strategy], int(sets), C.byref(r)))
-        return {"warp_set_limit": r.chosen.warp_set_limit, "helping": r.chosen.helping,
+        return {"warp_set_limit": r.chosen.warp_set_limit,
                 "early_sets_per_block": r.chosen.early_sets_per_block, "from_cache": bool(r.from_cache),
-                "candidates": [(r.warp_set_limit[i], r.helping[i], r.seconds[i]) for i in range(r.candidates)],
+                "candidates": [(r.warp_set_limit[i], r.seconds[i]) for i in range(r.candidates)],
                 "profile_key": r.profile_key}
 
     def set_wait_limit(self, iterations):

@@ -379,7 +379,6 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->wait_limit = r->wait_limit;
     h->warp_set_limit = r->warp_set_limit;
     h->early_sets_per_block = r->early_sets_per_block;
-    h->helping = r->helping;
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -483,10 +482,8 @@ hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning*
     if (t->warp_set_limit < 0 || t->warp_set_limit > 128) return set_error(HYPERIM_EINVAL, "warp_set_limit outside [0, 128]");
     if (t->early_sets_per_block < 1 || t->early_sets_per_block > 4096)
         return set_error(HYPERIM_EINVAL, "early_sets_per_block outside [1, 4096]");
-    if (t->helping < -1 || t->helping > 8) return set_error(HYPERIM_EINVAL, "helping outside [-1, 8]");
     g->warp_set_limit = t->warp_set_limit;
     g->early_sets_per_block = t->early_sets_per_block;
-    g->helping = t->helping;
     return HYPERIM_OK;
 }
 
@@ -494,7 +491,6 @@ hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out) 
     if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
     out->warp_set_limit = g->warp_set_limit;
     out->early_sets_per_block = g->early_sets_per_block;
-    out->helping = g->helping;
     return HYPERIM_OK;
 }
 
@@ -552,25 +548,22 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
             hyperim_tuning t = it->second;
             t.early_sets_per_block = g->early_sets_per_block;
             g->warp_set_limit = t.warp_set_limit;
-            g->helping = t.helping;
             out->chosen = t;
             out->from_cache = 1;
             return HYPERIM_OK;
         }
     }
     if (sets == 0) sets = 8 * (uint64_t)std::max(g->sm_count, 1);
-    const int32_t keep_w = g->warp_set_limit, keep_h = g->helping, keep_sched = g->schedule;
+    const int32_t keep_w = g->warp_set_limit, keep_sched = g->schedule;
     g->schedule = HYPERIM_SCHED_PERSISTENT;
-    // (warp_set_limit, helping): no warp phase; warp phase with teams of 1, 2, 4, 8 blocks
-    const int32_t cand[9][2] = {{0, -1}, {32, -1}, {32, 2}, {32, 4}, {32, 8}, {128, -1}, {128, 2}, {128, 4}, {128, 8}};
+    const int32_t cand[5] = {0, 16, 32, 64, 128};  // warp-phase set limits (0: none)
     double best = -1.0;
-    hyperim_tuning choice{keep_w, g->early_sets_per_block, keep_h};
+    hyperim_tuning choice{keep_w, g->early_sets_per_block};
     hyperim_status st = HYPERIM_OK;
     int c = 0;
     {
-        for (int ci = 0; ci < 9 && st == HYPERIM_OK; ++ci) {
-            g->warp_set_limit = cand[ci][0];
-            g->helping = cand[ci][1];
+        for (int ci = 0; ci < 5 && st == HYPERIM_OK; ++ci) {
+            g->warp_set_limit = cand[ci];
             double secs = -1.0;
             for (int rep = 0; rep < 2 && st == HYPERIM_OK; ++rep) {
                 hyperim_pool* p = nullptr;
@@ -584,14 +577,12 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
                 if (st == HYPERIM_OK && (secs < 0.0 || t < secs)) secs = t;
             }
             if (st != HYPERIM_OK) break;
-            out->warp_set_limit[c] = cand[ci][0];
-            out->helping[c] = cand[ci][1];
+            out->warp_set_limit[c] = cand[ci];
             out->seconds[c] = secs;
             ++c;
             if (best < 0.0 || secs < best) {
                 best = secs;
-                choice.warp_set_limit = cand[ci][0];
-                choice.helping = cand[ci][1];
+                choice.warp_set_limit = cand[ci];
             }
         }
     }
@@ -599,11 +590,9 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
     g->schedule = keep_sched;
     if (st != HYPERIM_OK) {
         g->warp_set_limit = keep_w;
-        g->helping = keep_h;
         return st;
     }
     g->warp_set_limit = choice.warp_set_limit;
-    g->helping = choice.helping;
     out->chosen = choice;
     std::lock_guard<std::mutex> lk(tune_mutex());
     tune_cache()[key] = choice;

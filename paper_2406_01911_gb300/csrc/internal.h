@@ -150,7 +150,6 @@ struct hyperim_graph {
     uint32_t wait_limit = 0;     // iterations of a bounded device wait (0: the default)
     int32_t warp_set_limit = 0;  // RR sets up to this size are built by one warp (0: no warp phase)
     int32_t early_sets_per_block = 4;  // BRR's first launch: sets per resident block and pool
-    int32_t helping = 0;         // block phase helping: 0 when bitmaps are global, 1 always, -1 never
     // caller's device allocator (hyperim_load_args); null: stream-ordered cudaMallocAsync
     void* (*alloc_fn)(size_t, void*, void*) = nullptr;
     void (*free_fn)(void*, void*, void*) = nullptr;

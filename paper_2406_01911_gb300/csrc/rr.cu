@@ -94,9 +94,6 @@ struct RRParams {
     int* esc_count;           // jobs the warp phase handed to the block phase
     int32_t* esc_list;        // those jobs
     int block_phase;          // 1: this launch runs the jobs of esc_list (else all jobs)
-    int team;                 // block phase with helping: blocks per team (the first leads)
-    struct SetCtl* sctl;      // block phase with helping: one set-control record per block
-    int32_t* gdefer;          // block phase with helping: kDCapG deferred pops per block (a ring)
     int warp_limit;           // warp phase: the largest RR set a warp builds alone (1..kWQ)
     int plain;                // 1: this launch runs jobs [plain_base, plain_base + gridDim.x), one per block
     int64_t plain_base;
@@ -319,9 +316,8 @@ __device__ __forceinline__ void push(const RRParams& P, Shared& S, uint32_t* vis
 }
 
 // Where a pop's activations go: the RR set of a block (its visited bitmap and work queue, the
-// queue's tail counter in shared memory, or in global memory for a set other blocks may help
-// with), or the RR set a warp builds alone (an open-addressing member set and a queue in shared
-// memory).
+// queue's tail counter in shared memory), or the RR set a warp builds alone (an open-addressing
+// member set and a queue in shared memory).
 struct QueueSink {
     uint32_t* vis;
     int32_t* list;
@@ -357,65 +353,6 @@ struct WarpSink {
         atomicMax(tail, limit + 1);  // no free slot (cannot happen below kWQ + 32 members)
     }
 };
-
-// The RR set a block builds in the helped block phase, with its queue counters in global memory so
-// that blocks without a job of their own can take pops of it. claim packs the set's epoch (bumped
-// at every new set of the block) with the number of queue slots claimed, so a claim never lands
-// in a later set. A claimed pop ends done, or deferred to the owner's block path: reserved in the
-// ring (ndef_res), written, then counted (ndef); the owner runs deferred pops once nothing is in
-// flight and counts them in ndef_done and done.
-struct SetCtl {
-    unsigned long long claim;  // (epoch << 32) | slots claimed in this epoch
-    int tail;                  // members pushed
-    int done;                  // pops finished
-    int ndef_res;              // deferred-ring slots reserved
-    int ndef;                  // deferred pops written
-    int ndef_done;             // deferred pops the owner has run
-    int job;                   // the set's job (valid for the epoch in claim)
-    int active;                // 1 while the owner works on a set
-    int finished;              // 1 once the owner has no job left
-};
-constexpr int kDCapG = 8192;       // deferred ring per block
-constexpr int kDClaimMax = 4096;   // no claim while this many deferred pops wait (ring margin)
-
-// Claim a queue slot of the set behind c in epoch `epoch` (lane 0). The owner waits (bounded)
-// while pops are in flight and returns -1 once nothing is (quiescent: every claimed pop is done
-// or deferred); a helper never waits: -1 when nothing is claimable or the set is gone.
-__device__ int claim_global(const RRParams& P, SetCtl* c, uint32_t epoch, int64_t job, bool owner) {
-    for (int it = 0; it < P.spin_limit; ++it) {
-        const int d = *(volatile int*)&c->done;
-        __threadfence();
-        const unsigned long long cl = *(volatile unsigned long long*)&c->claim;
-        __threadfence();
-        const int t = *(volatile int*)&c->tail;
-        const int nd = *(volatile int*)&c->ndef, ndd = *(volatile int*)&c->ndef_done;
-        if ((uint32_t)(cl >> 32) != epoch) return -1;  // (a helper) the set is finished
-        const int h = (int)(uint32_t)cl;
-        const int pending = nd - ndd;
-        if (h < t && pending < kDClaimMax) {
-            if (atomicCAS(&c->claim, cl, cl + 1) == cl) return h;
-            continue;
-        }
-        if (!owner) return -1;
-        if (h - pending == d) return -1;
-        __nanosleep(64);
-    }
-    if (owner) dev_fail(P.st, kErrSpin, (int32_t)job);
-    return -1;
-}
-
-// A claimed pop of the set behind c ends: counted done, or put in the owner's deferred ring
-__device__ __forceinline__ void end_pop_global(SetCtl* c, int32_t* ring, bool defer, int32_t mu) {
-    if (defer) {
-        const int d = atomicAdd(&c->ndef_res, 1);
-        ring[d & (kDCapG - 1)] = mu;
-        __threadfence();
-        atomicAdd(&c->ndef, 1);
-    } else {
-        __threadfence();  // this pop's pushes before its completion
-        atomicAdd(&c->done, 1);
-    }
-}
 
 // Work queue of one RR set (lane 0 of a warp). Slots [0, tail) are reserved, [0, head) claimed,
 // done pops are finished (their pushes are in), ndef claimed pops wait for the block path.
@@ -1610,169 +1547,6 @@ __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int
     }
 }
 
-// Block phase with helping (graphs whose visited bitmaps live in global memory): the blocks form
-// teams of P.team consecutive blocks. The first block of a team takes the listed jobs and builds
-// each set as k_rr does, but with the set's queue counters in its SetCtl; the other blocks of the
-// team only pop vertices of their leader's current set -- into its queue and bitmap; the draws
-// are keyed by (RR, vertex, layer), so who pops a vertex does not matter -- and leave once the
-// leader has no job left. A helper never makes its leader wait except for the pops it has claimed
-// (finite work), and waits for its leader's next set only in bounded rounds.
-__global__ void __launch_bounds__(kThreads, 1) k_rr_help(RRParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Shared& S = *reinterpret_cast<Shared*>(smem_raw);
-    const int b = blockIdx.x;
-    const int leader = b - b % P.team;
-    uint32_t* vis = P.gvis + (int64_t)b * P.vis_words;
-    int32_t* list = P.list + (int64_t)b * P.list_cap;
-    uint32_t* picks_g = P.picks + (int64_t)b * P.pick_cap;
-    uint32_t* big = P.big + (int64_t)b * P.big_cap;
-    int32_t* ring = P.gdefer + (int64_t)b * kDCapG;
-    SetCtl* c = P.sctl + b;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t njobs = (int64_t)*(volatile int*)P.esc_count;
-    if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
-    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
-    for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
-    __syncthreads();
-    uint32_t epoch = 0;
-    // a leader: the jobs
-    for (;;) {
-        if (leader != b) break;
-        if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(P.next_job + 1, 1);
-        __syncthreads();
-        const int64_t ticket = S.ctrl[C_JOB];
-        if (ticket >= njobs) break;
-        const int64_t job = (int64_t)P.esc_list[ticket];
-        const Job J = decode_job(P, job);
-        ++epoch;
-        if (threadIdx.x == 0) {
-            const int32_t root = draw_root(P, J);
-            list[0] = root;
-            vis[root >> 5] |= 1u << (root & 31);
-            c->tail = 1;
-            c->done = 0;
-            c->ndef_res = 0;
-            c->ndef = 0;
-            c->ndef_done = 0;
-            c->job = (int)job;
-            c->active = 1;
-            __threadfence();
-            atomicExch(&c->claim, (unsigned long long)epoch << 32);
-        }
-        __syncthreads();
-        const QueueSink sink{vis, list, &c->tail};
-        for (;;) {
-            for (;;) {
-                int idx = 0;
-                if (lane == 0) idx = claim_global(P, c, epoch, job, true);
-                idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-                if (idx < 0) break;
-                int32_t mu = 0;
-                if (lane == 0) mu = slot_value(P, list, idx, job);
-                mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
-                const bool defer = mu >= 0 && pop_warp(P, S, sink, J.j, J.ybase, mu);
-                __syncwarp();
-                if (lane == 0) end_pop_global(c, ring, defer, mu);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int nd = *(volatile int*)&c->ndef, ndd = *(volatile int*)&c->ndef_done;
-                S.ctrl[C_NDEF] = nd;
-                S.ctrl[C_CURSOR] = ndd;
-                S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0;
-                S.ctrl[C_STOP] = *(volatile int*)&c->done == *(volatile int*)&c->tail;
-            }
-            __syncthreads();
-            if (S.ctrl[C_STOP] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
-            const int nd = S.ctrl[C_NDEF], ndd = S.ctrl[C_CURSOR];
-            for (int d = ndd; d < nd; ++d)
-                pop_block(P, S, sink, J.j, J.ybase, __ldcg(ring + (d & (kDCapG - 1))), picks_g, big);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                c->ndef_done = nd;
-                __threadfence();
-                atomicAdd(&c->done, nd - ndd);
-            }
-            __syncthreads();
-        }
-        // counters of this set (its helpers flush their own), then the output
-        if (threadIdx.x < kNStat) {
-            unsigned long long sum = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                sum += S.wstat[w][threadIdx.x];
-                S.wstat[w][threadIdx.x] = 0;
-            }
-            S.stat[J.pi][threadIdx.x] += sum;
-        }
-        const int size = *(volatile int*)&c->tail;
-        __syncthreads();
-        write_set(P, S, vis, list, size, job);
-        for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
-        __syncthreads();
-    }
-    if (leader == b) {
-        if (threadIdx.x == 0) {
-            c->active = 0;
-            __threadfence();
-            c->finished = 1;
-        }
-    } else {
-        // a helper: pop vertices of the leader's current set, warp by warp
-        SetCtl* tc = P.sctl + leader;
-        int32_t* tlist = P.list + (int64_t)leader * P.list_cap;
-        int32_t* tring = P.gdefer + (int64_t)leader * kDCapG;
-        const QueueSink tsink{P.gvis + (int64_t)leader * P.vis_words, tlist, &tc->tail};
-        for (int idle = 0; idle < P.spin_limit;) {
-            int idx = -1, fin = 0;
-            int64_t job = 0;
-            if (lane == 0) {
-                fin = *(volatile int*)&tc->finished;
-                const unsigned long long cl = *(volatile unsigned long long*)&tc->claim;
-                __threadfence();
-                job = *(volatile int*)&tc->job;  // read before the claim: a claim in epoch cl >> 32 means it is that set's
-                if (!fin && *(volatile int*)&tc->active) idx = claim_global(P, tc, (uint32_t)(cl >> 32), -1, false);
-            }
-            fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
-            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-            if (fin || *(volatile int32_t*)&P.st->code != 0) break;
-            if (idx < 0) {
-                ++idle;
-                __nanosleep(256);
-                continue;
-            }
-            idle = 0;
-            job = __shfl_sync(0xFFFFFFFFu, job, 0);
-            int32_t mu = 0;
-            if (lane == 0) mu = slot_value(P, tlist, idx, job);
-            mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
-            const Job J = decode_job(P, job);
-            const bool defer = mu >= 0 && pop_warp(P, S, tsink, J.j, J.ybase, mu);
-            __syncwarp();
-            if (lane == 0) end_pop_global(tc, tring, defer, mu);
-            if (lane < kNStat) {
-                atomicAdd(&S.stat[J.pi][lane], S.wstat[wid][lane]);
-                S.wstat[wid][lane] = 0;
-            }
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < P.npools) {
-        RRCounters* cc = P.counters + threadIdx.x;
-        const unsigned long long* st = S.stat[threadIdx.x];
-        atomicAdd(&cc->pops, st[S_POPS]);
-        atomicAdd(&cc->layers_seen, st[S_LAYERS]);
-        atomicAdd(&cc->draws, st[S_DRAWS]);
-        atomicAdd(&cc->mats, st[S_MATS]);
-        atomicAdd(&cc->mat_he, st[S_MAT_HE]);
-        atomicAdd(&cc->mat_members, st[S_MAT_MEM]);
-        atomicAdd(&cc->selected, st[S_SEL]);
-        atomicAdd(&cc->gathered, st[S_GATH]);
-        atomicAdd(&cc->search_words, st[S_SRCH]);
-        atomicAdd(&cc->sectors, st[S_SECT]);
-    }
-}
-
 __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
@@ -1951,7 +1725,6 @@ hyperim_status allow_rr_smem() {
         if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(k_rr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WarpShared));
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(k_rr_help, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     });
     HYP_CUDA(err);
     return HYPERIM_OK;
@@ -2028,12 +1801,10 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     cudaStream_t s = g->stream;
     hyperim_status st;
 
-    // the visited bitmap goes on chip while the block still fits on an SM (and the tuning does not
-    // ask for global bitmaps, which let teams of blocks build one set)
+    // the visited bitmap goes on chip while the block still fits on an SM
     if ((st = allow_rr_smem())) return st;
     bool vis_smem = (int64_t)g->n <= kVisSmemBits &&
-                    sizeof(Shared) + sizeof(uint32_t) * (((size_t)g->n + 31) / 32) <= smem_optin() &&
-                    !(g->helping > 1 && g->schedule != HYPERIM_SCHED_PLAIN && g->warp_set_limit > 0);
+                    sizeof(Shared) + sizeof(uint32_t) * (((size_t)g->n + 31) / 32) <= smem_optin();
     size_t smem = 0;
     int per_sm = 0;
     for (;;) {
@@ -2081,17 +1852,6 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if ((st = tmp.alloc(&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
     if ((st = tmp.alloc(&d_esc, sizeof(int32_t) * (size_t)njobs))) return st;
     if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
-    // the block phase lets idle blocks help with other blocks' sets when the visited bitmaps are
-    // in global memory (every block can reach them)
-    // teams of blocks on the block phase's sets: the tuning's size, or 4 by default
-    const int team = g->helping > 1 ? std::min(g->helping, 8) : 4;
-    const bool helped = warp_phase && !vis_smem && g->helping >= 0 && team > 1;
-    SetCtl* d_sctl = nullptr;
-    int32_t* d_ring = nullptr;
-    if (helped) {
-        if ((st = tmp.alloc(&d_sctl, sizeof(SetCtl) * (size_t)blocks))) return st;
-        if ((st = tmp.alloc(&d_ring, sizeof(int32_t) * (size_t)kDCapG * (size_t)blocks))) return st;
-    }
     unsigned long long* d_used = &d_ctrl->arena_used;
     RRParams P;
     P.vinfo = g->vinfo;
@@ -2133,9 +1893,6 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.next_job = d_ctrl->next_job;
     P.esc_count = &d_ctrl->esc_count;
     P.esc_list = d_esc;
-    P.sctl = d_sctl;
-    P.gdefer = d_ring;
-    P.team = team;
     P.block_phase = 0;
     P.warp_limit = std::min(std::max(g->warp_set_limit, 1), kWQ);
     P.plain = g->schedule == HYPERIM_SCHED_PLAIN ? 1 : 0;
@@ -2169,7 +1926,6 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         P.arena = g->scratch.arena;
         P.arena_cap = g->scratch.arena_cap;
         HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
-        if (helped) HYP_CUDA(cudaMemsetAsync(d_sctl, 0, sizeof(SetCtl) * (size_t)blocks, s));
         HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
         HYP_CUDA(cudaEventRecord(ev0, s));
         if (P.plain) {
@@ -2187,12 +1943,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
             { k_rr_warp<<<wblocks, kPThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
             HYP_CUDA(cudaGetLastError());
             P.block_phase = 1;
-            if (helped) {
-                k_rr_help<<<blocks, kThreads, smem, s>>>(P);
-            } else {
-                k_rr<<<blocks, kThreads, smem, s>>>(P);
-            }
-            count_launch();
+            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
             P.block_phase = 0;
             ++launches;
         } else {
