@@ -298,6 +298,9 @@ def bench_gpu(args):
         # member ids gathered), per second of the timed region (this rank)
         "edge_traversals_per_s": sum(s["edges"] for s in stats) / t_local,
         "rr_sampling_seconds": sum(s["sample_seconds"] for s in stats) / args.steps,
+        # RR generation alone (sets per second of RR-kernel time): the quantity the oracle's timed
+        # sample measures (the reference arm and cpu_baseline time RR generation only)
+        "rr_generation_sets_per_s": rr_local / ksec if ksec > 0 else None,
         "wall_seconds_timed_region": t_wall,
         "e2e": {"value": rr_all / e2e_all, "unit": UNIT,
                 "h2d_bytes_per_step": int(off.nbytes + mem.nbytes),
@@ -511,7 +514,9 @@ def bench_reference(args):
     off, mem = make_hypergraph(w.graph)
     per_step = args.reference_seconds
     cores = host_cores()
+    t_build = time.perf_counter()
     og = oracle_graph(w, off, mem)
+    t_build = time.perf_counter() - t_build
     for i in range(args.warmup):
         oracle_rate_threads(w, og, min(per_step / 4, 2.0), w.query.seed + 7 + i, cores, tag=3)
     counts, times = [], []
@@ -533,6 +538,8 @@ def bench_reference(args):
                                    f"seed each step) on the same graph, {cores} threads with one "
                                    "worker view of the oracle graph each, graph build excluded"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        # the oracle's graph build (incidence lists and layer profile, one thread), outside the steps
+        "oracle_graph_build_seconds": t_build,
     }
     print(json.dumps(line), flush=True)
 
@@ -577,6 +584,34 @@ def _served(H, torch, loaded, queries, workers, budget, arrivals=None):
     return wall, res, st
 
 
+def _batch(H, torch, loaded, queries):
+    """All queries in one hyperim_select_seeds_batch call on fresh pools (one R1/R2 pair per graph,
+    shared by its queries): per BRR round one RR launch over every graph and one greedy launch."""
+    pools = {}
+    for gi, _, _ in queries:
+        if gi not in pools:
+            g = loaded[gi]
+            pools[gi] = (g.pool(tag=0, roots="stratified"), g.pool(tag=1, roots="stratified"))
+    batch = [(loaded[gi], pools[gi][0], pools[gi][1], k, eps, 1.0) for gi, k, eps in queries]
+    launches = H.hyperim_kernel_launches()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = H.hyperim_select_seeds_batch(batch)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = H.hyperim_kernel_launches() - launches
+    views = [p.view() for pair in pools.values() for p in pair]
+    stat = {"rounds": max(res["rounds"] for _, res in out), "kernel_launches": launches,
+            "rr_launches": max(v["rr_launches"] for v in views),
+            "rr_sets_generated": sum(v["count"] for v in views),
+            "rr_kernel_seconds": sum(v["rr_kernel_seconds"] for v in views)}
+    stat["rr_sets_per_s"] = stat["rr_sets_generated"] / wall
+    for pair in pools.values():
+        for p in pair:
+            p.close()
+    return wall, out, stat
+
+
 def _same_seeds(a, b):
     return all(x.tolist() == y.tolist() for x, y in zip(a, b))
 
@@ -584,10 +619,12 @@ def _same_seeds(a, b):
 def bench_batched(args):
     """The batched configuration: 64 hypergraphs of uneven size (n log-uniform in [1e3, 2e5],
     Zipf(2.1) sizes in [2, 300]), each queried with k in {10, 50, 100} at eps = 0.1 (weighted
-    cascade, stratified roots), resident in HBM. Three forms, same GPU, same queries, identical
+    cascade, stratified roots), resident in HBM. Four forms, same GPU, same queries, identical
     seeds: the plain form (one query at a time, fresh pools, RR sets one launch per batch of one
-    set per block), one query at a time with the persistent RR kernel, and the server (all 192
-    queries submitted at once to `--workers` workers; queries on one graph share its pools)."""
+    set per block), one query at a time with the persistent RR kernel, the server (all 192
+    queries submitted at once to `--workers` workers; queries on one graph share its pools), and
+    the batch (all 192 in one hyperim_select_seeds_batch call: per BRR round one RR launch over
+    every graph's pools and one greedy launch over every query; the line's value)."""
     import torch
     import paper_2406_01911_gb300 as H
     from workloads import batch_workload
@@ -601,13 +638,17 @@ def bench_batched(args):
     t_plain, plain = _sequential(H, torch, loaded, queries, "plain")
     t_seq, seq = _sequential(H, torch, loaded, queries, "persistent")
     t_srv, srv, st = _served(H, torch, loaded, queries, args.workers, int(args.budget_gb * 2**30))
+    _batch(H, torch, loaded, queries)  # warm-up: the first call pays for lazy setup
+    t_bat, bat, bstat = _batch(H, torch, loaded, queries)
     same = _same_seeds([x[1] for x in plain], [x[1] for x in seq]) and \
-        _same_seeds([x[1] for x in seq], [x[0] for x in srv])
+        _same_seeds([x[1] for x in seq], [x[0] for x in srv]) and \
+        _same_seeds([x[1] for x in seq], [x[0] for x in bat])
     sets_fresh = sum(x[3] for x in seq)
     line = {"metric": "batched IM queries per second (64 graphs x k in {10, 50, 100}, eps = 0.1)",
-            "value": len(queries) / t_srv, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True,
+            "value": len(queries) / t_bat, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True,
             "config": {"workload": "batched-64-graphs", "graphs": len(specs), "queries": len(queries),
                        "workers": args.workers, "model": "wc", "roots": "stratified"},
+            "batch": dict(bstat, wall_seconds=t_bat, queries_per_s=len(queries) / t_bat),
             "served": {"wall_seconds": t_srv, "queries_per_s": len(queries) / t_srv,
                        "rr_sets_generated": st["rr_sets_generated"],
                        "rr_sets_per_s": st["rr_sets_generated"] / t_srv,
@@ -618,6 +659,7 @@ def bench_batched(args):
             "plain_form": {"wall_seconds": t_plain, "queries_per_s": len(queries) / t_plain,
                            "rr_sets_per_s": sets_fresh / t_plain},
             "served_over_plain": t_plain / t_srv, "served_over_sequential": t_seq / t_srv,
+            "batch_over_plain": t_plain / t_bat, "batch_over_served": t_srv / t_bat,
             "identical_seeds": same, "failed": st["failed"]}
     print(json.dumps(line), flush=True)
     for g in loaded:
@@ -628,7 +670,9 @@ def bench_served(args):
     """The served configuration: 16 resident hypergraphs (n log-uniform in [1e5, 5e6],
     m = min(0.6 n, 3e6), Zipf(2.0) sizes in [2, 500]) and a Poisson stream of queries (mean 200
     per second; k uniform in [10, 200]; eps in {0.05, 0.1, 0.2}); the first `--queries` of the
-    stream are submitted at their arrival times. Latency is submit to completion. The plain form
+    stream are submitted at their arrival times. Latency is submit to completion. The same stream
+    is served again by one worker (one query at a time, same persistent kernels and shared pools,
+    latencies measured alike). The plain form
     (one query at a time on fresh pools, RR sets one launch per batch) runs the first
     `--plain-queries` of them; its latencies follow from its measured durations under the same
     arrivals with one query in service at a time (FIFO)."""
@@ -647,6 +691,7 @@ def bench_served(args):
     queries = [(q.graph, q.k, q.eps) for q in stream]
     arrivals = [q.arrival for q in stream]
     t_srv, srv, st = _served(H, torch, loaded, queries, args.workers, int(args.budget_gb * 2**30), arrivals)
+    t_one, one, st1 = _served(H, torch, loaded, queries, 1, int(args.budget_gb * 2**30), arrivals)
     npl = min(args.plain_queries, len(queries))
     t_plain, plain = _sequential(H, torch, loaded, queries[:npl], "plain")
     done, prev, lat = 0.0, 0.0, []
@@ -668,9 +713,15 @@ def bench_served(args):
                        "span_seconds": st["span_seconds"], "rr_sets_generated": st["rr_sets_generated"],
                        "evictions": st["evictions"], "max_running": st["max_running"], "failed": st["failed"],
                        "device_gb": st["device_bytes"] / 2**30},
+            "one_worker": {"queries_per_s": st1["queries_per_second"],
+                           "p50_latency_seconds": st1["p50_latency_seconds"],
+                           "p99_latency_seconds": st1["p99_latency_seconds"],
+                           "mean_latency_seconds": st1["mean_latency_seconds"],
+                           "rr_sets_generated": st1["rr_sets_generated"], "failed": st1["failed"]},
             "plain_form": {"queries": npl, "busy_seconds": t_plain, "queries_per_s": npl / t_plain,
-                           "p50_latency_seconds": pct(0.5), "p99_latency_seconds": pct(0.99)},
-            "identical_seeds": same}
+                           "p50_latency_seconds": pct(0.5), "p99_latency_seconds": pct(0.99),
+                           "latency": "from the measured durations, FIFO with one query in service"},
+            "identical_seeds": same and _same_seeds([x[0] for x in srv], [x[0] for x in one])}
     print(json.dumps(line), flush=True)
     for g in loaded:
         g.close()

@@ -460,6 +460,40 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
                                     int32_t* seeds_host, hyperim_select_result* out);
 
 /* ------------------------------------------------------------------------------------------
+ * hyperim_select_seeds_batch -- HyperIM_BRR (Alg. 4, Sec. 4.3) for many queries at once, on one
+ *   GPU, round by round: in round i every query still running grows its pools to
+ *   theta_i = theta_0 2^i, and the growth of all of them -- across graphs, k values and batches
+ *   of uneven size -- is ONE persistent RR-kernel launch whose blocks take (graph, pool, stratum,
+ *   j) jobs from a device work counter; then ONE launch runs greedy max coverage (Alg. 1, Eq. 2)
+ *   on every running query's R1 view and the coverage of its seeds on its R2 view (a block per
+ *   query); the host then takes each query's bounds and stop test (Eq. 1, Eq. upper_6, the
+ *   Sec. 4.2 lower bound). Each query's result is the one hyperim_select_seeds in BRR mode
+ *   gives it (closed upper bound, no theta cap): seeds, rounds, theta, Lambda per stratum and
+ *   bounds are identical, since every round reads the prefix view j < n_s(theta_i) of its pools.
+ *   queries[nq]: graph (a loaded graph or a share), r1 and r2 (two distinct empty or grown pools
+ *   of that graph, same root mode and strategy), k (1 <= k <= n), eps and ell as in
+ *   hyperim_select_opts; out: seeds_host[k] and *result. Queries may share pools (a graph's
+ *   queries with several k: the pools grow to the largest theta any of them needs). The pools
+ *   are held exclusively for the whole call. The device work runs on the first query's graph
+ *   stream, which waits for the work queued on the other graphs' streams; the call returns
+ *   after all of it. result->seconds_sample / seconds_select are the host wall time of the
+ *   whole batch's growth and greedy steps in the rounds the query ran (shared, not its own).
+ *   EINVAL: nq < 1, a null graph/pool/output, k out of range, bad eps/ell; ESTATE: a pool of
+ *   another graph, r1 == r2, pools of one query that differ in root mode or strategy;
+ *   EOVERFLOW: theta doubling past 2^62; errors of growth or greedy as in hyperim_sample_rr.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    hyperim_graph_t graph;
+    hyperim_pool_t r1, r2;
+    int32_t k;
+    double eps, ell;
+    int32_t* seeds_host;              /* out: k entries, S_k in pick order */
+    hyperim_select_result* result;    /* out */
+} hyperim_batch_query;
+
+hyperim_status hyperim_select_seeds_batch(const hyperim_batch_query* queries, int32_t nq);
+
+/* ------------------------------------------------------------------------------------------
  * hyperim_spread -- Eq. 1 estimate of the influence of seeds_host[k] from a pool:
  *   sigma = sum_s |V_s|/n_s Lambda_s, std_err^2 = sum_s (|V_s|/n_s)^2 n_s f_s (1 - f_s),
  *   f_s = Lambda_s / n_s. Seeds may repeat. EINVAL: a seed outside [0, n).

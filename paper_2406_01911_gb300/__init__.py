@@ -102,6 +102,12 @@ class SelectResult(C.Structure):
                 ("seconds_sample", C.c_double), ("seconds_select", C.c_double)]
 
 
+class BatchQuery(C.Structure):
+    _fields_ = [("graph", C.c_void_p), ("r1", C.c_void_p), ("r2", C.c_void_p), ("k", C.c_int32),
+                ("eps", C.c_double), ("ell", C.c_double), ("seeds_host", C.c_void_p),
+                ("result", C.POINTER(SelectResult))]
+
+
 class BrrRound(C.Structure):
     _fields_ = [("theta", C.c_uint64), ("sigma_r1", C.c_double), ("sigma_r2", C.c_double), ("upper", C.c_double),
                 ("lower", C.c_double), ("alpha", C.c_double), ("stop", C.c_int32)]
@@ -171,6 +177,7 @@ _SIGNATURES = {
     "hyperim_pool_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "hyperim_select_seeds": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(SelectOpts), _vp,
                                        C.POINTER(SelectResult)]),
+    "hyperim_select_seeds_batch": (C.c_int, [C.POINTER(BatchQuery), C.c_int32]),
     "hyperim_spread": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     "hyperim_coverage_noalloc": (C.c_int, [C.c_int32, _vp, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp,
@@ -316,6 +323,23 @@ def hyperim_select_seeds(h, r1, r2, k, mode="fixed", eps=0.1, ell=1.0, theta_cap
     res = SelectResult()
     _check(lib().hyperim_select_seeds(h, r1, r2, int(k), C.byref(opts), _ptr(seeds), C.byref(res)))
     return seeds, _select_result(res)
+
+
+def hyperim_select_seeds_batch(queries):
+    """HyperIM_BRR for many queries in one call (one RR launch and one greedy launch per round).
+    queries: sequence of (graph, r1, r2, k, eps, ell) with Graph / Pool objects. Returns a list of
+    (seeds, result) in query order, each as hyperim_select_seeds in BRR mode returns it."""
+    qs = (BatchQuery * len(queries))()
+    seeds, results = [], []
+    for i, (g, r1, r2, k, eps, ell) in enumerate(queries):
+        sd = np.zeros(int(k), dtype=np.int32)
+        res = SelectResult()
+        seeds.append(sd)
+        results.append(res)
+        qs[i] = BatchQuery(g.handle, r1.handle, r2.handle, int(k), float(eps), float(ell), _ptr(sd),
+                           C.pointer(res))
+    _check(lib().hyperim_select_seeds_batch(qs, len(queries)))
+    return [(sd, _select_result(res)) for sd, res in zip(seeds, results)]
 
 
 def _select_result(res):

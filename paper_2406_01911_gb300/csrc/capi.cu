@@ -889,6 +889,170 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     return HYPERIM_OK;
 }
 
+hyperim_status hyperim_select_seeds_batch(const hyperim_batch_query* queries, int32_t nq) {
+    if (!queries || nq < 1) return set_error(HYPERIM_EINVAL, "need at least one query");
+    hyperim_status st;
+    struct QS {
+        hyperim_theta_plan plan;
+        bool running;
+        double t_sample, t_select;
+    };
+    std::vector<QS> qs((size_t)nq);
+    std::vector<hyperim_pool*> pools;
+    for (int32_t q = 0; q < nq; ++q) {
+        const hyperim_batch_query& Q = queries[q];
+        if (!Q.graph || !Q.r1 || !Q.r2 || !Q.seeds_host || !Q.result) return set_error(HYPERIM_EINVAL, "null argument");
+        if (Q.k < 1 || Q.k > Q.graph->n) return set_error(HYPERIM_EINVAL, "need 1 <= k <= n");
+        if (graph_root(Q.r1->g) != graph_root(Q.graph) || graph_root(Q.r2->g) != graph_root(Q.graph))
+            return set_error(HYPERIM_ESTATE, "pool of another graph");
+        if (Q.r1 == Q.r2) return set_error(HYPERIM_ESTATE, "r1 and r2 must be distinct pools");
+        if (Q.r1->root_mode != Q.r2->root_mode || Q.r1->strategy != Q.r2->strategy)
+            return set_error(HYPERIM_ESTATE, "r1 and r2 differ in root mode or strategy");
+        if ((st = plan_theta(Q.graph->n, Q.k, Q.eps, Q.ell, &qs[q].plan))) return st;
+        qs[q].running = true;
+        qs[q].t_sample = qs[q].t_select = 0.0;
+        std::memset(Q.result, 0, sizeof(*Q.result));
+        for (hyperim_pool* p : {Q.r1, Q.r2})
+            if (std::find(pools.begin(), pools.end(), p) == pools.end()) pools.push_back(p);
+    }
+    // every pool held exclusively for the call, locks taken in address order
+    std::sort(pools.begin(), pools.end());
+    std::vector<std::unique_lock<std::shared_mutex>> locks;
+    locks.reserve(pools.size());
+    for (hyperim_pool* p : pools) locks.emplace_back(p->mu);
+    hyperim_graph* g0 = queries[0].graph;
+    {
+        std::vector<cudaStream_t> streams;
+        for (int32_t q = 0; q < nq; ++q)
+            if (std::find(streams.begin(), streams.end(), queries[q].graph->stream) == streams.end())
+                streams.push_back(queries[q].graph->stream);
+        for (cudaStream_t x : streams) HYP_CUDA(cudaStreamSynchronize(x));
+    }
+    using clk = std::chrono::steady_clock;
+    std::vector<uint64_t> v1((size_t)nq * HYPERIM_NSTRATA), v2((size_t)nq * HYPERIM_NSTRATA);
+    std::vector<uint64_t> target(pools.size() * HYPERIM_NSTRATA);
+    std::vector<hyperim_graph*> pool_graph(pools.size());
+    for (int32_t i = 0;; ++i) {
+        std::vector<int32_t> run;
+        for (int32_t q = 0; q < nq; ++q)
+            if (qs[q].running) run.push_back(q);
+        if (run.empty()) break;
+        if (i > 62) return set_error(HYPERIM_EOVERFLOW, "theta doubling overflow");
+        // growth targets: each pool to the largest allocation a running query reads from it
+        for (size_t x = 0; x < pools.size(); ++x)
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s) target[x * HYPERIM_NSTRATA + s] = pools[x]->n_s[s];
+        for (int32_t q : run) {
+            const hyperim_batch_query& Q = queries[q];
+            const uint64_t theta = qs[q].plan.theta0 << i;
+            uint64_t* a1 = &v1[(size_t)q * HYPERIM_NSTRATA];
+            uint64_t* a2 = &v2[(size_t)q * HYPERIM_NSTRATA];
+            allocate_strata(Q.graph, Q.r1->root_mode, theta, a1);
+            allocate_strata(Q.graph, Q.r2->root_mode, theta, a2);
+            const size_t x1 = (size_t)(std::lower_bound(pools.begin(), pools.end(), Q.r1) - pools.begin());
+            const size_t x2 = (size_t)(std::lower_bound(pools.begin(), pools.end(), Q.r2) - pools.begin());
+            pool_graph[x1] = Q.graph;
+            pool_graph[x2] = Q.graph;
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+                target[x1 * HYPERIM_NSTRATA + s] = std::max(target[x1 * HYPERIM_NSTRATA + s], a1[s]);
+                target[x2 * HYPERIM_NSTRATA + s] = std::max(target[x2 * HYPERIM_NSTRATA + s], a2[s]);
+            }
+        }
+        // one group per graph and pair of pools (same root mode and strategy) that must grow
+        std::vector<RRGroup> groups;
+        for (size_t x = 0; x < pools.size(); ++x) {
+            hyperim_pool* p = pools[x];
+            bool grow = false;
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s) grow = grow || target[x * HYPERIM_NSTRATA + s] > p->n_s[s];
+            if (!grow) continue;
+            RRGroup* G = nullptr;
+            for (RRGroup& c : groups)
+                if (c.npools == 1 && graph_root(c.g) == graph_root(p->g) && c.pools[0]->root_mode == p->root_mode &&
+                    c.pools[0]->strategy == p->strategy) {
+                    G = &c;
+                    break;
+                }
+            if (!G) {
+                groups.push_back(RRGroup{});
+                G = &groups.back();
+                G->g = pool_graph[x];
+                G->npools = 0;
+            }
+            G->pools[G->npools] = p;
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s) G->new_ns[G->npools][s] = target[x * HYPERIM_NSTRATA + s];
+            ++G->npools;
+        }
+        auto t0 = clk::now();
+        if (!groups.empty() && (st = sample_rr_batch(g0, groups.data(), (int)groups.size(), nullptr))) return st;
+        auto t1 = clk::now();
+        std::vector<GreedyBatchItem> items;
+        std::vector<int32_t> seeds;
+        std::vector<uint64_t> lam((size_t)run.size() * 2 * HYPERIM_NSTRATA);
+        size_t seeds_total = 0;
+        for (int32_t q : run) seeds_total += (size_t)queries[q].k;
+        seeds.resize(seeds_total);
+        size_t at = 0;
+        for (size_t r = 0; r < run.size(); ++r) {
+            const int32_t q = run[r];
+            const hyperim_batch_query& Q = queries[q];
+            GreedyBatchItem it;
+            it.g = Q.graph;
+            it.r1 = Q.r1;
+            it.r2 = Q.r2;
+            it.lim1 = &v1[(size_t)q * HYPERIM_NSTRATA];
+            it.lim2 = &v2[(size_t)q * HYPERIM_NSTRATA];
+            it.k = Q.k;
+            it.seeds_host = seeds.data() + at;
+            it.lambda_r1 = &lam[r * 2 * HYPERIM_NSTRATA];
+            it.lambda_r2 = &lam[r * 2 * HYPERIM_NSTRATA + HYPERIM_NSTRATA];
+            items.push_back(it);
+            at += (size_t)Q.k;
+        }
+        if ((st = greedy_batch(g0, items.data(), (int)items.size()))) return st;
+        auto t2 = clk::now();
+        const double ds = std::chrono::duration<double>(t1 - t0).count();
+        const double dg = std::chrono::duration<double>(t2 - t1).count();
+        for (size_t r = 0; r < run.size(); ++r) {
+            const int32_t q = run[r];
+            const hyperim_batch_query& Q = queries[q];
+            const GreedyBatchItem& it = items[r];
+            hyperim_select_result* out = Q.result;
+            const hyperim_theta_plan& plan = qs[q].plan;
+            const hyperim_graph* g = Q.graph;
+            const uint64_t* a1 = &v1[(size_t)q * HYPERIM_NSTRATA];
+            const uint64_t* a2 = &v2[(size_t)q * HYPERIM_NSTRATA];
+            std::memcpy(Q.seeds_host, it.seeds_host, sizeof(int32_t) * (size_t)Q.k);
+            uint64_t N1 = 0, N2 = 0;
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
+                out->lambda_r1[s] = it.lambda_r1[s];
+                out->lambda_r2[s] = it.lambda_r2[s];
+                N1 += a1[s];
+                N2 += a2[s];
+            }
+            const double s1 = estimate(g, Q.r1->root_mode, a1, out->lambda_r1);
+            const double s2 = estimate(g, Q.r2->root_mode, a2, out->lambda_r2);
+            const double up = upper_bound(s1 * (double)N1 / (double)g->n, Q.k, g->n, N1);
+            const double lo = lower_bound(s2 * (double)N2 / (double)g->n, plan.delta, g->n, N2);
+            const double alpha = lo / up;
+            out->rounds = i + 1;
+            out->theta = plan.theta0 << i;
+            out->pool_r1 = N1;
+            out->pool_r2 = N2;
+            out->sigma_r1 = s1;
+            out->sigma_r2 = s2;
+            out->upper = up;
+            out->lower = lo;
+            out->alpha = alpha;
+            if (i < 64) out->alpha_round[i] = alpha;
+            qs[q].t_sample += ds;
+            qs[q].t_select += dg;
+            out->seconds_sample = qs[q].t_sample;
+            out->seconds_select = qs[q].t_select;
+            if (alpha >= 1.0 - std::exp(-1.0) - Q.eps || i >= plan.i_max) qs[q].running = false;
+        }
+    }
+    return HYPERIM_OK;
+}
+
 }  // extern "C"
 
 struct hyperim_greedy {

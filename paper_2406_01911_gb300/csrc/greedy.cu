@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -314,6 +315,167 @@ __global__ void k_mark(const int32_t* __restrict__ seeds, int32_t k, uint8_t* __
         in_s[seeds[i]] = 1;
 }
 
+// ---- batched form: greedy max coverage and the R2 coverage of many queries, one block each ----
+// A query's block builds the inverted index of its R1 view, runs the k greedy rounds (argmax over
+// the unpicked vertices, lowest id on ties; retirement of the covered sets) and counts the sets
+// of its R2 view that hold a seed: the same integer arithmetic as the grid kernels above, so the
+// seeds and coverages are identical. Scratch per block, sized for the batch's largest graph and
+// view; queries are taken from a counter, so a block that finishes a small query takes the next.
+constexpr int kGBThreads = 1024;
+constexpr int kGBWarps = kGBThreads / 32;
+
+struct GreedyBatchQuery {
+    const int64_t* off1;
+    const int32_t* mem1;
+    const uint8_t* str1;
+    const uint32_t* j1;
+    int64_t count1;
+    Limits L1;
+    const int64_t* off2;
+    const int32_t* mem2;
+    const uint8_t* str2;
+    const uint32_t* j2;
+    int64_t count2;
+    Limits L2;
+    Weights W;
+    int32_t n, k;
+    int32_t* seeds;             // k entries
+    unsigned long long* lam;    // lambda_r1[16], lambda_r2[16]
+};
+
+struct GreedyBatchParams {
+    const GreedyBatchQuery* q;
+    int nq;
+    unsigned int* next;
+    unsigned long long* score;  // per block: n_cap
+    uint32_t* off;              // per block: n_cap + 1 (counts, then index ends)
+    uint8_t* picked;            // per block: n_cap
+    uint32_t* inv;              // per block: inv_cap
+    uint32_t* covered;          // per block: cov_cap
+    int64_t n_cap, inv_cap, cov_cap;
+};
+
+__global__ void __launch_bounds__(kGBThreads, 1) k_greedy_batch(GreedyBatchParams B) {
+    __shared__ unsigned long long s_lam[2 * HYPERIM_NSTRATA];
+    __shared__ unsigned long long ss[kGBWarps];
+    __shared__ uint32_t si[kGBWarps];
+    __shared__ uint32_t s_part[kGBWarps];
+    __shared__ int s_q, s_best;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long* score = B.score + (int64_t)blockIdx.x * B.n_cap;
+    uint32_t* off = B.off + (int64_t)blockIdx.x * (B.n_cap + 1);
+    uint8_t* picked = B.picked + (int64_t)blockIdx.x * B.n_cap;
+    uint32_t* inv = B.inv + (int64_t)blockIdx.x * B.inv_cap;
+    uint32_t* covered = B.covered + (int64_t)blockIdx.x * B.cov_cap;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = (int)atomicAdd(B.next, 1u);
+        __syncthreads();
+        if (s_q >= B.nq) break;
+        const GreedyBatchQuery& Q = B.q[s_q];
+        const int32_t n = Q.n;
+        for (int64_t v = threadIdx.x; v < n; v += kGBThreads) {
+            score[v] = 0;
+            off[v] = 0;
+            picked[v] = 0;
+        }
+        for (int64_t r = threadIdx.x; r < Q.count1; r += kGBThreads) covered[r] = 0;
+        if (threadIdx.x < 2 * HYPERIM_NSTRATA) s_lam[threadIdx.x] = 0;
+        __syncthreads();
+        // occurrences of each vertex over the R1 view
+        for (int64_t r = wid; r < Q.count1; r += kGBWarps) {
+            if (Q.L1.skip(Q.str1, Q.j1, r)) continue;
+            for (int64_t x = Q.off1[r] + lane; x < Q.off1[r + 1]; x += 32) atomicAdd(&off[Q.mem1[x]], 1u);
+        }
+        __syncthreads();
+        // exclusive scan of the counts, in place: each thread one contiguous range
+        {
+            const int64_t per = ((int64_t)n + kGBThreads - 1) / kGBThreads;
+            const int64_t b = (int64_t)threadIdx.x * per, e = min((int64_t)n, b + per);
+            uint32_t sum = 0;
+            for (int64_t v = b; v < e; ++v) sum += __ldcg(off + v);
+            uint32_t incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) s_part[wid] = incl;
+            __syncthreads();
+            uint32_t base = 0;
+            for (int w = 0; w < wid; ++w) base += s_part[w];
+            uint32_t run = base + incl - sum;
+            for (int64_t v = b; v < e; ++v) {
+                const uint32_t c = __ldcg(off + v);
+                off[v] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        // inverted index and initial scores; afterwards off[v] is the end of v's entries
+        for (int64_t r = wid; r < Q.count1; r += kGBWarps) {
+            if (Q.L1.skip(Q.str1, Q.j1, r)) continue;
+            const unsigned long long w = Q.W.w[Q.str1[r]];
+            for (int64_t x = Q.off1[r] + lane; x < Q.off1[r + 1]; x += 32) {
+                const int32_t v = Q.mem1[x];
+                inv[atomicAdd(&off[v], 1u)] = (uint32_t)r;
+                atomicAdd(&score[v], w);
+            }
+        }
+        __syncthreads();
+        for (int round = 0; round < Q.k; ++round) {
+            unsigned long long bs = 0;
+            uint32_t bi = 0xFFFFFFFFu;
+            for (int64_t v = threadIdx.x; v < n; v += kGBThreads) {
+                if (picked[v]) continue;
+                const unsigned long long sc = __ldcg(score + v);
+                if (better(sc, (uint32_t)v, bs, bi)) { bs = sc; bi = (uint32_t)v; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long os = __shfl_xor_sync(0xFFFFFFFFu, bs, o);
+                const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (better(os, oi, bs, bi)) { bs = os; bi = oi; }
+            }
+            if (lane == 0) { ss[wid] = bs; si[wid] = bi; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < kGBWarps; ++w)
+                    if (better(ss[w], si[w], bs, bi)) { bs = ss[w]; bi = si[w]; }
+                s_best = (int)bi;
+                Q.seeds[round] = (int32_t)bi;
+                picked[bi] = 1;
+            }
+            __syncthreads();
+            const int32_t v = s_best;
+            const int64_t b = v ? (int64_t)__ldcg(off + v - 1) : 0, e = __ldcg(off + v);
+            for (int64_t t = b + wid; t < e; t += kGBWarps) {
+                const uint32_t r = inv[t];
+                uint32_t old = 0;
+                if (lane == 0) old = atomicExch(&covered[r], 1u);
+                old = __shfl_sync(0xFFFFFFFFu, old, 0);
+                if (old) continue;
+                const int s = Q.str1[r];
+                const unsigned long long neg = 0ull - Q.W.w[s];
+                if (lane == 0) atomicAdd(&s_lam[s], 1ull);
+                for (int64_t x = Q.off1[r] + lane; x < Q.off1[r + 1]; x += 32) atomicAdd(&score[Q.mem1[x]], neg);
+            }
+            __syncthreads();
+        }
+        // coverage of the seed set on the R2 view
+        for (int64_t r = wid; r < Q.count2; r += kGBWarps) {
+            if (Q.L2.skip(Q.str2, Q.j2, r)) continue;
+            const int64_t b = Q.off2[r], e = Q.off2[r + 1];
+            bool hit = false;
+            for (int64_t base = b; base < e; base += 32) {
+                const int64_t x = base + lane;
+                if (__any_sync(0xFFFFFFFFu, x < e && picked[Q.mem2[x]] != 0)) { hit = true; break; }
+            }
+            if (hit && lane == 0) atomicAdd(&s_lam[HYPERIM_NSTRATA + Q.str2[r]], 1ull);
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 * HYPERIM_NSTRATA) Q.lam[threadIdx.x] = s_lam[threadIdx.x];
+        __syncthreads();
+    }
+}
+
 int grid_cap(int64_t items, int threads, int sm, int per_sm) {
     int64_t b = (items + threads - 1) / threads;
     const int64_t cap = (int64_t)sm * per_sm;
@@ -603,6 +765,98 @@ hyperim_status greedy_end(GreedyState* s, uint64_t lambda_s[HYPERIM_NSTRATA]) {
     free_state(s);
     if (e != cudaSuccess) return cuda_fail(e, "greedy end");
     return HYPERIM_OK;
+}
+
+hyperim_status greedy_batch(hyperim_graph* g0, const GreedyBatchItem* items, int nitems) {
+    if (nitems < 1) return HYPERIM_OK;
+    cudaStream_t s = g0->stream;
+    hyperim_status st;
+    std::vector<GreedyBatchQuery> hq((size_t)nitems);
+    int64_t n_cap = 1, inv_cap = 1, cov_cap = 1, kmax = 1;
+    for (int i = 0; i < nitems; ++i) {
+        const GreedyBatchItem& it = items[i];
+        const hyperim_pool *p1 = it.r1, *p2 = it.r2;
+        if (p1->count >= (int64_t)0xFFFFFFFFll || p1->total >= (int64_t)0xFFFFFFFFll)
+            return set_error(HYPERIM_EOVERFLOW, "more than 2^32 - 1 RR sets or members in a pool");
+        uint64_t v1[HYPERIM_NSTRATA], v2[HYPERIM_NSTRATA];
+        GreedyBatchQuery& Q = hq[i];
+        Q.off1 = p1->rr_off;
+        Q.mem1 = p1->rr_mem;
+        Q.str1 = p1->rr_stratum;
+        Q.j1 = p1->rr_j;
+        Q.count1 = p1->count;
+        Q.L1 = make_limits(p1, it.lim1, v1);
+        Q.off2 = p2->rr_off;
+        Q.mem2 = p2->rr_mem;
+        Q.str2 = p2->rr_stratum;
+        Q.j2 = p2->rr_j;
+        Q.count2 = p2->count;
+        Q.L2 = make_limits(p2, it.lim2, v2);
+        for (int x = 0; x < HYPERIM_NSTRATA; ++x) Q.W.w[x] = stratum_weight(it.g, p1->root_mode, v1[x], x);
+        Q.n = it.g->n;
+        Q.k = it.k;
+        n_cap = std::max<int64_t>(n_cap, it.g->n);
+        inv_cap = std::max<int64_t>(inv_cap, p1->total);
+        cov_cap = std::max<int64_t>(cov_cap, p1->count);
+        kmax = std::max<int64_t>(kmax, it.k);
+    }
+    // one block per SM at most, and no more blocks than the scratch budget allows
+    const size_t per_block = 8 * (size_t)n_cap + 4 * ((size_t)n_cap + 1) + (size_t)n_cap + 4 * (size_t)inv_cap +
+                             4 * (size_t)cov_cap;
+    const size_t budget = (size_t)2 << 30;
+    int blocks = (int)std::min<int64_t>(nitems, std::max(1, g0->sm_count));
+    blocks = (int)std::max<size_t>(1, std::min<size_t>((size_t)blocks, budget / std::max<size_t>(per_block, 1)));
+    CallBuffers tmp(g0);
+    GreedyBatchQuery* d_q = nullptr;
+    int32_t* d_seeds = nullptr;
+    unsigned long long* d_lam = nullptr;
+    unsigned int* d_next = nullptr;
+    unsigned long long* score = nullptr;
+    uint32_t *off = nullptr, *inv = nullptr, *covered = nullptr;
+    uint8_t* picked = nullptr;
+    if ((st = tmp.alloc(&d_q, sizeof(GreedyBatchQuery) * (size_t)nitems))) return st;
+    if ((st = tmp.alloc(&d_seeds, sizeof(int32_t) * (size_t)nitems * (size_t)kmax))) return st;
+    if ((st = tmp.alloc(&d_lam, sizeof(unsigned long long) * 2 * HYPERIM_NSTRATA * (size_t)nitems))) return st;
+    if ((st = tmp.alloc(&d_next, sizeof(unsigned int)))) return st;
+    if ((st = tmp.alloc(&score, sizeof(unsigned long long) * (size_t)n_cap * blocks))) return st;
+    if ((st = tmp.alloc(&off, sizeof(uint32_t) * ((size_t)n_cap + 1) * blocks))) return st;
+    if ((st = tmp.alloc(&picked, (size_t)n_cap * blocks))) return st;
+    if ((st = tmp.alloc(&inv, sizeof(uint32_t) * (size_t)inv_cap * blocks))) return st;
+    if ((st = tmp.alloc(&covered, sizeof(uint32_t) * (size_t)cov_cap * blocks))) return st;
+    for (int i = 0; i < nitems; ++i) {
+        hq[i].seeds = d_seeds + (size_t)i * (size_t)kmax;
+        hq[i].lam = d_lam + (size_t)i * 2 * HYPERIM_NSTRATA;
+    }
+    HYP_CUDA(cudaMemcpyAsync(d_q, hq.data(), sizeof(GreedyBatchQuery) * hq.size(), cudaMemcpyHostToDevice, s));
+    HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned int), s));
+    GreedyBatchParams B;
+    B.q = d_q;
+    B.nq = nitems;
+    B.next = d_next;
+    B.score = score;
+    B.off = off;
+    B.picked = picked;
+    B.inv = inv;
+    B.covered = covered;
+    B.n_cap = n_cap;
+    B.inv_cap = inv_cap;
+    B.cov_cap = cov_cap;
+    { k_greedy_batch<<<blocks, kGBThreads, 0, s>>>(B); count_launch(); }
+    HYP_CUDA(cudaGetLastError());
+    std::vector<int32_t> seeds((size_t)nitems * (size_t)kmax);
+    std::vector<unsigned long long> lam((size_t)nitems * 2 * HYPERIM_NSTRATA);
+    HYP_CUDA(cudaMemcpyAsync(seeds.data(), d_seeds, sizeof(int32_t) * seeds.size(), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaMemcpyAsync(lam.data(), d_lam, sizeof(unsigned long long) * lam.size(), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < nitems; ++i) {
+        const GreedyBatchItem& it = items[i];
+        for (int x = 0; x < it.k; ++x) it.seeds_host[x] = seeds[(size_t)i * (size_t)kmax + x];
+        for (int x = 0; x < HYPERIM_NSTRATA; ++x) {
+            it.lambda_r1[x] = lam[(size_t)i * 2 * HYPERIM_NSTRATA + x];
+            it.lambda_r2[x] = lam[(size_t)i * 2 * HYPERIM_NSTRATA + HYPERIM_NSTRATA + x];
+        }
+    }
+    return check_device_status(g0, "greedy (batch)");
 }
 
 }  // namespace hyperim

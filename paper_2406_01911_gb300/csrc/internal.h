@@ -250,6 +250,19 @@ hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_n
 hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
                                const uint64_t (*new_ns)[HYPERIM_NSTRATA]);
 
+// rr.cu: one launch over the pools of several graphs (the batched form of HyperIM_BRR). Group
+// q grows up to two pools of graph g (same root mode and strategy) to new_ns; every group's
+// sets are built by one persistent launch on g0's stream (which first waits for the work queued
+// on the groups' streams); each pool is compacted on its graph's stream. seconds: the launch's
+// CUDA-event time.
+struct RRGroup {
+    hyperim_graph* g;
+    hyperim_pool* pools[2];
+    int npools;
+    uint64_t new_ns[2][HYPERIM_NSTRATA];
+};
+hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngroups, double* seconds);
+
 // rr.cu: forward Monte-Carlo influence of a seed set (counts_host: nsims entries)
 hyperim_status forward_spread(hyperim_graph* g, const int32_t* seeds_host, int32_t k, uint64_t nsims,
                               uint64_t seed, uint32_t* counts_host);
@@ -269,6 +282,22 @@ hyperim_status greedy_begin(hyperim_graph* g, hyperim_pool* p, const uint64_t* l
 hyperim_status greedy_scores(GreedyState* st, unsigned long long* dev_out);
 hyperim_status greedy_pick(GreedyState* st, const unsigned long long* dev_total, int32_t* picked);
 hyperim_status greedy_end(GreedyState* st, uint64_t lambda_s[HYPERIM_NSTRATA]);
+
+// greedy.cu: the batched form -- greedy max coverage on the R1 view and the coverage of its seeds
+// on the R2 view for many queries in one launch (one block per query). lim1 / lim2: prefix views
+// (nullptr: the whole pool). Runs on g0's stream; the pools' arrays must be ready there.
+struct GreedyBatchItem {
+    hyperim_graph* g;
+    hyperim_pool* r1;
+    hyperim_pool* r2;
+    const uint64_t* lim1;
+    const uint64_t* lim2;
+    int32_t k;
+    int32_t* seeds_host;         // k entries
+    uint64_t* lambda_r1;         // HYPERIM_NSTRATA entries
+    uint64_t* lambda_r2;
+};
+hyperim_status greedy_batch(hyperim_graph* g0, const GreedyBatchItem* items, int nitems);
 
 // host arithmetic (plan.cpp)
 void allocate_strata(const hyperim_graph* g, int32_t root_mode, uint64_t theta,

@@ -12,7 +12,10 @@
 // Draws are keyed by (RR, vertex, layer), so the set does not depend on the pop order and the
 // parallel pops are deterministic. Picks already in R are skipped (visited bitmap).
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "device_math.cuh"
 #include "internal.h"
@@ -147,6 +150,11 @@ enum { C_JOB = 0, C_HEAD, C_TAIL, C_DONE, C_NDEF, C_ROOT, C_NNEED, C_CURSOR, C_S
        C_FAIL };
 // stat slots
 enum { S_POPS = 0, S_LAYERS, S_DRAWS, S_MATS, S_MAT_HE, S_MAT_MEM, S_SEL, S_GATH, S_SRCH, S_SECT };
+// the stat slots are the fields of RRCounters, in order
+static_assert(sizeof(RRCounters) == kNStat * sizeof(unsigned long long) &&
+                  offsetof(RRCounters, sectors) == S_SECT * sizeof(unsigned long long) &&
+                  offsetof(RRCounters, gathered) == S_GATH * sizeof(unsigned long long),
+              "RRCounters must list the stat slots in order");
 
 // 32-byte sectors spanned by the byte range [a, a + len) (0 when empty)
 __device__ __forceinline__ unsigned long long sectors_of(uint64_t a, uint64_t len) {
@@ -1547,6 +1555,84 @@ __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int
     }
 }
 
+// One RR set (job `job` of P's pools) built by the whole block: root draw, reverse BFS over the
+// block's asynchronous queue, output. Work counters go to the block's per-pool totals (flushed at
+// the end of the launch), or straight to the pool's counters when kFlushPerSet (a launch over the
+// pools of many graphs, whose blocks change graphs from set to set).
+template <bool kFlushPerSet>
+__device__ __forceinline__ void run_job(const RRParams& P, Shared& S, uint32_t* vis, int32_t* list,
+                                        uint32_t* picks_g, uint32_t* big, int64_t job) {
+    const int lane = threadIdx.x & 31;
+    const Job J = decode_job(P, job);
+    const int pi = J.pi;
+    const uint32_t j = J.j, ybase = J.ybase;
+    if (threadIdx.x == 0) {
+        const int32_t root = draw_root(P, J);
+        list[0] = root;
+        vis[root >> 5] |= 1u << (root & 31);
+        S.ctrl[C_HEAD] = 0;
+        S.ctrl[C_TAIL] = 1;
+        S.ctrl[C_DONE] = 0;
+        S.ctrl[C_NDEF] = 0;
+    }
+    __syncthreads();
+    // reverse BFS over an asynchronous queue: a warp pops any vertex already discovered
+    // (the draws are keyed by (RR, vertex, layer), so the order of pops does not change R);
+    // the block only meets when every pending pop needs the block path
+    for (;;) {
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = claim_slot(P, S, job);
+            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+            if (idx < 0) break;
+            int32_t mu = 0;
+            if (lane == 0) mu = slot_value(P, list, idx, job);
+            mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
+            const bool defer = mu >= 0 && pop_warp(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, mu);
+            __syncwarp();
+            if (lane == 0) {
+                if (defer) {
+                    S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
+                } else {
+                    __threadfence_block();  // this pop's pushes before its completion
+                    atomicAdd(&S.ctrl[C_DONE], 1);
+                }
+            }
+        }
+        if (threadIdx.x == 0) S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0;
+        __syncthreads();
+        if (S.ctrl[C_DONE] == S.ctrl[C_TAIL] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
+        // the block materialises the deferred pops
+        const int ndef = S.ctrl[C_NDEF];
+        for (int d = 0; d < ndef; ++d)
+            pop_block(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, S.deferred[d], picks_g, big);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.ctrl[C_DONE] += ndef;
+            S.ctrl[C_NDEF] = 0;
+        }
+        __syncthreads();
+    }
+    // work counters of this RR set go to its pool
+    if (threadIdx.x < kNStat) {
+        unsigned long long sum = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            sum += S.wstat[w][threadIdx.x];
+            S.wstat[w][threadIdx.x] = 0;
+        }
+        if (kFlushPerSet) {
+            if (sum) atomicAdd(&P.counters[pi].pops + threadIdx.x, sum);
+        } else {
+            S.stat[pi][threadIdx.x] += sum;
+        }
+    }
+    // output: members in ascending order
+    const int size = S.ctrl[C_TAIL];
+    write_set(P, S, vis, list, size, job);
+    for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& S = *reinterpret_cast<Shared*>(smem_raw);
@@ -1555,7 +1641,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     int32_t* list = P.list + (int64_t)blockIdx.x * P.list_cap;
     uint32_t* picks_g = P.picks + (int64_t)blockIdx.x * P.pick_cap;
     uint32_t* big = P.big + (int64_t)blockIdx.x * P.big_cap;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t njobs = P.block_phase ? (int64_t)*(volatile int*)P.esc_count : P.pool_start[P.npools];
     if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
@@ -1579,85 +1664,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
         if (ticket >= njobs) break;
         // the block phase takes the jobs the warp phase listed, in listed order
         const int64_t job = P.block_phase ? (int64_t)P.esc_list[ticket] : njobs - 1 - ticket;
-        const Job J = decode_job(P, job);
-        const int pi = J.pi;
-        const uint32_t j = J.j, ybase = J.ybase;
-        if (threadIdx.x == 0) {
-            const int32_t root = draw_root(P, J);
-            list[0] = root;
-            vis[root >> 5] |= 1u << (root & 31);
-            S.ctrl[C_HEAD] = 0;
-            S.ctrl[C_TAIL] = 1;
-            S.ctrl[C_DONE] = 0;
-            S.ctrl[C_NDEF] = 0;
-        }
-        __syncthreads();
-        // reverse BFS over an asynchronous queue: a warp pops any vertex already discovered
-        // (the draws are keyed by (RR, vertex, layer), so the order of pops does not change R);
-        // the block only meets when every pending pop needs the block path
-        for (;;) {
-            for (;;) {
-                int idx = 0;
-                if (lane == 0) idx = claim_slot(P, S, job);
-                idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-                if (idx < 0) break;
-                int32_t mu = 0;
-                if (lane == 0) mu = slot_value(P, list, idx, job);
-                mu = __shfl_sync(0xFFFFFFFFu, mu, 0);
-                const bool defer = mu >= 0 && pop_warp(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, mu);
-                __syncwarp();
-                if (lane == 0) {
-                    if (defer) {
-                        S.deferred[atomicAdd(&S.ctrl[C_NDEF], 1)] = mu;
-                    } else {
-                        __threadfence_block();  // this pop's pushes before its completion
-                        atomicAdd(&S.ctrl[C_DONE], 1);
-                    }
-                }
-            }
-            if (threadIdx.x == 0) S.ctrl[C_FAIL] = *(volatile int32_t*)&P.st->code != 0;
-            __syncthreads();
-            if (S.ctrl[C_DONE] == S.ctrl[C_TAIL] || S.ctrl[C_FAIL]) break;  // R is complete (or failed)
-            // the block materialises the deferred pops
-            const int ndef = S.ctrl[C_NDEF];
-            for (int d = 0; d < ndef; ++d)
-                pop_block(P, S, QueueSink{vis, list, &S.ctrl[C_TAIL]}, j, ybase, S.deferred[d], picks_g, big);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                S.ctrl[C_DONE] += ndef;
-                S.ctrl[C_NDEF] = 0;
-            }
-            __syncthreads();
-        }
-        // work counters of this RR set go to its pool
-        if (threadIdx.x < kNStat) {
-            unsigned long long sum = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                sum += S.wstat[w][threadIdx.x];
-                S.wstat[w][threadIdx.x] = 0;
-            }
-            S.stat[pi][threadIdx.x] += sum;
-        }
-        // output: members in ascending order
-        const int size = S.ctrl[C_TAIL];
-        write_set(P, S, vis, list, size, job);
-        for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
-        __syncthreads();
+        run_job<false>(P, S, vis, list, picks_g, big, job);
     }
     __syncthreads();
     if (threadIdx.x < P.npools) {
         RRCounters* c = P.counters + threadIdx.x;
         const unsigned long long* st = S.stat[threadIdx.x];
-        atomicAdd(&c->pops, st[S_POPS]);
-        atomicAdd(&c->layers_seen, st[S_LAYERS]);
-        atomicAdd(&c->draws, st[S_DRAWS]);
-        atomicAdd(&c->mats, st[S_MATS]);
-        atomicAdd(&c->mat_he, st[S_MAT_HE]);
-        atomicAdd(&c->mat_members, st[S_MAT_MEM]);
-        atomicAdd(&c->selected, st[S_SEL]);
-        atomicAdd(&c->gathered, st[S_GATH]);
-        atomicAdd(&c->search_words, st[S_SRCH]);
-        atomicAdd(&c->sectors, st[S_SECT]);
+        for (int i = 0; i < kNStat; ++i)
+            if (st[i]) atomicAdd(&c->pops + i, st[i]);
+    }
+}
+
+// A launch over the pools of several graphs (the batched form of HyperIM_BRR: every query's
+// round grows its graph's pools, all in one launch). Group g -- one graph and up to kMaxPools of
+// its pools -- owns the global jobs [group_start[g], group_start[g + 1]) and its own RRParams
+// (graph arrays, job maps, outputs, counters); the blocks share one work counter, one output
+// arena and one set of scratch buffers sized for the largest graph. A block copies the group of
+// its current job into shared memory and builds the set exactly as k_rr does.
+struct RRBatchParams {
+    const RRParams* groups;
+    const int64_t* group_start;  // ngroups + 1
+    int ngroups;
+    int* next_job;
+    int32_t* list;
+    int64_t list_cap;
+    uint32_t* gvis;
+    int vis_smem;
+    int64_t vis_words;
+    uint32_t* picks;
+    int64_t pick_cap;
+    uint32_t* big;
+    int64_t big_cap;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_rr_batch(RRBatchParams B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) RRParams Pc;  // the current job's group
+    Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+    uint32_t* vis = B.vis_smem ? reinterpret_cast<uint32_t*>(smem_raw + sizeof(Shared))
+                               : B.gvis + (int64_t)blockIdx.x * B.vis_words;
+    int32_t* list = B.list + (int64_t)blockIdx.x * B.list_cap;
+    uint32_t* picks_g = B.picks + (int64_t)blockIdx.x * B.pick_cap;
+    uint32_t* big = B.big + (int64_t)blockIdx.x * B.big_cap;
+    const int64_t njobs = B.group_start[B.ngroups];
+    if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
+    for (int64_t w = threadIdx.x; w < B.vis_words; w += kThreads) vis[w] = 0;
+    __syncthreads();
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(B.next_job, 1);
+        __syncthreads();
+        const int64_t ticket = S.ctrl[C_JOB];
+        if (ticket >= njobs) break;
+        const int64_t gjob = njobs - 1 - ticket;
+        int lo = 0, hi = B.ngroups - 1;  // the group holding gjob: last start <= gjob
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.group_start[mid] <= gjob) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {  // the previous set ended with a barrier: Pc is free
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(B.groups + lo);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&Pc);
+            for (int i = threadIdx.x; i < (int)(sizeof(RRParams) / 4); i += kThreads) dst[i] = src[i];
+            cur = lo;
+            __syncthreads();
+        }
+        run_job<true>(Pc, S, vis, list, picks_g, big, gjob - B.group_start[lo]);
     }
 }
 
@@ -1725,6 +1798,15 @@ hyperim_status allow_rr_smem() {
         if (err == cudaSuccess) err = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(k_rr_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WarpShared));
+        if (err == cudaSuccess) {
+            cudaFuncAttributes fa;
+            err = cudaFuncGetAttributes(&fa, k_rr_batch);
+            if (err == cudaSuccess) {
+                const size_t room = smem_optin() > fa.sharedSizeBytes ? smem_optin() - fa.sharedSizeBytes : 0;
+                const int batch_most = (int)std::min<size_t>(sizeof(Shared) + kVisSmemBits / 8, room);
+                err = cudaFuncSetAttribute(k_rr_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_most);
+            }
+        }
     });
     HYP_CUDA(err);
     return HYPERIM_OK;
@@ -1767,20 +1849,14 @@ hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
     return HYPERIM_OK;
 }
 
-}  // namespace
-
-hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
-                               const uint64_t (*new_ns)[HYPERIM_NSTRATA]) {
-    if (npools < 1 || npools > kMaxPools) return set_error(HYPERIM_EINVAL, "bad pool count");
-    for (int q = 1; q < npools; ++q)
-        if (pools[q]->root_mode != pools[0]->root_mode || pools[q]->strategy != pools[0]->strategy)
-            return set_error(HYPERIM_ESTATE, "pools grown together must share root mode and strategy");
-    RRJobMap jm[kMaxPools];
-    int64_t pool_start[kMaxPools + 1];
+// Job maps of a growth step: pool q's new sets are jobs [pool_start[q], pool_start[q + 1]),
+// stratum by stratum; a shard (rank r of W) holds the sets j = r (mod W) of each stratum's
+// allocation.
+hyperim_status make_job_maps(hyperim_pool* const* pools, int npools, const uint64_t (*new_ns)[HYPERIM_NSTRATA],
+                             RRJobMap* jm, int64_t* pool_start) {
     pool_start[0] = 0;
     for (int q = 0; q < npools; ++q) {
         hyperim_pool* p = pools[q];
-        // a shard (rank r of W) holds the sets j = r (mod W) of each stratum's allocation
         const uint64_t W = (uint64_t)std::max(p->shard_world, 1), R = (uint64_t)std::max(p->shard_rank, 0);
         jm[q].job_base[0] = 0;
         jm[q].j_step = (uint32_t)W;
@@ -1795,11 +1871,84 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         }
         pool_start[q + 1] = pool_start[q] + jm[q].job_base[HYPERIM_NSTRATA];
     }
+    return HYPERIM_OK;
+}
+
+// the graph's arrays and scalars in P (everything a set's construction reads of the graph)
+void fill_graph_params(RRParams& P, const hyperim_graph* g) {
+    P.vinfo = g->vinfo;
+    P.v_span = g->v_span;
+    P.he_mem = g->he_mem;
+    P.prof_off = g->prof_off;
+    P.prof = g->prof;
+    P.tab = g->cdf_tab;
+    P.tsum = g->tsum;
+    P.vs_off = g->vs_off;
+    P.vs_list = g->vs_list;
+    P.idx = g->idx;
+    P.idx_tab = g->idx_tab;
+    P.mat_sect = g->mat_sect;
+    P.he_dir = g->he_dir;
+    P.v_dir = g->v_dir;
+    P.n = g->n;
+    P.id_bits = g->id_bits;
+    P.seed = g->seed;
+}
+
+// The launch's sets of pool p (jobs [0, nq) of d_pos / d_size, sizes in the arena) appended to its
+// CSR arrays on g's stream (offsets by an exclusive scan of the sizes into d_boff, nq + 1
+// entries), and the pool's bookkeeping: allocation, counts, counters, kernel time (its share).
+hyperim_status compact_pool(hyperim_graph* g, hyperim_pool* p, const int32_t* arena, const int64_t* d_pos,
+                            const int32_t* d_size, int64_t nq, const RRJobMap& jm,
+                            const uint64_t new_ns[HYPERIM_NSTRATA], int64_t* d_boff, const RRCounters& c,
+                            double seconds, uint64_t launches) {
+    cudaStream_t s = g->stream;
+    hyperim_status st;
+    if (nq > 0) {
+        if ((st = exclusive_scan_u32_to_i64(g, reinterpret_cast<const uint32_t*>(d_size), d_boff, nq))) return st;
+        int64_t btotal = 0;
+        HYP_CUDA(cudaMemcpyAsync(&btotal, d_boff + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HYP_CUDA(cudaStreamSynchronize(s));
+        const size_t new_count = (size_t)(p->count + nq), new_total = (size_t)(p->total + btotal);
+        if ((st = grow_array(g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
+            return st;
+        if ((st = grow_array(g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
+        if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
+        if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
+        const int grid = (int)std::min<int64_t>((nq * 32 + 255) / 256, (int64_t)g->sm_count * 32);
+        { k_compact_rr<<<grid, 256, 0, s>>>(arena, d_pos, d_boff, nq, p->count, p->total, jm, p->rr_off,
+                                            p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
+        HYP_CUDA(cudaGetLastError());
+        for (int i = 0; i < HYPERIM_NSTRATA; ++i)
+            if (new_ns[i] > p->n_s[i]) p->n_s[i] = new_ns[i];
+        p->count = (int64_t)new_count;
+        p->total = (int64_t)new_total;
+        p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
+    }
+    unsigned long long* dst = &p->counters.pops;
+    const unsigned long long* src = &c.pops;
+    for (int i = 0; i < kNStat; ++i) dst[i] += src[i];
+    p->rr_kernel_seconds += seconds;
+    p->rr_launches += launches;
+    return HYPERIM_OK;
+}
+
+}  // namespace
+
+hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int npools,
+                               const uint64_t (*new_ns)[HYPERIM_NSTRATA]) {
+    if (npools < 1 || npools > kMaxPools) return set_error(HYPERIM_EINVAL, "bad pool count");
+    for (int q = 1; q < npools; ++q)
+        if (pools[q]->root_mode != pools[0]->root_mode || pools[q]->strategy != pools[0]->strategy)
+            return set_error(HYPERIM_ESTATE, "pools grown together must share root mode and strategy");
+    RRJobMap jm[kMaxPools];
+    int64_t pool_start[kMaxPools + 1];
+    hyperim_status st;
+    if ((st = make_job_maps(pools, npools, new_ns, jm, pool_start))) return st;
     const int64_t njobs = pool_start[npools];
     if (njobs == 0) return HYPERIM_OK;
     if (njobs >= (int64_t)0x7FFFFFFF) return set_error(HYPERIM_EOVERFLOW, "too many RR sets in one growth step");
     cudaStream_t s = g->stream;
-    hyperim_status st;
 
     // the visited bitmap goes on chip while the block still fits on an SM
     if ((st = allow_rr_smem())) return st;
@@ -1854,23 +2003,8 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
     unsigned long long* d_used = &d_ctrl->arena_used;
     RRParams P;
-    P.vinfo = g->vinfo;
-    P.v_span = g->v_span;
-    P.he_mem = g->he_mem;
-    P.prof_off = g->prof_off;
-    P.prof = g->prof;
-    P.tab = g->cdf_tab;
-    P.tsum = g->tsum;
-    P.vs_off = g->vs_off;
-    P.vs_list = g->vs_list;
-    P.idx = g->idx;
-    P.idx_tab = g->idx_tab;
-    P.mat_sect = g->mat_sect;
-    P.he_dir = g->he_dir;
-    P.v_dir = g->v_dir;
-    P.n = g->n;
-    P.id_bits = g->id_bits;
-    P.seed = g->seed;
+    std::memset(&P, 0, sizeof(P));
+    fill_graph_params(P, g);
     P.root_mode = pools[0]->root_mode;
     P.strategy = pools[0]->strategy;
     P.npools = npools;
@@ -1971,46 +2105,236 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     int64_t* d_boff = nullptr;
     if ((st = tmp.alloc(&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
     for (int q = 0; q < npools; ++q) {
-        hyperim_pool* p = pools[q];
         const int64_t b0 = pool_start[q], nq = pool_start[q + 1] - b0;
-        if (nq > 0) {
-            if ((st = exclusive_scan_u32_to_i64(g, reinterpret_cast<const uint32_t*>(d_size + b0), d_boff, nq)))
-                return st;
-            int64_t btotal = 0;
-            HYP_CUDA(cudaMemcpyAsync(&btotal, d_boff + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            HYP_CUDA(cudaStreamSynchronize(s));
-            const size_t new_count = (size_t)(p->count + nq), new_total = (size_t)(p->total + btotal);
-            if ((st = grow_array(g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
-                return st;
-            if ((st = grow_array(g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
-            if ((st = grow_array(g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
-            if ((st = grow_array(g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
-            const int grid = (int)std::min<int64_t>((nq * 32 + 255) / 256, (int64_t)g->sm_count * 32);
-            { k_compact_rr<<<grid, 256, 0, s>>>(g->scratch.arena, d_pos + b0, d_boff, nq, p->count, p->total,
-                                                jm[q], p->rr_off, p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
-            HYP_CUDA(cudaGetLastError());
-            for (int i = 0; i < HYPERIM_NSTRATA; ++i)
-                if (new_ns[q][i] > p->n_s[i]) p->n_s[i] = new_ns[q][i];
-            p->count = (int64_t)new_count;
-            p->total = (int64_t)new_total;
-            p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
-        }
-        p->counters.pops += c[q].pops;
-        p->counters.layers_seen += c[q].layers_seen;
-        p->counters.draws += c[q].draws;
-        p->counters.mats += c[q].mats;
-        p->counters.mat_he += c[q].mat_he;
-        p->counters.mat_members += c[q].mat_members;
-        p->counters.selected += c[q].selected;
-        p->counters.gathered += c[q].gathered;
-        p->counters.search_words += c[q].search_words;
-        p->counters.sectors += c[q].sectors;
         // the launch's time and count are shared by the pools it grew, in proportion to their jobs
         const double share = (double)nq / (double)njobs;
-        p->rr_kernel_seconds += seconds * share;
-        if (q == 0) p->rr_launches += (uint64_t)launches;
+        if ((st = compact_pool(g, pools[q], g->scratch.arena, d_pos + b0, d_size + b0, nq, jm[q], new_ns[q], d_boff,
+                               c[q], seconds * share, q == 0 ? (uint64_t)launches : 0)))
+            return st;
     }
     return check_device_status(g, "RR compaction");
+}
+
+hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngroups, double* seconds_out) {
+    if (seconds_out) *seconds_out = 0.0;
+    if (ngroups < 1) return HYPERIM_OK;
+    hyperim_status st;
+    std::vector<RRJobMap> jm((size_t)ngroups * kMaxPools);
+    std::vector<int64_t> pstart((size_t)ngroups * (kMaxPools + 1));
+    std::vector<int64_t> gstart((size_t)ngroups + 1, 0);
+    std::vector<cudaStream_t> streams{g0->stream};
+    int64_t n_max = 1, deg_max = 1, tsum_max = 1;
+    for (int q = 0; q < ngroups; ++q) {
+        const RRGroup& G = groups[q];
+        if (G.npools < 1 || G.npools > kMaxPools) return set_error(HYPERIM_EINVAL, "bad pool count");
+        for (int i = 0; i < G.npools; ++i) {
+            if (graph_root(G.pools[i]->g) != graph_root(G.g)) return set_error(HYPERIM_ESTATE, "pool of another graph");
+            if (G.pools[i]->root_mode != G.pools[0]->root_mode || G.pools[i]->strategy != G.pools[0]->strategy)
+                return set_error(HYPERIM_ESTATE, "pools grown together must share root mode and strategy");
+        }
+        if ((st = make_job_maps(G.pools, G.npools, G.new_ns, &jm[(size_t)q * kMaxPools],
+                                &pstart[(size_t)q * (kMaxPools + 1)])))
+            return st;
+        gstart[q + 1] = gstart[q] + pstart[(size_t)q * (kMaxPools + 1) + G.npools];
+        n_max = std::max<int64_t>(n_max, G.g->n);
+        deg_max = std::max<int64_t>(deg_max, G.g->max_deg);
+        tsum_max = std::max<int64_t>(tsum_max, G.g->max_tsum);
+        if (std::find(streams.begin(), streams.end(), G.g->stream) == streams.end()) streams.push_back(G.g->stream);
+    }
+    const int64_t njobs = gstart[ngroups];
+    if (njobs == 0) return HYPERIM_OK;
+    if (njobs >= (int64_t)0x7FFFFFFF) return set_error(HYPERIM_EOVERFLOW, "too many RR sets in one growth step");
+    cudaStream_t s = g0->stream;
+    // the launch runs on g0's stream after the work already queued on every graph's stream, and
+    // each graph's compaction runs on its own stream once the launch is done (host-synchronised)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> waits;
+    struct Events {
+        cudaEvent_t* a;
+        cudaEvent_t* b;
+        std::vector<cudaEvent_t>* w;
+        ~Events() {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+            for (cudaEvent_t e : *w) cudaEventDestroy(e);
+        }
+    } events{&ev0, &ev1, &waits};
+    for (size_t i = 1; i < streams.size(); ++i) {
+        cudaEvent_t e = nullptr;
+        HYP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        waits.push_back(e);
+        HYP_CUDA(cudaEventRecord(e, streams[i]));
+        HYP_CUDA(cudaStreamWaitEvent(s, e, 0));
+    }
+
+    if ((st = allow_rr_smem())) return st;
+    cudaFuncAttributes fa;
+    HYP_CUDA(cudaFuncGetAttributes(&fa, k_rr_batch));
+    const size_t words_max = ((size_t)n_max + 31) / 32;
+    bool vis_smem = n_max <= kVisSmemBits && sizeof(Shared) + sizeof(uint32_t) * words_max + fa.sharedSizeBytes <= smem_optin();
+    size_t smem = 0;
+    int per_sm = 0;
+    for (;;) {
+        smem = sizeof(Shared) + (vis_smem ? sizeof(uint32_t) * words_max : 0);
+        HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rr_batch, kThreads, smem));
+        if (per_sm >= 1 || !vis_smem) break;
+        vis_smem = false;
+    }
+    if (per_sm < 1) return set_error(HYPERIM_ECUDA, "batched RR kernel does not fit on an SM");
+    int blocks = g0->sm_count * per_sm;
+    if ((int64_t)blocks > njobs) blocks = (int)njobs;
+
+    // scratch of this call, sized for the largest graph: queue (empty slots), visited bitmap,
+    // picks and bucketed neighbourhoods per block
+    CallBuffers tmp(g0);
+    int32_t* list = nullptr;
+    uint32_t *gvis = nullptr, *picks = nullptr, *big = nullptr;
+    if ((st = tmp.alloc(&list, sizeof(int32_t) * (size_t)n_max * blocks))) return st;
+    HYP_CUDA(cudaMemsetAsync(list, 0xFF, sizeof(int32_t) * (size_t)n_max * blocks, s));
+    if (!vis_smem) {
+        if ((st = tmp.alloc(&gvis, sizeof(uint32_t) * words_max * blocks))) return st;
+        HYP_CUDA(cudaMemsetAsync(gvis, 0, sizeof(uint32_t) * words_max * blocks, s));
+    }
+    if ((st = tmp.alloc(&picks, sizeof(uint32_t) * (size_t)deg_max * blocks))) return st;
+    if ((st = tmp.alloc(&big, sizeof(uint32_t) * (size_t)tsum_max * blocks))) return st;
+    struct Ctrl {
+        int next_job;
+        int pad;
+        unsigned long long arena_used;
+    };
+    int64_t* d_pos = nullptr;
+    int32_t* d_size = nullptr;
+    Ctrl* d_ctrl = nullptr;
+    RRParams* d_groups = nullptr;
+    int64_t* d_gstart = nullptr;
+    RRCounters* d_counters = nullptr;
+    if ((st = tmp.alloc(&d_pos, sizeof(int64_t) * (size_t)njobs))) return st;
+    if ((st = tmp.alloc(&d_size, sizeof(int32_t) * (size_t)njobs))) return st;
+    if ((st = tmp.alloc(&d_ctrl, sizeof(Ctrl)))) return st;
+    if ((st = tmp.alloc(&d_groups, sizeof(RRParams) * (size_t)ngroups))) return st;
+    if ((st = tmp.alloc(&d_gstart, sizeof(int64_t) * ((size_t)ngroups + 1)))) return st;
+    if ((st = tmp.alloc(&d_counters, sizeof(RRCounters) * (size_t)ngroups * kMaxPools))) return st;
+
+    double want_d = 4096.0;
+    for (int q = 0; q < ngroups; ++q)
+        for (int i = 0; i < groups[q].npools; ++i) {
+            const hyperim_pool* p = groups[q].pools[i];
+            const int64_t* ps = &pstart[(size_t)q * (kMaxPools + 1)];
+            const double hint = p->mean_size_hint > 0 ? p->mean_size_hint : 8.0;
+            want_d += (double)(ps[i + 1] - ps[i]) * hint * 1.25;
+        }
+    uint64_t want = (uint64_t)want_d;
+    // the arena: reallocated when a launch overflows it
+    struct Arena {
+        hyperim_graph* g;
+        int32_t* p = nullptr;
+        uint64_t cap = 0;
+        ~Arena() {
+            if (p) dev_free(g, p, sizeof(int32_t) * cap);
+        }
+    } arena{g0};
+
+    std::vector<RRParams> hp((size_t)ngroups);
+    for (int q = 0; q < ngroups; ++q) {
+        const RRGroup& G = groups[q];
+        RRParams& P = hp[q];
+        std::memset(&P, 0, sizeof(P));
+        fill_graph_params(P, G.g);
+        P.root_mode = G.pools[0]->root_mode;
+        P.strategy = G.pools[0]->strategy;
+        P.npools = G.npools;
+        for (int i = 0; i <= G.npools; ++i) P.pool_start[i] = pstart[(size_t)q * (kMaxPools + 1) + i];
+        for (int i = 0; i < G.npools; ++i) {
+            P.tags[i] = G.pools[i]->tag;
+            P.jm[i] = jm[(size_t)q * kMaxPools + i];
+        }
+        P.list = list;
+        P.list_cap = n_max;
+        P.gvis = gvis;
+        P.vis_smem = vis_smem ? 1 : 0;
+        P.vis_words = (int64_t)words_max;
+        P.picks = picks;
+        P.pick_cap = deg_max;
+        P.big = big;
+        P.big_cap = tsum_max;
+        P.out_pos = d_pos + gstart[q];
+        P.out_size = d_size + gstart[q];
+        P.arena_used = &d_ctrl->arena_used;
+        P.st = g0->d_status;
+        P.counters = d_counters + (size_t)q * kMaxPools;
+        P.spin_limit = wait_rounds(g0);
+    }
+    RRBatchParams B;
+    B.groups = d_groups;
+    B.group_start = d_gstart;
+    B.ngroups = ngroups;
+    B.next_job = &d_ctrl->next_job;
+    B.list = list;
+    B.list_cap = n_max;
+    B.gvis = gvis;
+    B.vis_smem = vis_smem ? 1 : 0;
+    B.vis_words = (int64_t)words_max;
+    B.picks = picks;
+    B.pick_cap = deg_max;
+    B.big = big;
+    B.big_cap = tsum_max;
+    HYP_CUDA(cudaMemcpyAsync(d_gstart, gstart.data(), sizeof(int64_t) * ((size_t)ngroups + 1), cudaMemcpyHostToDevice, s));
+    HYP_CUDA(cudaEventCreate(&ev0));
+    HYP_CUDA(cudaEventCreate(&ev1));
+    unsigned long long used = 0;
+    double seconds = 0.0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if (arena.cap < want) {
+            if (arena.p) dev_free(g0, arena.p, sizeof(int32_t) * arena.cap);
+            arena.p = nullptr;
+            arena.cap = 0;
+            if ((st = dev_alloc(g0, (void**)&arena.p, sizeof(int32_t) * want))) return st;
+            arena.cap = want;
+        }
+        for (RRParams& P : hp) {
+            P.arena = arena.p;
+            P.arena_cap = arena.cap;
+        }
+        HYP_CUDA(cudaMemcpyAsync(d_groups, hp.data(), sizeof(RRParams) * hp.size(), cudaMemcpyHostToDevice, s));
+        HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
+        HYP_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(RRCounters) * (size_t)ngroups * kMaxPools, s));
+        HYP_CUDA(cudaEventRecord(ev0, s));
+        { k_rr_batch<<<blocks, kThreads, smem, s>>>(B); count_launch(); }
+        HYP_CUDA(cudaGetLastError());
+        HYP_CUDA(cudaEventRecord(ev1, s));
+        HYP_CUDA(cudaMemcpyAsync(&used, &d_ctrl->arena_used, sizeof(used), cudaMemcpyDeviceToHost, s));
+        if ((st = check_device_status(g0, "RR generation (batch)"))) return st;  // synchronises s
+        float ms = 0.f;
+        HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        seconds += 1e-3 * (double)ms;
+        if (used <= arena.cap) break;
+        want = used + used / 8 + 4096;
+    }
+    if (used > arena.cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
+    if (seconds_out) *seconds_out = seconds;
+    std::vector<RRCounters> c((size_t)ngroups * kMaxPools);
+    HYP_CUDA(cudaMemcpyAsync(c.data(), d_counters, sizeof(RRCounters) * c.size(), cudaMemcpyDeviceToHost, s));
+    // compaction on each graph's stream; separate offset buffers, since those streams overlap
+    int64_t* d_boff = nullptr;
+    if ((st = tmp.alloc(&d_boff, sizeof(int64_t) * ((size_t)njobs + (size_t)ngroups * kMaxPools)))) return st;
+    HYP_CUDA(cudaStreamSynchronize(s));
+    int64_t boff_at = 0;
+    hyperim_status cst = HYPERIM_OK;
+    for (int q = 0; q < ngroups && cst == HYPERIM_OK; ++q) {
+        const RRGroup& G = groups[q];
+        const int64_t* ps = &pstart[(size_t)q * (kMaxPools + 1)];
+        for (int i = 0; i < G.npools && cst == HYPERIM_OK; ++i) {
+            const int64_t b0 = gstart[q] + ps[i], nq = ps[i + 1] - ps[i];
+            cst = compact_pool(G.g, G.pools[i], arena.p, d_pos + b0, d_size + b0, nq, jm[(size_t)q * kMaxPools + i],
+                               G.new_ns[i], d_boff + boff_at, c[(size_t)q * kMaxPools + i],
+                               seconds * (double)nq / (double)njobs, 1);
+            boff_at += nq + 1;
+        }
+    }
+    // the call's buffers are released on s: every compaction has finished first
+    for (cudaStream_t x : streams) cudaStreamSynchronize(x);
+    if (cst != HYPERIM_OK) return cst;
+    return check_device_status(g0, "RR compaction (batch)");
 }
 
 hyperim_status sample_rr(hyperim_graph* g, hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA]) {
