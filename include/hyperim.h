@@ -212,11 +212,17 @@ hyperim_status hyperim_graph_set_schedule(hyperim_graph_t g, int32_t schedule);
  *   early_sets_per_block: BRR (hyperim_select_seeds) grows R1 and R2 in its first launch to at
  *     least this many sets per resident block of the RR kernel per pool (the rounds up to that
  *     theta read their prefixes of it). >= 1; default 4.
+ *   arena_entries_per_set: the output arena of a growth step starts at this many entries per
+ *     new RR set (0, the default: 1.25 x the pool's mean set size so far, or the handle's last
+ *     growth's, or min(sets x n, 2^27) entries with no history). A set that does not fit is
+ *     built again by a repair launch and written to the slot the first launch reserved for it,
+ *     so a small value costs time, never results. 0..2^20.
  *   EINVAL: g or t NULL, a value out of range. No device work.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int32_t warp_set_limit;
     int32_t early_sets_per_block;
+    int32_t arena_entries_per_set;
 } hyperim_tuning;
 hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning* t);
 hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out);

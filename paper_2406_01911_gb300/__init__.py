@@ -78,7 +78,8 @@ class PoolView(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32)]
+    _fields_ = [("warp_set_limit", C.c_int32), ("early_sets_per_block", C.c_int32),
+                ("arena_entries_per_set", C.c_int32)]
 
 
 class AutotuneResult(C.Structure):
@@ -434,13 +435,15 @@ class Graph:
     def tuning(self):
         t = Tuning()
         _check(lib().hyperim_graph_get_tuning(self._h, C.byref(t)))
-        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block}
+        return {"warp_set_limit": t.warp_set_limit, "early_sets_per_block": t.early_sets_per_block,
+                "arena_entries_per_set": t.arena_entries_per_set}
 
-    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None):
+    def set_tuning(self, warp_set_limit=None, early_sets_per_block=None, arena_entries_per_set=None):
         """RR-generation scheduling (hyperim_graph_set_tuning); the results never change."""
         cur = self.tuning()
         pick = lambda v, k: int(cur[k] if v is None else v)
-        t = Tuning(pick(warp_set_limit, "warp_set_limit"), pick(early_sets_per_block, "early_sets_per_block"))
+        t = Tuning(pick(warp_set_limit, "warp_set_limit"), pick(early_sets_per_block, "early_sets_per_block"),
+                   pick(arena_entries_per_set, "arena_entries_per_set"))
         _check(lib().hyperim_graph_set_tuning(self._h, C.byref(t)))
 
     def autotune(self, roots="stratified", strategy="paper", sets=0):

@@ -379,6 +379,8 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->wait_limit = r->wait_limit;
     h->warp_set_limit = r->warp_set_limit;
     h->early_sets_per_block = r->early_sets_per_block;
+    h->arena_entries_per_set = r->arena_entries_per_set;
+    h->set_size_hint = r->set_size_hint;
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -482,8 +484,11 @@ hyperim_status hyperim_graph_set_tuning(hyperim_graph_t g, const hyperim_tuning*
     if (t->warp_set_limit < 0 || t->warp_set_limit > 128) return set_error(HYPERIM_EINVAL, "warp_set_limit outside [0, 128]");
     if (t->early_sets_per_block < 1 || t->early_sets_per_block > 4096)
         return set_error(HYPERIM_EINVAL, "early_sets_per_block outside [1, 4096]");
+    if (t->arena_entries_per_set < 0 || t->arena_entries_per_set > (1 << 20))
+        return set_error(HYPERIM_EINVAL, "arena_entries_per_set outside [0, 2^20]");
     g->warp_set_limit = t->warp_set_limit;
     g->early_sets_per_block = t->early_sets_per_block;
+    g->arena_entries_per_set = t->arena_entries_per_set;
     return HYPERIM_OK;
 }
 
@@ -491,6 +496,7 @@ hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out) 
     if (!g || !out) return set_error(HYPERIM_EINVAL, "null argument");
     out->warp_set_limit = g->warp_set_limit;
     out->early_sets_per_block = g->early_sets_per_block;
+    out->arena_entries_per_set = g->arena_entries_per_set;
     return HYPERIM_OK;
 }
 
@@ -547,6 +553,7 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
         if (it != tune_cache().end()) {
             hyperim_tuning t = it->second;
             t.early_sets_per_block = g->early_sets_per_block;
+            t.arena_entries_per_set = g->arena_entries_per_set;
             g->warp_set_limit = t.warp_set_limit;
             out->chosen = t;
             out->from_cache = 1;
@@ -558,7 +565,7 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
     g->schedule = HYPERIM_SCHED_PERSISTENT;
     const int32_t cand[5] = {0, 16, 32, 64, 128};  // warp-phase set limits (0: none)
     double best = -1.0;
-    hyperim_tuning choice{keep_w, g->early_sets_per_block};
+    hyperim_tuning choice{keep_w, g->early_sets_per_block, g->arena_entries_per_set};
     hyperim_status st = HYPERIM_OK;
     int c = 0;
     {

@@ -150,6 +150,8 @@ struct hyperim_graph {
     uint32_t wait_limit = 0;     // iterations of a bounded device wait (0: the default)
     int32_t warp_set_limit = 0;  // RR sets up to this size are built by one warp (0: no warp phase)
     int32_t early_sets_per_block = 4;  // BRR's first launch: sets per resident block and pool
+    double set_size_hint = 0.0;  // mean RR-set size of this handle's last growth (0: none yet)
+    int32_t arena_entries_per_set = 0;  // tuning: initial output arena per new set (0: automatic)
     // caller's device allocator (hyperim_load_args); null: stream-ordered cudaMallocAsync
     void* (*alloc_fn)(size_t, void*, void*) = nullptr;
     void (*free_fn)(void*, void*, void*) = nullptr;

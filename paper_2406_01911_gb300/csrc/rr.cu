@@ -100,6 +100,8 @@ struct RRParams {
     int warp_limit;           // warp phase: the largest RR set a warp builds alone (1..kWQ)
     int plain;                // 1: this launch runs jobs [plain_base, plain_base + gridDim.x), one per block
     int64_t plain_base;
+    int rewrite;              // 1: a repair launch -- sets go to the arena slots recorded by the first
+                              // launch (out_pos), whose arena was too small; no counters are added
     DevStatus* st;
     RRCounters* counters;                    // kMaxPools entries
     int spin_limit;                          // rounds of a bounded wait before it gives up
@@ -1499,9 +1501,16 @@ __global__ void __launch_bounds__(kPThreads, 2) k_rr_warp(RRParams P) {
 __device__ void write_set(const RRParams& P, Shared& S, uint32_t* vis, const int32_t* list, int size, int64_t job) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        const unsigned long long pos = atomicAdd(P.arena_used, (unsigned long long)size);
-        P.out_pos[job] = (int64_t)pos;
-        P.out_size[job] = size;
+        unsigned long long pos;
+        if (P.rewrite) {
+            // the slot the first launch reserved for this set (the same set: keyed draws)
+            pos = (unsigned long long)P.out_pos[job];
+            if (P.out_size[job] != size) dev_fail(P.st, kErrCapacity, (int32_t)job);
+        } else {
+            pos = atomicAdd(P.arena_used, (unsigned long long)size);
+            P.out_pos[job] = (int64_t)pos;
+            P.out_size[job] = size;
+        }
         S.ctrl[C_ROOT] = pos + (unsigned long long)size <= P.arena_cap ? 1 : 0;
         S.out_pos = pos;
     }
@@ -1621,7 +1630,7 @@ __device__ __forceinline__ void run_job(const RRParams& P, Shared& S, uint32_t* 
             S.wstat[w][threadIdx.x] = 0;
         }
         if (kFlushPerSet) {
-            if (sum) atomicAdd(&P.counters[pi].pops + threadIdx.x, sum);
+            if (sum && !P.rewrite) atomicAdd(&P.counters[pi].pops + threadIdx.x, sum);
         } else {
             S.stat[pi][threadIdx.x] += sum;
         }
@@ -1667,12 +1676,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
         run_job<false>(P, S, vis, list, picks_g, big, job);
     }
     __syncthreads();
-    if (threadIdx.x < P.npools) {
+    if (threadIdx.x < P.npools && !P.rewrite) {
         RRCounters* c = P.counters + threadIdx.x;
         const unsigned long long* st = S.stat[threadIdx.x];
         for (int i = 0; i < kNStat; ++i)
             if (st[i]) atomicAdd(&c->pops + i, st[i]);
     }
+}
+
+// The jobs whose sets did not fit in an arena of `cap` entries (slot [pos, pos + size) past it).
+__global__ void k_overflow_jobs(const int64_t* __restrict__ pos, const int32_t* __restrict__ size, int64_t njobs,
+                                uint64_t cap, int32_t* __restrict__ list, int* __restrict__ count) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < njobs;
+         j += (int64_t)gridDim.x * blockDim.x)
+        if ((uint64_t)pos[j] + (uint64_t)size[j] > cap) list[atomicAdd(count, 1)] = (int32_t)j;
 }
 
 // A launch over the pools of several graphs (the batched form of HyperIM_BRR: every query's
@@ -1686,6 +1703,8 @@ struct RRBatchParams {
     const int64_t* group_start;  // ngroups + 1
     int ngroups;
     int* next_job;
+    const int32_t* rerun;        // a repair launch: the global jobs to build again (else null)
+    const int* rerun_count;
     int32_t* list;
     int64_t list_cap;
     uint32_t* gvis;
@@ -1707,6 +1726,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr_batch(RRBatchParams B) {
     uint32_t* picks_g = B.picks + (int64_t)blockIdx.x * B.pick_cap;
     uint32_t* big = B.big + (int64_t)blockIdx.x * B.big_cap;
     const int64_t njobs = B.group_start[B.ngroups];
+    const int64_t ntickets = B.rerun ? (int64_t)*(volatile const int*)B.rerun_count : njobs;
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
     for (int64_t w = threadIdx.x; w < B.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
@@ -1715,8 +1735,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr_batch(RRBatchParams B) {
         if (threadIdx.x == 0) S.ctrl[C_JOB] = atomicAdd(B.next_job, 1);
         __syncthreads();
         const int64_t ticket = S.ctrl[C_JOB];
-        if (ticket >= njobs) break;
-        const int64_t gjob = njobs - 1 - ticket;
+        if (ticket >= ntickets) break;
+        const int64_t gjob = B.rerun ? (int64_t)B.rerun[ticket] : njobs - 1 - ticket;
         int lo = 0, hi = B.ngroups - 1;  // the group holding gjob: last start <= gjob
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -1849,6 +1869,40 @@ hyperim_status ensure_scratch(hyperim_graph* g, int blocks, bool vis_smem) {
     return HYPERIM_OK;
 }
 
+// Output arena entries for a growth step: 1.25 x the expected members (each pool's mean set size
+// so far, else the graph handle's last growth's). With no size history at all the sets may hold
+// anything up to n members: the arena then takes min(jobs x n, 2^27) entries, so that a first
+// growth rarely needs the repair launch (which builds again every set that did not fit).
+uint64_t arena_want(const hyperim_graph* g, hyperim_pool* const* pools, int npools, const int64_t* pool_start,
+                    int64_t n) {
+    if (g->arena_entries_per_set > 0)
+        return std::max<uint64_t>(1, (uint64_t)(pool_start[npools] - pool_start[0]) * (uint64_t)g->arena_entries_per_set);
+    double want = 4096.0;
+    bool unknown = false;
+    for (int q = 0; q < npools; ++q) {
+        const double jobs = (double)(pool_start[q + 1] - pool_start[q]);
+        const double hint = pools[q]->mean_size_hint > 0 ? pools[q]->mean_size_hint : g->set_size_hint;
+        if (hint > 0) want += jobs * hint * 1.25;
+        else unknown = unknown || jobs > 0;
+    }
+    if (unknown) {
+        const double jobs = (double)(pool_start[npools] - pool_start[0]);
+        want = std::max(want, std::min(jobs * (double)std::max<int64_t>(n, 1), (double)(1ull << 27)));
+    }
+    return (uint64_t)want;
+}
+
+// after a growth: the handle's set-size hint, and an idle arena far larger than what the growth
+// used is released (the next growth allocates what its hint asks for)
+void after_growth(hyperim_graph* g, uint64_t used, int64_t njobs, int32_t** arena, uint64_t* cap) {
+    if (njobs > 0) g->set_size_hint = std::max(1.0, (double)used / (double)njobs);
+    if (*arena && *cap > (1ull << 24) && *cap > 4 * used + 4096) {
+        dev_free(g, *arena, sizeof(int32_t) * *cap);
+        *arena = nullptr;
+        *cap = 0;
+    }
+}
+
 // Job maps of a growth step: pool q's new sets are jobs [pool_start[q], pool_start[q + 1]),
 // stratum by stratum; a shard (rank r of W) holds the sets j = r (mod W) of each stratum's
 // allocation.
@@ -1968,13 +2022,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if ((int64_t)blocks > njobs) blocks = (int)njobs;
     if ((st = ensure_scratch(g, blocks, vis_smem))) return st;
 
-    // output arena sized from the pools' running mean set size, relaunched on overflow
-    double want_d = 4096.0;
-    for (int q = 0; q < npools; ++q) {
-        const double hint = pools[q]->mean_size_hint > 0 ? pools[q]->mean_size_hint : 8.0;
-        want_d += (double)(pool_start[q + 1] - pool_start[q]) * hint * 1.25;
-    }
-    uint64_t want = (uint64_t)want_d;
+    const uint64_t want = arena_want(g, pools, npools, pool_start, g->n);
     // the warp phase (one RR set per warp) runs first in the persistent schedule, unless the
     // graph's tuning turned it off; its grid
     const bool warp_phase = g->schedule != HYPERIM_SCHED_PLAIN && g->warp_set_limit > 0;
@@ -2049,56 +2097,87 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     HYP_CUDA(cudaEventCreate(&ev1));
     double seconds = 0.0;
     int launches = 0;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        if (g->scratch.arena_cap < want) {
-            if (g->scratch.arena) dev_free(g, g->scratch.arena, sizeof(int32_t) * g->scratch.arena_cap);
-            g->scratch.arena = nullptr;
-            g->scratch.arena_cap = 0;
-            if ((st = dev_alloc(g, (void**)&g->scratch.arena, sizeof(int32_t) * want))) return st;
-            g->scratch.arena_cap = want;
-        }
-        P.arena = g->scratch.arena;
-        P.arena_cap = g->scratch.arena_cap;
-        HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
-        HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
-        HYP_CUDA(cudaEventRecord(ev0, s));
-        if (P.plain) {
-            // the comparison form: one launch per batch of `blocks` sets, one set per block
-            for (int64_t base = 0; base < njobs; base += blocks) {
-                P.plain_base = base;
-                const int grid = (int)std::min<int64_t>(blocks, njobs - base);
-                { k_rr<<<grid, kThreads, smem, s>>>(P); count_launch(); }
-                HYP_CUDA(cudaGetLastError());
-                ++launches;
-            }
-        } else if (warp_phase) {
-            // warp phase over every job, then the block phase over the jobs it listed
-            P.block_phase = 0;
-            { k_rr_warp<<<wblocks, kPThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
+    if (g->scratch.arena_cap < want) {
+        if (g->scratch.arena) dev_free(g, g->scratch.arena, sizeof(int32_t) * g->scratch.arena_cap);
+        g->scratch.arena = nullptr;
+        g->scratch.arena_cap = 0;
+        if ((st = dev_alloc(g, (void**)&g->scratch.arena, sizeof(int32_t) * want))) return st;
+        g->scratch.arena_cap = want;
+    }
+    P.arena = g->scratch.arena;
+    P.arena_cap = g->scratch.arena_cap;
+    P.rewrite = 0;
+    HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
+    HYP_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(RRCounters) * kMaxPools, s));
+    HYP_CUDA(cudaEventRecord(ev0, s));
+    if (P.plain) {
+        // the comparison form: one launch per batch of `blocks` sets, one set per block
+        for (int64_t base = 0; base < njobs; base += blocks) {
+            P.plain_base = base;
+            const int grid = (int)std::min<int64_t>(blocks, njobs - base);
+            { k_rr<<<grid, kThreads, smem, s>>>(P); count_launch(); }
             HYP_CUDA(cudaGetLastError());
-            P.block_phase = 1;
-            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
-            P.block_phase = 0;
-            ++launches;
-        } else {
-            { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
             ++launches;
         }
+    } else if (warp_phase) {
+        // warp phase over every job, then the block phase over the jobs it listed
+        P.block_phase = 0;
+        { k_rr_warp<<<wblocks, kPThreads, sizeof(WarpShared), s>>>(P); count_launch(); }
+        HYP_CUDA(cudaGetLastError());
+        P.block_phase = 1;
+        { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+        P.block_phase = 0;
+        ++launches;
+    } else {
+        { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
+        ++launches;
+    }
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(cudaEventRecord(ev1, s));
+    HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
+    auto failed = [&](hyperim_status code) {
+        // a failed launch may leave queue slots filled: empty them for the next one
+        cudaMemsetAsync(g->scratch.list, 0xFF, sizeof(int32_t) * g->scratch.list_cap * g->scratch.blocks, s);
+        return code;
+    };
+    if ((st = check_device_status(g, "RR generation"))) return failed(st);
+    float ms = 0.f;
+    HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    seconds += 1e-3 * (double)ms;
+    if (used > g->scratch.arena_cap) {
+        // The arena (sized from the pools' mean set size so far) was too small: every set has its
+        // slot reserved in [0, used), and the sets that fit are written. The arena grows (its
+        // written part copied), and a repair launch builds again only the sets that did not fit
+        // and writes them to their reserved slots.
+        const uint64_t old_cap = g->scratch.arena_cap;
+        const uint64_t new_cap = used + used / 8 + 4096;
+        int32_t* na = nullptr;
+        if ((st = dev_alloc(g, (void**)&na, sizeof(int32_t) * new_cap))) return st;
+        HYP_CUDA(cudaMemcpyAsync(na, g->scratch.arena, sizeof(int32_t) * old_cap, cudaMemcpyDeviceToDevice, s));
+        dev_free(g, g->scratch.arena, sizeof(int32_t) * old_cap);
+        g->scratch.arena = na;
+        g->scratch.arena_cap = new_cap;
+        HYP_CUDA(cudaMemsetAsync(&d_ctrl->next_job[1], 0, 2 * sizeof(int), s));  // block-phase counter, list size
+        { k_overflow_jobs<<<(int)std::min<int64_t>((njobs + 255) / 256, (int64_t)g->sm_count * 8), 256, 0, s>>>(
+              d_pos, d_size, njobs, old_cap, d_esc, &d_ctrl->esc_count); count_launch(); }
+        const int plain = P.plain;
+        P.arena = na;
+        P.arena_cap = new_cap;
+        P.plain = 0;
+        P.block_phase = 1;
+        P.rewrite = 1;
+        HYP_CUDA(cudaEventRecord(ev0, s));
+        { k_rr<<<blocks, kThreads, smem, s>>>(P); count_launch(); }
         HYP_CUDA(cudaGetLastError());
         HYP_CUDA(cudaEventRecord(ev1, s));
-        HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
-        if ((st = check_device_status(g, "RR generation"))) {
-            // a failed launch may leave queue slots filled: empty them for the next one
-            cudaMemsetAsync(g->scratch.list, 0xFF, sizeof(int32_t) * g->scratch.list_cap * g->scratch.blocks, s);
-            return st;
-        }
-        float ms = 0.f;
+        P.plain = plain;
+        P.block_phase = 0;
+        P.rewrite = 0;
+        ++launches;
+        if ((st = check_device_status(g, "RR generation (arena repair)"))) return failed(st);
         HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
         seconds += 1e-3 * (double)ms;
-        if (used <= g->scratch.arena_cap) break;
-        want = used + used / 8 + 4096;
     }
-    if (used > g->scratch.arena_cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
     RRCounters c[kMaxPools];
     HYP_CUDA(cudaMemcpyAsync(c, g->d_counters, sizeof(RRCounters) * kMaxPools, cudaMemcpyDeviceToHost, s));
     // compaction, pool by pool: CSR offsets by an exclusive scan of the sizes
@@ -2112,6 +2191,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
                                c[q], seconds * share, q == 0 ? (uint64_t)launches : 0)))
             return st;
     }
+    after_growth(g, used, njobs, &g->scratch.arena, &g->scratch.arena_cap);
     return check_device_status(g, "RR compaction");
 }
 
@@ -2199,7 +2279,7 @@ hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngr
     if ((st = tmp.alloc(&big, sizeof(uint32_t) * (size_t)tsum_max * blocks))) return st;
     struct Ctrl {
         int next_job;
-        int pad;
+        int rerun_count;  // sets listed for an arena repair
         unsigned long long arena_used;
     };
     int64_t* d_pos = nullptr;
@@ -2215,15 +2295,10 @@ hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngr
     if ((st = tmp.alloc(&d_gstart, sizeof(int64_t) * ((size_t)ngroups + 1)))) return st;
     if ((st = tmp.alloc(&d_counters, sizeof(RRCounters) * (size_t)ngroups * kMaxPools))) return st;
 
-    double want_d = 4096.0;
+    uint64_t want = 0;
     for (int q = 0; q < ngroups; ++q)
-        for (int i = 0; i < groups[q].npools; ++i) {
-            const hyperim_pool* p = groups[q].pools[i];
-            const int64_t* ps = &pstart[(size_t)q * (kMaxPools + 1)];
-            const double hint = p->mean_size_hint > 0 ? p->mean_size_hint : 8.0;
-            want_d += (double)(ps[i + 1] - ps[i]) * hint * 1.25;
-        }
-    uint64_t want = (uint64_t)want_d;
+        want += arena_want(groups[q].g, groups[q].pools, groups[q].npools, &pstart[(size_t)q * (kMaxPools + 1)],
+                           n_max);
     // the arena: reallocated when a launch overflows it
     struct Arena {
         hyperim_graph* g;
@@ -2283,34 +2358,58 @@ hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngr
     HYP_CUDA(cudaEventCreate(&ev1));
     unsigned long long used = 0;
     double seconds = 0.0;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        if (arena.cap < want) {
-            if (arena.p) dev_free(g0, arena.p, sizeof(int32_t) * arena.cap);
-            arena.p = nullptr;
-            arena.cap = 0;
-            if ((st = dev_alloc(g0, (void**)&arena.p, sizeof(int32_t) * want))) return st;
-            arena.cap = want;
-        }
+    if ((st = dev_alloc(g0, (void**)&arena.p, sizeof(int32_t) * want))) return st;
+    arena.cap = want;
+    for (RRParams& P : hp) {
+        P.arena = arena.p;
+        P.arena_cap = arena.cap;
+    }
+    B.rerun = nullptr;
+    B.rerun_count = nullptr;
+    HYP_CUDA(cudaMemcpyAsync(d_groups, hp.data(), sizeof(RRParams) * hp.size(), cudaMemcpyHostToDevice, s));
+    HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
+    HYP_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(RRCounters) * (size_t)ngroups * kMaxPools, s));
+    HYP_CUDA(cudaEventRecord(ev0, s));
+    { k_rr_batch<<<blocks, kThreads, smem, s>>>(B); count_launch(); }
+    HYP_CUDA(cudaGetLastError());
+    HYP_CUDA(cudaEventRecord(ev1, s));
+    HYP_CUDA(cudaMemcpyAsync(&used, &d_ctrl->arena_used, sizeof(used), cudaMemcpyDeviceToHost, s));
+    if ((st = check_device_status(g0, "RR generation (batch)"))) return st;  // synchronises s
+    float ms = 0.f;
+    HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    seconds += 1e-3 * (double)ms;
+    if (used > arena.cap) {
+        // as in sample_rr_multi: a larger arena (written part copied) and a repair launch over the
+        // sets that did not fit, written to the slots the first launch reserved
+        const uint64_t old_cap = arena.cap;
+        const uint64_t new_cap = used + used / 8 + 4096;
+        int32_t* na = nullptr;
+        if ((st = dev_alloc(g0, (void**)&na, sizeof(int32_t) * new_cap))) return st;
+        HYP_CUDA(cudaMemcpyAsync(na, arena.p, sizeof(int32_t) * old_cap, cudaMemcpyDeviceToDevice, s));
+        dev_free(g0, arena.p, sizeof(int32_t) * old_cap);
+        arena.p = na;
+        arena.cap = new_cap;
+        int32_t* d_list = nullptr;
+        if ((st = tmp.alloc(&d_list, sizeof(int32_t) * (size_t)njobs))) return st;
+        HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(int) * 2, s));  // job counter, list size
+        { k_overflow_jobs<<<(int)std::min<int64_t>((njobs + 255) / 256, (int64_t)g0->sm_count * 8), 256, 0, s>>>(
+              d_pos, d_size, njobs, old_cap, d_list, &d_ctrl->rerun_count); count_launch(); }
         for (RRParams& P : hp) {
             P.arena = arena.p;
             P.arena_cap = arena.cap;
+            P.rewrite = 1;
         }
         HYP_CUDA(cudaMemcpyAsync(d_groups, hp.data(), sizeof(RRParams) * hp.size(), cudaMemcpyHostToDevice, s));
-        HYP_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), s));
-        HYP_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(RRCounters) * (size_t)ngroups * kMaxPools, s));
+        B.rerun = d_list;
+        B.rerun_count = &d_ctrl->rerun_count;
         HYP_CUDA(cudaEventRecord(ev0, s));
         { k_rr_batch<<<blocks, kThreads, smem, s>>>(B); count_launch(); }
         HYP_CUDA(cudaGetLastError());
         HYP_CUDA(cudaEventRecord(ev1, s));
-        HYP_CUDA(cudaMemcpyAsync(&used, &d_ctrl->arena_used, sizeof(used), cudaMemcpyDeviceToHost, s));
-        if ((st = check_device_status(g0, "RR generation (batch)"))) return st;  // synchronises s
-        float ms = 0.f;
+        if ((st = check_device_status(g0, "RR generation (batch, arena repair)"))) return st;
         HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
         seconds += 1e-3 * (double)ms;
-        if (used <= arena.cap) break;
-        want = used + used / 8 + 4096;
     }
-    if (used > arena.cap) return set_error(HYPERIM_EOVERFLOW, "RR arena kept overflowing");
     if (seconds_out) *seconds_out = seconds;
     std::vector<RRCounters> c((size_t)ngroups * kMaxPools);
     HYP_CUDA(cudaMemcpyAsync(c.data(), d_counters, sizeof(RRCounters) * c.size(), cudaMemcpyDeviceToHost, s));

@@ -162,3 +162,21 @@ def test_batch_edge_cases(H):
     share.close()
     for g in (g0, gt, ge, g1):
         g.close()
+
+
+def test_batch_arena_repair_equals_the_oracle(H, oracle):
+    # an output arena of one entry per set: every round's batched launch is repaired
+    n, hes = gc.random_graph(6, 3000, 2500, 6)
+    off, mem = gc.csr(hes)
+    g = H.Graph(n, off, mem, "wc", 0, seed=17)
+    g.set_tuning(arena_entries_per_set=1)
+    og = oracle.Graph(n, off, mem, "wc", 0)
+    r1, r2 = g.pool(tag=0, roots="stratified"), g.pool(tag=1, roots="stratified")
+    queries = [(g, r1, r2, k, 0.2, 1.0) for k in (5, 10, 20)]
+    out = H.hyperim_select_seeds_batch(queries)
+    for (_, _, _, k, eps, ell), (seeds, res) in zip(queries, out):
+        oseeds, ores = oracle.brr(og, 17, k, eps, ell, 0, "stratified")
+        _same(res, ores, seeds, oseeds.tolist())
+    r1.close()
+    r2.close()
+    g.close()

@@ -49,6 +49,31 @@ def test_tunings_give_the_oracle_sets(H, oracle, name, make, thr, roots, theta, 
     g.close()
 
 
+@pytest.mark.parametrize("name,make,thr,roots,theta", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("warp,arena,schedule", [(0, 1, "persistent"), (64, 3, "persistent"), (0, 2, "plain")])
+def test_arena_repair_gives_the_oracle_sets(H, oracle, name, make, thr, roots, theta, warp, arena, schedule):
+    # an output arena of 1-3 entries per set: nearly every set is built a second time by the
+    # repair launch and written to the slot the first launch reserved; sets and work counters
+    # (counted once) must still be the oracle's
+    n, hes = make()
+    off, mem = gc.csr(hes)
+    g = H.Graph(n, off, mem, "uniform_pair", thr, seed=9)
+    g.set_tuning(warp_set_limit=warp, arena_entries_per_set=arena)
+    g.set_schedule(schedule)
+    assert g.tuning()["arena_entries_per_set"] == arena
+    og = oracle.Graph(n, off, mem, "uniform_pair", thr)
+    op = oracle.Pool(og, seed=9, tag=0, roots=roots)
+    op.grow_theta(theta // 2)
+    op.grow_theta(theta)
+    p = g.pool(tag=0, roots=roots).sample(theta // 2).sample(theta)
+    gc.assert_same_pool(p, op)
+    gc.assert_same_counters(p, op)
+    if schedule == "persistent":
+        assert p.view()["rr_launches"] > 2  # two growths, at least one of them repaired
+    p.close()
+    g.close()
+
+
 def test_autotune_choice_and_cache(H):
     n, hes = gc.hub_graph(seed=6)
     off, mem = gc.csr(hes)
