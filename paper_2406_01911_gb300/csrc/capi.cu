@@ -381,6 +381,8 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->early_sets_per_block = r->early_sets_per_block;
     h->arena_entries_per_set = r->arena_entries_per_set;
     h->set_size_hint = r->set_size_hint;
+    h->set_cycles_mean = r->set_cycles_mean;
+    h->set_cycles_max = r->set_cycles_max;
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -668,21 +670,39 @@ static hyperim_status pool_create(hyperim_graph* g, uint32_t tag, int32_t root_m
     return HYPERIM_OK;
 }
 
-// R1 and R2 of a BRR round grow by the same allocation: one launch generates both
-static hyperim_status pool_grow_pair(hyperim_graph* g, hyperim_pool* r1, hyperim_pool* r2, uint64_t theta) {
+// R1 and R2 of a BRR round grow by the same allocation: one launch generates both.
+// theta_last > theta: the growth may go ahead to a later round's theta (doubling, at most
+// theta_last) while the new sets' work per block would stay below the longest set of the
+// handle's last launch -- such a launch lasts about as long as that set whatever it holds, so
+// the later rounds' sets come at little cost, and a query that stops first wastes at most about
+// one such tail. Rounds read only their own prefix views, so results never change.
+static hyperim_status pool_grow_pair(hyperim_graph* g, hyperim_pool* r1, hyperim_pool* r2, uint64_t theta,
+                                     uint64_t theta_last = 0) {
     uint64_t ns[2][HYPERIM_NSTRATA];
     hyperim_pool* pools[2] = {r1, r2};
     // growth is exclusive; the two locks are taken in address order
     std::unique_lock<std::shared_mutex> la(r1 < r2 ? r1->mu : r2->mu), lb(r1 < r2 ? r2->mu : r1->mu);
-    bool need = false;
-    for (int q = 0; q < 2; ++q) {
-        allocate_strata(g, pools[q]->root_mode, theta, ns[q]);
-        for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
-            need = need || ns[q][s] > pools[q]->n_s[s];
-            ns[q][s] = std::max(ns[q][s], pools[q]->n_s[s]);
+    auto new_sets = [&](uint64_t t) {
+        uint64_t add = 0;
+        for (int q = 0; q < 2; ++q) {
+            allocate_strata(g, pools[q]->root_mode, t, ns[q]);
+            for (int s = 0; s < HYPERIM_NSTRATA; ++s)
+                add += ns[q][s] > pools[q]->n_s[s] ? ns[q][s] - pools[q]->n_s[s] : 0;
         }
+        return add;
+    };
+    uint64_t add = new_sets(theta);
+    if (add == 0) return HYPERIM_OK;  // an earlier query grew both pools past theta
+    if (theta_last > theta && g->schedule == HYPERIM_SCHED_PERSISTENT && g->set_cycles_mean > 0.0) {
+        const double blocks = (double)std::max(g->sm_count, 1);  // one RR block per SM
+        while (theta < theta_last && (double)add * g->set_cycles_mean / blocks < g->set_cycles_max) {
+            theta = std::min(theta_last, theta * 2);
+            add = new_sets(theta);
+        }
+        new_sets(theta);
     }
-    if (!need) return HYPERIM_OK;  // an earlier query grew both pools past theta
+    for (int q = 0; q < 2; ++q)
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) ns[q][s] = std::max(ns[q][s], pools[q]->n_s[s]);
     return sample_rr_multi(g, pools, 2, ns);
 }
 
@@ -843,6 +863,9 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
     uint64_t theta_early = (uint64_t)std::max(g->early_sets_per_block, 1) * (uint64_t)std::max(g->sm_count, 1);
     if (plan.i_max < 40) theta_early = std::min<uint64_t>(theta_early, plan.theta0 << plan.i_max);
     if (opts->theta_cap) theta_early = std::min<uint64_t>(theta_early, opts->theta_cap);
+    // the largest theta a round of this query can ask for (growth never goes past it)
+    uint64_t theta_last = plan.i_max < 62 ? plan.theta0 << plan.i_max : (uint64_t)1 << 62;
+    if (opts->theta_cap) theta_last = std::min<uint64_t>(theta_last, opts->theta_cap);
     for (int32_t i = 0;; ++i) {
         if (i > 62) return set_error(HYPERIM_EOVERFLOW, "theta doubling overflow");
         const uint64_t theta = plan.theta0 << i;
@@ -854,7 +877,7 @@ hyperim_status hyperim_select_seeds(hyperim_graph_t g, hyperim_pool_t r1, hyperi
         allocate_strata(g, r1->root_mode, theta, v1);
         allocate_strata(g, r2->root_mode, theta, v2);
         auto t0 = clk::now();
-        if ((st = pool_grow_pair(g, r1, r2, std::max(theta, theta_early)))) return st;
+        if ((st = pool_grow_pair(g, r1, r2, std::max(theta, theta_early), theta_last))) return st;
         auto t1 = clk::now();
         {
             std::shared_lock<std::shared_mutex> lk(r1->mu);

@@ -158,7 +158,7 @@ __global__ void k_idx_word(const int32_t* __restrict__ list, int32_t nlist, cons
 // each distinct neighbour (multiplicity w -> layer by search in the descending w list) adds one
 // to its (layer, chunk) count, kept on chip when the l x 2^c table fits, else in the table
 // itself. Every layer row then becomes an exclusive prefix along the chunks, one warp per row.
-constexpr int kFillThreads = 256;
+constexpr int kFillThreads = 512;  // two blocks (32 warps) per SM: the sorts are latency-bound
 constexpr int kFillBuf = 8192;  // members sorted on chip at once (power of two)
 constexpr int kFillCnt = 8192;  // (layer, chunk) counts kept on chip
 constexpr int kFillBkt = kBins;
@@ -180,7 +180,7 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
     int* bkt = reinterpret_cast<int*>(lw + kIdxMaxL);                   // kFillBkt (on-chip sorts)
     int* bucket_end = bkt + kFillBkt;                                   // kFillBkt (top-bit buckets)
     int* pre = bucket_end + kFillBkt;                                   // 2 kFillThreads + 1
-    int* ctrl = pre + 2 * kFillThreads + 1;                             // kFillCtrl
+    int* ctrl = pre + 2 * kFillThreads + 1;  // kFillCtrl: [0] ticket, [8, 8 + warps) maxima, [32, 48) sort scratch
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kFillThreads / 32;
     uint32_t* big = scratch + (int64_t)blockIdx.x * scratch_cap;
@@ -216,7 +216,7 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
         };
         if (T <= kFillBuf) {
             const int got = sorted_nbhd<kFillThreads>(v_span, he_mem, mu, vi.z, vi.w, T, id_bits, buf, bkt, 12,
-                                                      pre, ctrl + 16);
+                                                      pre, ctrl + 32);
             walk_runs<kFillThreads>(buf, got, count_run);
         } else {
             if ((int64_t)T > scratch_cap) {
@@ -254,7 +254,7 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
             for (int q = 0; q < nb; ++q) {
                 const int end = bucket_end[q];
                 if (end > begin) {
-                    sort_chunk<kFillThreads>(big + begin, end - begin, bshift, buf, bkt, 12, ctrl + 16);
+                    sort_chunk<kFillThreads>(big + begin, end - begin, bshift, buf, bkt, 12, ctrl + 32);
                     walk_runs<kFillThreads>(buf, end - begin, count_run);
                     __syncthreads();
                 }

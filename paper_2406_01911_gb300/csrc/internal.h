@@ -152,6 +152,8 @@ struct hyperim_graph {
     int32_t early_sets_per_block = 4;  // BRR's first launch: sets per resident block and pool
     double set_size_hint = 0.0;  // mean RR-set size of this handle's last growth (0: none yet)
     int32_t arena_entries_per_set = 0;  // tuning: initial output arena per new set (0: automatic)
+    // per-set SM cycles of this handle's last persistent RR launch (mean, maximum; 0: none yet)
+    double set_cycles_mean = 0.0, set_cycles_max = 0.0;
     // caller's device allocator (hyperim_load_args); null: stream-ordered cudaMallocAsync
     void* (*alloc_fn)(size_t, void*, void*) = nullptr;
     void (*free_fn)(void*, void*, void*) = nullptr;

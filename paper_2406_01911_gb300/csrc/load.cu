@@ -16,7 +16,7 @@
 namespace hyperim {
 namespace {
 
-constexpr int kProfThreads = 256;
+constexpr int kProfThreads = 512;  // two blocks (32 warps) per SM: the sorts are latency-bound
 constexpr int kProfBuf = 8192;  // on-chip keys of the profile kernel (power of two)
 constexpr int kProfHist = 4096; // on-chip multiplicity histogram bins
 constexpr int kBucketsMax = 4096;
@@ -295,7 +295,8 @@ k_profile(Incidence I, const int2* __restrict__ v_span, const int32_t* __restric
     int* bucket_cnt = (int*)(hist_s + kProfHist);          // kBucketsMax (first-level chunks)
     int* bkt = bucket_cnt + kBucketsMax;                   // kBucketsMax (on-chip sort)
     int* pre = bkt + kBucketsMax;                          // 2 kProfThreads + 1
-    int* ctrl = pre + 2 * kProfThreads + 1;                // small control block
+    int* ctrl = pre + 2 * kProfThreads + 1;                // control block: [0] ticket, [8, 8 + warps)
+                                                           // per-warp maxima, [32, 32 + warps) sort scratch
     using Gr = Group<kProfThreads>;
     uint32_t* big = S.big + (int64_t)blockIdx.x * S.big_cap;
     uint32_t* hist_g = S.hist + (int64_t)blockIdx.x * S.hist_cap;
@@ -323,7 +324,7 @@ k_profile(Incidence I, const int2* __restrict__ v_span, const int32_t* __restric
         const int T = tsum[mu] - dh;  // members other than mu
         if (T <= kProfBuf) {
             const int got = sorted_nbhd<kProfThreads>(v_span, I.he_mem, mu, e0, dh, T, id_bits, buf, bkt, 12,
-                                                      pre, ctrl + 16);
+                                                      pre, ctrl + 32);
             walk_runs<kProfThreads>(buf, got, count_runs);
         } else {
             // bucket the members by their top id bits so each bucket fits on chip
@@ -386,7 +387,7 @@ k_profile(Incidence I, const int2* __restrict__ v_span, const int32_t* __restric
                 const int end = bucket_cnt[q];
                 const int cnt = end - begin;
                 if (cnt > 0) {
-                    sort_chunk<kProfThreads>(big + begin, cnt, shift, buf, bkt, 12, ctrl + 16);
+                    sort_chunk<kProfThreads>(big + begin, cnt, shift, buf, bkt, 12, ctrl + 32);
                     walk_runs<kProfThreads>(buf, cnt, count_runs);
                     __syncthreads();
                 }
@@ -703,7 +704,7 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     { k_profile_warp<kProfWarpT, kPWWarps><<<grid_for((int64_t)n * 32, kPWThreads, sm), kPWThreads, 0, s>>>(
         n, nullptr, g->v_off, g->v_span, g->he_mem, g->tsum, g->id_bits, d_pairs, d_nl, d_deg, d_max); count_launch(); }
     const size_t prof_smem = sizeof(uint32_t) * (kProfBuf + kProfHist) +
-                             sizeof(int) * (2 * kBucketsMax + 2 * kProfThreads + 1 + 32);
+                             sizeof(int) * (2 * kBucketsMax + 2 * kProfThreads + 1 + 64);
     HYP_CUDA(cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)prof_smem));
     int per_sm = 0;

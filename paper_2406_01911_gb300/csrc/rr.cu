@@ -105,6 +105,7 @@ struct RRParams {
     DevStatus* st;
     RRCounters* counters;                    // kMaxPools entries
     int spin_limit;                          // rounds of a bounded wait before it gives up
+    unsigned long long* set_cycles;          // optional {sum, max, count} of per-set SM cycles
 };
 
 struct Need {                    // a layer with h > 0 at the current pop
@@ -133,6 +134,8 @@ struct Shared {
     unsigned long long stat[kMaxPools][kNStat];  // per pool work counters of this block
     unsigned long long wstat[kWarps][kNStat];    // per-warp counters of the current RR set (lane 0)
     unsigned long long out_pos;
+    unsigned long long cyc_sum, cyc_max, cyc_count;  // per-set SM cycles of this block's sets
+    long long cyc_start;                              // clock of the current set's start
     int32_t deferred[kDCap];
     Need wneed[kWarps][kLQ];
     int wcursor[kWarps];
@@ -1576,6 +1579,7 @@ __device__ __forceinline__ void run_job(const RRParams& P, Shared& S, uint32_t* 
     const int pi = J.pi;
     const uint32_t j = J.j, ybase = J.ybase;
     if (threadIdx.x == 0) {
+        S.cyc_start = clock64();
         const int32_t root = draw_root(P, J);
         list[0] = root;
         vis[root >> 5] |= 1u << (root & 31);
@@ -1639,6 +1643,13 @@ __device__ __forceinline__ void run_job(const RRParams& P, Shared& S, uint32_t* 
     const int size = S.ctrl[C_TAIL];
     write_set(P, S, vis, list, size, job);
     for (int i = threadIdx.x; i < size; i += kThreads) list[i] = -1;  // queue slots empty again
+    if (!kFlushPerSet && threadIdx.x == 0) {
+        // the set's duration on this SM (its launch's scheduling uses the mean and the maximum)
+        const unsigned long long d = (unsigned long long)(clock64() - S.cyc_start);
+        S.cyc_sum += d;
+        S.cyc_max = d > S.cyc_max ? d : S.cyc_max;
+        S.cyc_count += 1;
+    }
     __syncthreads();
 }
 
@@ -1653,6 +1664,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     const int64_t njobs = P.block_phase ? (int64_t)*(volatile int*)P.esc_count : P.pool_start[P.npools];
     if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x == 0) S.cyc_sum = S.cyc_max = S.cyc_count = 0;
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
     int64_t plain_ticket = P.plain_base + blockIdx.x;  // the plain schedule's one job
@@ -1681,6 +1693,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
         const unsigned long long* st = S.stat[threadIdx.x];
         for (int i = 0; i < kNStat; ++i)
             if (st[i]) atomicAdd(&c->pops + i, st[i]);
+    }
+    if (threadIdx.x == 0 && P.set_cycles && !P.rewrite && S.cyc_count) {
+        atomicAdd(P.set_cycles, S.cyc_sum);
+        atomicMax(P.set_cycles + 1, S.cyc_max);
+        atomicAdd(P.set_cycles + 2, S.cyc_count);
     }
 }
 
@@ -2039,6 +2056,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         int esc_count;
         int pad;
         unsigned long long arena_used;
+        unsigned long long set_cycles[3];  // sum, max, count over the sets the block kernel built
     };
     int64_t* d_pos = nullptr;
     int32_t* d_size = nullptr;
@@ -2083,7 +2101,9 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.st = g->d_status;
     P.counters = g->d_counters;
     P.spin_limit = wait_rounds(g);
+    P.set_cycles = d_ctrl->set_cycles;
     unsigned long long used = 0;
+    unsigned long long cycles[3] = {0, 0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct Events {
         cudaEvent_t* a;
@@ -2135,6 +2155,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     HYP_CUDA(cudaGetLastError());
     HYP_CUDA(cudaEventRecord(ev1, s));
     HYP_CUDA(cudaMemcpyAsync(&used, d_used, sizeof(used), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaMemcpyAsync(cycles, d_ctrl->set_cycles, sizeof(cycles), cudaMemcpyDeviceToHost, s));
     auto failed = [&](hyperim_status code) {
         // a failed launch may leave queue slots filled: empty them for the next one
         cudaMemsetAsync(g->scratch.list, 0xFF, sizeof(int32_t) * g->scratch.list_cap * g->scratch.blocks, s);
@@ -2144,6 +2165,10 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     float ms = 0.f;
     HYP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
     seconds += 1e-3 * (double)ms;
+    if (cycles[2] > 0 && !P.plain) {
+        g->set_cycles_mean = (double)cycles[0] / (double)cycles[2];
+        g->set_cycles_max = (double)cycles[1];
+    }
     if (used > g->scratch.arena_cap) {
         // The arena (sized from the pools' mean set size so far) was too small: every set has its
         // slot reserved in [0, used), and the sets that fit are written. The arena grows (its
