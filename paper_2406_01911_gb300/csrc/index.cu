@@ -72,7 +72,8 @@ __device__ void warp0_exclusive_scan(int* a, int count) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_idx_plan(const int32_t* __restrict__ list, int32_t nlist, const int4* __restrict__ vinfo,
+k_idx_plan(const int32_t* __restrict__ list, int32_t nlist, const int32_t* __restrict__ order,
+           int* __restrict__ next, const int4* __restrict__ vinfo,
            const int2* __restrict__ v_span, const int32_t* __restrict__ he_mem,
            const int32_t* __restrict__ tsum, const uint4* __restrict__ prof, int id_bits,
            uint8_t* __restrict__ bits_out, uint32_t* __restrict__ entries) {
@@ -80,10 +81,17 @@ k_idx_plan(const int32_t* __restrict__ list, int32_t nlist, const int4* __restri
     __shared__ int hist_b[kBins / 2];
     __shared__ int pre[2 * kThreads + 1];
     __shared__ int wmax[kThreads / 32];
-    __shared__ int target_s;
+    __shared__ int target_s, ticket_s;
     const int hb = id_bits < kIdxMaxBits ? id_bits : kIdxMaxBits;
     const int shift = id_bits - hb;
-    for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
+    for (;;) {
+        // candidates largest first, from a counter
+        if (threadIdx.x == 0) ticket_s = atomicAdd(next, 1);
+        __syncthreads();
+        const int ticket = ticket_s;
+        __syncthreads();
+        if (ticket >= nlist) break;
+        const int i = order[ticket];
         const int32_t mu = list[i];
         const int4 vi = vinfo[mu];
         if (threadIdx.x == 0) {
@@ -172,7 +180,8 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
            const int4* __restrict__ vinfo, const int2* __restrict__ v_span,
            const int32_t* __restrict__ he_mem, const int32_t* __restrict__ tsum,
            const uint4* __restrict__ prof, int id_bits, uint32_t* __restrict__ tab,
-           uint32_t* __restrict__ scratch, int64_t scratch_cap, int* __restrict__ next, DevStatus* st) {
+           uint32_t* __restrict__ scratch, int64_t scratch_cap, const int32_t* __restrict__ order,
+           int* __restrict__ next, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char fill_smem[];
     uint32_t* buf = reinterpret_cast<uint32_t*>(fill_smem);             // kFillBuf
     uint32_t* cnt_s = buf + kFillBuf;                                   // kFillCnt
@@ -187,9 +196,10 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
     for (;;) {
         if (threadIdx.x == 0) ctrl[0] = atomicAdd(next, 1);
         __syncthreads();
-        const int i = ctrl[0];
+        const int ticket = ctrl[0];
         __syncthreads();
-        if (i >= nlist) break;
+        if (ticket >= nlist) break;
+        const int i = order[ticket];  // largest first
         if (entries[i] == 0) continue;
         const int32_t mu = list[i];
         const int4 vi = vinfo[mu];
@@ -325,9 +335,16 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
     if ((st = tmp.alloc(&d_off, sizeof(int64_t) * ((size_t)ncand + 1)))) return st;
     { k_idx_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_flag, d_pos, d_list); count_launch(); }
     const int nl = (int)ncand;
+    // the candidates' indices, largest neighbourhood first (both passes take them in this order)
+    int32_t* d_order = nullptr;
+    int* d_next = nullptr;
+    if ((st = tmp.alloc(&d_order, sizeof(int32_t) * (size_t)ncand))) return st;
+    if ((st = tmp.alloc(&d_next, sizeof(int)))) return st;
+    if ((st = size_order(g, d_list, ncand, true, d_order))) return st;
+    HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
     const int pblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * 4);
-    { k_idx_plan<<<pblocks, kThreads, 0, s>>>(d_list, nl, g->vinfo, g->v_span, g->he_mem, g->tsum, g->prof,
-                                              g->id_bits, d_bits, d_entries); count_launch(); }
+    { k_idx_plan<<<pblocks, kThreads, 0, s>>>(d_list, nl, d_order, d_next, g->vinfo, g->v_span, g->he_mem, g->tsum,
+                                              g->prof, g->id_bits, d_bits, d_entries); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_entries, d_off, ncand))) return st;
     int64_t total = 0;
     HYP_CUDA(cudaMemcpyAsync(&total, d_off + ncand, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -347,13 +364,11 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         // keep the scratch area within 1 GiB
         while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)1 << 30)) fblocks -= sm;
         uint32_t* d_scratch = nullptr;
-        int* d_next = nullptr;
         if ((st = tmp.alloc(&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
-        if ((st = tmp.alloc(&d_next, sizeof(int)))) return st;
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
         { k_idx_fill<<<fblocks, kFillThreads, kFillSmem, s>>>(d_list, nl, d_bits, d_entries, d_off, g->vinfo, g->v_span,
                                                   g->he_mem, g->tsum, g->prof, g->id_bits, g->idx_tab, d_scratch,
-                                                  cap, d_next, g->d_status); count_launch(); }
+                                                  cap, d_order, d_next, g->d_status); count_launch(); }
         if ((st = check_device_status(g, "chunk index"))) return st;
         // indexed vertices
         std::vector<uint32_t> e((size_t)ncand);

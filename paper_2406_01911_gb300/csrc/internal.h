@@ -241,6 +241,10 @@ hyperim_status check_device_status(hyperim_graph* g, const char* where);
 hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off, const int32_t* he_mem,
                            int32_t nnz_in, bool on_device);
 
+// load.cu: the listed vertices by descending neighbourhood size (quarter-octave buckets of tsum):
+// out[j] = list[i] (or i, emit_index) for the j-th largest; order within a bucket unspecified
+hyperim_status size_order(hyperim_graph* g, const int32_t* list, int64_t count, bool emit_index, int32_t* out);
+
 // index.cu: chunk index of the vertices with large neighbourhoods (after the layer profile)
 hyperim_status build_chunk_index(hyperim_graph* g);
 

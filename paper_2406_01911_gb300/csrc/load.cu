@@ -264,6 +264,49 @@ k_profile_warp(int32_t n, const int32_t* __restrict__ list, const int32_t* __res
     }
 }
 
+// ---- largest first: an order of listed vertices by descending neighbourhood size ----------
+// The block-per-vertex kernels take their vertices from a counter; a hub taken last would leave
+// one block running while the rest of the grid idles. Listing vertices in descending size (by
+// buckets of a quarter octave: exact order within a bucket does not matter) lets the largest start
+// first. Each vertex's output does not depend on the order in which vertices are processed.
+constexpr int kSizeBuckets = 128;
+
+__device__ __forceinline__ int size_bucket(int32_t t) {
+    if (t < 4) return 0;
+    const int lg = 31 - __clz(t);
+    return min(kSizeBuckets - 1, 4 * lg + (int)(((uint32_t)t >> (lg - 2)) & 3u));
+}
+
+__global__ void k_size_hist(const int32_t* __restrict__ list, int64_t count, const int32_t* __restrict__ tsum,
+                            unsigned int* __restrict__ hist) {
+    __shared__ unsigned int h[kSizeBuckets];
+    for (int i = threadIdx.x; i < kSizeBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[size_bucket(tsum[list[i]])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSizeBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// one thread: bucket starts in descending bucket order
+__global__ void k_size_starts(unsigned int* __restrict__ hist) {
+    unsigned int run = 0;
+    for (int b = kSizeBuckets - 1; b >= 0; --b) {
+        const unsigned int c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+}
+
+__global__ void k_size_scatter(const int32_t* __restrict__ list, int64_t count, const int32_t* __restrict__ tsum,
+                               unsigned int* __restrict__ start, int emit_index, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = list[i];
+        out[atomicAdd(&start[size_bucket(tsum[v])], 1u)] = emit_index ? (int32_t)i : v;
+    }
+}
+
 // Vertices with d_H >= 2 and lo < positions <= hi (the mid-size warp kernel's, then the block
 // kernel's with hi = INT_MAX).
 __global__ void k_big_flags(int32_t n, const int32_t* __restrict__ v_off, const int32_t* __restrict__ tsum,
@@ -608,6 +651,22 @@ int grid_for(int64_t items, int threads, int sm) {
 
 }  // namespace
 
+hyperim_status size_order(hyperim_graph* g, const int32_t* list, int64_t count, bool emit_index, int32_t* out) {
+    if (count <= 0) return HYPERIM_OK;
+    cudaStream_t s = g->stream;
+    hyperim_status st;
+    CallBuffers tmp(g);
+    unsigned int* hist = nullptr;
+    if ((st = tmp.alloc(&hist, sizeof(unsigned int) * kSizeBuckets))) return st;
+    HYP_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kSizeBuckets, s));
+    const int grid = grid_for(count, 256, g->sm_count);
+    { k_size_hist<<<grid, 256, 0, s>>>(list, count, g->tsum, hist); count_launch(); }
+    { k_size_starts<<<1, 1, 0, s>>>(hist); count_launch(); }
+    { k_size_scatter<<<grid, 256, 0, s>>>(list, count, g->tsum, hist, emit_index ? 1 : 0, out); count_launch(); }
+    HYP_CUDA(cudaGetLastError());
+    return HYPERIM_OK;
+}
+
 hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int32_t* he_mem_in,
                            int32_t nnz_in, bool on_device) {
     cudaStream_t s = g->stream;
@@ -750,8 +809,11 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     if ((st = tmp.alloc(&d_blist, sizeof(int32_t) * (size_t)(nbig > 0 ? nbig : 1)))) return st;
     if (nbig > 0) {
         { k_big_list<<<grid_for(n, 256, sm), 256, 0, s>>>(n, d_bflag, d_bpos, d_blist); count_launch(); }
+        // largest first (into the flag array, no longer needed: n >= nbig words)
+        int32_t* d_border = reinterpret_cast<int32_t*>(d_bflag);
+        if ((st = size_order(g, d_blist, nbig, false, d_border))) return st;
         { k_profile<<<(int)std::min<int64_t>(pblocks, nbig), kProfThreads, prof_smem, s>>>(
-            I, g->v_span, d_blist, (int32_t)nbig, g->id_bits, g->tsum, d_pairs, d_nl, d_deg, d_next, PS,
+            I, g->v_span, d_border, (int32_t)nbig, g->id_bits, g->tsum, d_pairs, d_nl, d_deg, d_next, PS,
             g->d_status, d_max); count_launch(); }
     }
     if ((st = check_device_status(g, "layer profile"))) return st;
