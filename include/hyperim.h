@@ -236,8 +236,11 @@ hyperim_status hyperim_graph_get_tuning(hyperim_graph_t g, hyperim_tuning* out);
  *   candidate -- warp_set_limit in {0 (no warp phase), 16, 32, 64, 128} -- grows a scratch
  *   pool (tag 255) to `sets` RR sets (0: 8 per SM), the same sets each time since they are keyed
  *   by (stratum, index), and the candidate with the least RR-kernel time (CUDA events, best of
- *   two) is applied to g and cached under the key. early_sets_per_block is left as it is. The
- *   RR sets, seeds and estimates never depend on the choice. EINVAL: g or out NULL, bad mode or
+ *   two) is applied to g and cached under the key, with the per-set SM cycles (mean, maximum)
+ *   the candidate without warp phase measured; a graph that takes a cached choice and has no
+ *   launch of its own yet starts with those cycles (used by BRR's growing ahead, see
+ *   hyperim_select_seeds). early_sets_per_block is left as it is. The RR sets, seeds and
+ *   estimates never depend on the choice. EINVAL: g or out NULL, bad mode or
  *   strategy. Synchronises the stream.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -419,6 +422,13 @@ hyperim_status hyperim_pool_copy(hyperim_pool_t p, int64_t* rr_off, int32_t* rr_
  *          p_max = 1); lower bound ((sqrt(Lambda_R2 + 2 ln(1/delta)/9) - sqrt(ln(1/delta)/2))^2 -
  *          ln(1/delta)/18) n/|R2| (Sec. 4.2); stop once lower/upper >= 1 - 1/e - eps or after
  *          i_max doublings. theta_cap > 0 bounds theta_i (EOVERFLOW beyond it).
+ *          Round i reads only the sets (s, j) with j < n_s(theta_i) of each pool, so the pools
+ *          may be grown further than a round needs without changing any result: the first
+ *          growth reaches at least early_sets_per_block sets per resident RR block, and in the
+ *          persistent schedule a growth goes on to later rounds' theta (doubling, at most
+ *          theta0 2^i_max and the cap) while its new sets' work per block stays below the
+ *          longest set of the handle's last RR launch (per-set SM cycles recorded by the RR
+ *          kernel, or those of the autotuner's cache entry for the graph's profile).
  *          upper_mode HYPERIM_UPPER_PREFIX replaces the closed form (the one Alg. 4 uses) by
  *          the bound it closes, Eq. upper_2 with p_max = 1: the minimum over the greedy's
  *          prefixes S_i (0 <= i <= k) of the weighted coverage of S_i plus the k largest

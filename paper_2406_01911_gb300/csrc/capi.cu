@@ -534,8 +534,14 @@ std::mutex& tune_mutex() {
     return m;
 }
 
-std::map<uint64_t, hyperim_tuning>& tune_cache() {
-    static std::map<uint64_t, hyperim_tuning> c;
+// a cached choice, with the per-set SM cycles (mean, maximum) its candidate measured: a graph of
+// the same profile starts with them, so BRR can grow ahead from its first launch
+struct TuneEntry {
+    hyperim_tuning t;
+    double cycles_mean, cycles_max;
+};
+std::map<uint64_t, TuneEntry>& tune_cache() {
+    static std::map<uint64_t, TuneEntry> c;
     return c;
 }
 }  // namespace
@@ -553,10 +559,14 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
         std::lock_guard<std::mutex> lk(tune_mutex());
         auto it = tune_cache().find(key);
         if (it != tune_cache().end()) {
-            hyperim_tuning t = it->second;
+            hyperim_tuning t = it->second.t;
             t.early_sets_per_block = g->early_sets_per_block;
             t.arena_entries_per_set = g->arena_entries_per_set;
             g->warp_set_limit = t.warp_set_limit;
+            if (g->set_cycles_mean <= 0.0) {
+                g->set_cycles_mean = it->second.cycles_mean;
+                g->set_cycles_max = it->second.cycles_max;
+            }
             out->chosen = t;
             out->from_cache = 1;
             return HYPERIM_OK;
@@ -566,14 +576,14 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
     const int32_t keep_w = g->warp_set_limit, keep_sched = g->schedule;
     g->schedule = HYPERIM_SCHED_PERSISTENT;
     const int32_t cand[5] = {0, 16, 32, 64, 128};  // warp-phase set limits (0: none)
-    double best = -1.0;
+    double best = -1.0, best_mean = 0.0, best_max = 0.0;
     hyperim_tuning choice{keep_w, g->early_sets_per_block, g->arena_entries_per_set};
     hyperim_status st = HYPERIM_OK;
     int c = 0;
     {
         for (int ci = 0; ci < 5 && st == HYPERIM_OK; ++ci) {
             g->warp_set_limit = cand[ci];
-            double secs = -1.0;
+            double secs = -1.0, c_mean = 0.0, c_max = 0.0;
             for (int rep = 0; rep < 2 && st == HYPERIM_OK; ++rep) {
                 hyperim_pool* p = nullptr;
                 if ((st = pool_create(g, 0xFF, root_mode, strategy, &p))) break;
@@ -583,7 +593,11 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
                 }
                 const double t = p->rr_kernel_seconds;
                 hyperim_pool_free(p);
-                if (st == HYPERIM_OK && (secs < 0.0 || t < secs)) secs = t;
+                if (st == HYPERIM_OK && (secs < 0.0 || t < secs)) {
+                    secs = t;
+                    c_mean = g->set_cycles_mean;  // the growth's per-set cycles (block kernel's sets)
+                    c_max = g->set_cycles_max;
+                }
             }
             if (st != HYPERIM_OK) break;
             out->warp_set_limit[c] = cand[ci];
@@ -592,6 +606,10 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
             if (best < 0.0 || secs < best) {
                 best = secs;
                 choice.warp_set_limit = cand[ci];
+            }
+            if (cand[ci] == 0) {  // every set on the block kernel: its cycles describe all of them
+                best_mean = c_mean;
+                best_max = c_max;
             }
         }
     }
@@ -602,9 +620,13 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
         return st;
     }
     g->warp_set_limit = choice.warp_set_limit;
+    if (best_mean > 0.0) {
+        g->set_cycles_mean = best_mean;
+        g->set_cycles_max = best_max;
+    }
     out->chosen = choice;
     std::lock_guard<std::mutex> lk(tune_mutex());
-    tune_cache()[key] = choice;
+    tune_cache()[key] = TuneEntry{choice, best_mean, best_max};
     return HYPERIM_OK;
 }
 

@@ -79,6 +79,39 @@ __device__ __forceinline__ bool better(unsigned long long s1, uint32_t i1, unsig
     return s1 > s2 || (s1 == s2 && i1 < i2);
 }
 
+// The best (score, id) among the unpicked vertices of [0, n) visited by one thread (first index
+// t, stride T): four consecutive vertices per step, their flags and scores loaded together
+// without depending on one another (vectorised: score and picked are 16- and 4-byte aligned).
+// `load` reads a score (plain, or through L2 where other threads of the block change scores by
+// atomics).
+template <bool kL2Scores = false>
+__device__ __forceinline__ void scan_unpicked(const unsigned long long* __restrict__ score,
+                                              const uint8_t* __restrict__ picked, int64_t n, int64_t t, int64_t T,
+                                              unsigned long long& bs, uint32_t& bi) {
+    const int64_t n4 = n >> 2;
+    for (int64_t q = t; q < n4; q += T) {
+        const uchar4 pk = reinterpret_cast<const uchar4*>(picked)[q];
+        ulonglong2 a, b;
+        if (kL2Scores) {
+            a = __ldcg(reinterpret_cast<const ulonglong2*>(score) + 2 * q);
+            b = __ldcg(reinterpret_cast<const ulonglong2*>(score) + 2 * q + 1);
+        } else {
+            a = reinterpret_cast<const ulonglong2*>(score)[2 * q];
+            b = reinterpret_cast<const ulonglong2*>(score)[2 * q + 1];
+        }
+        const uint32_t v = (uint32_t)(4 * q);
+        if (!pk.x && better(a.x, v, bs, bi)) { bs = a.x; bi = v; }
+        if (!pk.y && better(a.y, v + 1, bs, bi)) { bs = a.y; bi = v + 1; }
+        if (!pk.z && better(b.x, v + 2, bs, bi)) { bs = b.x; bi = v + 2; }
+        if (!pk.w && better(b.y, v + 3, bs, bi)) { bs = b.y; bi = v + 3; }
+    }
+    for (int64_t v = 4 * n4 + t; v < n; v += T) {
+        if (picked[v]) continue;
+        const unsigned long long sc = kL2Scores ? __ldcg(score + v) : score[v];
+        if (better(sc, (uint32_t)v, bs, bi)) { bs = sc; bi = (uint32_t)v; }
+    }
+}
+
 // argmax of score over unpicked vertices, lowest id on ties; the last block to finish reduces
 // the per-block winners, records the seed and marks it picked.
 // Eq. upper_2 state (see the top-k kernels below)
@@ -101,12 +134,8 @@ k_argmax(const unsigned long long* __restrict__ score, uint8_t* __restrict__ pic
     __shared__ bool last;
     unsigned long long bs = 0;
     uint32_t bi = 0xFFFFFFFFu;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        if (picked[v]) continue;
-        const unsigned long long s = score[v];
-        if (better(s, (uint32_t)v, bs, bi)) { bs = s; bi = (uint32_t)v; }
-    }
+    scan_unpicked(score, picked, n, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x, bs, bi);
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long os = __shfl_xor_sync(0xFFFFFFFFu, bs, o);
         const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
@@ -424,11 +453,7 @@ __global__ void __launch_bounds__(kGBThreads, 1) k_greedy_batch(GreedyBatchParam
         for (int round = 0; round < Q.k; ++round) {
             unsigned long long bs = 0;
             uint32_t bi = 0xFFFFFFFFu;
-            for (int64_t v = threadIdx.x; v < n; v += kGBThreads) {
-                if (picked[v]) continue;
-                const unsigned long long sc = __ldcg(score + v);
-                if (better(sc, (uint32_t)v, bs, bi)) { bs = sc; bi = (uint32_t)v; }
-            }
+            scan_unpicked<true>(score, picked, n, threadIdx.x, kGBThreads, bs, bi);
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long os = __shfl_xor_sync(0xFFFFFFFFu, bs, o);
                 const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
@@ -800,6 +825,7 @@ hyperim_status greedy_batch(hyperim_graph* g0, const GreedyBatchItem* items, int
         cov_cap = std::max<int64_t>(cov_cap, p1->count);
         kmax = std::max<int64_t>(kmax, it.k);
     }
+    n_cap = (n_cap + 3) & ~(int64_t)3;  // per-block score / flag arrays stay 16- and 4-byte aligned
     // one block per SM at most, and no more blocks than the scratch budget allows
     const size_t per_block = 8 * (size_t)n_cap + 4 * ((size_t)n_cap + 1) + (size_t)n_cap + 4 * (size_t)inv_cap +
                              4 * (size_t)cov_cap;
