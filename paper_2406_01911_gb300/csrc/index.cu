@@ -168,11 +168,13 @@ __global__ void k_idx_word(const int32_t* __restrict__ list, int32_t nlist, cons
 // itself. Every layer row then becomes an exclusive prefix along the chunks, one warp per row.
 constexpr int kFillThreads = 512;  // two blocks (32 warps) per SM: the sorts are latency-bound
 constexpr int kFillBuf = 8192;  // members sorted on chip at once (power of two)
-constexpr int kFillCnt = 8192;  // (layer, chunk) counts kept on chip
+constexpr int kFillCnt = 4096;  // (layer, chunk) counts kept on chip (more: in the table itself)
 constexpr int kFillBkt = kBins;
+constexpr int kFillTop = 1 << (kIdxMaxBits - 3);  // top-bit buckets: eight whole chunks each
+// the shared memory above fits three 512-thread blocks per SM
 constexpr int kFillCtrl = 64;
 constexpr size_t kFillSmem = sizeof(uint32_t) * (kFillBuf + kFillCnt + kIdxMaxL) +
-                             sizeof(int) * (2 * kFillBkt + 2 * kFillThreads + 1 + kFillCtrl);
+                             sizeof(int) * (kFillBkt + kFillTop + 2 * kFillThreads + 1 + kFillCtrl);
 
 __global__ void __launch_bounds__(kFillThreads)
 k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __restrict__ bits_in,
@@ -188,7 +190,7 @@ k_idx_fill(const int32_t* __restrict__ list, int32_t nlist, const uint8_t* __res
     uint32_t* lw = cnt_s + kFillCnt;                                    // kIdxMaxL
     int* bkt = reinterpret_cast<int*>(lw + kIdxMaxL);                   // kFillBkt (on-chip sorts)
     int* bucket_end = bkt + kFillBkt;                                   // kFillBkt (top-bit buckets)
-    int* pre = bucket_end + kFillBkt;                                   // 2 kFillThreads + 1
+    int* pre = bucket_end + kFillTop;                                   // 2 kFillThreads + 1
     int* ctrl = pre + 2 * kFillThreads + 1;  // kFillCtrl: [0] ticket, [8, 8 + warps) maxima, [32, 48) sort scratch
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kFillThreads / 32;
@@ -342,7 +344,7 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
     if ((st = tmp.alloc(&d_next, sizeof(int)))) return st;
     if ((st = size_order(g, d_list, ncand, true, d_order))) return st;
     HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
-    const int pblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * 4);
+    const int pblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * 8);  // 8 x 256 threads per SM
     { k_idx_plan<<<pblocks, kThreads, 0, s>>>(d_list, nl, d_order, d_next, g->vinfo, g->v_span, g->he_mem, g->tsum,
                                               g->prof, g->id_bits, d_bits, d_entries); count_launch(); }
     if ((st = exclusive_scan_u32_to_i64(g, d_entries, d_off, ncand))) return st;
@@ -361,8 +363,8 @@ hyperim_status build_chunk_index(hyperim_graph* g) {
         if (per_sm < 1) per_sm = 1;
         const int64_t cap = g->max_tsum;
         int fblocks = (int)std::min<int64_t>(ncand, (int64_t)sm * per_sm);
-        // keep the scratch area within 1 GiB
-        while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)1 << 30)) fblocks -= sm;
+        // keep the scratch area within 2 GiB
+        while (fblocks > sm && (int64_t)fblocks * cap * 4 > ((int64_t)2 << 30)) fblocks -= sm;
         uint32_t* d_scratch = nullptr;
         if ((st = tmp.alloc(&d_scratch, sizeof(uint32_t) * (size_t)cap * fblocks))) return st;
         HYP_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));

@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kProfThreads = 512;  // two blocks (32 warps) per SM: the sorts are latency-bound
 constexpr int kProfBuf = 8192;  // on-chip keys of the profile kernel (power of two)
-constexpr int kProfHist = 4096; // on-chip multiplicity histogram bins
+constexpr int kProfHist = 1024; // on-chip multiplicity histogram bins (d_H >= this: global)
 constexpr int kBucketsMax = 4096;
 constexpr int kProfWarpT = 1024;  // vertices with at most this many positions: warp profile
 constexpr int kPWWarps = 4;
@@ -770,9 +770,11 @@ hyperim_status build_graph(hyperim_graph* g, const int32_t* he_off_in, const int
     HYP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_profile, kProfThreads,
                                                            prof_smem));
     if (per_sm < 1) per_sm = 1;
-    const int pblocks = sm * per_sm;
     ProfScratch PS;
     PS.big_cap = g->max_tsum > kProfBuf ? g->max_tsum : 1;
+    int pblocks = sm * per_sm;
+    // keep the bucketing scratch area within 2 GiB
+    while (pblocks > sm && (int64_t)pblocks * PS.big_cap * 4 > ((int64_t)2 << 30)) pblocks -= sm;
     PS.hist_cap = g->max_dh >= kProfHist ? (int64_t)g->max_dh + 1 : 1;
     if ((st = tmp.alloc(&PS.big, sizeof(uint32_t) * (size_t)PS.big_cap * pblocks)))
         return st;
