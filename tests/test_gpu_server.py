@@ -97,6 +97,25 @@ def test_alone_and_in_the_mix(H, oracle):
         assert res["lambda_r2"].tolist() == ores["lambda_r2"].tolist()
 
 
+def test_served_graphs_alone_and_in_the_mix(H):
+    # the served configuration's two smallest resident graphs (~10^5 vertices, Zipf(2.0) sizes in
+    # [2, 500]) and the stream's first queries on them (k in [10, 200], eps in {0.05, 0.1, 0.2}),
+    # four workers sharing one pool pair per graph: each result equals the query run alone
+    from workloads import serving_queries, serving_workload
+    specs = serving_workload()
+    order = sorted(range(len(specs)), key=lambda i: specs[i].n)[:2]
+    graphs = [(specs[i], *make_hypergraph(specs[i])) for i in order]
+    picked = [q for q in serving_queries() if q.graph in order][:8]
+    assert len(picked) == 8
+    queries = [(order.index(q.graph), q.k, q.eps) for q in picked]
+    alone = [_alone(H, *graphs[gi], k, eps) for gi, k, eps in queries]
+    mixed, stats = _serve(H, graphs, queries, workers=4)
+    for (gi, k, eps), a, (seeds, res) in zip(queries, alone, mixed):
+        assert res["status"] == 0, (gi, k, eps, res.get("message"))
+        _same((seeds, res), a)
+    assert stats["completed"] == len(queries) and stats["failed"] == 0
+
+
 def test_budget_admission(H):
     graphs = _graphs()
     queries = QUERIES[:8]
