@@ -383,7 +383,6 @@ hyperim_status hyperim_graph_share(hyperim_graph_t g, void* cuda_stream, hyperim
     h->set_size_hint = r->set_size_hint;
     h->set_cycles_mean = r->set_cycles_mean;
     h->set_cycles_max = r->set_cycles_max;
-    for (int s = 0; s < HYPERIM_NSTRATA; ++s) h->stratum_cycles[s] = r->stratum_cycles[s];
     h->alloc_fn = r->alloc_fn;
     h->free_fn = r->free_fn;
     h->alloc_ctx = r->alloc_ctx;
@@ -540,7 +539,6 @@ std::mutex& tune_mutex() {
 struct TuneEntry {
     hyperim_tuning t;
     double cycles_mean, cycles_max;
-    double stratum_cycles[HYPERIM_NSTRATA];
 };
 std::map<uint64_t, TuneEntry>& tune_cache() {
     static std::map<uint64_t, TuneEntry> c;
@@ -568,7 +566,6 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
             if (g->set_cycles_mean <= 0.0) {
                 g->set_cycles_mean = it->second.cycles_mean;
                 g->set_cycles_max = it->second.cycles_max;
-                for (int x = 0; x < HYPERIM_NSTRATA; ++x) g->stratum_cycles[x] = it->second.stratum_cycles[x];
             }
             out->chosen = t;
             out->from_cache = 1;
@@ -580,14 +577,13 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
     g->schedule = HYPERIM_SCHED_PERSISTENT;
     const int32_t cand[5] = {0, 16, 32, 64, 128};  // warp-phase set limits (0: none)
     double best = -1.0, best_mean = 0.0, best_max = 0.0;
-    double best_strata[HYPERIM_NSTRATA] = {};
     hyperim_tuning choice{keep_w, g->early_sets_per_block, g->arena_entries_per_set};
     hyperim_status st = HYPERIM_OK;
     int c = 0;
     {
         for (int ci = 0; ci < 5 && st == HYPERIM_OK; ++ci) {
             g->warp_set_limit = cand[ci];
-            double secs = -1.0, c_mean = 0.0, c_max = 0.0, c_strata[HYPERIM_NSTRATA] = {};
+            double secs = -1.0, c_mean = 0.0, c_max = 0.0;
             for (int rep = 0; rep < 2 && st == HYPERIM_OK; ++rep) {
                 hyperim_pool* p = nullptr;
                 if ((st = pool_create(g, 0xFF, root_mode, strategy, &p))) break;
@@ -601,7 +597,6 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
                     secs = t;
                     c_mean = g->set_cycles_mean;  // the growth's per-set cycles (block kernel's sets)
                     c_max = g->set_cycles_max;
-                    for (int x = 0; x < HYPERIM_NSTRATA; ++x) c_strata[x] = g->stratum_cycles[x];
                 }
             }
             if (st != HYPERIM_OK) break;
@@ -615,7 +610,6 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
             if (cand[ci] == 0) {  // every set on the block kernel: its cycles describe all of them
                 best_mean = c_mean;
                 best_max = c_max;
-                for (int x = 0; x < HYPERIM_NSTRATA; ++x) best_strata[x] = c_strata[x];
             }
         }
     }
@@ -629,13 +623,10 @@ hyperim_status hyperim_graph_autotune(hyperim_graph_t g, int32_t root_mode, int3
     if (best_mean > 0.0) {
         g->set_cycles_mean = best_mean;
         g->set_cycles_max = best_max;
-        for (int x = 0; x < HYPERIM_NSTRATA; ++x) g->stratum_cycles[x] = best_strata[x];
     }
     out->chosen = choice;
     std::lock_guard<std::mutex> lk(tune_mutex());
-    TuneEntry e{choice, best_mean, best_max, {}};
-    for (int x = 0; x < HYPERIM_NSTRATA; ++x) e.stratum_cycles[x] = best_strata[x];
-    tune_cache()[key] = e;
+    tune_cache()[key] = TuneEntry{choice, best_mean, best_max};
     return HYPERIM_OK;
 }
 

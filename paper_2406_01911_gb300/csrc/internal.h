@@ -154,7 +154,6 @@ struct hyperim_graph {
     int32_t arena_entries_per_set = 0;  // tuning: initial output arena per new set (0: automatic)
     // per-set SM cycles of this handle's last persistent RR launch (mean, maximum; 0: none yet)
     double set_cycles_mean = 0.0, set_cycles_max = 0.0;
-    double stratum_cycles[HYPERIM_NSTRATA] = {};  // mean per-set SM cycles by root stratum (0: unknown)
     // caller's device allocator (hyperim_load_args); null: stream-ordered cudaMallocAsync
     void* (*alloc_fn)(size_t, void*, void*) = nullptr;
     void (*free_fn)(void*, void*, void*) = nullptr;

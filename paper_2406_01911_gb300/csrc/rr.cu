@@ -50,10 +50,9 @@ constexpr int kWHashBits = 8;
 constexpr int kWHash = 1 << kWHashBits;  // per-warp open-addressing member set
 
 struct RRJobMap {
-    int64_t job_base[HYPERIM_NSTRATA + 1];  // by position k: the jobs of stratum order[k]
-    uint32_t j_base[HYPERIM_NSTRATA];       // by stratum
+    int64_t job_base[HYPERIM_NSTRATA + 1];
+    uint32_t j_base[HYPERIM_NSTRATA];
     uint32_t j_step;   // the pool's shard stride: job x of stratum s is j = j_base[s] + x j_step
-    uint8_t order[HYPERIM_NSTRATA];         // position -> stratum (launches take the last jobs first)
 };
 
 struct RRParams {
@@ -136,8 +135,6 @@ struct Shared {
     unsigned long long wstat[kWarps][kNStat];    // per-warp counters of the current RR set (lane 0)
     unsigned long long out_pos;
     unsigned long long cyc_sum, cyc_max, cyc_count;  // per-set SM cycles of this block's sets
-    unsigned long long cyc_stratum[HYPERIM_NSTRATA]; // the same per stratum: sum
-    unsigned int cyc_stratum_n[HYPERIM_NSTRATA];     // and count
     long long cyc_start;                              // clock of the current set's start
     int32_t deferred[kDCap];
     Need wneed[kWarps][kLQ];
@@ -1378,10 +1375,9 @@ __device__ __forceinline__ Job decode_job(const RRParams& P, int64_t job) {
     while (J.pi + 1 < P.npools && job >= P.pool_start[J.pi + 1]) ++J.pi;
     const RRJobMap& jm = P.jm[J.pi];
     const int64_t local = job - P.pool_start[J.pi];
-    int k = 0;
-    while (k < HYPERIM_NSTRATA - 1 && local >= jm.job_base[k + 1]) ++k;
-    J.s = jm.order[k];
-    J.j = jm.j_base[J.s] + (uint32_t)(local - jm.job_base[k]) * jm.j_step;
+    J.s = 0;
+    while (J.s < HYPERIM_NSTRATA - 1 && local >= jm.job_base[J.s + 1]) ++J.s;
+    J.j = jm.j_base[J.s] + (uint32_t)(local - jm.job_base[J.s]) * jm.j_step;
     const uint32_t sfield = P.root_mode == HYPERIM_ROOTS_PLAIN ? 0xFFu : (uint32_t)J.s;
     J.ybase = stream_ybase(P.tags[J.pi], sfield);
     return J;
@@ -1653,8 +1649,6 @@ __device__ __forceinline__ void run_job(const RRParams& P, Shared& S, uint32_t* 
         S.cyc_sum += d;
         S.cyc_max = d > S.cyc_max ? d : S.cyc_max;
         S.cyc_count += 1;
-        S.cyc_stratum[J.s] += d;
-        S.cyc_stratum_n[J.s] += 1;
     }
     __syncthreads();
 }
@@ -1671,10 +1665,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
     if (threadIdx.x < kMaxPools * kNStat) (&S.stat[0][0])[threadIdx.x] = 0;
     if (threadIdx.x < kWarps * kNStat) (&S.wstat[0][0])[threadIdx.x] = 0;
     if (threadIdx.x == 0) S.cyc_sum = S.cyc_max = S.cyc_count = 0;
-    if (threadIdx.x < HYPERIM_NSTRATA) {
-        S.cyc_stratum[threadIdx.x] = 0;
-        S.cyc_stratum_n[threadIdx.x] = 0;
-    }
     for (int64_t w = threadIdx.x; w < P.vis_words; w += kThreads) vis[w] = 0;
     __syncthreads();
     int64_t plain_ticket = P.plain_base + blockIdx.x;  // the plain schedule's one job
@@ -1708,10 +1698,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rr(RRParams P) {
         atomicAdd(P.set_cycles, S.cyc_sum);
         atomicMax(P.set_cycles + 1, S.cyc_max);
         atomicAdd(P.set_cycles + 2, S.cyc_count);
-    }
-    if (threadIdx.x < HYPERIM_NSTRATA && P.set_cycles && !P.rewrite && S.cyc_stratum_n[threadIdx.x]) {
-        atomicAdd(P.set_cycles + 3 + threadIdx.x, S.cyc_stratum[threadIdx.x]);
-        atomicAdd(P.set_cycles + 3 + HYPERIM_NSTRATA + threadIdx.x, (unsigned long long)S.cyc_stratum_n[threadIdx.x]);
     }
 }
 
@@ -1804,12 +1790,11 @@ __global__ void k_compact_rr(const int32_t* __restrict__ arena, const int64_t* _
         const int64_t src = out_pos[r], dst = base_total + boff[r], len = boff[r + 1] - boff[r];
         for (int64_t i = lane; i < len; i += 32) rr_mem[dst + i] = arena[src + i];
         if (lane == 0) {
-            int k = 0;
-            while (k < HYPERIM_NSTRATA - 1 && r >= jm.job_base[k + 1]) ++k;
-            const int s = jm.order[k];
+            int s = 0;
+            while (s < HYPERIM_NSTRATA - 1 && r >= jm.job_base[s + 1]) ++s;
             rr_off[base_count + r] = dst;
             rr_stratum[base_count + r] = (uint8_t)s;
-            rr_j[base_count + r] = jm.j_base[s] + (uint32_t)(r - jm.job_base[k]) * jm.j_step;
+            rr_j[base_count + r] = jm.j_base[s] + (uint32_t)(r - jm.job_base[s]) * jm.j_step;
             if (r == njobs - 1) rr_off[base_count + njobs] = base_total + boff[njobs];
         }
     }
@@ -1935,43 +1920,25 @@ void after_growth(hyperim_graph* g, uint64_t used, int64_t njobs, int32_t** aren
     }
 }
 
-// The order of the strata in a launch's job space. Launches take the last jobs first, so the
-// strata go in ascending mean cost per RR set (SM cycles measured by the handle's earlier
-// launches): the costliest stratum starts first and its large sets do not end the launch late.
-// Strata never measured keep their index order below the measured ones (without any measurement:
-// the highest stratum first).
-void stratum_order(const hyperim_graph* g, uint8_t order[HYPERIM_NSTRATA]) {
-    int idx[HYPERIM_NSTRATA];
-    for (int s = 0; s < HYPERIM_NSTRATA; ++s) idx[s] = s;
-    std::stable_sort(idx, idx + HYPERIM_NSTRATA, [g](int a, int b) {
-        const double ca = g->stratum_cycles[a], cb = g->stratum_cycles[b];
-        if ((ca > 0.0) != (cb > 0.0)) return cb > 0.0;  // unmeasured before measured
-        return ca < cb;
-    });
-    for (int k = 0; k < HYPERIM_NSTRATA; ++k) order[k] = (uint8_t)idx[k];
-}
-
 // Job maps of a growth step: pool q's new sets are jobs [pool_start[q], pool_start[q + 1]),
 // stratum by stratum; a shard (rank r of W) holds the sets j = r (mod W) of each stratum's
 // allocation.
 hyperim_status make_job_maps(hyperim_pool* const* pools, int npools, const uint64_t (*new_ns)[HYPERIM_NSTRATA],
-                             RRJobMap* jm, int64_t* pool_start, const uint8_t* order) {
+                             RRJobMap* jm, int64_t* pool_start) {
     pool_start[0] = 0;
     for (int q = 0; q < npools; ++q) {
         hyperim_pool* p = pools[q];
         const uint64_t W = (uint64_t)std::max(p->shard_world, 1), R = (uint64_t)std::max(p->shard_rank, 0);
         jm[q].job_base[0] = 0;
         jm[q].j_step = (uint32_t)W;
-        for (int k = 0; k < HYPERIM_NSTRATA; ++k) {
-            const int s = order[k];
-            jm[q].order[k] = (uint8_t)s;
+        for (int s = 0; s < HYPERIM_NSTRATA; ++s) {
             const uint64_t old = p->n_s[s];
             if (new_ns[q][s] > 0xFFFFFFFFull)
                 return set_error(HYPERIM_EOVERFLOW, "an RR index within a stratum would reach 2^32");
             const uint64_t j0 = old + (R + W - old % W) % W;  // first j >= old of this shard
             const uint64_t add = new_ns[q][s] > j0 ? (new_ns[q][s] - 1 - j0) / W + 1 : 0;
             jm[q].j_base[s] = (uint32_t)std::min<uint64_t>(j0, 0xFFFFFFFFull);
-            jm[q].job_base[k + 1] = jm[q].job_base[k] + (int64_t)add;
+            jm[q].job_base[s + 1] = jm[q].job_base[s] + (int64_t)add;
         }
         pool_start[q + 1] = pool_start[q] + jm[q].job_base[HYPERIM_NSTRATA];
     }
@@ -2048,9 +2015,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     RRJobMap jm[kMaxPools];
     int64_t pool_start[kMaxPools + 1];
     hyperim_status st;
-    uint8_t order[HYPERIM_NSTRATA];
-    stratum_order(g, order);
-    if ((st = make_job_maps(pools, npools, new_ns, jm, pool_start, order))) return st;
+    if ((st = make_job_maps(pools, npools, new_ns, jm, pool_start))) return st;
     const int64_t njobs = pool_start[npools];
     if (njobs == 0) return HYPERIM_OK;
     if (njobs >= (int64_t)0x7FFFFFFF) return set_error(HYPERIM_EOVERFLOW, "too many RR sets in one growth step");
@@ -2091,8 +2056,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
         int esc_count;
         int pad;
         unsigned long long arena_used;
-        // SM cycles of the sets the block kernel built: sum, max, count, then per stratum sums and counts
-        unsigned long long set_cycles[3 + 2 * HYPERIM_NSTRATA];
+        unsigned long long set_cycles[3];  // sum, max, count over the sets the block kernel built
     };
     int64_t* d_pos = nullptr;
     int32_t* d_size = nullptr;
@@ -2139,7 +2103,7 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     P.spin_limit = wait_rounds(g);
     P.set_cycles = d_ctrl->set_cycles;
     unsigned long long used = 0;
-    unsigned long long cycles[3 + 2 * HYPERIM_NSTRATA] = {};
+    unsigned long long cycles[3] = {0, 0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct Events {
         cudaEvent_t* a;
@@ -2204,9 +2168,6 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
     if (cycles[2] > 0 && !P.plain) {
         g->set_cycles_mean = (double)cycles[0] / (double)cycles[2];
         g->set_cycles_max = (double)cycles[1];
-        for (int x = 0; x < HYPERIM_NSTRATA; ++x)
-            if (cycles[3 + HYPERIM_NSTRATA + x] > 0)
-                g->stratum_cycles[x] = (double)cycles[3 + x] / (double)cycles[3 + HYPERIM_NSTRATA + x];
     }
     if (used > g->scratch.arena_cap) {
         // The arena (sized from the pools' mean set size so far) was too small: every set has its
@@ -2276,10 +2237,8 @@ hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngr
             if (G.pools[i]->root_mode != G.pools[0]->root_mode || G.pools[i]->strategy != G.pools[0]->strategy)
                 return set_error(HYPERIM_ESTATE, "pools grown together must share root mode and strategy");
         }
-        uint8_t order[HYPERIM_NSTRATA];
-        stratum_order(G.g, order);
         if ((st = make_job_maps(G.pools, G.npools, G.new_ns, &jm[(size_t)q * kMaxPools],
-                                &pstart[(size_t)q * (kMaxPools + 1)], order)))
+                                &pstart[(size_t)q * (kMaxPools + 1)])))
             return st;
         gstart[q + 1] = gstart[q] + pstart[(size_t)q * (kMaxPools + 1) + G.npools];
         n_max = std::max<int64_t>(n_max, G.g->n);
