@@ -1800,6 +1800,53 @@ __global__ void k_compact_rr(const int32_t* __restrict__ arena, const int64_t* _
     }
 }
 
+// The batched form's compaction: every pool of a launch in one kernel. Pool d's new sets are the
+// global jobs [job_begin, job_begin + jobs); boff is the exclusive scan of all the launch's set
+// sizes; the pool's arrays were grown beforehand.
+struct CompactDesc {
+    int64_t job_begin, jobs, boff_begin, base_count, base_total;
+    int64_t* rr_off;
+    int32_t* rr_mem;
+    uint8_t* rr_stratum;
+    uint32_t* rr_j;
+    RRJobMap jm;
+};
+
+__global__ void k_compact_batch(const int32_t* __restrict__ arena, const int64_t* __restrict__ out_pos,
+                                const int64_t* __restrict__ boff, int64_t njobs, const CompactDesc* __restrict__ D,
+                                int nd) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < njobs; r += nwarps) {
+        int lo = 0, hi = nd - 1;  // the pool holding job r: last job_begin <= r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (D[mid].job_begin <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        const CompactDesc& d = D[lo];
+        const int64_t local = r - d.job_begin;
+        if (local < 0 || local >= d.jobs) continue;  // jobs of pools not listed (none by construction)
+        const int64_t src = out_pos[r], len = boff[r + 1] - boff[r];
+        const int64_t dst = d.base_total + (boff[r] - d.boff_begin);
+        for (int64_t i = lane; i < len; i += 32) d.rr_mem[dst + i] = arena[src + i];
+        if (lane == 0) {
+            int k = 0;
+            while (k < HYPERIM_NSTRATA - 1 && local >= d.jm.job_base[k + 1]) ++k;
+            d.rr_off[d.base_count + local] = dst;
+            d.rr_stratum[d.base_count + local] = (uint8_t)k;
+            d.rr_j[d.base_count + local] = d.jm.j_base[k] + (uint32_t)(local - d.jm.job_base[k]) * d.jm.j_step;
+            if (local == d.jobs - 1) d.rr_off[d.base_count + d.jobs] = dst + len;
+        }
+    }
+}
+
+__global__ void k_gather_i64(const int64_t* __restrict__ src, const int64_t* __restrict__ idx, int n,
+                             int64_t* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = src[idx[i]];
+}
+
 template <typename T>
 hyperim_status grow_array(hyperim_graph* g, T** arr, size_t used, size_t* cap, size_t need) {
     if (need <= *cap) return HYPERIM_OK;
@@ -1966,6 +2013,24 @@ void fill_graph_params(RRParams& P, const hyperim_graph* g) {
     P.seed = g->seed;
 }
 
+// a pool's bookkeeping after its new sets were appended (allocation covered, counts, size hint)
+void pool_appended(hyperim_pool* p, const uint64_t new_ns[HYPERIM_NSTRATA], int64_t new_count, int64_t new_total) {
+    for (int i = 0; i < HYPERIM_NSTRATA; ++i)
+        if (new_ns[i] > p->n_s[i]) p->n_s[i] = new_ns[i];
+    p->count = new_count;
+    p->total = new_total;
+    p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
+}
+
+// and its work counters, kernel time (its share of the launch's) and launches
+void pool_counted(hyperim_pool* p, const RRCounters& c, double seconds, uint64_t launches) {
+    unsigned long long* dst = &p->counters.pops;
+    const unsigned long long* src = &c.pops;
+    for (int i = 0; i < kNStat; ++i) dst[i] += src[i];
+    p->rr_kernel_seconds += seconds;
+    p->rr_launches += launches;
+}
+
 // The launch's sets of pool p (jobs [0, nq) of d_pos / d_size, sizes in the arena) appended to its
 // CSR arrays on g's stream (offsets by an exclusive scan of the sizes into d_boff, nq + 1
 // entries), and the pool's bookkeeping: allocation, counts, counters, kernel time (its share).
@@ -1990,17 +2055,9 @@ hyperim_status compact_pool(hyperim_graph* g, hyperim_pool* p, const int32_t* ar
         { k_compact_rr<<<grid, 256, 0, s>>>(arena, d_pos, d_boff, nq, p->count, p->total, jm, p->rr_off,
                                             p->rr_mem, p->rr_stratum, p->rr_j); count_launch(); }
         HYP_CUDA(cudaGetLastError());
-        for (int i = 0; i < HYPERIM_NSTRATA; ++i)
-            if (new_ns[i] > p->n_s[i]) p->n_s[i] = new_ns[i];
-        p->count = (int64_t)new_count;
-        p->total = (int64_t)new_total;
-        p->mean_size_hint = p->count > 0 ? (double)p->total / (double)p->count : 0.0;
+        pool_appended(p, new_ns, (int64_t)new_count, (int64_t)new_total);
     }
-    unsigned long long* dst = &p->counters.pops;
-    const unsigned long long* src = &c.pops;
-    for (int i = 0; i < kNStat; ++i) dst[i] += src[i];
-    p->rr_kernel_seconds += seconds;
-    p->rr_launches += launches;
+    pool_counted(p, c, seconds, launches);
     return HYPERIM_OK;
 }
 
@@ -2438,26 +2495,73 @@ hyperim_status sample_rr_batch(hyperim_graph* g0, const RRGroup* groups, int ngr
     if (seconds_out) *seconds_out = seconds;
     std::vector<RRCounters> c((size_t)ngroups * kMaxPools);
     HYP_CUDA(cudaMemcpyAsync(c.data(), d_counters, sizeof(RRCounters) * c.size(), cudaMemcpyDeviceToHost, s));
-    // compaction on each graph's stream; separate offset buffers, since those streams overlap
-    int64_t* d_boff = nullptr;
-    if ((st = tmp.alloc(&d_boff, sizeof(int64_t) * ((size_t)njobs + (size_t)ngroups * kMaxPools)))) return st;
+    // Compaction of every pool in one kernel on s: one scan of all the sizes, each pool's new total
+    // read off the scan at its job range's ends, the pools' arrays grown (on their graphs' streams,
+    // then joined), and one copy kernel for all of them.
     HYP_CUDA(cudaStreamSynchronize(s));
-    int64_t boff_at = 0;
-    hyperim_status cst = HYPERIM_OK;
-    for (int q = 0; q < ngroups && cst == HYPERIM_OK; ++q) {
+    int64_t* d_boff = nullptr;
+    if ((st = tmp.alloc(&d_boff, sizeof(int64_t) * ((size_t)njobs + 1)))) return st;
+    if ((st = exclusive_scan_u32_to_i64(g0, reinterpret_cast<const uint32_t*>(d_size), d_boff, njobs))) return st;
+    struct Slot {
+        hyperim_pool* p;
+        hyperim_graph* g;
+        const uint64_t* new_ns;
+        const RRJobMap* jm;
+        int64_t b0, nq;
+        const RRCounters* c;
+    };
+    std::vector<Slot> slots;
+    std::vector<int64_t> marks;  // job range ends of every pool: boff[b0], boff[b0 + nq]
+    for (int q = 0; q < ngroups; ++q) {
         const RRGroup& G = groups[q];
         const int64_t* ps = &pstart[(size_t)q * (kMaxPools + 1)];
-        for (int i = 0; i < G.npools && cst == HYPERIM_OK; ++i) {
+        for (int i = 0; i < G.npools; ++i) {
             const int64_t b0 = gstart[q] + ps[i], nq = ps[i + 1] - ps[i];
-            cst = compact_pool(G.g, G.pools[i], arena.p, d_pos + b0, d_size + b0, nq, jm[(size_t)q * kMaxPools + i],
-                               G.new_ns[i], d_boff + boff_at, c[(size_t)q * kMaxPools + i],
-                               seconds * (double)nq / (double)njobs, 1);
-            boff_at += nq + 1;
+            slots.push_back(Slot{G.pools[i], G.g, G.new_ns[i], &jm[(size_t)q * kMaxPools + i], b0, nq,
+                                 &c[(size_t)q * kMaxPools + i]});
+            marks.push_back(b0);
+            marks.push_back(b0 + nq);
         }
     }
-    // the call's buffers are released on s: every compaction has finished first
-    for (cudaStream_t x : streams) cudaStreamSynchronize(x);
-    if (cst != HYPERIM_OK) return cst;
+    int64_t *d_marks = nullptr, *d_vals = nullptr;
+    if ((st = tmp.alloc(&d_marks, sizeof(int64_t) * marks.size()))) return st;
+    if ((st = tmp.alloc(&d_vals, sizeof(int64_t) * marks.size()))) return st;
+    std::vector<int64_t> vals(marks.size());
+    HYP_CUDA(cudaMemcpyAsync(d_marks, marks.data(), sizeof(int64_t) * marks.size(), cudaMemcpyHostToDevice, s));
+    { k_gather_i64<<<(int)std::min<size_t>((marks.size() + 255) / 256, 1024), 256, 0, s>>>(d_boff, d_marks,
+                                                                                       (int)marks.size(), d_vals); count_launch(); }
+    HYP_CUDA(cudaMemcpyAsync(vals.data(), d_vals, sizeof(int64_t) * vals.size(), cudaMemcpyDeviceToHost, s));
+    HYP_CUDA(cudaStreamSynchronize(s));
+    std::vector<CompactDesc> desc;
+    for (size_t x = 0; x < slots.size(); ++x) {
+        const Slot& sl = slots[x];
+        hyperim_pool* p = sl.p;
+        if (sl.nq == 0) continue;
+        const int64_t btotal = vals[2 * x + 1] - vals[2 * x];
+        const size_t new_count = (size_t)(p->count + sl.nq), new_total = (size_t)(p->total + btotal);
+        if ((st = grow_array(sl.g, &p->rr_off, p->count ? (size_t)p->count + 1 : 0, &p->cap_off, new_count + 1)))
+            return st;
+        if ((st = grow_array(sl.g, &p->rr_stratum, (size_t)p->count, &p->cap_stratum, new_count))) return st;
+        if ((st = grow_array(sl.g, &p->rr_j, (size_t)p->count, &p->cap_j, new_count))) return st;
+        if ((st = grow_array(sl.g, &p->rr_mem, (size_t)p->total, &p->cap_total, new_total))) return st;
+        desc.push_back(CompactDesc{sl.b0, sl.nq, vals[2 * x], p->count, p->total, p->rr_off, p->rr_mem,
+                                   p->rr_stratum, p->rr_j, *sl.jm});
+    }
+    for (cudaStream_t x : streams) HYP_CUDA(cudaStreamSynchronize(x));  // the grown arrays are ready
+    if (!desc.empty()) {
+        CompactDesc* d_desc = nullptr;
+        if ((st = tmp.alloc(&d_desc, sizeof(CompactDesc) * desc.size()))) return st;
+        HYP_CUDA(cudaMemcpyAsync(d_desc, desc.data(), sizeof(CompactDesc) * desc.size(), cudaMemcpyHostToDevice, s));
+        const int grid = (int)std::min<int64_t>((njobs * 32 + 255) / 256, (int64_t)g0->sm_count * 32);
+        { k_compact_batch<<<grid, 256, 0, s>>>(arena.p, d_pos, d_boff, njobs, d_desc, (int)desc.size()); count_launch(); }
+        HYP_CUDA(cudaGetLastError());
+        HYP_CUDA(cudaStreamSynchronize(s));
+    }
+    for (size_t x = 0; x < slots.size(); ++x) {
+        const Slot& sl = slots[x];
+        if (sl.nq > 0) pool_appended(sl.p, sl.new_ns, sl.p->count + sl.nq, sl.p->total + (vals[2 * x + 1] - vals[2 * x]));
+        pool_counted(sl.p, *sl.c, seconds * (double)sl.nq / (double)njobs, 1);
+    }
     return check_device_status(g0, "RR compaction (batch)");
 }
 
