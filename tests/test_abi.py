@@ -60,3 +60,17 @@ def test_load_rejects_bad_arguments_before_touching_the_device(libpath):
         assert e.value.status == -1
     with pytest.raises(H.HyperIMError):
         H.hyperim_load(0, off, mem, stream=0)
+
+
+def test_batch_and_tuning_reject_bad_arguments_before_touching_the_device(libpath):
+    # argument checks of the batched seed selection and the tuning calls run on the host alone
+    import ctypes as C
+    import paper_2406_01911_gb300 as H
+    lib = H.lib()
+    assert lib.hyperim_select_seeds_batch(None, 0) == -1  # no queries
+    q = (H.BatchQuery * 1)()
+    q[0] = H.BatchQuery(None, None, None, 5, 0.1, 1.0, None, None)
+    assert lib.hyperim_select_seeds_batch(q, 1) == -1  # null graph and pools
+    assert lib.hyperim_graph_set_tuning(None, C.byref(H.Tuning(0, 4, 0))) == -1
+    assert lib.hyperim_graph_set_wait_limit(None, 1) == -1
+    assert "null" in lib.hyperim_last_error().decode()
