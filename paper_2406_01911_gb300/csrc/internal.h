@@ -261,8 +261,8 @@ hyperim_status sample_rr_multi(hyperim_graph* g, hyperim_pool* const* pools, int
 // rr.cu: one launch over the pools of several graphs (the batched form of HyperIM_BRR). Group
 // q grows up to two pools of graph g (same root mode and strategy) to new_ns; every group's
 // sets are built by one persistent launch on g0's stream (which first waits for the work queued
-// on the groups' streams); each pool is compacted on its graph's stream. seconds: the launch's
-// CUDA-event time.
+// on the groups' streams), and one compaction kernel there appends them to their pools (each
+// pool's arrays grown beforehand on its graph's stream). seconds: the launch's CUDA-event time.
 struct RRGroup {
     hyperim_graph* g;
     hyperim_pool* pools[2];
